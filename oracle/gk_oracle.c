@@ -1,0 +1,408 @@
+/*
+ * gk_oracle.c -- sequential CPU oracle (test infrastructure only; see the
+ * header).  Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC.
+ *
+ * Each function states the passage of arXiv:2006.16852 (or the textbook
+ * definition the paper cites) that it follows.  Nothing here is blocked,
+ * fused or reordered beyond what the definition says.
+ */
+#include "gk_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Sparse matrix-vector product                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Section 4.2: the simple apply x = A b and the advanced apply
+ * x = alpha*A*b + beta*x, with "simple = advanced(alpha=1, beta=0)".
+ * Row sum: s = 0; for k in increasing order, s = fma(a_ik, b_k, s).
+ * beta == 0 does not read the old output (BLAS convention), so a NaN there
+ * does not propagate; otherwise the result is fma(beta, y_old, alpha*s). */
+void or_csr_spmv(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
+                 const double* x, double alpha, double beta, double* y) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    double s = 0.0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], x[col[k]], s);
+    double as = alpha * s;
+    y[i] = (beta == 0.0) ? as : fma(beta, y[i], as);
+  }
+}
+
+/* Error-free transformations (Ogita, Rump, Oishi, "Accurate sum and dot
+ * product", SIAM J. Sci. Comput. 26(6), 2005): TwoSum (Knuth) and
+ * TwoProduct via fma; Dot2 accumulates the rounding errors separately and is
+ * as accurate as a dot product computed in twice the working precision. */
+static void two_sum(double a, double b, double* s, double* e) {
+  double x = a + b;
+  double z = x - a;
+  *e = (a - (x - z)) + (b - z);
+  *s = x;
+}
+
+static void two_prod(double a, double b, double* p, double* e) {
+  double x = a * b;
+  *e = fma(a, b, -x);
+  *p = x;
+}
+
+void or_csr_spmv_dot2(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
+                      const double* x, double* y_acc, double* abs_ax) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    double p = 0.0, s = 0.0, bound = 0.0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      double h, r, q;
+      two_prod(val[k], x[col[k]], &h, &r);
+      two_sum(p, h, &p, &q);
+      s += q + r;
+      bound += fabs(val[k]) * fabs(x[col[k]]);
+    }
+    y_acc[i] = p + s;
+    abs_ax[i] = bound;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense vector kernels (the scale / add_scaled / dot of Section 4.2)        */
+/* ------------------------------------------------------------------------ */
+
+double or_dot(int64_t n, const double* x, const double* y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+double or_norm2(int64_t n, const double* x) { return sqrt(or_dot(n, x, x)); }
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi preconditioners (Section 3.2; block inversion by Gauss-Jordan     */
+/* elimination with pivoting, Section 7.5)                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Diagonal entry a_ii of a CSR row, or 0 with *found = 0 when absent. */
+static double diag_entry(const int32_t* rowptr, const int32_t* col, const double* val, int64_t i,
+                         int* found) {
+  for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+    if (col[k] == i) {
+      *found = 1;
+      return val[k];
+    }
+  }
+  *found = 0;
+  return 0.0;
+}
+
+/* Scalar Jacobi, Section 3.2 ("diagonal scaling"): M = diag(A). */
+int or_jacobi_scalar(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     double* dinv) {
+  for (int64_t i = 0; i < n; ++i) {
+    int found;
+    double d = diag_entry(rowptr, col, val, i, &found);
+    if (!found || d == 0.0) return OR_ERR_SINGULAR;
+    dinv[i] = 1.0 / d;
+  }
+  return OR_OK;
+}
+
+int64_t or_block_jacobi_size(int64_t n, int32_t bs) {
+  if (bs <= 0) return 0;
+  int64_t full = n / bs, last = n % bs;
+  return full * (int64_t)bs * bs + last * last;
+}
+
+/* Block-Jacobi generate, Sections 3.2 and 7.5: diagonal block D_k holds the
+ * entries of A in rows and columns [k*bs, min((k+1)*bs, n)); it is inverted
+ * by Gauss-Jordan elimination on the augmented matrix [D_k | I] with partial
+ * (row) pivoting.  Pivot: the largest |entry| in the column at or below the
+ * diagonal, the lowest row on ties.  Pivot row scaled by its reciprocal;
+ * every other row eliminated with w_ij = fma(-w_ik, w_kj, w_ij). */
+int or_block_jacobi_generate(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                             int32_t bs, double* blocks, int64_t* bad_block) {
+  if (bs <= 0) return OR_ERR_ARG;
+  int64_t nblocks = (n + bs - 1) / bs;
+  double* w = (double*)malloc(sizeof(double) * (size_t)bs * 2 * bs);
+  if (!w) return OR_ERR_ARG;
+  int64_t off = 0;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    int64_t r0 = b * bs;
+    int64_t m = (r0 + bs <= n) ? bs : n - r0;
+    int64_t wd = 2 * m; /* row stride of the augmented matrix */
+    memset(w, 0, sizeof(double) * (size_t)m * wd);
+    for (int64_t i = 0; i < m; ++i) {
+      for (int64_t k = rowptr[r0 + i]; k < rowptr[r0 + i + 1]; ++k) {
+        int64_t c = col[k];
+        if (c >= r0 && c < r0 + m) w[i * wd + (c - r0)] = val[k];
+      }
+      w[i * wd + m + i] = 1.0;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+      int64_t piv = k;
+      double best = fabs(w[k * wd + k]);
+      for (int64_t i = k + 1; i < m; ++i) {
+        double a = fabs(w[i * wd + k]);
+        if (a > best) {
+          best = a;
+          piv = i;
+        }
+      }
+      if (best == 0.0) {
+        free(w);
+        if (bad_block) *bad_block = b;
+        return OR_ERR_SINGULAR;
+      }
+      if (piv != k) {
+        for (int64_t j = 0; j < wd; ++j) {
+          double t = w[k * wd + j];
+          w[k * wd + j] = w[piv * wd + j];
+          w[piv * wd + j] = t;
+        }
+      }
+      double rcp = 1.0 / w[k * wd + k];
+      for (int64_t j = 0; j < wd; ++j) w[k * wd + j] = w[k * wd + j] * rcp;
+      for (int64_t i = 0; i < m; ++i) {
+        if (i == k) continue;
+        double f = w[i * wd + k];
+        for (int64_t j = 0; j < wd; ++j) w[i * wd + j] = fma(-f, w[k * wd + j], w[i * wd + j]);
+      }
+    }
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < m; ++j) blocks[off + i * m + j] = w[i * wd + m + j];
+    off += m * m;
+  }
+  free(w);
+  return OR_OK;
+}
+
+/* z = M^{-1} r.  Block case: z_i = sum_j (D_k^{-1})_{ij} r_j, a dense
+ * row-major matvec per block with the sum in increasing j via fma. */
+void or_precond_apply(int64_t n, const or_precond* P, const double* r, double* z) {
+  if (!P || P->kind == OR_PREC_NONE) {
+    for (int64_t i = 0; i < n; ++i) z[i] = r[i];
+    return;
+  }
+  if (P->kind == OR_PREC_SCALAR_JACOBI) {
+    for (int64_t i = 0; i < n; ++i) z[i] = P->dinv[i] * r[i];
+    return;
+  }
+  int64_t bs = P->block_size;
+  int64_t off = 0;
+  for (int64_t r0 = 0; r0 < n; r0 += bs) {
+    int64_t m = (r0 + bs <= n) ? bs : n - r0;
+    for (int64_t i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int64_t j = 0; j < m; ++j) s = fma(P->blocks[off + i * m + j], r[r0 + j], s);
+      z[r0 + i] = s;
+    }
+    off += m * m;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hybrid ELL + COO split                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Brute force over every candidate width K = 0 .. max row length. */
+int64_t or_hyb_width(int64_t n_rows, const int32_t* rowptr, int64_t vt, int64_t it) {
+  int64_t maxlen = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t l = rowptr[i + 1] - rowptr[i];
+    if (l > maxlen) maxlen = l;
+  }
+  int64_t bestk = 0, bestcost = -1;
+  for (int64_t K = 0; K <= maxlen; ++K) {
+    int64_t coo = 0;
+    for (int64_t i = 0; i < n_rows; ++i) {
+      int64_t l = rowptr[i + 1] - rowptr[i];
+      if (l > K) coo += l - K;
+    }
+    int64_t cost = K * n_rows * (vt + it) + coo * (vt + 2 * it);
+    if (bestcost < 0 || cost < bestcost) {
+      bestcost = cost;
+      bestk = K;
+    }
+  }
+  return bestk;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Krylov solvers                                                             */
+/* ------------------------------------------------------------------------ */
+
+static int is_finite(double v) { return isfinite(v) != 0; }
+
+/* r = b - A x, with A x by the ordered row sum of or_csr_spmv. */
+static void residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* b, const double* x, double* r) {
+  or_csr_spmv(n, rowptr, col, val, x, 1.0, 0.0, r);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+}
+
+/* Stopping criteria of Section 2.5, combined by logical OR (Listing 1):
+ * ResidualNormReduction first, then Iteration.  A non-finite residual norm
+ * ends the solve (it can neither converge nor recover). */
+static int check_stop(double rnorm, double tol_abs, int64_t k, int64_t max_iters) {
+  if (!is_finite(rnorm)) return OR_STOP_NAN;
+  if (rnorm <= tol_abs) return OR_STOP_CONVERGED;
+  if (k >= max_iters) return OR_STOP_MAX_ITERS;
+  return OR_STOP_NONE;
+}
+
+static void finish(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                   const double* b, const double* x, double ref, double rnorm, or_status* st,
+                   double* work) {
+  residual(n, rowptr, col, val, b, x, work);
+  st->spmvs += 1;
+  st->rel_res = rnorm / ref;
+  st->rel_res_true = or_norm2(n, work) / ref;
+  st->ref_norm = ref;
+}
+
+/* Preconditioned CG (the CG of Section 3.1, Listing 1; the textbook
+ * algorithm of Saad, "Iterative Methods for Sparse Linear Systems", which the
+ * paper cites).  With M the preconditioner:
+ *   r = b - A x;  z = M^{-1} r;  p = z;  rho = r.z
+ *   repeat: q = A p;  sigma = p.q;  alpha = rho / sigma
+ *           x = x + alpha p;  r = r - alpha q
+ *           z = M^{-1} r;  rho' = r.z;  beta = rho' / rho;  p = z + beta p
+ * sigma <= 0 (or not finite) on a nonzero p is a breakdown. */
+int or_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+          const or_precond* P, const double* b, double* x, const or_criteria* crit,
+          or_status* st, double* res_hist) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* z = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* p = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* q = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  if (!r || !z || !p || !q) {
+    free(r); free(z); free(p); free(q);
+    return OR_ERR_ARG;
+  }
+  residual(n, rowptr, col, val, b, x, r);
+  st->spmvs = 1;
+  double bnorm = or_norm2(n, b);
+  double rnorm = or_norm2(n, r);
+  double ref = crit->rel_to_b ? bnorm : rnorm;
+  if (ref == 0.0) ref = 1.0; /* b = 0 (or r_0 = 0): absolute criterion */
+  double tol = crit->reduction_factor * ref;
+  or_precond_apply(n, P, r, z);
+  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  double rho = or_dot(n, r, z);
+  int64_t k = 0;
+  int stop;
+  if (res_hist) res_hist[0] = rnorm / ref;
+  while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+    or_csr_spmv(n, rowptr, col, val, p, 1.0, 0.0, q);
+    st->spmvs += 1;
+    double sigma = or_dot(n, p, q);
+    if (!is_finite(sigma)) { stop = OR_STOP_NAN; break; }
+    if (sigma <= 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    double alpha = rho / sigma;
+    for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, p[i], x[i]);
+    for (int64_t i = 0; i < n; ++i) r[i] = fma(-alpha, q[i], r[i]);
+    k += 1;
+    rnorm = or_norm2(n, r);
+    if (res_hist) res_hist[k] = rnorm / ref;
+    or_precond_apply(n, P, r, z);
+    double rho_new = or_dot(n, r, z);
+    double beta = rho_new / rho;
+    for (int64_t i = 0; i < n; ++i) p[i] = fma(beta, p[i], z[i]);
+    rho = rho_new;
+  }
+  st->iters = k;
+  st->stop_reason = stop;
+  finish(n, rowptr, col, val, b, x, ref, rnorm, st, q);
+  free(r); free(z); free(p); free(q);
+  return OR_OK;
+}
+
+/* Preconditioned BiCGSTAB (Section 3.1, Listing 3; van der Vorst 1992 in the
+ * form of Barrett et al., "Templates for the Solution of Linear Systems",
+ * 1994), shadow residual r^ = r_0:
+ *   rho = r^.r;  beta = (rho/rho_prev)(alpha/omega);  p = r + beta (p - omega v)
+ *   p^ = M^{-1} p;  v = A p^;  alpha = rho / (r^.v);  s = r - alpha v
+ *   if ||s|| meets the criterion: x = x + alpha p^ and stop (half step)
+ *   s^ = M^{-1} s;  t = A s^;  omega = (t.s)/(t.t)
+ *   x = x + alpha p^ + omega s^;  r = s - omega t
+ * rho = 0, r^.v = 0, t.t = 0 or omega = 0 are breakdowns.  A half-step exit
+ * counts as one iteration. */
+int or_bicgstab(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                const or_precond* P, const double* b, double* x, const or_criteria* crit,
+                or_status* st, double* res_hist) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t sz = sizeof(double) * (size_t)(n + 1);
+  double *r = malloc(sz), *rh = malloc(sz), *p = malloc(sz), *v = malloc(sz), *ph = malloc(sz),
+         *s = malloc(sz), *sh = malloc(sz), *t = malloc(sz);
+  if (!r || !rh || !p || !v || !ph || !s || !sh || !t) {
+    free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
+    return OR_ERR_ARG;
+  }
+  residual(n, rowptr, col, val, b, x, r);
+  st->spmvs = 1;
+  double bnorm = or_norm2(n, b);
+  double rnorm = or_norm2(n, r);
+  double ref = crit->rel_to_b ? bnorm : rnorm;
+  if (ref == 0.0) ref = 1.0;
+  double tol = crit->reduction_factor * ref;
+  for (int64_t i = 0; i < n; ++i) {
+    rh[i] = r[i];
+    p[i] = 0.0;
+    v[i] = 0.0;
+  }
+  double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  int64_t k = 0;
+  int stop;
+  if (res_hist) res_hist[0] = rnorm / ref;
+  while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+    double rho = or_dot(n, rh, r);
+    if (!is_finite(rho)) { stop = OR_STOP_NAN; break; }
+    if (rho == 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    double beta = (rho / rho_prev) * (alpha / omega);
+    for (int64_t i = 0; i < n; ++i) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+    or_precond_apply(n, P, p, ph);
+    or_csr_spmv(n, rowptr, col, val, ph, 1.0, 0.0, v);
+    st->spmvs += 1;
+    double rhv = or_dot(n, rh, v);
+    if (!is_finite(rhv)) { stop = OR_STOP_NAN; break; }
+    if (rhv == 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    alpha = rho / rhv;
+    for (int64_t i = 0; i < n; ++i) s[i] = fma(-alpha, v[i], r[i]);
+    double snorm = or_norm2(n, s);
+    if (is_finite(snorm) && snorm <= tol) {
+      for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, ph[i], x[i]);
+      for (int64_t i = 0; i < n; ++i) r[i] = s[i];
+      k += 1;
+      rnorm = snorm;
+      if (res_hist) res_hist[k] = rnorm / ref;
+      stop = OR_STOP_CONVERGED;
+      break;
+    }
+    or_precond_apply(n, P, s, sh);
+    or_csr_spmv(n, rowptr, col, val, sh, 1.0, 0.0, t);
+    st->spmvs += 1;
+    double tt = or_dot(n, t, t);
+    double ts = or_dot(n, t, s);
+    if (!is_finite(tt) || !is_finite(ts)) { stop = OR_STOP_NAN; break; }
+    if (tt == 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    omega = ts / tt;
+    for (int64_t i = 0; i < n; ++i) x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+    for (int64_t i = 0; i < n; ++i) r[i] = fma(-omega, t[i], s[i]);
+    rho_prev = rho;
+    k += 1;
+    rnorm = or_norm2(n, r);
+    if (res_hist) res_hist[k] = rnorm / ref;
+    if (omega == 0.0) {
+      stop = check_stop(rnorm, tol, k, crit->max_iters);
+      if (stop == OR_STOP_NONE) stop = OR_STOP_BREAKDOWN;
+      break;
+    }
+  }
+  st->iters = k;
+  st->stop_reason = stop;
+  finish(n, rowptr, col, val, b, x, ref, rnorm, st, t);
+  free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
+  return OR_OK;
+}

@@ -1,0 +1,115 @@
+/*
+ * gk_oracle.h -- plain, slow, sequential CPU oracle for the sparse
+ * linear-operator hot path of "Ginkgo: A Modern Linear Operator Algebra
+ * Framework for High Performance Computing" (arXiv:2006.16852).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this code; only the tests, the smoke check and the benchmark's
+ * CPU baseline do.  It shares no code, header, table or helper with the CUDA
+ * path.
+ *
+ * Conventions: FP64 values, int32 column indices and row pointers, int64
+ * sizes.  Every floating-point step is written in the order the definition
+ * or algorithm states; the library is compiled with -ffp-contract=off so
+ * that the only fused multiply-adds are the explicit fma() calls.
+ *
+ * Parity status: every function below is pinned by the CPU tests against
+ * brute force, closed forms or invariants (tests/test_oracle_*.py).
+ */
+#ifndef GK_ORACLE_H
+#define GK_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes shared by the oracle's own functions */
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_SINGULAR 2
+
+/* stop reasons (criteria of Section 2.5) */
+#define OR_STOP_NONE 0
+#define OR_STOP_CONVERGED 1
+#define OR_STOP_MAX_ITERS 2
+#define OR_STOP_BREAKDOWN 3
+#define OR_STOP_NAN 4
+
+/* preconditioner kinds (Section 3.2) */
+#define OR_PREC_NONE 0
+#define OR_PREC_SCALAR_JACOBI 1
+#define OR_PREC_BLOCK_JACOBI 2
+
+typedef struct {
+  int64_t max_iters;        /* Iteration criterion (Listing 8): stop once k >= max_iters        */
+  double reduction_factor;  /* ResidualNormReduction: stop once ||r_k|| <= factor * ref        */
+  int32_t rel_to_b;         /* ref = ||b|| if nonzero, else ||r_0||                          */
+} or_criteria;
+
+typedef struct {
+  int64_t iters;         /* iterations performed                                 */
+  int64_t spmvs;         /* matrix applications, including the initial residual  */
+  double rel_res;        /* recurred ||r|| / ref at exit                           */
+  double rel_res_true;   /* ||b - A x|| / ref recomputed at exit                  */
+  double ref_norm;       /* ref used by the criterion                            */
+  int32_t stop_reason;   /* OR_STOP_*                                            */
+  int32_t pad_;
+} or_status;
+
+typedef struct {
+  int32_t kind;            /* OR_PREC_*                                            */
+  int32_t block_size;      /* block size for OR_PREC_BLOCK_JACOBI                  */
+  const double* dinv;      /* scalar: n inverse diagonal entries                   */
+  const double* blocks;    /* block: inverse blocks, row-major, concatenated       */
+} or_precond;
+
+/* x = alpha*A*b + beta*x (Section 4.2, simple and advanced apply). */
+void or_csr_spmv(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
+                 const double* x, double alpha, double beta, double* y);
+
+/* Accurate row sums by Dot2 (Ogita, Rump, Oishi 2005) and the bound (|A||x|)_i. */
+void or_csr_spmv_dot2(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
+                      const double* x, double* y_acc, double* abs_ax);
+
+/* Plain dot product and 2-norm: sum in increasing index order. */
+double or_dot(int64_t n, const double* x, const double* y);
+double or_norm2(int64_t n, const double* x);
+
+/* Scalar Jacobi: dinv_i = 1 / a_ii.  OR_ERR_SINGULAR if a diagonal is missing or zero. */
+int or_jacobi_scalar(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     double* dinv);
+
+/* Number of doubles the block-Jacobi inverse blocks occupy for (n, bs). */
+int64_t or_block_jacobi_size(int64_t n, int32_t bs);
+
+/* Block-Jacobi generate: contiguous blocks of bs rows (last one shorter), each
+ * diagonal block inverted by Gauss-Jordan elimination with partial pivoting.
+ * Blocks are written row-major and concatenated.  On a zero pivot returns
+ * OR_ERR_SINGULAR and stores the failing block index in *bad_block. */
+int or_block_jacobi_generate(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                             int32_t bs, double* blocks, int64_t* bad_block);
+
+/* z = M^{-1} r for the given preconditioner (scalar, block, or copy). */
+void or_precond_apply(int64_t n, const or_precond* P, const double* r, double* z);
+
+/* Width K of the ELL part of the hybrid format: the smallest K minimising
+ * K*n*(vt+it) + nnz_coo(K)*(vt+2*it), nnz_coo(K) = sum_i max(0, len_i - K). */
+int64_t or_hyb_width(int64_t n_rows, const int32_t* rowptr, int64_t vt, int64_t it);
+
+/* Preconditioned conjugate gradients (Section 3.1, Listing 1). x holds x_0 on
+ * entry and the solution on exit.  res_hist (nullable, max_iters+1 entries)
+ * receives the recurred relative residual of every iterate. */
+int or_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+          const or_precond* P, const double* b, double* x, const or_criteria* crit,
+          or_status* st, double* res_hist);
+
+/* Preconditioned BiCGSTAB (Section 3.1, Listing 3). */
+int or_bicgstab(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                const or_precond* P, const double* b, double* x, const or_criteria* crit,
+                or_status* st, double* res_hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

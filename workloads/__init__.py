@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module builds matrices and vectors only; it holds none of the solver or
+SpMV arithmetic.  Matrices are returned as CSR triples
+``(rowptr int32[n+1], col int32[nnz], val float64[nnz])`` with sorted, unique
+column indices in every row.  Random numbers come from numpy's PCG64
+(``np.random.default_rng(seed)``).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "poisson1d", "poisson2d", "stencil27", "powerlaw", "random_csr", "diagonal",
+    "convdiff2d", "uniform_vector", "csr_to_dense", "scaled_identity",
+]
+
+
+def _finish(rowptr, col, val):
+    return (np.ascontiguousarray(rowptr, dtype=np.int32), np.ascontiguousarray(col, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=np.float64))
+
+
+def _from_offsets(shape, offsets, weights):
+    """Structured-grid stencil matrix.  ``offsets`` are tuples over the grid
+    axes (slowest first), sorted so that column indices increase within a
+    row; unknowns outside the grid are dropped (homogeneous Dirichlet)."""
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    idx = np.indices(shape).reshape(len(shape), -1)
+    strides = np.array([int(np.prod(shape[d + 1:])) for d in range(len(shape))], dtype=np.int64)
+    cols = np.empty((n, len(offsets)), dtype=np.int32)
+    mask = np.empty((n, len(offsets)), dtype=bool)
+    vals = np.empty((n, len(offsets)), dtype=np.float64)
+    ar = np.arange(n, dtype=np.int64)
+    for j, off in enumerate(offsets):
+        ok = np.ones(n, dtype=bool)
+        delta = 0
+        for d, o in enumerate(off):
+            if o:
+                ok &= (idx[d] + o >= 0) & (idx[d] + o < shape[d])
+                delta += o * int(strides[d])
+        mask[:, j] = ok
+        cols[:, j] = (ar + delta).astype(np.int32)
+        vals[:, j] = weights[j]
+    lens = mask.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    return _finish(rowptr, cols[mask], vals[mask])
+
+
+def poisson1d(n: int, diag: float = 2.0, off: float = -1.0):
+    """Tridiagonal 1D Poisson matrix (2 on the diagonal, -1 beside it; Section 4.2)."""
+    return _from_offsets((n,), [(-1,), (0,), (1,)], [off, diag, off])
+
+
+def poisson2d(nx: int, ny: int | None = None):
+    """5-point 2D Poisson stencil, 4 on the diagonal and -1 for the four
+    neighbours, natural (row-major) ordering, no 1/h^2 scaling.  64x64 gives
+    n = 4096 and nnz = 20224."""
+    ny = nx if ny is None else ny
+    offs = [(-1, 0), (0, -1), (0, 0), (0, 1), (1, 0)]
+    return _from_offsets((ny, nx), offs, [-1.0, -1.0, 4.0, -1.0, -1.0])
+
+
+def stencil27(N: int):
+    """27-point stencil on an N^3 grid: 26 on the diagonal, -1 for each of the
+    26 neighbours.  N = 128 gives n = 2,097,152 and nnz = 55,742,968."""
+    offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    w = [26.0 if o == (0, 0, 0) else -1.0 for o in offs]
+    return _from_offsets((N, N, N), offs, w)
+
+
+def _coo_to_csr(n_rows, r, c, v, sum_duplicates=True):
+    key = r.astype(np.int64) * np.int64(max(n_rows, 1)) + c.astype(np.int64)
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    v = v[order]
+    if sum_duplicates and key.size:
+        first = np.ones(key.size, dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        starts = np.flatnonzero(first)
+        v = np.add.reduceat(v, starts)
+        key = key[starts]
+    r = key // max(n_rows, 1)
+    c = key % max(n_rows, 1)
+    rowptr = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=n_rows), out=rowptr[1:])
+    return _finish(rowptr, c, v)
+
+
+def powerlaw(n: int, alpha: float = 1.8, cap: int = 10_000, seed: int = 3):
+    """Power-law SPD matrix.
+
+    B: row lengths l ~ P(l = k) proportional to k^-alpha on k = 1..cap, columns
+    uniform over [0, n) (repeats within a row dropped, so a row holds distinct
+    columns), values N(0, 1).  A = B + B^T on the union pattern (coinciding
+    entries summed), then a_ii = sum_{j != i} |a_ij| + 1, making A strictly
+    diagonally dominant with a positive diagonal, hence SPD.
+    """
+    rng = np.random.default_rng(seed)
+    k = np.arange(1, cap + 1, dtype=np.float64)
+    p = k ** (-alpha)
+    p /= p.sum()
+    lens = rng.choice(np.arange(1, cap + 1), size=n, p=p)
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    cols = rng.integers(0, n, size=rows.size, dtype=np.int64)
+    vals = rng.standard_normal(rows.size)
+    key = rows * n + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    first = np.ones(key.size, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    key, vals = key[first], vals[first]
+    r, c = key // n, key % n
+    off = r != c
+    r, c, vals = r[off], c[off], vals[off]
+    R = np.concatenate([r, c])
+    C = np.concatenate([c, r])
+    V = np.concatenate([vals, vals])
+    rowptr, col, val = _coo_to_csr(n, R, C, V)
+    rows_of = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    diag = np.bincount(rows_of, weights=np.abs(val), minlength=n) + 1.0
+    R2 = np.concatenate([rows_of, np.arange(n)])
+    C2 = np.concatenate([col.astype(np.int64), np.arange(n)])
+    V2 = np.concatenate([val, diag])
+    return _coo_to_csr(n, R2, C2, V2, sum_duplicates=False)
+
+
+def random_csr(m: int, n: int, seed: int, max_len: int | None = None, empty_frac: float = 0.1,
+               long_rows: int = 0, long_len: int | None = None, values: str = "normal"):
+    """Random rectangular CSR with uneven rows, some empty rows and optionally
+    a few long rows (lengths capped at ``n``)."""
+    rng = np.random.default_rng(seed)
+    max_len = min(n, max_len if max_len is not None else max(1, min(n, 40)))
+    lens = rng.integers(0, max_len + 1, size=m)
+    lens[rng.random(m) < empty_frac] = 0
+    if long_rows and m:
+        ll = min(n, long_len if long_len is not None else n)
+        lens[rng.choice(m, size=min(long_rows, m), replace=False)] = ll
+    cols = [np.sort(rng.choice(n, size=int(l), replace=False)) for l in lens]
+    col = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
+    if values == "normal":
+        val = rng.standard_normal(col.size)
+    else:
+        val = rng.uniform(-1.0, 1.0, size=col.size)
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    return _finish(rowptr, col, val)
+
+
+def diagonal(d):
+    d = np.asarray(d, dtype=np.float64)
+    n = d.size
+    return _finish(np.arange(n + 1), np.arange(n), d)
+
+
+def scaled_identity(n: int, c: float):
+    return diagonal(np.full(n, c))
+
+
+def convdiff2d(nx: int, wind: float = 0.5):
+    """Nonsymmetric 2D convection-diffusion (first-order upwind, wind along
+    +x): 4 + wind on the diagonal, -1 - wind for the upwind x-neighbour, -1
+    for the other three neighbours."""
+    offs = [(-1, 0), (0, -1), (0, 0), (0, 1), (1, 0)]
+    return _from_offsets((nx, nx), offs, [-1.0, -1.0 - wind, 4.0 + wind, -1.0, -1.0])
+
+
+def uniform_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=n)
+
+
+def csr_to_dense(A, n_cols: int | None = None):
+    rowptr, col, val = A
+    m = rowptr.size - 1
+    n_cols = m if n_cols is None else n_cols
+    D = np.zeros((m, n_cols))
+    rows = np.repeat(np.arange(m), np.diff(rowptr))
+    D[rows, col] = val
+    return D

@@ -1,0 +1,205 @@
+/*
+ * gk.h -- C ABI of the GB300 sparse linear-operator library.
+ *
+ * The calls follow the linear-operator statement of arXiv:2006.16852
+ * (Ginkgo): every object is an operator L with apply(b, x): x = L(b)
+ * (Section 2.2.2); solvers S_A and preconditioners P_A are produced from the
+ * system operator L_A by generate() (Section 2.2.3); the simple apply
+ * x = A b and the advanced apply x = alpha A b + beta x are both provided
+ * (Section 4.2); iterations stop on combined criteria (Section 2.5).
+ *
+ * Conventions shared by every call
+ *  - Return value: GK_OK (0) or a GK_ERR_* code; the thread-local message of
+ *    the last failure is returned by gk_last_error().  No call throws.
+ *  - Values are FP64 (gk_dtype GK_F64), indices int32, sizes int64.
+ *  - Vector arguments are plain pointers to n contiguous doubles.  They may
+ *    be device memory (cudaMalloc, torch CUDA tensors, managed memory) or
+ *    host memory (pinned or pageable).  Host vectors are staged through a
+ *    library-owned device buffer; a call given a host output returns only
+ *    after the result is back in host memory.
+ *  - Ownership mirrors the paper's lend/share/give (Section 2.4): vectors
+ *    are lent for the duration of the call; gk_matrix_create_csr copies the
+ *    caller's CSR arrays into library-owned storage; solvers and
+ *    preconditioners share ownership of the matrix (and preconditioner) they
+ *    were generated from, so the caller may destroy its handles in any order.
+ *  - stream is a cudaStream_t (NULL = the legacy default stream).  All device
+ *    work is enqueued on it.  gk_apply/gk_apply_adv/gk_precond_apply with
+ *    device vectors are asynchronous; gk_solve returns after the solve has
+ *    finished and its status has been read back.
+ *  - Calls on one handle must not overlap in time on different streams: each
+ *    handle owns its reduction scratch.
+ *  - The device current at creation time owns a handle; calls switch to it.
+ */
+#ifndef GK_H
+#define GK_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GK_API __attribute__((visibility("default")))
+#else
+#define GK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define GK_OK 0
+#define GK_ERR_ARG 1         /* null handle/pointer, negative size, bad enum        */
+#define GK_ERR_DIM 2         /* operator and vector sizes do not conform (Sec. 4.2) */
+#define GK_ERR_DTYPE 3       /* value type not supported                            */
+#define GK_ERR_NOT_DEVICE 4  /* pointer from another device                         */
+#define GK_ERR_CSR 5         /* rowptr not monotone / columns unsorted, repeated or */
+                             /* out of range                                        */
+#define GK_ERR_FORMAT 6      /* format refused (ELL padding over 8x nnz)            */
+#define GK_ERR_SINGULAR 7    /* zero/missing diagonal or singular diagonal block    */
+#define GK_ERR_UNSUPPORTED 8 /* combination not built                               */
+#define GK_ERR_CUDA 9        /* CUDA runtime error (message in gk_last_error)       */
+#define GK_ERR_ALLOC 10      /* device allocation failed                            */
+#define GK_ERR_TIMEOUT 11    /* a device-side wait exceeded its iteration limit     */
+
+/* ---- enums -------------------------------------------------------------- */
+#define GK_F64 0
+#define GK_F32 1
+
+/* Storage formats of the system matrix. */
+#define GK_CSR 0        /* CSR, rows binned by length: runs of short rows thread-per-row
+                           from shared-memory-staged tiles, long rows warp-per-row      */
+#define GK_CSR_MERGE 1  /* CSR, merge-path split of rows+nonzeros into equal tiles      */
+#define GK_ELL 2        /* ELLPACK, column-major, padded to the longest row             */
+#define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows */
+#define GK_AUTO 4       /* GK_CSR for regular row lengths, GK_CSR_MERGE otherwise       */
+
+#define GK_CG 0
+#define GK_BICGSTAB 1
+
+/* Stop reasons (the stopping_status of Section 2.5). */
+#define GK_STOP_NONE 0
+#define GK_STOP_CONVERGED 1  /* ||r_k|| <= reduction_factor * ref                       */
+#define GK_STOP_MAX_ITERS 2  /* k >= max_iters (Iteration criterion)                    */
+#define GK_STOP_BREAKDOWN 3  /* p.Ap <= 0 (CG); rho, r^.v or t.t zero (BiCGSTAB)          */
+#define GK_STOP_NAN 4        /* a residual norm or a reduction became NaN/Inf           */
+#define GK_STOP_TIME 5       /* time_limit_s exceeded (Time criterion)                  */
+
+typedef struct gk_matrix_s* gk_matrix;
+typedef struct gk_precond_s* gk_precond;
+typedef struct gk_solver_s* gk_solver;
+
+/* Combined stopping criteria (Section 2.5, Listing 1): the first one met
+ * stops the iteration.  ResidualNormReduction: ||r_k||_2 <= reduction_factor
+ * * ref with ref = ||b||_2 if rel_to_b != 0, else ||r_0||_2.  Iteration:
+ * k >= max_iters.  Time: wall time > time_limit_s (<= 0 disables it).
+ * check_every <= 0 (the default) runs the whole solve as one CUDA graph whose
+ * loop is controlled on the device (the criteria, Time included, are
+ * evaluated by the GPU after every iteration); check_every > 0 instead
+ * launches the iterations from the host and reads the stop flag back after
+ * every check_every iterations. */
+typedef struct {
+  int64_t max_iters;
+  double reduction_factor;
+  int32_t rel_to_b;
+  int32_t check_every;
+  double time_limit_s;
+} gk_criteria;
+
+/* Convergence record of one solve (the Convergence logger of Section 2.6). */
+typedef struct {
+  int64_t iters;        /* iterations performed (a BiCGSTAB half step counts as one) */
+  int64_t spmvs;        /* matrix applications including the initial residual and    */
+                        /* the final true-residual check                             */
+  double rel_res;       /* recurred ||r_k|| / ref at exit                             */
+  double rel_res_true;  /* ||b - A x|| / ref recomputed at exit                       */
+  double ref_norm;      /* ref used by the residual criterion                         */
+  int32_t stop_reason;  /* GK_STOP_*                                                  */
+  int32_t device_error; /* nonzero if a device-side wait timed out                    */
+} gk_status;
+
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  int32_t format;          /* the format actually built (GK_AUTO resolved)     */
+  int32_t dtype;
+  int64_t ell_width;       /* K for ELL/HYB, else 0                            */
+  int64_t tail_rows;       /* HYB: rows with more than K entries               */
+  int64_t tail_nnz;        /* HYB: entries stored outside the ELL part          */
+  int64_t short_items;     /* GK_CSR: warp items of up to 32 short rows         */
+  int64_t long_rows;       /* GK_CSR: rows processed warp-per-row               */
+  int64_t tiles;           /* GK_CSR_MERGE: merge-path tiles                    */
+  int64_t device_bytes;    /* bytes of library-owned device storage             */
+  int64_t spmv_bytes;      /* algorithmic bytes of one simple apply, x counted   */
+                           /* once (see the library's documentation)           */
+} gk_matrix_info;
+
+/* ---- errors ------------------------------------------------------------- */
+/* Message of the last failing call on this thread ("" if none).  The string
+ * is owned by the library and valid until the next call on this thread. */
+GK_API const char* gk_last_error(void);
+GK_API int32_t gk_version(void);
+
+/* ---- matrices (the CSR LinOp of Section 2.2.4) --------------------------- */
+/* Builds a library-owned copy of the n_rows x n_cols CSR matrix
+ * (rowptr[n_rows+1], col[nnz], val[nnz]; any of them host or device memory)
+ * in the requested format.  Columns must be sorted and unique within each
+ * row and in [0, n_cols); rowptr[0] = 0, nondecreasing, rowptr[n_rows] = nnz.
+ * Violations return GK_ERR_CSR.  GK_ELL is refused (GK_ERR_FORMAT) when its
+ * padded size exceeds 8 * nnz + n_rows slots.  On success *out owns the copy. */
+GK_API int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* rowptr,
+                         const int32_t* col, const void* val, int32_t dtype, int32_t format,
+                         void* stream, gk_matrix* out);
+GK_API int gk_matrix_get_info(gk_matrix A, gk_matrix_info* info);
+GK_API int gk_matrix_destroy(gk_matrix A);
+
+/* Simple apply, Section 4.2: x = A b (b has n_cols entries, x n_rows).
+ * Row sums accumulate with one fused multiply-add per stored entry. */
+GK_API int gk_apply(gk_matrix A, const void* b, void* x, void* stream);
+
+/* Advanced apply, Section 4.2: x = alpha A b + beta x.  beta == 0 does not
+ * read x (BLAS convention), so gk_apply == gk_apply_adv(1, A, b, 0, x). */
+GK_API int gk_apply_adv(double alpha, gk_matrix A, const void* b, double beta, void* x, void* stream);
+
+/* ---- preconditioners (Section 3.2) -------------------------------------- */
+/* Jacobi preconditioner P_A = M^{-1} generated from A (square).
+ * block_size 1: scalar Jacobi, M = diag(A).  block_size 2..32: block Jacobi
+ * on contiguous blocks of block_size rows (the last one shorter), each
+ * diagonal block inverted by Gauss-Jordan elimination with partial pivoting
+ * (Section 7.5).  A zero/missing diagonal or a singular block returns
+ * GK_ERR_SINGULAR. */
+GK_API int gk_precond_generate(gk_matrix A, int32_t block_size, void* stream, gk_precond* out);
+
+/* z = M^{-1} r (the preconditioner as a LinOp). */
+GK_API int gk_precond_apply(gk_precond P, const void* r, void* z, void* stream);
+
+/* Copies the inverse diagonal blocks, row-major and concatenated (block k
+ * holds m_k*m_k doubles, m_k = block_size except for the last block), into
+ * host memory out[n_out].  For block_size 1 this is 1/a_ii.  n_out must be
+ * at least the total size. */
+GK_API int gk_precond_get_blocks(gk_precond P, double* out, int64_t n_out, void* stream);
+GK_API int gk_precond_destroy(gk_precond P);
+
+/* ---- solvers (Section 3.1) ---------------------------------------------- */
+/* S_A = generate(A): a CG or BiCGSTAB operator bound to A, optionally
+ * preconditioned by P (NULL for none), stopping on *crit. */
+GK_API int gk_solver_generate(gk_matrix A, gk_precond P, int32_t kind, const gk_criteria* crit,
+                       gk_solver* out);
+
+/* x = S_A(b): x holds the initial guess on entry and the solution on exit
+ * (Section 2.1).  *st (nullable) receives the convergence record.
+ * Non-convergence is not an error: GK_OK is returned and st->stop_reason
+ * says which criterion ended the iteration. */
+GK_API int gk_solve(gk_solver S, const void* b, void* x, gk_status* st, void* stream);
+GK_API int gk_solver_destroy(gk_solver S);
+
+/* ---- reductions ---------------------------------------------------------- */
+/* result[0] = sum_i x_i y_i in FP64 with a fixed, run-to-run reproducible
+ * reduction order (per-block trees, then one block over the block partials;
+ * Section 7.4 stresses the weight of such global reductions in Krylov
+ * solvers).  x, y, result: device memory of the current device.  The library
+ * keeps one reduction workspace per device, so gk_dot calls on one device
+ * must be ordered (issued to one stream, or synchronized). */
+GK_API int gk_dot(int64_t n, const double* x, const double* y, double* result, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GK_H */

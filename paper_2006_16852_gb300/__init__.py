@@ -1,0 +1,292 @@
+"""Python binding of the GB300 sparse linear-operator library (``libgk.so``).
+
+The functions mirror the C ABI of ``include/gk.h`` one to one and only
+marshal arguments: every step of the computation runs in the library's CUDA
+kernels.  Vectors may be torch CUDA tensors (the usual case; their data
+pointers are passed through) or host arrays (numpy or CPU tensors), which the
+library stages itself.  Work goes to the current torch CUDA stream unless a
+stream is given.
+
+There is no fallback: ``load()`` raises if ``libgk.so`` has not been built
+(``python -m paper_2006_16852_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgk.so")
+
+OK = 0
+ERR_NAMES = {1: "GK_ERR_ARG", 2: "GK_ERR_DIM", 3: "GK_ERR_DTYPE", 4: "GK_ERR_NOT_DEVICE",
+             5: "GK_ERR_CSR", 6: "GK_ERR_FORMAT", 7: "GK_ERR_SINGULAR", 8: "GK_ERR_UNSUPPORTED",
+             9: "GK_ERR_CUDA", 10: "GK_ERR_ALLOC", 11: "GK_ERR_TIMEOUT"}
+F64, F32 = 0, 1
+FORMATS = {"csr": 0, "csr_merge": 1, "ell": 2, "hyb": 3, "auto": 4}
+FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
+SOLVERS = {"cg": 0, "bicgstab": 1}
+STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME = range(6)
+
+# every symbol include/gk.h declares
+EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get_info",
+           "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
+           "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
+           "gk_solver_destroy", "gk_dot")
+
+
+class GkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Criteria(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int64), ("reduction_factor", ctypes.c_double),
+                ("rel_to_b", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("time_limit_s", ctypes.c_double)]
+
+
+class Status(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("spmvs", ctypes.c_int64), ("rel_res", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("ref_norm", ctypes.c_double),
+                ("stop_reason", ctypes.c_int32), ("device_error", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MatrixInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("format", ctypes.c_int32), ("dtype", ctypes.c_int32), ("ell_width", ctypes.c_int64),
+                ("tail_rows", ctypes.c_int64), ("tail_nnz", ctypes.c_int64),
+                ("short_items", ctypes.c_int64), ("long_rows", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("spmv_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["format_name"] = FORMAT_NAMES.get(self.format, str(self.format))
+        return d
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load ``libgk.so`` and declare the C signatures.  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(the library has no CPU fallback)")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.gk_last_error.restype = ctypes.c_char_p
+    L.gk_last_error.argtypes = []
+    L.gk_version.restype = i32
+    L.gk_version.argtypes = []
+    sig = {
+        "gk_matrix_create_csr": [i64, i64, i64, vp, vp, vp, i32, i32, vp, ctypes.POINTER(vp)],
+        "gk_matrix_get_info": [vp, ctypes.POINTER(MatrixInfo)],
+        "gk_matrix_destroy": [vp],
+        "gk_apply": [vp, vp, vp, vp],
+        "gk_apply_adv": [f64, vp, vp, f64, vp, vp],
+        "gk_precond_generate": [vp, i32, vp, ctypes.POINTER(vp)],
+        "gk_precond_apply": [vp, vp, vp, vp],
+        "gk_precond_get_blocks": [vp, vp, i64, vp],
+        "gk_precond_destroy": [vp],
+        "gk_solver_generate": [vp, vp, i32, ctypes.POINTER(Criteria), ctypes.POINTER(vp)],
+        "gk_solve": [vp, vp, vp, ctypes.POINTER(Status), vp],
+        "gk_solver_destroy": [vp],
+        "gk_dot": [i64, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GkError(rc, lib().gk_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> int:
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream, *arrays) -> int:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    for a in arrays:
+        if getattr(a, "is_cuda", False):
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+def _check_vec(a, n: int, name: str, dtype_bits: int = 64):
+    if a is None:
+        raise ValueError(f"{name} is None")
+    size = a.numel() if hasattr(a, "numel") else a.size
+    if size != n:
+        raise GkError(2, f"{name} has {size} entries, expected {n}")
+    dt = str(a.dtype)
+    if "float64" not in dt:
+        raise GkError(3, f"{name} must be float64, got {dt}")
+
+
+class Matrix:
+    """A CSR operator (library-owned copy) in one of the storage formats."""
+
+    def __init__(self, rowptr, col, val, n_cols: int | None = None, fmt: str = "csr", stream=None):
+        n_rows = (rowptr.numel() if hasattr(rowptr, "numel") else rowptr.size) - 1
+        nnz = col.numel() if hasattr(col, "numel") else col.size
+        n_cols = n_rows if n_cols is None else int(n_cols)
+        for a, want in ((rowptr, "int32"), (col, "int32"), (val, "float64")):
+            if want not in str(a.dtype):
+                raise GkError(3, f"CSR arrays must be int32/int32/float64, got {a.dtype}")
+        h = ctypes.c_void_p()
+        _check(lib().gk_matrix_create_csr(n_rows, n_cols, nnz, _ptr(rowptr), _ptr(col), _ptr(val), F64,
+                                          FORMATS[fmt], _stream(stream, rowptr, col, val),
+                                          ctypes.byref(h)))
+        self.handle = h
+        self.n_rows, self.n_cols, self.nnz = n_rows, n_cols, nnz
+
+    def info(self) -> dict:
+        inf = MatrixInfo()
+        _check(lib().gk_matrix_get_info(self.handle, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.gk_matrix_destroy(h)
+            self.handle = None
+
+
+def apply(A: Matrix, b, x, stream=None):
+    """x = A b (Section 4.2)."""
+    _check_vec(b, A.n_cols, "b")
+    _check_vec(x, A.n_rows, "x")
+    _check(lib().gk_apply(A.handle, _ptr(b), _ptr(x), _stream(stream, b, x)))
+    return x
+
+
+def apply_adv(alpha: float, A: Matrix, b, beta: float, x, stream=None):
+    """x = alpha A b + beta x (Section 4.2)."""
+    _check_vec(b, A.n_cols, "b")
+    _check_vec(x, A.n_rows, "x")
+    _check(lib().gk_apply_adv(float(alpha), A.handle, _ptr(b), float(beta), _ptr(x), _stream(stream, b, x)))
+    return x
+
+
+class Precond:
+    """Jacobi (block_size 1) or block-Jacobi (2..32) preconditioner of A."""
+
+    def __init__(self, A: Matrix, block_size: int = 1, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().gk_precond_generate(A.handle, int(block_size), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.n = A.n_rows
+        self.block_size = int(block_size)
+
+    def blocks(self, stream=None):
+        import numpy as np
+        bs, n = self.block_size, self.n
+        total = n if bs == 1 else (n // bs) * bs * bs + (n % bs) ** 2
+        out = np.zeros(max(total, 1))
+        _check(lib().gk_precond_get_blocks(self.handle, out.ctypes.data, out.size, _stream(stream)))
+        return out[:total]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.gk_precond_destroy(h)
+            self.handle = None
+
+
+def precond_generate(A: Matrix, block_size: int = 1, stream=None) -> Precond:
+    return Precond(A, block_size, stream)
+
+
+def precond_apply(P: Precond, r, z, stream=None):
+    """z = M^{-1} r."""
+    _check_vec(r, P.n, "r")
+    _check_vec(z, P.n, "z")
+    _check(lib().gk_precond_apply(P.handle, _ptr(r), _ptr(z), _stream(stream, r, z)))
+    return z
+
+
+@dataclass
+class SolveStatus:
+    iters: int
+    spmvs: int
+    rel_res: float
+    rel_res_true: float
+    ref_norm: float
+    stop_reason: int
+    device_error: int
+
+
+class Solver:
+    """CG or BiCGSTAB operator S_A bound to A (Section 3.1)."""
+
+    def __init__(self, A: Matrix, P: Precond | None = None, kind: str = "cg", max_iters: int = 1000,
+                 reduction_factor: float = 1e-10, rel_to_b: bool = True, check_every: int = 0,
+                 time_limit_s: float = 0.0):
+        crit = Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, int(check_every),
+                        float(time_limit_s))
+        h = ctypes.c_void_p()
+        _check(lib().gk_solver_generate(A.handle, P.handle if P is not None else None, SOLVERS[kind],
+                                        ctypes.byref(crit), ctypes.byref(h)))
+        self.handle = h
+        self.n = A.n_rows
+        self._keep = (A, P)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.gk_solver_destroy(h)
+            self.handle = None
+
+
+def solver_generate(A: Matrix, P: Precond | None = None, kind: str = "cg", **criteria) -> Solver:
+    return Solver(A, P, kind, **criteria)
+
+
+def solve(S: Solver, b, x, stream=None) -> SolveStatus:
+    """x = S_A(b); x holds the initial guess on entry (Section 2.1)."""
+    _check_vec(b, S.n, "b")
+    _check_vec(x, S.n, "x")
+    st = Status()
+    _check(lib().gk_solve(S.handle, _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream, b, x)))
+    return SolveStatus(**{f: getattr(st, f) for f, _ in Status._fields_})
+
+
+def dot(x, y, result, stream=None):
+    """result[0] = x . y with a reproducible reduction order (device tensors)."""
+    n = x.numel()
+    _check_vec(y, n, "y")
+    _check(lib().gk_dot(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
+    return result

@@ -1,0 +1,221 @@
+// capi.cu -- error reporting, allocation helpers, host/device vector
+// arguments, the apply calls (Section 4.2) and the reproducible dot product.
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "gk_device.cuh"
+#include "gk_internal.h"
+
+namespace gk {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error so later calls can proceed
+  return set_error(e == cudaErrorMemoryAllocation ? GK_ERR_ALLOC : GK_ERR_CUDA, "%s: %s (%s)", what,
+                   cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int dalloc(void** p, size_t bytes, int64_t* counter) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(GK_ERR_ALLOC, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  if (counter) *counter += static_cast<int64_t>(bytes);
+  return GK_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return d;
+}
+
+int sm_count() {
+  static int cache[64] = {};
+  int d = current_device();
+  if (d >= 0 && d < 64 && cache[d]) return cache[d];
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    v = 1;
+  }
+  if (d >= 0 && d < 64) cache[d] = v;
+  return v;
+}
+
+int vec_in(VecArg& v, const void* p, int64_t n, double* staging, bool copy_in, int device,
+           cudaStream_t s) {
+  v.user = p;
+  v.staged = false;
+  v.dev = nullptr;
+  if (n == 0) return GK_OK;
+  if (!p) return set_error(GK_ERR_ARG, "NULL vector");
+  if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return set_error(GK_ERR_ARG, "vector not 8-byte aligned");
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+      return set_error(GK_ERR_NOT_DEVICE, "vector lives on device %d, operator on device %d", at.device,
+                       device);
+    v.dev = static_cast<double*>(const_cast<void*>(p));
+    return GK_OK;
+  }
+  if (!staging) return set_error(GK_ERR_ARG, "no staging buffer for a host vector");
+  v.staged = true;
+  v.dev = staging;
+  if (copy_in)
+    GK_TRY_CUDA(cudaMemcpyAsync(staging, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  return GK_OK;
+}
+
+int vec_out(VecArg& v, int64_t n, cudaStream_t s) {
+  if (!v.staged || n == 0) return GK_OK;
+  GK_TRY_CUDA(cudaMemcpyAsync(const_cast<void*>(v.user), v.dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                              s));
+  GK_TRY_CUDA(cudaStreamSynchronize(s));
+  return GK_OK;
+}
+
+namespace {
+
+// True for host memory (pinned or pageable).
+bool is_host(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// Deterministic dot product: per-thread fma accumulation over a grid-stride
+// range, then the fixed-order grid reduction.
+__global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                  int64_t n, double* partials, unsigned int* counter,
+                                                  double* result) {
+  __shared__ double scratch[64];
+  double a[1] = {0.0};
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    a[0] = fma(__ldg(x + i), __ldg(y + i), a[0]);
+  double out[1];
+  if (grid_sum<1>(a, partials, counter, scratch, out) && threadIdx.x == 0) result[0] = out[0];
+}
+
+struct DotWorkspace {
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  int grid = 0;
+};
+std::mutex g_dot_mu;
+DotWorkspace g_dot_ws[64];
+
+}  // namespace
+
+int dot_grid() { return 4 * sm_count(); }
+
+}  // namespace gk
+
+using namespace gk;
+
+namespace {
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
+extern "C" const char* gk_last_error(void) { return gk::g_last_error.c_str(); }
+
+extern "C" int32_t gk_version(void) { return 100; }
+
+extern "C" int gk_apply_adv(double alpha, gk_matrix h, const void* b, double beta, void* x, void* stream) {
+  Matrix* A = as_matrix(h);
+  if (!A) return set_error(GK_ERR_ARG, "gk_apply: NULL matrix");
+  if (b == x && A->n_rows > 0) return set_error(GK_ERR_ARG, "gk_apply: b and x must not alias");
+  DeviceGuard g(A->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A->n_rows == 0) return GK_OK;
+  if (is_host(b) && !A->stage_in) GK_TRY(dalloc_n(&A->stage_in, A->n_cols + 1, &A->device_bytes));
+  if (is_host(x) && !A->stage_out) GK_TRY(dalloc_n(&A->stage_out, A->n_rows + 1, &A->device_bytes));
+  VecArg vb, vx;
+  GK_TRY(vec_in(vb, b, A->n_cols, A->stage_in, true, A->device, s));
+  GK_TRY(vec_in(vx, x, A->n_rows, A->stage_out, beta != 0.0, A->device, s));
+  Epi e;
+  e.mode = EPI_PLAIN;
+  e.alpha = alpha;
+  e.beta = beta;
+  e.y = vx.dev;
+  e.err = A->err;
+  GK_TRY(spmv_launch(*A, vb.dev, e, s));
+  return vec_out(vx, A->n_rows, s);
+}
+
+extern "C" int gk_apply(gk_matrix h, const void* b, void* x, void* stream) {
+  return gk_apply_adv(1.0, h, b, 0.0, x, stream);
+}
+
+extern "C" int gk_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return set_error(GK_ERR_ARG, "gk_dot: bad argument");
+  if (is_host(x) || is_host(y) || is_host(result))
+    return set_error(GK_ERR_NOT_DEVICE, "gk_dot: x, y and result must be device memory");
+  int dev = current_device();
+  if (dev < 0 || dev >= 64) return set_error(GK_ERR_UNSUPPORTED, "gk_dot: device index %d", dev);
+  DotWorkspace* ws;
+  {
+    std::lock_guard<std::mutex> lock(g_dot_mu);
+    ws = &g_dot_ws[dev];
+    if (!ws->partials) {
+      ws->grid = dot_grid();
+      GK_TRY(dalloc_n(&ws->partials, static_cast<size_t>(ws->grid), nullptr));
+      GK_TRY(dalloc_n(&ws->counter, 1, nullptr));
+      GK_TRY_CUDA(cudaMemset(ws->counter, 0, sizeof(unsigned int)));
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dot_kernel<<<ws->grid, 256, 0, s>>>(x, y, n, ws->partials, ws->counter, result);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}

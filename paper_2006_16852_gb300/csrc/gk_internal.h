@@ -1,0 +1,234 @@
+// gk_internal.h -- host/device declarations shared by the library's
+// translation units: handle structures, the device solver state, the SpMV
+// epilogue descriptor and the launchers.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gk.h"
+
+namespace gk {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define GK_TRY_CUDA(call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::gk::cuda_error(e_, #call); \
+  } while (0)
+
+#define GK_TRY(call)            \
+  do {                          \
+    int rc_ = (call);           \
+    if (rc_ != GK_OK) return rc_; \
+  } while (0)
+
+// Device allocation that records its size in *counter (may be null).
+int dalloc(void** p, size_t bytes, int64_t* counter);
+template <class T>
+int dalloc_n(T** p, size_t n, int64_t* counter) {
+  return dalloc(reinterpret_cast<void**>(p), n * sizeof(T), counter);
+}
+void dfree(void* p);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+int current_device();
+
+// ---------------------------------------------------------------------------
+// device-side solver state (one per solver handle; also used by gk_dot)
+// ---------------------------------------------------------------------------
+struct SolverState {
+  double rho, rho_prev, alpha, beta, omega;
+  double factor, ref, tol;   // residual criterion: ||r|| <= tol = factor * ref
+  double rnorm, snorm;       // last recurred ||r||, ||s|| (BiCGSTAB)
+  double bnorm, rnorm0;
+  double red[2];             // raw sums of the last reduction (diagnostics)
+  double true_rr;            // ||b - A x||^2 of the final check
+  long long iter, max_iters, spmvs;
+  long long iter_guard;      // iterations the device-side loop has run
+  unsigned long long t_start_ns, time_limit_ns;
+  int stop;                  // GK_STOP_*
+  int half;                  // BiCGSTAB: converged at the half step
+  int rel_to_b;
+  int err;                   // device error bits (kErrTimeout)
+};
+
+// What the last block of a reduction does with the sums.
+enum Fin : int {
+  FIN_NONE = 0,
+  FIN_SETUP_RESID,  // sums = (||r0||^2, ||b||^2): set ref and tol
+  FIN_CG_START,     // sums = (r.z): rho; check the criteria at k = 0
+  FIN_CG_SIGMA,     // sums = (p.q): alpha = rho / sigma
+  FIN_CG_ITER,      // sums = (r.z, r.r): k += 1, criteria, beta
+  FIN_BI_START,     // sums = (r^.r): criteria at k = 0, first rho and beta
+  FIN_BI_RHV,       // sums = (r^.v): alpha
+  FIN_BI_S,         // sums = (s.s): half-step test
+  FIN_BI_OMEGA,     // sums = (s.t, t.t): omega
+  FIN_BI_ITER,      // sums = (r^.r, r.r): k += 1, criteria, next rho/beta
+  FIN_TRUE_RESID,   // sums = (||b - A x||^2, -): store
+};
+
+// ---------------------------------------------------------------------------
+// SpMV epilogue: what happens to each finished row sum s_i
+// ---------------------------------------------------------------------------
+enum EpiMode : int {
+  EPI_PLAIN = 0,  // y_i = alpha s_i (beta == 0) or fma(beta, y_i, alpha s_i)
+  EPI_RESID = 1,  // y_i = u_i - s_i (u = b): sums (y.y, u.u)
+  EPI_DOT = 2,    // y_i = s_i: sums (u.y)
+  EPI_DOT2 = 3,   // y_i = s_i: sums (u.y, y.y)
+};
+
+struct Epi {
+  int mode = EPI_PLAIN;
+  int fin = FIN_NONE;
+  double alpha = 1.0, beta = 0.0;
+  const double* u = nullptr;
+  double* y = nullptr;
+  SolverState* st = nullptr;  // scalars the reduction feeds
+  int skip_mode = 0;          // 0 never skip, 1 skip if st->stop, 2 if st->stop || st->half
+  double* partials = nullptr; // reduction scratch (>= grid * 2 doubles)
+  unsigned int* counter = nullptr;
+  int* err = nullptr;         // device error word for bounded waits
+};
+
+// ---------------------------------------------------------------------------
+// matrix handle
+// ---------------------------------------------------------------------------
+constexpr int kMergeThreads = 128;
+constexpr int kMergeItems = 16;  // merge-path items (row ends + nonzeros) per thread
+constexpr int kMergeTile = kMergeThreads * kMergeItems;
+constexpr int kBinWarps = 8;       // warps per block of the binned kernel
+constexpr int kBinRowsMax = 32;    // rows per warp item
+constexpr int kBinShortMax = 32;   // longest "short" row
+constexpr int kBinItemNnz = kBinRowsMax * kBinShortMax;
+constexpr int kEllThreads = 256;
+
+struct MergePlan {
+  int64_t n_rows = 0, nnz = 0, n_tiles = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  int32_t* tile_i = nullptr;  // [n_tiles + 1] merge coordinates of tile starts
+  int32_t* tile_j = nullptr;
+  // per-apply scratch: partial sums of rows cut by tile boundaries
+  double* head_val = nullptr;
+  int32_t* head_row = nullptr;
+  double* carry_val = nullptr;
+  int32_t* carry_row = nullptr;
+  int32_t* cont = nullptr;
+  int grid = 0;
+};
+
+struct Matrix {
+  std::atomic<int> refs{1};
+  int device = 0;
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  int format = GK_CSR;
+  int64_t device_bytes = 0;
+  // CSR copy (every format keeps it)
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  std::vector<int32_t> h_rowptr;  // host copy of the row pointers (planning)
+  // GK_CSR: warp items of short rows and the list of long rows
+  int32_t* item_r0 = nullptr;
+  int32_t* item_r1 = nullptr;
+  int64_t n_items = 0;
+  int32_t* long_rows = nullptr;
+  int64_t n_long = 0;
+  int grid_bin = 0;
+  // GK_CSR_MERGE
+  MergePlan merge;
+  // GK_ELL / GK_HYB
+  int64_t K = 0, ld = 0;
+  int32_t* ell_col = nullptr;
+  double* ell_val = nullptr;
+  int grid_ell = 0;
+  // GK_HYB overflow ("tail"): CSR over the rows longer than K
+  int64_t m_tail = 0, tail_nnz = 0;
+  int32_t* tail_rows = nullptr;
+  int32_t* tail_rowptr = nullptr;
+  int32_t* tail_col = nullptr;
+  double* tail_val = nullptr;
+  int32_t* tail_slot = nullptr;  // [n_rows] index into tail_sum or -1
+  double* tail_sum = nullptr;    // [m_tail]
+  MergePlan tail;
+  // scratch of gk_apply / precond generation
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  int* err = nullptr;
+  double* stage_in = nullptr;   // host-vector staging
+  double* stage_out = nullptr;
+  int max_grid = 0;             // partials hold max_grid * 2 doubles
+};
+
+void matrix_release(Matrix* A);
+
+// Enqueue y = op(A x) with the epilogue e on stream s.  x has n_cols entries.
+int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s);
+
+// Grid size used by SpMV launches of this matrix (for scratch sizing).
+int spmv_max_grid(const Matrix& A);
+// Persistent grid sizes of the SpMV kernels for a given amount of work.
+int merge_grid(int64_t n_tiles);
+int bin_grid(int64_t work_warps);
+int ell_grid(int64_t n_rows);
+
+// Format construction (matrix.cu).
+int build_merge_plan(MergePlan& P, int64_t n_rows, int64_t nnz, const int32_t* rowptr,
+                     const int32_t* col, const double* val, int64_t* bytes, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// vector arguments (host or device)
+// ---------------------------------------------------------------------------
+struct VecArg {
+  const void* user = nullptr;
+  double* dev = nullptr;  // device pointer the kernels use
+  bool staged = false;    // user pointer is host memory
+};
+// Classifies p; for host memory copies n doubles into staging (if copy_in).
+int vec_in(VecArg& v, const void* p, int64_t n, double* staging, bool copy_in, int device,
+           cudaStream_t s);
+// For staged outputs: copies back and synchronizes s.
+int vec_out(VecArg& v, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// preconditioner handle
+// ---------------------------------------------------------------------------
+struct Precond {
+  std::atomic<int> refs{1};
+  int device = 0;
+  Matrix* A = nullptr;
+  int64_t n = 0;
+  int bs = 1;
+  int64_t nblocks = 0;
+  double* dinv = nullptr;    // scalar Jacobi: 1/a_ii
+  double* blocks = nullptr;  // block Jacobi: inverse blocks, each column-major
+  int64_t block_elems = 0;
+  double* stage_in = nullptr;
+  double* stage_out = nullptr;
+  int64_t device_bytes = 0;
+};
+
+void precond_release(Precond* P);
+
+enum PrecKind : int { PREC_NONE = 0, PREC_SCALAR = 1, PREC_BLOCK = 2 };
+
+// z = M^{-1} r as a standalone launch.
+int precond_apply_launch(const Precond* P, const double* r, double* z, cudaStream_t s);
+
+}  // namespace gk
+
+// The opaque C handles are the C++ objects themselves.
+inline gk::Matrix* as_matrix(gk_matrix h) { return reinterpret_cast<gk::Matrix*>(h); }
+inline gk::Precond* as_precond(gk_precond h) { return reinterpret_cast<gk::Precond*>(h); }

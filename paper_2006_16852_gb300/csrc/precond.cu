@@ -1,0 +1,340 @@
+// precond.cu -- Jacobi preconditioners (Section 3.2): scalar diagonal scaling
+// and block Jacobi whose diagonal blocks are inverted by Gauss-Jordan
+// elimination with partial pivoting (Section 7.5), one warp per block.
+#include <algorithm>
+#include <climits>
+#include <memory>
+
+#include "gk_device.cuh"
+#include "gk_internal.h"
+#include "precond_device.cuh"
+
+namespace gk {
+
+namespace {
+
+__global__ void jacobi_scalar_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, int n, double* dinv, int* bad) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    double d = 0.0;
+    bool found = false;
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      if (col[k] == r) {
+        d = val[k];
+        found = true;
+        break;
+      }
+    }
+    if (!found || d == 0.0) {
+      atomicMin(bad, r);
+      dinv[r] = 0.0;
+    } else {
+      dinv[r] = 1.0 / d;
+    }
+  }
+}
+
+// Gauss-Jordan inversion of one diagonal block per warp on the augmented
+// matrix [D | I] held in shared memory (row stride 65 doubles: conflict-free
+// column access).  Pivot: largest |entry| in column k at or below row k,
+// lowest row on ties.  The pivot row is scaled by the reciprocal of the pivot
+// and every other row i is updated w_ij = fma(-w_ik, w_kj, w_ij).  Columns
+// left of and at k are not needed again once step k is done, so only
+// columns j > k are updated: the right half (the inverse) receives exactly
+// the operations of the full elimination.
+constexpr int kBjWarps = 4;
+constexpr int kBjStride = 65;
+constexpr int kBjWarpDoubles = 32 * kBjStride;
+
+__global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
+    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+    int n, int bs, int nblocks, double* blocks, int* bad) {
+  extern __shared__ double bj_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* W = bj_smem + warp * kBjWarpDoubles;
+  for (int blk = blockIdx.x * kBjWarps + warp; blk < nblocks; blk += gridDim.x * kBjWarps) {
+    const int r0 = blk * bs;
+    const int m = min(bs, n - r0);
+    const int wd = 2 * m;
+    for (int idx = lane; idx < 32 * kBjStride; idx += 32) W[idx] = 0.0;
+    __syncwarp();
+    if (lane < m) {
+      const int r = r0 + lane;
+      for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+        const int c = col[k];
+        if (c >= r0 && c < r0 + m) W[lane * kBjStride + (c - r0)] = val[k];
+      }
+      W[lane * kBjStride + m + lane] = 1.0;
+    }
+    __syncwarp();
+    bool singular = false;
+    for (int k = 0; k < m; ++k) {
+      double a = (lane >= k && lane < m) ? fabs(W[lane * kBjStride + k]) : -1.0;
+      int idx = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (a2 > a || (a2 == a && i2 < idx)) {
+          a = a2;
+          idx = i2;
+        }
+      }
+      if (!(a > 0.0)) {
+        singular = true;
+        break;
+      }
+      const int piv = idx;
+      __syncwarp();
+      if (piv != k) {
+        for (int j = k + lane; j < wd; j += 32) {
+          const double t = W[k * kBjStride + j];
+          W[k * kBjStride + j] = W[piv * kBjStride + j];
+          W[piv * kBjStride + j] = t;
+        }
+      }
+      __syncwarp();
+      const double rcp = 1.0 / W[k * kBjStride + k];
+      __syncwarp();
+      for (int j = k + 1 + lane; j < wd; j += 32) W[k * kBjStride + j] = W[k * kBjStride + j] * rcp;
+      __syncwarp();
+      if (lane < m && lane != k) {
+        const double f = W[lane * kBjStride + k];
+        for (int j = k + 1; j < wd; ++j)
+          W[lane * kBjStride + j] = fma(-f, W[k * kBjStride + j], W[lane * kBjStride + j]);
+      }
+      __syncwarp();
+    }
+    if (singular && lane == 0) atomicMin(bad, blk);
+    const int64_t off = static_cast<int64_t>(blk) * bs * bs;
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int j = idx / m, i = idx - j * m;
+      blocks[off + idx] = W[i * kBjStride + m + j];
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void scalar_apply_kernel(const double* __restrict__ dinv, const double* __restrict__ r, double* z,
+                                    int64_t n) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    z[i] = dinv[i] * r[i];
+}
+
+__global__ void bj_apply_kernel(const double* __restrict__ blocks, int n, int bs, int nblocks,
+                                const double* __restrict__ r, double* z) {
+  const int lane = threadIdx.x & 31;
+  const int bpw = 32 / bs;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * bpw < nblocks; w += nw) {
+    const BjLane L = bj_lane(w * bpw, lane, bs, n, nblocks);
+    const double rm = L.active ? r[L.row] : 0.0;
+    const double zz = bj_apply_lane(blocks, L, bs, rm);
+    if (L.active) z[L.row] = zz;
+  }
+}
+
+// Row-major, concatenated copy of the column-major device blocks (the layout
+// of gk_precond_get_blocks).
+__global__ void bj_export_kernel(const double* __restrict__ blocks, int n, int bs, int nblocks, double* out) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t total = static_cast<int64_t>(nblocks - 1) * bs * bs +
+                        static_cast<int64_t>(n - (nblocks - 1) * bs) * (n - (nblocks - 1) * bs);
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t blk = e / (static_cast<int64_t>(bs) * bs);
+    const int64_t off = blk * bs * bs;
+    const int64_t rem = static_cast<int64_t>(n) - blk * bs;
+    const int m = static_cast<int>(rem < bs ? rem : bs);
+    const int idx = static_cast<int>(e - off);
+    const int i = idx / m, j = idx - i * m;
+    out[e] = blocks[off + static_cast<int64_t>(j) * m + i];
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8 * sm_count())));
+}
+
+struct PrecondDeleter {
+  void operator()(Precond* p) const { precond_release(p); }
+};
+
+}  // namespace
+
+int64_t bj_total_elems(int64_t n, int bs) {
+  if (n == 0) return 0;
+  int64_t full = n / bs, last = n % bs;
+  return full * bs * bs + last * last;
+}
+
+void precond_release(Precond* P) {
+  if (!P) return;
+  if (P->refs.fetch_sub(1) != 1) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  dfree(P->dinv);
+  dfree(P->blocks);
+  dfree(P->stage_in);
+  dfree(P->stage_out);
+  matrix_release(P->A);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete P;
+}
+
+int precond_apply_launch(const Precond* P, const double* r, double* z, cudaStream_t s) {
+  if (P->n == 0) return GK_OK;
+  if (P->bs == 1) {
+    scalar_apply_kernel<<<grid_for(P->n, 256), 256, 0, s>>>(P->dinv, r, z, P->n);
+  } else {
+    const int bpw = 32 / P->bs;
+    const int64_t warps = (P->nblocks + bpw - 1) / bpw;
+    bj_apply_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(P->blocks, static_cast<int>(P->n), P->bs,
+                                                              static_cast<int>(P->nblocks), r, z);
+  }
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream, gk_precond* out) {
+  if (!out) return set_error(GK_ERR_ARG, "gk_precond_generate: out is NULL");
+  *out = nullptr;
+  Matrix* A = as_matrix(h);
+  if (!A) return set_error(GK_ERR_ARG, "gk_precond_generate: NULL matrix");
+  if (A->n_rows != A->n_cols) return set_error(GK_ERR_DIM, "gk_precond_generate: matrix is not square");
+  if (block_size < 1 || block_size > 32)
+    return set_error(GK_ERR_ARG, "gk_precond_generate: block_size %d not in [1, 32]", block_size);
+  int prev = current_device();
+  if (prev != A->device) cudaSetDevice(A->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::unique_ptr<Precond, PrecondDeleter> hold(new Precond);
+  Precond* P = hold.get();
+  P->device = A->device;
+  A->refs.fetch_add(1);
+  P->A = A;
+  P->n = A->n_rows;
+  P->bs = block_size;
+  int rc = GK_OK;
+  do {
+    int bad = INT_MAX, bad_init = INT_MAX;
+    if (cudaMemcpyAsync(A->err + 1, &bad_init, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
+      break;
+    }
+    if (block_size == 1) {
+      P->nblocks = P->n;
+      if ((rc = dalloc_n(&P->dinv, static_cast<size_t>(std::max<int64_t>(P->n, 1)), &P->device_bytes)))
+        break;
+      if (P->n > 0)
+        jacobi_scalar_kernel<<<grid_for(P->n, 256), 256, 0, s>>>(A->rowptr, A->col, A->val,
+                                                                  static_cast<int>(P->n), P->dinv, A->err + 1);
+    } else {
+      P->nblocks = (P->n + block_size - 1) / block_size;
+      P->block_elems = bj_total_elems(P->n, block_size);
+      if ((rc = dalloc_n(&P->blocks, static_cast<size_t>(std::max<int64_t>(P->block_elems, 1)),
+                         &P->device_bytes)))
+        break;
+      const size_t smem = sizeof(double) * kBjWarpDoubles * kBjWarps;
+      cudaFuncSetAttribute(bj_generate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+      if (P->nblocks > 0)
+        bj_generate_kernel<<<grid_for(P->nblocks * 32, kBjWarps * 32), kBjWarps * 32, smem, s>>>(
+            A->rowptr, A->col, A->val, static_cast<int>(P->n), block_size, static_cast<int>(P->nblocks),
+            P->blocks, A->err + 1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      rc = cuda_error(e, "Jacobi generate launch");
+      break;
+    }
+    if (cudaMemcpyAsync(&bad, A->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = cuda_error(cudaGetLastError(), "Jacobi generate");
+      break;
+    }
+    if (bad != INT_MAX) {
+      rc = block_size == 1 ? set_error(GK_ERR_SINGULAR, "zero or missing diagonal in row %d", bad)
+                           : set_error(GK_ERR_SINGULAR, "diagonal block %d is singular", bad);
+      break;
+    }
+  } while (false);
+  if (prev != A->device) cudaSetDevice(prev);
+  if (rc != GK_OK) return rc;
+  *out = reinterpret_cast<gk_precond>(hold.release());
+  return GK_OK;
+}
+
+extern "C" int gk_precond_apply(gk_precond h, const void* r, void* z, void* stream) {
+  Precond* P = as_precond(h);
+  if (!P) return set_error(GK_ERR_ARG, "gk_precond_apply: NULL preconditioner");
+  if (r == z && P->n > 0) return set_error(GK_ERR_ARG, "gk_precond_apply: r and z must not alias");
+  int prev = current_device();
+  if (prev != P->device) cudaSetDevice(P->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = GK_OK;
+  do {
+    cudaPointerAttributes at;
+    bool host_r = cudaPointerGetAttributes(&at, r) != cudaSuccess ||
+                  at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+    cudaGetLastError();
+    bool host_z = cudaPointerGetAttributes(&at, z) != cudaSuccess ||
+                  at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+    cudaGetLastError();
+    if (host_r && !P->stage_in && (rc = dalloc_n(&P->stage_in, P->n + 1, &P->device_bytes))) break;
+    if (host_z && !P->stage_out && (rc = dalloc_n(&P->stage_out, P->n + 1, &P->device_bytes))) break;
+    VecArg vr, vz;
+    if ((rc = vec_in(vr, r, P->n, P->stage_in, true, P->device, s))) break;
+    if ((rc = vec_in(vz, z, P->n, P->stage_out, false, P->device, s))) break;
+    if ((rc = precond_apply_launch(P, vr.dev, vz.dev, s))) break;
+    rc = vec_out(vz, P->n, s);
+  } while (false);
+  if (prev != P->device) cudaSetDevice(prev);
+  return rc;
+}
+
+extern "C" int gk_precond_get_blocks(gk_precond h, double* out, int64_t n_out, void* stream) {
+  Precond* P = as_precond(h);
+  if (!P || !out) return set_error(GK_ERR_ARG, "gk_precond_get_blocks: NULL argument");
+  const int64_t total = P->bs == 1 ? P->n : P->block_elems;
+  if (n_out < total) return set_error(GK_ERR_DIM, "gk_precond_get_blocks: need %lld doubles", (long long)total);
+  if (total == 0) return GK_OK;
+  int prev = current_device();
+  if (prev != P->device) cudaSetDevice(P->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = GK_OK;
+  double* tmp = nullptr;
+  do {
+    if (P->bs == 1) {
+      if (cudaMemcpyAsync(out, P->dinv, sizeof(double) * total, cudaMemcpyDefault, s) != cudaSuccess) {
+        rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
+        break;
+      }
+    } else {
+      if ((rc = dalloc_n(&tmp, static_cast<size_t>(total), nullptr))) break;
+      bj_export_kernel<<<grid_for(total, 256), 256, 0, s>>>(P->blocks, static_cast<int>(P->n), P->bs,
+                                                            static_cast<int>(P->nblocks), tmp);
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpyAsync(out, tmp, sizeof(double) * total, cudaMemcpyDefault, s) != cudaSuccess) {
+        rc = cuda_error(cudaGetLastError(), "export blocks");
+        break;
+      }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "sync");
+  } while (false);
+  dfree(tmp);
+  if (prev != P->device) cudaSetDevice(prev);
+  return rc;
+}
+
+extern "C" int gk_precond_destroy(gk_precond h) {
+  if (!h) return set_error(GK_ERR_ARG, "gk_precond_destroy: NULL handle");
+  precond_release(as_precond(h));
+  return GK_OK;
+}

@@ -1,0 +1,518 @@
+// spmv.cu -- sparse matrix-vector products y = op(A x) for the four storage
+// formats (Section 4.2's simple and advanced apply), each with a fused
+// epilogue that can also produce the dot products a Krylov step needs.
+//
+// FP64 throughput shapes every kernel here: the GPU retires about two FP64
+// fused multiply-adds per SM per clock, barely more than the ~1.9 nonzeros
+// per SM per clock that HBM delivers for 12-byte (value + index) entries.  So
+// each stored entry costs exactly one DFMA, warps keep all 32 lanes busy in
+// the DFMA loops, and reductions of partial sums are kept off the
+// per-nonzero path.
+#include <algorithm>
+#include <cstdio>
+
+#include "gk_device.cuh"
+#include "gk_internal.h"
+#include "solver_state.cuh"
+
+namespace gk {
+
+// ---------------------------------------------------------------------------
+// epilogue
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool epi_skip(const Epi& e) {
+  if (e.st == nullptr || e.skip_mode == 0) return false;
+  const volatile int* f = &e.st->stop;
+  if (f[0] != 0) return true;
+  return e.skip_mode == 2 && f[1] != 0;  // f[1] is st->half
+}
+
+__device__ __forceinline__ void epi_row(const Epi& e, int row, double s, double& a0, double& a1) {
+  switch (e.mode) {
+    case EPI_PLAIN: {
+      double as = e.alpha * s;
+      e.y[row] = (e.beta == 0.0) ? as : fma(e.beta, e.y[row], as);
+      break;
+    }
+    case EPI_RESID: {
+      double b = e.u[row];
+      double r = b - s;
+      e.y[row] = r;
+      a0 = fma(r, r, a0);
+      a1 = fma(b, b, a1);
+      break;
+    }
+    case EPI_DOT:
+      e.y[row] = s;
+      a0 = fma(e.u[row], s, a0);
+      break;
+    default:  // EPI_DOT2
+      e.y[row] = s;
+      a0 = fma(e.u[row], s, a0);
+      a1 = fma(s, s, a1);
+      break;
+  }
+}
+
+// Grid-wide reduction of (a0, a1) and the scalar step that consumes it.
+__device__ __forceinline__ void epi_finish(const Epi& e, double a0, double a1, double* scratch) {
+  if (e.mode == EPI_PLAIN) return;
+  double v[2] = {a0, a1}, out[2];
+  if (grid_sum<2>(v, e.partials, e.counter, scratch, out)) {
+    if (threadIdx.x == 0 && e.st) finalize(e.fin, out, e.st);
+  }
+}
+
+// Block partials only; a later launch finishes the reduction.
+__device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, double* scratch) {
+  if (e.mode == EPI_PLAIN) return;
+  double v[2] = {a0, a1};
+  block_sum<2>(v, scratch);
+  if (threadIdx.x == 0) {
+    e.partials[2 * blockIdx.x] = v[0];
+    e.partials[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GK_CSR: rows binned by length.
+// Short rows (<= 32 entries) are grouped into warp items of up to 32
+// consecutive rows; a warp bulk-copies the item's values and column indices
+// into its own shared-memory stage (TMA, one mbarrier per warp) and each lane
+// sums one row sequentially -- the same fma order as the CPU reference, so
+// these rows are bit-identical to it.  Long rows are processed one per warp
+// with coalesced loads and an xor-butterfly sum.
+// ---------------------------------------------------------------------------
+
+constexpr int kBinStage = kBinItemNnz + 8;
+constexpr int kBinValBytes = kBinStage * 8;
+constexpr int kBinColBytes = kBinStage * 4;
+constexpr int kBinWarpBytes = kBinValBytes + kBinColBytes + 16;
+static_assert(kBinWarpBytes % 16 == 0, "warp stage must keep 16-byte alignment");
+constexpr int kBinSmem = kBinWarps * kBinWarpBytes;
+
+struct BinArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const int32_t* item_r0;
+  const int32_t* item_r1;
+  int n_items;
+  const int32_t* long_rows;
+  int n_long;
+  const double* x;
+};
+
+__global__ void __launch_bounds__(kBinWarps * 32) spmv_binned_kernel(BinArgs a, Epi e) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_scratch[64];
+  if (epi_skip(e)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* base = smem_raw + warp * kBinWarpBytes;
+  double* val_s = reinterpret_cast<double*>(base);
+  int32_t* col_s = reinterpret_cast<int32_t*>(base + kBinValBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + kBinValBytes + kBinColBytes);
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  double a0 = 0.0, a1 = 0.0;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int gw = blockIdx.x * kBinWarps + warp, nwarps = gridDim.x * kBinWarps;
+  for (int it = gw; ok && it < a.n_items; it += nwarps) {
+    const int r0 = __ldg(a.item_r0 + it), r1 = __ldg(a.item_r1 + it);
+    const int k0 = __ldg(a.rowptr + r0), k1 = __ldg(a.rowptr + r1);
+    const int ka = k0 & ~3, kb = (k1 + 3) & ~3;
+    const uint32_t nb = static_cast<uint32_t>(kb - ka);
+    if (nb > 0) {
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, nb * 12u);
+        bulk_g2s(val_s, a.val + ka, nb * 8u, bar);
+        bulk_g2s(col_s, a.col + ka, nb * 4u, bar);
+      }
+      bool w = mbar_wait(bar, phase, e.err);
+      phase ^= 1u;
+      ok = __all_sync(0xffffffffu, w);
+    }
+    const int row = r0 + lane;
+    if (ok && row < r1) {
+      const int kk0 = __ldg(a.rowptr + row) - ka, kk1 = __ldg(a.rowptr + row + 1) - ka;
+      double s = 0.0;
+      for (int k = kk0; k < kk1; ++k) s = fma(val_s[k], __ldg(a.x + col_s[k]), s);
+      epi_row(e, row, s, a0, a1);
+    }
+    __syncwarp();
+  }
+  for (int lr = gw; ok && lr < a.n_long; lr += nwarps) {
+    const int row = __ldg(a.long_rows + lr);
+    const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+    double s = 0.0;
+    for (int k = k0 + lane; k < k1; k += 32) s = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) epi_row(e, row, s, a0, a1);
+  }
+  epi_finish(e, a0, a1, red_scratch);
+}
+
+// ---------------------------------------------------------------------------
+// GK_ELL (and the ELL part of GK_HYB): column-major slots, one row per
+// thread, padding slots carry column -1 and are skipped.  Rows with an
+// overflow in the HYB tail add its precomputed partial sum.
+// ---------------------------------------------------------------------------
+
+struct EllArgs {
+  const int32_t* col;
+  const double* val;
+  int64_t ld;
+  int K;
+  int n_rows;
+  const double* x;
+  const int32_t* tail_slot;
+  const double* tail_sum;
+};
+
+__global__ void __launch_bounds__(kEllThreads) spmv_ell_kernel(EllArgs a, Epi e) {
+  __shared__ double red_scratch[64];
+  if (epi_skip(e)) return;
+  double a0 = 0.0, a1 = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < a.n_rows; row += stride) {
+    double s = 0.0;
+    const int32_t* cp = a.col + row;
+    const double* vp = a.val + row;
+    for (int j = 0; j < a.K; ++j) {
+      const int c = __ldg(cp + j * a.ld);
+      if (c >= 0) s = fma(__ldg(vp + j * a.ld), __ldg(a.x + c), s);
+    }
+    if (a.tail_slot) {
+      const int t = __ldg(a.tail_slot + row);
+      if (t >= 0) s += __ldcg(a.tail_sum + t);
+    }
+    epi_row(e, row, s, a0, a1);
+  }
+  epi_finish(e, a0, a1, red_scratch);
+}
+
+// ---------------------------------------------------------------------------
+// GK_CSR_MERGE (and the HYB tail): merge-path SpMV.  The sequence of
+// n_rows row ends and nnz entries is cut into tiles of kMergeTile items and
+// each thread walks kMergeItems consecutive items, so every thread does the
+// same amount of work whatever the row lengths.  A row split between threads
+// is completed in a second, row-parallel pass that adds the pieces in a
+// fixed order; a row split between tiles is completed by a one-block fix-up
+// launch.  Tiles (row pointers, columns, values) are bulk-copied to shared
+// memory.
+// ---------------------------------------------------------------------------
+
+constexpr int kMergeStage = kMergeTile + 8;
+struct MergeSmem {
+  double val[kMergeStage];
+  double ys[kMergeTile];
+  double head_val[kMergeThreads];
+  double carry_val[kMergeThreads];
+  int32_t rp[kMergeStage];
+  int32_t col[kMergeStage];
+  int32_t head_row[kMergeThreads];
+  int32_t carry_row[kMergeThreads];
+  int32_t cont[kMergeThreads];
+  uint64_t bar;
+  double red[64];
+};
+
+struct MergeArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const int32_t* tile_i;
+  const int32_t* tile_j;
+  double* head_val;
+  int32_t* head_row;
+  double* carry_val;
+  int32_t* carry_row;
+  int32_t* cont;
+  int n_rows;
+  int nnz;
+  int n_tiles;
+  const double* x;
+};
+
+__global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, Epi e) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MergeSmem& S = *reinterpret_cast<MergeSmem*>(smem_raw);
+  if (epi_skip(e)) return;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int total = a.n_rows + a.nnz;
+  double a0 = 0.0, a1 = 0.0;
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int ti = __ldg(a.tile_i + tile), tj = __ldg(a.tile_j + tile);
+    const int ti1 = __ldg(a.tile_i + tile + 1), tj1 = __ldg(a.tile_j + tile + 1);
+    const int d0 = tile * kMergeTile;
+    const int d1 = min(d0 + kMergeTile, total);
+    const int rp_last = min(ti1 + 1, a.n_rows);
+    const int ra = ti & ~3, rb = (rp_last + 1 + 3) & ~3;
+    const int ja = tj & ~3, jb = (tj1 + 3) & ~3;
+    const uint32_t nrp = static_cast<uint32_t>(rb - ra), nj = static_cast<uint32_t>(jb - ja);
+    if (t == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&S.bar, nrp * 4u + nj * 12u);
+      bulk_g2s(S.rp, a.rowptr + ra, nrp * 4u, &S.bar);
+      if (nj > 0) {
+        bulk_g2s(S.val, a.val + ja, nj * 8u, &S.bar);
+        bulk_g2s(S.col, a.col + ja, nj * 4u, &S.bar);
+      }
+    }
+    const bool w = mbar_wait(&S.bar, phase, e.err);
+    phase ^= 1u;
+    if (!__syncthreads_and(w)) break;
+#define RP(r) S.rp[(r) - ra]
+    const bool tile_mid = tj > RP(ti);
+    // ---- phase 1: each thread walks its items ----------------------------
+    const int dt = d0 + t * kMergeItems;
+    if (dt < d1) {
+      int lo = max(ti, dt - tj1), hi = min(ti1, dt - tj);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (RP(mid + 1) <= dt - mid - 1) lo = mid + 1;
+        else hi = mid;
+      }
+      int row = lo, k = dt - lo;
+      const bool mid_row = k > RP(row);
+      bool first = true;
+      int head = -1;
+      double sum = 0.0;
+      const int dend = min(dt + kMergeItems, d1);
+      int re = RP(row + 1);
+      for (int d = dt; d < dend; ++d) {
+        if (k < re) {
+          sum = fma(S.val[k - ja], __ldg(a.x + S.col[k - ja]), sum);
+          ++k;
+        } else {
+          if (first && mid_row) {
+            S.head_val[t] = sum;
+            head = row;
+          } else {
+            S.ys[row - ti] = sum;
+          }
+          first = false;
+          sum = 0.0;
+          ++row;
+          re = (row < a.n_rows) ? RP(row + 1) : 0x7fffffff;
+        }
+      }
+      S.head_row[t] = head;
+      S.carry_row[t] = row;
+      S.carry_val[t] = sum;
+      S.cont[t] = (first && mid_row) ? 1 : 0;
+    } else {
+      S.head_row[t] = -1;
+      S.carry_row[t] = -1;
+      S.carry_val[t] = 0.0;
+      S.cont[t] = 0;
+    }
+    __syncthreads();
+    // ---- phase 2: rows whose end lies in this tile, one per thread --------
+    if (t == 0) a.head_row[tile] = -1;
+    for (int r = ti + t; r < ti1; r += kMergeThreads) {
+      const int ds = RP(r) + r, de = RP(r + 1) + r;
+      const int t_end = (de - d0) / kMergeItems;
+      if (ds < d0) {
+        // the row began in an earlier tile: leave it to the fix-up launch
+        double v = S.head_val[t_end];
+        for (int u = t_end - 1; u >= 0; --u) v += S.carry_val[u];
+        a.head_val[tile] = v;
+        a.head_row[tile] = r;
+      } else {
+        const int t_start = (ds - d0) / kMergeItems;
+        double v;
+        if (t_start == t_end) {
+          v = S.ys[r - ti];
+        } else {
+          v = S.head_val[t_end];
+          for (int u = t_end - 1; u >= t_start; --u) v += S.carry_val[u];
+        }
+        epi_row(e, r, v, a0, a1);
+      }
+    }
+    // ---- the row left open at the tile end -------------------------------
+    if (t == 0) {
+      int crow = -1, ccont = 0;
+      double cv = 0.0;
+      if (tile != a.n_tiles - 1 && tj1 > RP(ti1)) {
+        crow = ti1;
+        for (int u = kMergeThreads - 1; u >= 0; --u) {
+          if (S.carry_row[u] != crow) break;
+          cv += S.carry_val[u];
+          if (!S.cont[u]) break;
+        }
+        ccont = (ti1 == ti && tile_mid) ? 1 : 0;
+      }
+      a.carry_row[tile] = crow;
+      a.carry_val[tile] = cv;
+      a.cont[tile] = ccont;
+    }
+#undef RP
+    __syncthreads();
+  }
+  epi_partial(e, a0, a1, S.red);
+}
+
+// Completes rows that cross tile boundaries and finishes the epilogue's
+// reduction over the main launch's block partials.
+__global__ void __launch_bounds__(1024) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
+  __shared__ double red_scratch[64];
+  if (epi_skip(e)) return;
+  double a0 = 0.0, a1 = 0.0;
+  for (int t = threadIdx.x; t < a.n_tiles; t += blockDim.x) {
+    const int h = a.head_row[t];
+    if (h < 0) continue;
+    double v = a.head_val[t];
+    for (int u = t - 1; u >= 0; --u) {
+      if (a.carry_row[u] != h) break;
+      v += a.carry_val[u];
+      if (!a.cont[u]) break;
+    }
+    epi_row(e, h, v, a0, a1);
+  }
+  if (e.mode == EPI_PLAIN) return;
+  for (int b = threadIdx.x; b < main_grid; b += blockDim.x) {
+    a0 += e.partials[2 * b];
+    a1 += e.partials[2 * b + 1];
+  }
+  double v[2] = {a0, a1};
+  block_sum<2>(v, red_scratch);
+  if (threadIdx.x == 0 && e.st) finalize(e.fin, v, e.st);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct KernelGrids {
+  int bin = 0, ell = 0, merge = 0;
+};
+
+int occupancy_grid(const void* fn, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * sm_count();
+}
+
+bool g_attr_done[64] = {};
+
+int ensure_attributes() {
+  int dev = current_device();
+  if (dev >= 0 && dev < 64 && g_attr_done[dev]) return GK_OK;
+  GK_TRY_CUDA(cudaFuncSetAttribute(spmv_binned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kBinSmem));
+  GK_TRY_CUDA(cudaFuncSetAttribute(spmv_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(MergeSmem)));
+  if (dev >= 0 && dev < 64) g_attr_done[dev] = true;
+  return GK_OK;
+}
+
+MergeArgs merge_args(const MergePlan& P, const double* x) {
+  MergeArgs m;
+  m.rowptr = P.rowptr;
+  m.col = P.col;
+  m.val = P.val;
+  m.tile_i = P.tile_i;
+  m.tile_j = P.tile_j;
+  m.head_val = P.head_val;
+  m.head_row = P.head_row;
+  m.carry_val = P.carry_val;
+  m.carry_row = P.carry_row;
+  m.cont = P.cont;
+  m.n_rows = static_cast<int>(P.n_rows);
+  m.nnz = static_cast<int>(P.nnz);
+  m.n_tiles = static_cast<int>(P.n_tiles);
+  m.x = x;
+  return m;
+}
+
+int launch_merge(const MergePlan& P, const double* x, const Epi& e, cudaStream_t s) {
+  if (P.n_tiles == 0) return GK_OK;
+  MergeArgs m = merge_args(P, x);
+  spmv_merge_kernel<<<P.grid, kMergeThreads, sizeof(MergeSmem), s>>>(m, e);
+  GK_TRY_CUDA(cudaGetLastError());
+  spmv_merge_fixup_kernel<<<1, 1024, 0, s>>>(m, e, P.grid);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
+}  // namespace
+
+int merge_grid(int64_t n_tiles) {
+  if (ensure_attributes() != GK_OK) return 1;
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_merge_kernel), kMergeThreads,
+                         sizeof(MergeSmem));
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, n_tiles)));
+}
+
+int bin_grid(int64_t work_warps) {
+  if (ensure_attributes() != GK_OK) return 1;
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_binned_kernel), kBinWarps * 32, kBinSmem);
+  int64_t need = (work_warps + kBinWarps - 1) / kBinWarps;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
+}
+
+int ell_grid(int64_t n_rows) {
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_ell_kernel), kEllThreads, 0);
+  int64_t need = (n_rows + kEllThreads - 1) / kEllThreads;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
+}
+
+int spmv_max_grid(const Matrix& A) {
+  return std::max({A.grid_bin, A.grid_ell, A.merge.grid, 1});
+}
+
+int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) {
+  GK_TRY(ensure_attributes());
+  if (A.n_rows == 0) return GK_OK;
+  switch (A.format) {
+    case GK_CSR: {
+      BinArgs b{A.rowptr, A.col, A.val, A.item_r0, A.item_r1, static_cast<int>(A.n_items),
+                A.long_rows, static_cast<int>(A.n_long), x};
+      spmv_binned_kernel<<<A.grid_bin, kBinWarps * 32, kBinSmem, s>>>(b, e);
+      GK_TRY_CUDA(cudaGetLastError());
+      return GK_OK;
+    }
+    case GK_CSR_MERGE:
+      return launch_merge(A.merge, x, e, s);
+    case GK_ELL:
+    case GK_HYB: {
+      if (A.format == GK_HYB && A.m_tail > 0) {
+        Epi te;
+        te.mode = EPI_PLAIN;
+        te.y = A.tail_sum;
+        te.st = e.st;
+        te.skip_mode = e.skip_mode;
+        te.err = e.err;
+        GK_TRY(launch_merge(A.tail, x, te, s));
+      }
+      EllArgs ea{A.ell_col, A.ell_val, A.ld, static_cast<int>(A.K), static_cast<int>(A.n_rows), x,
+                 A.format == GK_HYB ? A.tail_slot : nullptr, A.tail_sum};
+      spmv_ell_kernel<<<A.grid_ell, kEllThreads, 0, s>>>(ea, e);
+      GK_TRY_CUDA(cudaGetLastError());
+      return GK_OK;
+    }
+    default:
+      return set_error(GK_ERR_UNSUPPORTED, "unknown format %d", A.format);
+  }
+}
+
+}  // namespace gk

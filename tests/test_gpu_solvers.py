@@ -1,0 +1,175 @@
+"""GPU parity of the CG and BiCGSTAB solver operators (Section 3.1) against
+the oracle, and the stopping criteria of Section 2.5.
+
+The GPU sums dot products in a fixed tree order and the oracle sequentially,
+so iterates differ by rounding.  What is compared: the stop reason; the
+iteration count within max(2, 3%) of the oracle's; the true relative residual
+(<= 1e-10 * 1.5 at a 1e-10 target); and the solution against the oracle's and
+the manufactured one to kappa * tol.  Invariants that hold bit for bit on the
+GPU itself are checked bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _kappa_poisson2d(m):
+    lmin = 4 - 4 * math.cos(math.pi / (m + 1))
+    lmax = 4 + 4 * math.cos(math.pi / (m + 1))
+    return lmax / lmin
+
+
+def _solve(gk, A, b, x0=None, fmt="csr", prec=None, kind="cg", **crit):
+    n = A[0].size - 1
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt=fmt)
+    P = gk.Precond(M, prec) if prec else None
+    S = gk.Solver(M, P, kind, **crit)
+    x = to_dev(np.zeros(n) if x0 is None else x0)
+    st = gk.solve(S, to_dev(b), x)
+    return st, to_np(x)
+
+
+def _iters_close(a, b):
+    return abs(a - b) <= max(2, int(0.03 * max(a, b)))
+
+
+@pytest.mark.parametrize("fmt", ["csr", "csr_merge", "ell", "hyb"])
+@pytest.mark.parametrize("prec", [None, 1, 8])
+def test_cg_poisson_matches_oracle(gk, orc, fmt, prec):
+    A = W.poisson2d(64)
+    xs = W.uniform_vector(4096, 1)
+    b = orc.spmv(A, xs)
+    st, x = _solve(gk, A, b, fmt=fmt, prec=prec, max_iters=2000, reduction_factor=1e-10)
+    P = orc.precond(A, {None: "none", 1: "jacobi", 8: "block_jacobi"}[prec], 8)
+    ref = orc.cg(A, b, P=P, tol=1e-10, max_iters=2000)
+    assert st.stop_reason == gk.STOP_CONVERGED == ref.stop_reason
+    assert _iters_close(st.iters, ref.iters), (st.iters, ref.iters)
+    assert st.spmvs == st.iters + 2
+    assert st.rel_res <= 1e-10 and st.rel_res_true <= 1.5e-10
+    kappa = _kappa_poisson2d(64)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= kappa * 2e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * 2e-10
+
+
+def test_cg_jacobi_bit_identical_to_plain_on_poisson(gk):
+    """a_ii = 4: scaling by 1/4 is exact in every product and sum of the GPU
+    kernels too, so Jacobi-PCG must reproduce plain CG bit for bit; block
+    Jacobi with bs = 1 is the same operator."""
+    A = W.poisson2d(64)
+    b = W.uniform_vector(4096, 2)
+    s0, x0 = _solve(gk, A, b, prec=None)
+    s1, x1 = _solve(gk, A, b, prec=1)
+    assert s0.iters == s1.iters and np.array_equal(x0, x1)
+
+
+def test_host_loop_equals_graph_loop(gk):
+    A = W.poisson2d(48)
+    b = W.uniform_vector(48 * 48, 3)
+    for kind in ("cg", "bicgstab"):
+        s0, x0 = _solve(gk, A, b, kind=kind, prec=1, check_every=0)
+        s1, x1 = _solve(gk, A, b, kind=kind, prec=1, check_every=7)
+        assert s0.iters == s1.iters and np.array_equal(x0, x1), kind
+
+
+@pytest.mark.parametrize("prec", [None, 1, 4, 16])
+@pytest.mark.parametrize("fmt", ["csr", "csr_merge", "hyb"])
+def test_bicgstab_nonsymmetric_matches_oracle(gk, orc, prec, fmt):
+    A = W.convdiff2d(40, wind=2.0)
+    D = W.csr_to_dense(A)
+    xs = W.uniform_vector(1600, 4)
+    b = orc.spmv(A, xs)
+    st, x = _solve(gk, A, b, fmt=fmt, prec=prec, kind="bicgstab", max_iters=3000, reduction_factor=1e-10)
+    P = orc.precond(A, {None: "none", 1: "jacobi"}.get(prec, "block_jacobi"), prec or 1)
+    ref = orc.bicgstab(A, b, P=P, tol=1e-10, max_iters=3000)
+    assert st.stop_reason == gk.STOP_CONVERGED == ref.stop_reason
+    assert _iters_close(st.iters, ref.iters), (st.iters, ref.iters)
+    assert st.rel_res_true <= 2e-10
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * 2e-10
+
+
+def test_cg_powerlaw_matches_oracle(gk, orc):
+    A = W.powerlaw(20000, seed=5)
+    b = W.uniform_vector(20000, 6)
+    for fmt in ("csr_merge", "hyb", "csr"):
+        st, x = _solve(gk, A, b, fmt=fmt, prec=1, max_iters=500)
+        ref = orc.cg(A, b, P=orc.precond(A, "jacobi"), tol=1e-10, max_iters=500)
+        assert st.stop_reason == gk.STOP_CONVERGED
+        assert _iters_close(st.iters, ref.iters)
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+
+
+def test_criteria_edge_cases(gk, orc):
+    A = W.poisson2d(8)
+    xs = W.uniform_vector(64, 5)
+    b = orc.spmv(A, xs)
+    # max_iters = 0: nothing changes
+    x0 = W.uniform_vector(64, 6)
+    st, x = _solve(gk, A, b, x0=x0, max_iters=0)
+    assert st.iters == 0 and st.stop_reason == gk.STOP_MAX_ITERS and np.array_equal(x, x0)
+    # x0 = exact solution: r_0 = b - A x* = 0 exactly (binned rows sum in the oracle's order)
+    st, x = _solve(gk, A, b, x0=xs)
+    assert st.iters == 0 and st.stop_reason == gk.STOP_CONVERGED and np.array_equal(x, xs)
+    # NaN right-hand side (Section 7.2's set-up) ends with NAN, never hangs
+    for kind in ("cg", "bicgstab"):
+        st, _ = _solve(gk, A, np.full(64, np.nan), kind=kind, max_iters=1000)
+        assert st.stop_reason == gk.STOP_NAN and st.iters == 0
+    # n = 1
+    st, x = _solve(gk, W.diagonal([3.0]), np.array([6.0]))
+    assert st.iters == 1 and x[0] == 2.0
+    # iteration limit
+    st, _ = _solve(gk, A, b, max_iters=3, reduction_factor=1e-14)
+    assert st.iters == 3 and st.stop_reason == gk.STOP_MAX_ITERS
+    # breakdown on an indefinite matrix
+    st, _ = _solve(gk, W.diagonal([1.0, -1.0]), np.array([1.0, 1.0]))
+    assert st.stop_reason == gk.STOP_BREAKDOWN
+    # BiCGSTAB half step on c*I
+    st, x = _solve(gk, W.scaled_identity(50, 3.0), np.ones(50), kind="bicgstab")
+    assert st.iters == 1 and st.spmvs == 3 and st.stop_reason == gk.STOP_CONVERGED
+
+
+def test_time_criterion_on_device(gk):
+    A = W.stencil27(40)
+    b = W.uniform_vector(64000, 7)
+    st, _ = _solve(gk, A, b, max_iters=100000, reduction_factor=1e-300, time_limit_s=0.002)
+    assert st.stop_reason == gk.STOP_TIME and 0 < st.iters < 100000
+
+
+def test_host_vectors_in_solve(gk, orc):
+    A = W.poisson2d(32)
+    b = W.uniform_vector(1024, 8)
+    M = gk.Matrix(A[0], A[1], A[2])
+    S = gk.Solver(M, gk.Precond(M, 1), "cg")
+    x = np.zeros(1024)
+    st = gk.solve(S, b, x)
+    assert st.stop_reason == gk.STOP_CONVERGED and st.rel_res_true <= 1.5e-10
+    ref = orc.cg(A, b, tol=1e-10)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= _kappa_poisson2d(32) * 2e-10
+
+
+def test_cg_full_size_stencil27(gk):
+    """The benchmark's CG: 27-point stencil on 128^3 to 1e-10, manufactured
+    solution; kappa from the closed-form spectrum 27 - prod_d (1 + 2 cos(k_d pi/129))."""
+    N = 128
+    A = W.stencil27(N)
+    n = N ** 3
+    xs = W.uniform_vector(n, 2)
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="csr")
+    bt = to_dev(np.zeros(n))
+    gk.apply(M, to_dev(xs), bt)
+    S = gk.Solver(M, gk.Precond(M, 1), "cg", max_iters=2000, reduction_factor=1e-10)
+    x = to_dev(np.zeros(n))
+    st = gk.solve(S, bt, x)
+    c = 1 + 2 * math.cos(math.pi / (N + 1))
+    lmin = 27 - c ** 3
+    lmax = 27 + c * c  # two factors near 3 and one near -1
+    kappa = lmax / lmin
+    assert st.stop_reason == gk.STOP_CONVERGED and st.rel_res_true <= 1.5e-10
+    err = np.linalg.norm(to_np(x) - xs) / np.linalg.norm(xs)
+    assert err <= kappa * 2e-10, (err, kappa)

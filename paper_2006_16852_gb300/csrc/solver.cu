@@ -331,9 +331,10 @@ VecArgs vec_args(const Solver& S, int use_cond) {
   a.q = S.q;
   a.z = S.z;
   a.rh = S.rh;
-  a.ph = S.ph;
   a.s = S.s;
-  a.sh = S.sh;
+  // without a preconditioner p^ = p and s^ = s
+  a.ph = S.ph ? S.ph : S.p;
+  a.sh = S.sh ? S.sh : S.s;
   a.t = S.t;
   a.st = S.st;
   a.partials = S.partials;

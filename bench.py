@@ -1,0 +1,573 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse linear-operator hot path on one GB300 (or N replicas).
+
+One step is one pass of the whole path over the "SpMV and FP64 CG sweep"
+workload:
+
+  (a) 27-point stencil on a 128^3 grid (n = 2,097,152, nnz = 55,742,968)
+  (b) power-law matrix, n = 1,000,000, row lengths Zipf(1.8) capped at 10^4,
+      symmetrised and made diagonally dominant (nnz ~ 29M)
+
+  * SpMV x -> A x once in every format: (a) CSR-binned, CSR-merge, ELL, HYB;
+    (b) CSR-merge, HYB, CSR-binned (ELL refuses (b): padding > 8x nnz)
+  * preconditioner generation: scalar Jacobi and block Jacobi (bs 8) of (a),
+    block Jacobi (bs 4) of (b)
+  * (a) CG to ||r|| <= 1e-10 ||b|| from x0 = 0, b = A x*: plain FP64 CG,
+    Jacobi-CG and block-Jacobi-CG
+  * (b) Jacobi-CG and block-Jacobi BiCGSTAB to 1e-10
+
+value = algorithmic bytes of the step / device time of the step (GB/s).
+Inputs are larger than the 129 MB L2 (711 MB and ~371 MB per SpMV).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s (% HBM peak); time to 1e-10 residual, chosen form vs plain FP64 CG"
+UNIT = "GB/s"
+WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point stencil 128^3 "
+            "(n=2,097,152, nnz=55,742,968), (b) power-law Zipf(1.8) cap 1e4, n=1,000,000, symmetrised, "
+            "diagonally dominant")
+
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel per launch on workload (a); valid only while spmv.cu is the
+# file it was measured on (sha256 prefix).
+NCU_TRAFFIC = {}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic byte model (value 8 B, index 4 B; a gathered vector is counted
+# once, as if it stayed in L2 after its first use)
+# ---------------------------------------------------------------------------
+
+def spmv_bytes(nnz, n_rows, n_cols, beta=False):
+    return nnz * 12 + (n_rows + 1) * 4 + n_cols * 8 + n_rows * 8 + (n_rows * 8 if beta else 0)
+
+
+def resid_bytes(nnz, n):  # r = b - A x with ||r||, ||b||
+    return spmv_bytes(nnz, n, n) + 8 * n
+
+
+def prec_extra(prec, bs):
+    """Bytes per row one preconditioner apply reads beyond its input vector."""
+    if prec == "none":
+        return 0
+    if prec == "jacobi":
+        return 8
+    return 8 * bs
+
+
+def cg_bytes(iters, nnz, n, prec="none", bs=1):
+    pe = prec_extra(prec, bs)
+    setup = resid_bytes(nnz, n) + (16 + pe) * n
+    z_store = 8 if prec == "block" else 0
+    # K1: SpMV q = A p (p.q in the epilogue); K2: x, p, q, r (+M) in, x, r (+z) out;
+    # K3: p, r or z (+dinv) in, p out
+    k2 = (32 + pe + 16 + z_store) * n
+    k3 = (24 + (8 if prec == "jacobi" else 0)) * n
+    per_it = spmv_bytes(nnz, n, n) + k2 + k3
+    return setup + iters * per_it + resid_bytes(nnz, n)
+
+
+def bicgstab_bytes(iters, spmvs, nnz, n, prec="none", bs=1):
+    pe = prec_extra(prec, bs)
+    hat = 0 if prec == "none" else 8
+    full = (spmvs - 2 - iters)  # SpMVs of full iterations beyond one per iteration
+    half = iters - full         # iterations that ended at the half step
+    setup = resid_bytes(nnz, n) + 32 * n
+    k1 = (24 + pe + 8 + hat) * n
+    k3 = (16 + pe + 8 + hat) * n
+    k5 = 64 * n
+    full_it = 2 * spmv_bytes(nnz, n, n) + 16 * n + k1 + k3 + k5
+    half_it = spmv_bytes(nnz, n, n) + 8 * n + k1 + k3 + 40 * n
+    return setup + full * full_it + half * half_it + resid_bytes(nnz, n)
+
+
+def precond_bytes(nnz, n, bs):
+    return nnz * 12 + (n + 1) * 4 + 8 * n * (1 if bs == 1 else bs)
+
+
+def table2_cg_bytes(iters, nnz, n, vt=8, it=4):
+    """Memory access volume of a full CG run as the paper models it (Table 2)."""
+    reads = (4 * n + 2 * nnz) * vt + 2 * nnz * it + iters * ((15 * n + 2 * nnz) * vt + 2 * nnz * it)
+    writes = (5 * n + 2) * vt + iters * ((5 * n + 2) * vt)
+    return reads + writes
+
+
+def table2_bicgstab_bytes(iters, nnz, n, vt=8, it=4):
+    """Memory access volume of a full BiCGSTAB run as the paper models it (Table 2)."""
+    c, f = (iters + 1) // 2, iters // 2
+    reads = ((5 * n + 2 * nnz) * vt + 2 * nnz * it + c * ((16 * n + 2 * nnz) * vt + 2 * nnz * it)
+             + f * ((13 * n + 2 * nnz) * vt + 2 * nnz * it))
+    writes = (10 * n + 6) * vt + c * ((4 * n + 2) * vt) + f * ((4 * n + 3) * vt)
+    return reads + writes
+
+
+def spmv_launches(info):
+    f = info["format_name"]
+    if f == "csr_merge":
+        return 2
+    if f == "hyb":
+        return 3 if info["tail_rows"] > 0 else 1
+    return 1
+
+
+def solve_launches(kind, iters, spmvs, spmv_l):
+    if kind == "cg":
+        # init, setup SpMV, start, iters x (SpMV + 2), final SpMV
+        return 2 + spmv_l + iters * (spmv_l + 2) + spmv_l
+    full = spmvs - 2 - iters
+    half = iters - full
+    return 2 + spmv_l + full * (2 * spmv_l + 3) + half * (spmv_l + 3) + spmv_l
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+REASON_FIELDS = ["clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                 "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gk_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        q = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," + ",".join(REASON_FIELDS)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                               parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_inputs(small=False):
+    import workloads as W
+    if small:
+        A = W.stencil27(32)
+        B = W.powerlaw(20000, seed=3)
+    else:
+        A = W.stencil27(128)
+        B = W.powerlaw(1_000_000, seed=3)
+    na, nb = A[0].size - 1, B[0].size - 1
+    return {"a": A, "b": B, "xa": W.uniform_vector(na, 2), "xb": W.uniform_vector(nb, 3),
+            "xs_a": W.uniform_vector(na, 4), "xs_b": W.uniform_vector(nb, 5)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def spmv_source_hash():
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2006_16852_gb300", "csrc", "spmv.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class GpuStep:
+    """All handles and device buffers of one step, created once."""
+
+    def __init__(self, inp, dev, tol=1e-10, check_every=0):
+        import torch
+        import paper_2006_16852_gb300 as gk
+        self.gk, self.torch, self.dev = gk, torch, dev
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        A, B = inp["a"], inp["b"]
+        self.na, self.nb = A[0].size - 1, B[0].size - 1
+        self.nnza, self.nnzb = A[1].size, B[1].size
+        dA = [t(v) for v in A]
+        dB = [t(v) for v in B]
+        self.mats = {}
+        for f in ("csr", "csr_merge", "ell", "hyb"):
+            self.mats[("a", f)] = gk.Matrix(*dA, fmt=f)
+        for f in ("csr_merge", "hyb", "csr"):
+            self.mats[("b", f)] = gk.Matrix(*dB, fmt=f)
+        self.dA, self.dB = dA, dB
+        self.x = {"a": t(inp["xa"]), "b": t(inp["xb"])}
+        self.y = {"a": torch.zeros(self.na, dtype=torch.float64, device=dev),
+                  "b": torch.zeros(self.nb, dtype=torch.float64, device=dev)}
+        # right-hand sides b = A x* (computed by the library on the device)
+        self.rhs = {}
+        for k, xs in (("a", inp["xs_a"]), ("b", inp["xs_b"])):
+            r = torch.zeros(self.na if k == "a" else self.nb, dtype=torch.float64, device=dev)
+            gk.apply(self.mats[(k, "csr" if k == "a" else "csr_merge")], t(xs), r)
+            self.rhs[k] = r
+        Ma, Mb = self.mats[("a", "csr")], self.mats[("b", "csr_merge")]
+        crit = dict(max_iters=5000, reduction_factor=tol, check_every=check_every)
+        self.solvers = {
+            "a_cg_plain": (gk.Solver(Ma, None, "cg", **crit), "a", "none", 1, "cg"),
+            "a_cg_jacobi": (gk.Solver(Ma, gk.Precond(Ma, 1), "cg", **crit), "a", "jacobi", 1, "cg"),
+            "a_cg_bj8": (gk.Solver(Ma, gk.Precond(Ma, 8), "cg", **crit), "a", "block", 8, "cg"),
+            "b_cg_jacobi": (gk.Solver(Mb, gk.Precond(Mb, 1), "cg", **crit), "b", "jacobi", 1, "cg"),
+            "b_bicgstab_bj4": (gk.Solver(Mb, gk.Precond(Mb, 4), "bicgstab", **crit), "b", "block", 4,
+                               "bicgstab"),
+        }
+        self.xsol = {k: torch.zeros(self.na if v[1] == "a" else self.nb, dtype=torch.float64, device=dev)
+                     for k, v in self.solvers.items()}
+        self.gens = [("a", "csr", 1), ("a", "csr", 8), ("b", "csr_merge", 4)]
+        self.stream = torch.cuda.current_stream(dev)
+
+    def n_of(self, k):
+        return self.na if k == "a" else self.nb
+
+    def nnz_of(self, k):
+        return self.nnza if k == "a" else self.nnzb
+
+    def run(self, record=None, host=None):
+        """One step.  record: dict receiving per-part event pairs.  host: if
+        given, a dict of pinned host buffers; vectors then go through the C
+        ABI as host pointers (end-to-end mode)."""
+        gk, torch = self.gk, self.torch
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        parts = []
+        for (k, f), M in self.mats.items():
+            e0, e1 = ev(), ev()
+            e0.record(self.stream)
+            if host is None:
+                gk.apply(M, self.x[k], self.y[k])
+            else:
+                gk.apply(M, host["x" + k], host["y" + k])
+            e1.record(self.stream)
+            parts.append((f"spmv_{k}_{f}", e0, e1, ("spmv", k, M)))
+        for k, f, bs in self.gens:
+            e0, e1 = ev(), ev()
+            e0.record(self.stream)
+            P = gk.Precond(self.mats[(k, f)], bs)
+            e1.record(self.stream)
+            parts.append((f"precond_{k}_bs{bs}", e0, e1, ("precond", k, bs)))
+            del P
+        statuses = {}
+        for name, (S, k, prec, bs, kind) in self.solvers.items():
+            e0, e1 = ev(), ev()
+            e0.record(self.stream)
+            if host is None:
+                self.xsol[name].zero_()
+                st = gk.solve(S, self.rhs[k], self.xsol[name])
+            else:
+                host["x0" + k][:] = 0.0
+                st = gk.solve(S, host["rhs" + k], host["x0" + k])
+            e1.record(self.stream)
+            statuses[name] = st
+            parts.append((f"solve_{name}", e0, e1, ("solve", name, st)))
+        if record is not None:
+            record.append(parts)
+        return statuses
+
+    def part_bytes(self, tag):
+        kind = tag[0]
+        if kind == "spmv":
+            k = tag[1]
+            return spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k))
+        if kind == "precond":
+            k, bs = tag[1], tag[2]
+            return precond_bytes(self.nnz_of(k), self.n_of(k), bs)
+        name, st = tag[1], tag[2]
+        S, k, prec, bs, sk = self.solvers[name]
+        if sk == "cg":
+            return cg_bytes(st.iters, self.nnz_of(k), self.n_of(k), prec, bs)
+        return bicgstab_bytes(st.iters, st.spmvs, self.nnz_of(k), self.n_of(k), prec, bs)
+
+    def part_launches(self, tag):
+        kind = tag[0]
+        if kind == "spmv":
+            return spmv_launches(tag[2].info())
+        if kind == "precond":
+            return 1
+        name, st = tag[1], tag[2]
+        S, k, prec, bs, sk = self.solvers[name]
+        M = self.mats[(k, "csr" if k == "a" else "csr_merge")]
+        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(M.info()))
+
+
+def run_gpu(args):
+    import torch
+    import paper_2006_16852_gb300 as gk
+    gk.load()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    inp = make_inputs(args.small)
+    step = GpuStep(inp, dev, check_every=args.host_loop)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step.run()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    rec = []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(step.stream)
+    for _ in range(args.steps):
+        step.run(record=rec)
+    t1.record(step.stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    # per-part figures from the recorded events
+    part_ms, part_bytes, launches = {}, {}, 0
+    iters = {}
+    for parts in rec:
+        for name, e0, e1, tag in parts:
+            part_ms.setdefault(name, []).append(e0.elapsed_time(e1))
+            part_bytes.setdefault(name, []).append(step.part_bytes(tag))
+            launches += step.part_launches(tag)
+            if tag[0] == "solve":
+                iters[tag[1]] = tag[2].iters
+                if tag[2].stop_reason != gk.STOP_CONVERGED:
+                    raise RuntimeError(f"{tag[1]} did not converge: {tag[2]}")
+    step_bytes = sum(sum(v) for v in part_bytes.values()) / args.steps
+    ms_per_step = total_ms / args.steps
+    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    dom = "spmv_a_csr"
+    dom_ms = statistics.mean(part_ms[dom])
+    dom_bytes = part_bytes[dom][0]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get(spmv_source_hash())
+    roofline = {"kernel": "spmv_binned_kernel (CSR-binned SpMV, workload (a))", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
+                "frac": round(achieved / (hbm if hbm else 6800.0), 4),
+                "traffic": tr, "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
+
+    def summary(name):
+        ms = statistics.median(part_ms[name])
+        by = part_bytes[name][0]
+        return {"ms": round(ms, 4), "GB/s": round(by / (ms * 1e-3) / 1e9, 1),
+                "frac_hbm": round(by / (ms * 1e-3) / 1e9 / (hbm or 6800.0), 3)}
+
+    spmv = {n[5:]: summary(n) for n in part_ms if n.startswith("spmv_")}
+    solves = {}
+    for n in part_ms:
+        if n.startswith("solve_"):
+            s = summary(n)
+            s["iters"] = iters[n[6:]]
+            solves[n[6:]] = s
+    precs = {n[8:]: summary(n) for n in part_ms if n.startswith("precond_")}
+    plain = solves["a_cg_plain"]["ms"]
+    chosen = min(("a_cg_jacobi", "a_cg_bj8"), key=lambda k: solves[k]["ms"])
+
+    # end to end: the same step through the C ABI with pinned host vectors
+    host = {}
+    for k in ("a", "b"):
+        n = step.n_of(k)
+        for nm in ("x", "y", "rhs", "x0"):
+            host[nm + k] = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        host["x" + k][:] = inp["x" + k]
+        host["rhs" + k][:] = step.rhs[k].cpu().numpy()
+    h2d = d2h = 0
+    for (k, f) in step.mats:
+        h2d += 8 * step.n_of(k)
+        d2h += 8 * step.n_of(k)
+    for name, (S, k, prec, bs, kind) in step.solvers.items():
+        h2d += 16 * step.n_of(k)
+        d2h += 8 * step.n_of(k)
+    for _ in range(max(1, args.warmup // 2)):
+        step.run(host=host)
+    barrier()
+    e2e_steps = max(1, min(args.steps, 5))
+    w0 = time.perf_counter()
+    e2e_bytes = 0
+    for _ in range(e2e_steps):
+        rr = []
+        step.run(record=rr, host=host)
+        e2e_bytes += sum(step.part_bytes(tag) for _, _, _, tag in rr[0])
+    barrier()
+    e2e_s = (time.perf_counter() - w0)
+    if dist is not None:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * (e2e_bytes / e2e_steps) / (e2e_s / e2e_steps) / 1e9
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else "small test variant (27-pt 32^3, power-law 2e4)",
+                   "formats": {"a": ["csr", "csr_merge", "ell", "hyb"], "b": ["csr_merge", "hyb", "csr"]},
+                   "solvers": {k: f"{v[4]} + {v[2]}{'' if v[2] != 'block' else ' bs%d' % v[3]} on ({v[1]})"
+                               for k, v in step.solvers.items()},
+                   "tolerance": "||r|| <= 1e-10 ||b||, x0 = 0, b = A x*",
+                   "l2": "inputs larger than L2 (129 MB): no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "frac_hbm": round(value / (hbm or 6800.0), 4),
+        "time_to_tol_ms": {"plain_fp64_cg": plain, "chosen_form": chosen, "chosen_ms": solves[chosen]["ms"]},
+        "spmv": spmv, "solves": solves, "precond_generate": precs,
+        "paper_table2_cg_bytes_plain": table2_cg_bytes(solves["a_cg_plain"]["iters"], step.nnza, step.na),
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
+    if dist is not None:
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(inp, cg_iters):
+    """A bounded slice of the step on the oracle: one SpMV of (a) and of (b)
+    and cg_iters Jacobi-CG iterations on (a).  Returns (bytes, seconds)."""
+    import oracle
+    A, B = inp["a"], inp["b"]
+    na, nb = A[0].size - 1, B[0].size - 1
+    t0 = time.perf_counter()
+    oracle.spmv(A, inp["xa"])
+    oracle.spmv(B, inp["xb"])
+    b = oracle.spmv(A, inp["xs_a"])
+    t1 = time.perf_counter()
+    P = oracle.precond(A, "jacobi")
+    t2 = time.perf_counter()
+    r = oracle.cg(A, b, P=P, tol=1e-10, max_iters=cg_iters)
+    t3 = time.perf_counter()
+    by = (spmv_bytes(A[1].size, na, na) * 2 + spmv_bytes(B[1].size, nb, nb)
+          + cg_bytes(r.iters, A[1].size, na, "jacobi"))
+    return by, (t1 - t0) + (t3 - t2), r.iters
+
+
+def cpu_baseline(inp, budget_s):
+    import oracle
+    oracle.build()
+    # size the CG part to about budget_s seconds from two short probes
+    _, s2, _ = oracle_sample(inp, 2)
+    _, s6, _ = oracle_sample(inp, 6)
+    per_it = max((s6 - s2) / 4.0, 1e-4)
+    it = max(2, int((budget_s - s2) / per_it))
+    by, s, iters = oracle_sample(inp, it)
+    return {"value": round(by / s / 1e9, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (plain C, one thread): SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for "
+                      f"{iters} iterations; {s:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm, on the same metric and config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    inp = make_inputs(args.small)
+    cg_iters = 2
+    for _ in range(args.warmup):
+        oracle_sample(inp, cg_iters)
+    tot_b = tot_s = 0.0
+    for _ in range(args.steps):
+        b, s, _ = oracle_sample(inp, cg_iters)
+        tot_b += b
+        tot_s += s
+    value = tot_b / tot_s / 1e9
+    sample = (f"oracle (plain C, one thread), per step: SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for "
+              f"{cg_iters} iterations")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_s / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if not args.small else "small test variant"},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gk", "reference"], default="gk")
+    ap.add_argument("--small", action="store_true", help="small matrices (quick checks)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
+    ap.add_argument("--host-loop", type=int, default=0, metavar="K",
+                    help="launch solver iterations from the host, reading the stop flag every K "
+                         "iterations, instead of the device-side graph loop (profilers cannot see "
+                         "kernels inside conditional graph nodes)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gk" and not args.small:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -199,6 +199,27 @@ GK_API int gk_solver_destroy(gk_solver S);
  * must be ordered (issued to one stream, or synchronized). */
 GK_API int gk_dot(int64_t n, const double* x, const double* y, double* result, void* stream);
 
+/* gk_dot without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for example
+ * code whose GPU memory is entirely reserved by another allocator (a
+ * framework's caching pool sized to the whole device), or a host application
+ * that forbids libraries from owning device allocations -- whereas gk_dot
+ * allocates its reduction workspace on its first call on each device.
+ *   - Scratch: a static device array inside the library holding 1024 block
+ *     partial sums plus one counter (about 8 KB); every GPU that loads the
+ *     library keeps it until the process exits.  The reduction uses 4 blocks
+ *     per SM, so GPUs with more than 256 SMs are rejected with
+ *     GK_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - The scratch is shared by every call on a device and keeps the last
+ *     call's contents; each call clears the counter on its stream before the
+ *     kernel.  Calls that overlap on the GPU (different streams, no ordering)
+ *     race on it: order them.
+ *   - Result, order of summation and arguments as gk_dot. */
+GK_API int gk_dot_noalloc(int64_t n, const double* x, const double* y, double* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

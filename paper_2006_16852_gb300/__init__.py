@@ -33,7 +33,7 @@ STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME =
 EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get_info",
            "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
            "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
-           "gk_solver_destroy", "gk_dot")
+           "gk_solver_destroy", "gk_dot", "gk_dot_noalloc")
 
 
 class GkError(RuntimeError):
@@ -102,6 +102,7 @@ def load(path: str | None = None):
         "gk_solve": [vp, vp, vp, ctypes.POINTER(Status), vp],
         "gk_solver_destroy": [vp],
         "gk_dot": [i64, vp, vp, vp, vp],
+        "gk_dot_noalloc": [i64, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -289,4 +290,12 @@ def dot(x, y, result, stream=None):
     n = x.numel()
     _check_vec(y, n, "y")
     _check(lib().gk_dot(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
+    return result
+
+
+def dot_noalloc(x, y, result, stream=None):
+    """As dot(), through the entry point that allocates no device memory."""
+    n = x.numel()
+    _check_vec(y, n, "y")
+    _check(lib().gk_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
     return result

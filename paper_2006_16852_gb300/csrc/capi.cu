@@ -219,3 +219,52 @@ extern "C" int gk_dot(int64_t n, const double* x, const double* y, double* resul
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gk_dot_noalloc: gk_dot for callers that cannot allocate device memory.  The
+// reduction scratch (one partial sum per block, then the arrival counter) is
+// a file-scope device array instead of a cudaMalloc'd workspace.  Its host
+// address is looked up once per device with cudaGetSymbolAddress (the host
+// name of the array is only a stand-in and must never reach a kernel).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;
+// [0, kNoAllocMaxBlocks): block partials; the next 8 bytes: the counter.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 32];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};
+
+}  // namespace
+
+extern "C" int gk_dot_noalloc(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return set_error(GK_ERR_ARG, "gk_dot_noalloc: bad argument");
+  if (is_host(x) || is_host(y) || is_host(result))
+    return set_error(GK_ERR_NOT_DEVICE, "gk_dot_noalloc: x, y and result must be device memory");
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return set_error(GK_ERR_UNSUPPORTED, "gk_dot_noalloc: device index %d", dev);
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_error(e, "gk_dot_noalloc: cudaGetSymbolAddress");
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  const int grid = dot_grid();
+  if (grid > kNoAllocMaxBlocks)
+    return set_error(GK_ERR_UNSUPPORTED,
+                     "gk_dot_noalloc: the reduction needs %d block partials, the static scratch holds %d "
+                     "(GPUs with more than %d SMs are not supported)",
+                     grid, kNoAllocMaxBlocks, kNoAllocMaxBlocks / 4);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocMaxBlocks);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  GK_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  dot_kernel<<<grid, 256, 0, s>>>(x, y, n, scratch, counter, result);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(libgk):
     assert declared, "no declarations found"
     for name in declared:
         assert hasattr(libgk, name), f"{name} not exported"
-    assert declared <= set(gk.EXPORTS) | {n for n in declared if n.endswith("_noalloc")}
+    assert declared <= set(gk.EXPORTS)
 
 
 def test_version_and_error_string(libgk):

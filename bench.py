@@ -548,6 +548,36 @@ def run_reference(args):
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_spmv_only(args):
+    """Repeated applies of one matrix/format (for profiler captures)."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    gk.load()
+    mat, fmt = args.spmv_only.split(":")
+    if mat == "a":
+        A = W.stencil27(128 if not args.small else 32)
+    else:
+        A = W.powerlaw(1_000_000 if not args.small else 20000, seed=3)
+    n = A[0].size - 1
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    M = gk.Matrix(t(A[0]), t(A[1]), t(A[2]), fmt=fmt)
+    x, y = t(W.uniform_vector(n, 2)), torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        gk.apply(M, x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        gk.apply(M, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    by = spmv_bytes(A[1].size, n, n)
+    return {"spmv_only": args.spmv_only, "ms": round(ms, 4), "GB/s": round(by / ms / 1e6, 1),
+            "info": M.info()}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,6 +587,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="small matrices (quick checks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
+    ap.add_argument("--spmv-only", metavar="MAT:FMT", default=None,
+                    help="only time repeated applies of matrix a|b in one format (profiling aid)")
     ap.add_argument("--host-loop", type=int, default=0, metavar="K",
                     help="launch solver iterations from the host, reading the stop flag every K "
                          "iterations, instead of the device-side graph loop (profilers cannot see "
@@ -564,7 +596,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.spmv_only:
+        out = run_spmv_only(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out))
 

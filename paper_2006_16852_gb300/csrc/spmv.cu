@@ -75,6 +75,40 @@ __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, 
   }
 }
 
+// Sequential row sum s = fma(v_k, x_{c_k}, s) over k in [k0, k1) of staged
+// values/indices, with the gathers of x issued in batches so that several are
+// in flight per lane; the fma order is unchanged (increasing k).
+__device__ __forceinline__ double row_sum_staged(const double* __restrict__ v, const int32_t* __restrict__ c,
+                                                 int k0, int k1, const double* __restrict__ x) {
+  double s = 0.0;
+  int k = k0;
+  for (; k + 8 <= k1; k += 8) {
+    int cc[8];
+    double xv[8], vv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cc[u] = c[k + u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = __ldg(x + cc[u]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) vv[u] = v[k + u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s = fma(vv[u], xv[u], s);
+  }
+  for (; k < k1; k += 4) {
+    double xv[4], vv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = k + u < k1;
+      xv[u] = in ? __ldg(x + c[k + u]) : 0.0;
+      vv[u] = in ? v[k + u] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u < k1) s = fma(vv[u], xv[u], s);
+  }
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // GK_CSR: rows binned by length.
 // Short rows (<= 32 entries) are grouped into warp items of up to 32
@@ -127,6 +161,12 @@ __global__ void __launch_bounds__(kBinWarps * 32) spmv_binned_kernel(BinArgs a, 
     const int k0 = __ldg(a.rowptr + r0), k1 = __ldg(a.rowptr + r1);
     const int ka = k0 & ~3, kb = (k1 + 3) & ~3;
     const uint32_t nb = static_cast<uint32_t>(kb - ka);
+    const int row = r0 + lane;
+    int kk0 = 0, kk1 = 0;
+    if (row < r1) {
+      kk0 = __ldg(a.rowptr + row) - ka;
+      kk1 = __ldg(a.rowptr + row + 1) - ka;
+    }
     if (nb > 0) {
       if (lane == 0) {
         fence_proxy_async_smem();
@@ -138,11 +178,8 @@ __global__ void __launch_bounds__(kBinWarps * 32) spmv_binned_kernel(BinArgs a, 
       phase ^= 1u;
       ok = __all_sync(0xffffffffu, w);
     }
-    const int row = r0 + lane;
     if (ok && row < r1) {
-      const int kk0 = __ldg(a.rowptr + row) - ka, kk1 = __ldg(a.rowptr + row + 1) - ka;
-      double s = 0.0;
-      for (int k = kk0; k < kk1; ++k) s = fma(val_s[k], __ldg(a.x + col_s[k]), s);
+      const double s = row_sum_staged(val_s, col_s, kk0, kk1, a.x);
       epi_row(e, row, s, a0, a1);
     }
     __syncwarp();
@@ -185,9 +222,32 @@ __global__ void __launch_bounds__(kEllThreads) spmv_ell_kernel(EllArgs a, Epi e)
     double s = 0.0;
     const int32_t* cp = a.col + row;
     const double* vp = a.val + row;
-    for (int j = 0; j < a.K; ++j) {
-      const int c = __ldg(cp + j * a.ld);
-      if (c >= 0) s = fma(__ldg(vp + j * a.ld), __ldg(a.x + c), s);
+    int j = 0;
+    for (; j + 8 <= a.K; j += 8) {
+      int cc[8];
+      double xv[8], vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cc[u] = __ldg(cp + (j + u) * a.ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) vv[u] = __ldg(vp + (j + u) * a.ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
+    }
+    for (; j < a.K; j += 4) {
+      int cc[4];
+      double xv[4], vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cc[u] = (j + u < a.K) ? __ldg(cp + (j + u) * a.ld) : -1;
+        vv[u] = cc[u] >= 0 ? __ldg(vp + (j + u) * a.ld) : 0.0;
+        xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
     }
     if (a.tail_slot) {
       const int t = __ldg(a.tail_slot + row);
@@ -278,37 +338,67 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
 #define RP(r) S.rp[(r) - ra]
     const bool tile_mid = tj > RP(ti);
     // ---- phase 1: each thread walks its items ----------------------------
+    // The thread's items are the row ends and entries between merge
+    // diagonals dt and dte: entries [k, k_end) and the ends of rows
+    // [row, row_end).  Its (at most kMergeItems) values and gathered x are
+    // loaded first, with static register indices, then the walk consumes a
+    // row end whenever the next entry lies past it.
     const int dt = d0 + t * kMergeItems;
     if (dt < d1) {
+      const int dte = min(dt + kMergeItems, d1);
       int lo = max(ti, dt - tj1), hi = min(ti1, dt - tj);
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (RP(mid + 1) <= dt - mid - 1) lo = mid + 1;
         else hi = mid;
       }
-      int row = lo, k = dt - lo;
+      int lo2 = max(ti, dte - tj1), hi2 = min(ti1, dte - tj);
+      while (lo2 < hi2) {
+        const int mid = (lo2 + hi2) >> 1;
+        if (RP(mid + 1) <= dte - mid - 1) lo2 = mid + 1;
+        else hi2 = mid;
+      }
+      int row = lo;
+      const int k = dt - lo;
+      const int row_end = lo2, cnt = (dte - lo2) - k;
+      double vv[kMergeItems], xv[kMergeItems];
+#pragma unroll
+      for (int u = 0; u < kMergeItems; ++u) {
+        const bool in = u < cnt;
+        vv[u] = in ? S.val[k + u - ja] : 0.0;
+        xv[u] = in ? __ldg(a.x + S.col[k + u - ja]) : 0.0;
+      }
       const bool mid_row = k > RP(row);
       bool first = true;
       int head = -1;
       double sum = 0.0;
-      const int dend = min(dt + kMergeItems, d1);
-      int re = RP(row + 1);
-      for (int d = dt; d < dend; ++d) {
-        if (k < re) {
-          sum = fma(S.val[k - ja], __ldg(a.x + S.col[k - ja]), sum);
-          ++k;
-        } else {
-          if (first && mid_row) {
-            S.head_val[t] = sum;
-            head = row;
-          } else {
-            S.ys[row - ti] = sum;
+#pragma unroll
+      for (int u = 0; u < kMergeItems; ++u) {
+        if (u < cnt) {
+          while (RP(row + 1) <= k + u) {
+            if (first && mid_row) {
+              S.head_val[t] = sum;
+              head = row;
+            } else {
+              S.ys[row - ti] = sum;
+            }
+            first = false;
+            sum = 0.0;
+            ++row;
           }
-          first = false;
-          sum = 0.0;
-          ++row;
-          re = (row < a.n_rows) ? RP(row + 1) : 0x7fffffff;
+          sum = fma(vv[u], xv[u], sum);
         }
+      }
+      while (row < row_end) {
+        if (first && mid_row) {
+          S.head_val[t] = sum;
+          head = row;
+        } else {
+          S.ys[row - ti] = sum;
+        }
+        first = false;
+        sum = 0.0;
+        ++row;
       }
       S.head_row[t] = head;
       S.carry_row[t] = row;

@@ -46,6 +46,10 @@ WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point sten
 # file it was measured on (sha256 prefix).
 NCU_TRAFFIC = {}
 
+# back-to-back applies per format and matrix in one step (the per-launch time
+# of the roofline is their average)
+SPMV_REPS = 3
+
 
 # ---------------------------------------------------------------------------
 # algorithmic byte model (value 8 B, index 4 B; a gathered vector is counted
@@ -246,15 +250,19 @@ class GpuStep:
             r = torch.zeros(self.na if k == "a" else self.nb, dtype=torch.float64, device=dev)
             gk.apply(self.mats[(k, "csr" if k == "a" else "csr_merge")], t(xs), r)
             self.rhs[k] = r
-        Ma, Mb = self.mats[("a", "csr")], self.mats[("b", "csr_merge")]
         crit = dict(max_iters=5000, reduction_factor=tol, check_every=check_every)
+        M = self.mats
+        # name: (solver, matrix key, preconditioner kind, block size, method, format)
         self.solvers = {
-            "a_cg_plain": (gk.Solver(Ma, None, "cg", **crit), "a", "none", 1, "cg"),
-            "a_cg_jacobi": (gk.Solver(Ma, gk.Precond(Ma, 1), "cg", **crit), "a", "jacobi", 1, "cg"),
-            "a_cg_bj8": (gk.Solver(Ma, gk.Precond(Ma, 8), "cg", **crit), "a", "block", 8, "cg"),
-            "b_cg_jacobi": (gk.Solver(Mb, gk.Precond(Mb, 1), "cg", **crit), "b", "jacobi", 1, "cg"),
-            "b_bicgstab_bj4": (gk.Solver(Mb, gk.Precond(Mb, 4), "bicgstab", **crit), "b", "block", 4,
-                               "bicgstab"),
+            "a_cg_plain_csr": (gk.Solver(M[("a", "csr")], None, "cg", **crit), "a", "none", 1, "cg", "csr"),
+            "a_cg_jacobi_ell": (gk.Solver(M[("a", "ell")], gk.Precond(M[("a", "ell")], 1), "cg", **crit), "a",
+                                "jacobi", 1, "cg", "ell"),
+            "a_cg_bj8_ell": (gk.Solver(M[("a", "ell")], gk.Precond(M[("a", "ell")], 8), "cg", **crit), "a",
+                             "block", 8, "cg", "ell"),
+            "b_cg_jacobi_hyb": (gk.Solver(M[("b", "hyb")], gk.Precond(M[("b", "hyb")], 1), "cg", **crit), "b",
+                                "jacobi", 1, "cg", "hyb"),
+            "b_bicgstab_bj4_hyb": (gk.Solver(M[("b", "hyb")], gk.Precond(M[("b", "hyb")], 4), "bicgstab", **crit),
+                                   "b", "block", 4, "bicgstab", "hyb"),
         }
         self.xsol = {k: torch.zeros(self.na if v[1] == "a" else self.nb, dtype=torch.float64, device=dev)
                      for k, v in self.solvers.items()}
@@ -277,10 +285,11 @@ class GpuStep:
         for (k, f), M in self.mats.items():
             e0, e1 = ev(), ev()
             e0.record(self.stream)
-            if host is None:
-                gk.apply(M, self.x[k], self.y[k])
-            else:
-                gk.apply(M, host["x" + k], host["y" + k])
+            for _ in range(SPMV_REPS):
+                if host is None:
+                    gk.apply(M, self.x[k], self.y[k])
+                else:
+                    gk.apply(M, host["x" + k], host["y" + k])
             e1.record(self.stream)
             parts.append((f"spmv_{k}_{f}", e0, e1, ("spmv", k, M)))
         for k, f, bs in self.gens:
@@ -291,7 +300,7 @@ class GpuStep:
             parts.append((f"precond_{k}_bs{bs}", e0, e1, ("precond", k, bs)))
             del P
         statuses = {}
-        for name, (S, k, prec, bs, kind) in self.solvers.items():
+        for name, (S, k, prec, bs, kind, fmt) in self.solvers.items():
             e0, e1 = ev(), ev()
             e0.record(self.stream)
             if host is None:
@@ -311,12 +320,12 @@ class GpuStep:
         kind = tag[0]
         if kind == "spmv":
             k = tag[1]
-            return spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k))
+            return SPMV_REPS * spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k))
         if kind == "precond":
             k, bs = tag[1], tag[2]
             return precond_bytes(self.nnz_of(k), self.n_of(k), bs)
         name, st = tag[1], tag[2]
-        S, k, prec, bs, sk = self.solvers[name]
+        S, k, prec, bs, sk, fmt = self.solvers[name]
         if sk == "cg":
             return cg_bytes(st.iters, self.nnz_of(k), self.n_of(k), prec, bs)
         return bicgstab_bytes(st.iters, st.spmvs, self.nnz_of(k), self.n_of(k), prec, bs)
@@ -324,13 +333,12 @@ class GpuStep:
     def part_launches(self, tag):
         kind = tag[0]
         if kind == "spmv":
-            return spmv_launches(tag[2].info())
+            return SPMV_REPS * spmv_launches(tag[2].info())
         if kind == "precond":
             return 1
         name, st = tag[1], tag[2]
-        S, k, prec, bs, sk = self.solvers[name]
-        M = self.mats[(k, "csr" if k == "a" else "csr_merge")]
-        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(M.info()))
+        S, k, prec, bs, sk, fmt = self.solvers[name]
+        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(self.mats[(k, fmt)].info()))
 
 
 def run_gpu(args):
@@ -393,8 +401,8 @@ def run_gpu(args):
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     dom = "spmv_a_csr"
-    dom_ms = statistics.mean(part_ms[dom])
-    dom_bytes = part_bytes[dom][0]
+    dom_ms = statistics.mean(part_ms[dom]) / SPMV_REPS
+    dom_bytes = part_bytes[dom][0] // SPMV_REPS
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     tr = NCU_TRAFFIC.get(spmv_source_hash())
     roofline = {"kernel": "spmv_binned_kernel (CSR-binned SpMV, workload (a))", "bound": "hbm",
@@ -404,8 +412,9 @@ def run_gpu(args):
                 "traffic": tr, "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
 
     def summary(name):
-        ms = statistics.median(part_ms[name])
-        by = part_bytes[name][0]
+        reps = SPMV_REPS if name.startswith("spmv_") else 1
+        ms = statistics.median(part_ms[name]) / reps
+        by = part_bytes[name][0] / reps
         return {"ms": round(ms, 4), "GB/s": round(by / (ms * 1e-3) / 1e9, 1),
                 "frac_hbm": round(by / (ms * 1e-3) / 1e9 / (hbm or 6800.0), 3)}
 
@@ -417,8 +426,8 @@ def run_gpu(args):
             s["iters"] = iters[n[6:]]
             solves[n[6:]] = s
     precs = {n[8:]: summary(n) for n in part_ms if n.startswith("precond_")}
-    plain = solves["a_cg_plain"]["ms"]
-    chosen = min(("a_cg_jacobi", "a_cg_bj8"), key=lambda k: solves[k]["ms"])
+    plain = solves["a_cg_plain_csr"]["ms"]
+    chosen = min(("a_cg_jacobi_ell", "a_cg_bj8_ell"), key=lambda k: solves[k]["ms"])
 
     # end to end: the same step through the C ABI with pinned host vectors
     host = {}
@@ -430,9 +439,9 @@ def run_gpu(args):
         host["rhs" + k][:] = step.rhs[k].cpu().numpy()
     h2d = d2h = 0
     for (k, f) in step.mats:
-        h2d += 8 * step.n_of(k)
-        d2h += 8 * step.n_of(k)
-    for name, (S, k, prec, bs, kind) in step.solvers.items():
+        h2d += SPMV_REPS * 8 * step.n_of(k)
+        d2h += SPMV_REPS * 8 * step.n_of(k)
+    for name, (S, k, prec, bs, kind, fmt) in step.solvers.items():
         h2d += 16 * step.n_of(k)
         d2h += 8 * step.n_of(k)
     for _ in range(max(1, args.warmup // 2)):
@@ -459,15 +468,15 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.small else "small test variant (27-pt 32^3, power-law 2e4)",
                    "formats": {"a": ["csr", "csr_merge", "ell", "hyb"], "b": ["csr_merge", "hyb", "csr"]},
-                   "solvers": {k: f"{v[4]} + {v[2]}{'' if v[2] != 'block' else ' bs%d' % v[3]} on ({v[1]})"
-                               for k, v in step.solvers.items()},
+                   "solvers": {k: f"{v[4]} + {v[2]}{'' if v[2] != 'block' else ' bs%d' % v[3]} on ({v[1]}) "
+                                  f"in {v[5]}" for k, v in step.solvers.items()},
                    "tolerance": "||r|| <= 1e-10 ||b||, x0 = 0, b = A x*",
                    "l2": "inputs larger than L2 (129 MB): no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "frac_hbm": round(value / (hbm or 6800.0), 4),
         "time_to_tol_ms": {"plain_fp64_cg": plain, "chosen_form": chosen, "chosen_ms": solves[chosen]["ms"]},
         "spmv": spmv, "solves": solves, "precond_generate": precs,
-        "paper_table2_cg_bytes_plain": table2_cg_bytes(solves["a_cg_plain"]["iters"], step.nnza, step.na),
+        "paper_table2_cg_bytes_plain": table2_cg_bytes(solves["a_cg_plain_csr"]["iters"], step.nnza, step.na),
         "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -578,6 +587,44 @@ def run_spmv_only(args):
             "info": M.info()}
 
 
+def run_solve_only(args):
+    """Repeated solves of one configuration MAT:FMT:PREC:KIND, e.g. a:ell:1:cg
+    (PREC = 0 none, 1 scalar Jacobi, 2..32 block Jacobi), for profiling."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    gk.load()
+    mat, fmt, prec, kind = args.solve_only.split(":")
+    prec = int(prec)
+    if mat == "a":
+        A = W.stencil27(128 if not args.small else 32)
+    else:
+        A = W.powerlaw(1_000_000 if not args.small else 20000, seed=3)
+    n = A[0].size - 1
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    M = gk.Matrix(t(A[0]), t(A[1]), t(A[2]), fmt=fmt)
+    P = gk.Precond(M, prec) if prec else None
+    S = gk.Solver(M, P, kind, max_iters=5000, reduction_factor=1e-10, check_every=args.host_loop)
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gk.apply(M, t(W.uniform_vector(n, 4)), b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        x.zero_()
+        gk.solve(S, b, x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        x.zero_()
+        st = gk.solve(S, b, x)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"solve_only": args.solve_only, "ms": round(ms, 3), "iters": st.iters,
+            "us_per_iter": round(1e3 * ms / max(st.iters, 1), 2), "stop": st.stop_reason,
+            "rel_res_true": st.rel_res_true}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,6 +636,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
     ap.add_argument("--spmv-only", metavar="MAT:FMT", default=None,
                     help="only time repeated applies of matrix a|b in one format (profiling aid)")
+    ap.add_argument("--solve-only", metavar="MAT:FMT:PREC:KIND", default=None,
+                    help="only time repeated solves of one configuration (profiling aid)")
     ap.add_argument("--host-loop", type=int, default=0, metavar="K",
                     help="launch solver iterations from the host, reading the stop flag every K "
                          "iterations, instead of the device-side graph loop (profilers cannot see "
@@ -598,6 +647,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.spmv_only:
         out = run_spmv_only(args)
+    elif args.solve_only:
+        out = run_solve_only(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:

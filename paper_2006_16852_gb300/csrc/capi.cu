@@ -69,7 +69,7 @@ int sm_count() {
   return v;
 }
 
-int vec_in(VecArg& v, const void* p, int64_t n, double* staging, bool copy_in, int device,
+int vec_in(VecArg& v, const void* p, int64_t n, double** staging, int64_t* bytes, bool copy_in, int device,
            cudaStream_t s) {
   v.user = p;
   v.staged = false;
@@ -90,11 +90,11 @@ int vec_in(VecArg& v, const void* p, int64_t n, double* staging, bool copy_in, i
     v.dev = static_cast<double*>(const_cast<void*>(p));
     return GK_OK;
   }
-  if (!staging) return set_error(GK_ERR_ARG, "no staging buffer for a host vector");
+  if (!*staging) GK_TRY(dalloc_n(staging, static_cast<size_t>(n + 1), bytes));
   v.staged = true;
-  v.dev = staging;
+  v.dev = *staging;
   if (copy_in)
-    GK_TRY_CUDA(cudaMemcpyAsync(staging, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    GK_TRY_CUDA(cudaMemcpyAsync(*staging, p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   return GK_OK;
 }
 
@@ -178,15 +178,14 @@ extern "C" int gk_apply_adv(double alpha, gk_matrix h, const void* b, double bet
   DeviceGuard g(A->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (A->n_rows == 0) return GK_OK;
-  if (is_host(b) && !A->stage_in) GK_TRY(dalloc_n(&A->stage_in, A->n_cols + 1, &A->device_bytes));
-  if (is_host(x) && !A->stage_out) GK_TRY(dalloc_n(&A->stage_out, A->n_rows + 1, &A->device_bytes));
   VecArg vb, vx;
-  GK_TRY(vec_in(vb, b, A->n_cols, A->stage_in, true, A->device, s));
-  GK_TRY(vec_in(vx, x, A->n_rows, A->stage_out, beta != 0.0, A->device, s));
+  GK_TRY(vec_in(vb, b, A->n_cols, &A->stage_in, &A->device_bytes, true, A->device, s));
+  GK_TRY(vec_in(vx, x, A->n_rows, &A->stage_out, &A->device_bytes, beta != 0.0, A->device, s));
   Epi e;
-  e.mode = EPI_PLAIN;
+  e.mode = (alpha == 1.0 && beta == 0.0) ? EPI_COPY : EPI_PLAIN;
   e.alpha = alpha;
   e.beta = beta;
+  e.beta_zero = beta == 0.0 ? 1 : 0;
   e.y = vx.dev;
   e.err = A->err;
   GK_TRY(spmv_launch(*A, vb.dev, e, s));

@@ -82,6 +82,7 @@ enum Fin : int {
 // SpMV epilogue: what happens to each finished row sum s_i
 // ---------------------------------------------------------------------------
 enum EpiMode : int {
+  EPI_COPY = 4,   // y_i = s_i (alpha = 1, beta = 0: no FP64 work beyond the row sum)
   EPI_PLAIN = 0,  // y_i = alpha s_i (beta == 0) or fma(beta, y_i, alpha s_i)
   EPI_RESID = 1,  // y_i = u_i - s_i (u = b): sums (y.y, u.u)
   EPI_DOT = 2,    // y_i = s_i: sums (u.y)
@@ -92,6 +93,7 @@ struct Epi {
   int mode = EPI_PLAIN;
   int fin = FIN_NONE;
   double alpha = 1.0, beta = 0.0;
+  int beta_zero = 1;          // beta == 0, decided on the host (no FP64 compare per row)
   const double* u = nullptr;
   double* y = nullptr;
   SolverState* st = nullptr;  // scalars the reduction feeds
@@ -107,7 +109,7 @@ struct Epi {
 constexpr int kMergeThreads = 128;
 constexpr int kMergeItems = 16;  // merge-path items (row ends + nonzeros) per thread
 constexpr int kMergeTile = kMergeThreads * kMergeItems;
-constexpr int kBinWarps = 8;       // warps per block of the binned kernel
+constexpr int kBinWarps = 8;       // warps per block of the binned kernel (one block per SM)
 constexpr int kBinRowsMax = 32;    // rows per warp item
 constexpr int kBinShortMax = 32;   // longest "short" row
 constexpr int kBinItemNnz = kBinRowsMax * kBinShortMax;
@@ -196,8 +198,10 @@ struct VecArg {
   double* dev = nullptr;  // device pointer the kernels use
   bool staged = false;    // user pointer is host memory
 };
-// Classifies p; for host memory copies n doubles into staging (if copy_in).
-int vec_in(VecArg& v, const void* p, int64_t n, double* staging, bool copy_in, int device,
+// Classifies p with one pointer query: device memory of `device` is used in
+// place; host memory is staged through *staging (allocated on first use,
+// n doubles, size added to *bytes) and copied in when copy_in.
+int vec_in(VecArg& v, const void* p, int64_t n, double** staging, int64_t* bytes, bool copy_in, int device,
            cudaStream_t s);
 // For staged outputs: copies back and synchronizes s.
 int vec_out(VecArg& v, int64_t n, cudaStream_t s);

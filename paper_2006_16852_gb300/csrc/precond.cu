@@ -280,18 +280,9 @@ extern "C" int gk_precond_apply(gk_precond h, const void* r, void* z, void* stre
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = GK_OK;
   do {
-    cudaPointerAttributes at;
-    bool host_r = cudaPointerGetAttributes(&at, r) != cudaSuccess ||
-                  at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
-    cudaGetLastError();
-    bool host_z = cudaPointerGetAttributes(&at, z) != cudaSuccess ||
-                  at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
-    cudaGetLastError();
-    if (host_r && !P->stage_in && (rc = dalloc_n(&P->stage_in, P->n + 1, &P->device_bytes))) break;
-    if (host_z && !P->stage_out && (rc = dalloc_n(&P->stage_out, P->n + 1, &P->device_bytes))) break;
     VecArg vr, vz;
-    if ((rc = vec_in(vr, r, P->n, P->stage_in, true, P->device, s))) break;
-    if ((rc = vec_in(vz, z, P->n, P->stage_out, false, P->device, s))) break;
+    if ((rc = vec_in(vr, r, P->n, &P->stage_in, &P->device_bytes, true, P->device, s))) break;
+    if ((rc = vec_in(vz, z, P->n, &P->stage_out, &P->device_bytes, false, P->device, s))) break;
     if ((rc = precond_apply_launch(P, vr.dev, vz.dev, s))) break;
     rc = vec_out(vz, P->n, s);
   } while (false);

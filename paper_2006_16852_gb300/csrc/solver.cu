@@ -81,6 +81,23 @@ __global__ void solver_init_kernel(SolverState* st, double factor, long long max
   for (int w_ = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w_ * bpw_ < a.nblocks; w_ += nw_) \
     for (BjLane L = bj_lane(w_ * bpw_, lane_, a.bs, a.n, a.nblocks), *once_ = &L; once_; once_ = nullptr)
 
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// Scalar-Jacobi / unpreconditioned vector kernels run at 8 blocks of 256
+// threads per SM (32 registers) with 128-bit loads of row pairs; the
+// block-Jacobi variants keep the default register budget.
+template <int PK>
+struct VecMinBlocks {
+  static constexpr int value = PK == PREC_BLOCK ? 1 : 8;
+};
+
+// Grid-stride loop over row pairs (2 i2, 2 i2 + 1).
+#define FOR_PAIRS(i2) \
+  for (int i2 = blockIdx.x * blockDim.x + threadIdx.x; 2 * i2 < a.n; i2 += gridDim.x * blockDim.x)
+
 __device__ __forceinline__ void reduce_finalize(const VecArgs& a, double s0, double s1, int fin,
                                                 double* scratch, bool control) {
   double v[2] = {s0, s1}, out[2];
@@ -119,7 +136,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
 
 // x += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); k += 1 and criteria.
 template <int PK>
-__global__ void __launch_bounds__(kVecThreads) cg_update_kernel(VecArgs a) {
+__global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
   __shared__ double scratch[64];
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
@@ -140,12 +157,27 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(VecArgs a) {
       }
     }
   } else {
-    FOR_ROWS(i) {
-      a.x[i] = fma(alpha, a.p[i], a.x[i]);
-      const double rn = fma(-alpha, a.q[i], a.r[i]);
-      a.r[i] = rn;
-      rr = fma(rn, rn, rr);
-      if (PK == PREC_SCALAR) rz = fma(rn, a.dinv[i] * rn, rz);
+    FOR_PAIRS(i2) {
+      const int i = 2 * i2;
+      if (i + 1 < a.n) {
+        const double2 xv = ld2(a.x + i), pv = ld2(a.p + i), qv = ld2(a.q + i), rv = ld2(a.r + i);
+        st2(a.x + i, fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
+        const double r0 = fma(-alpha, qv.x, rv.x), r1 = fma(-alpha, qv.y, rv.y);
+        st2(a.r + i, r0, r1);
+        rr = fma(r0, r0, rr);
+        rr = fma(r1, r1, rr);
+        if (PK == PREC_SCALAR) {
+          const double2 d = ld2(a.dinv + i);
+          rz = fma(r0, d.x * r0, rz);
+          rz = fma(r1, d.y * r1, rz);
+        }
+      } else {
+        a.x[i] = fma(alpha, a.p[i], a.x[i]);
+        const double rn = fma(-alpha, a.q[i], a.r[i]);
+        a.r[i] = rn;
+        rr = fma(rn, rn, rr);
+        if (PK == PREC_SCALAR) rz = fma(rn, a.dinv[i] * rn, rz);
+      }
     }
     if (PK == PREC_NONE) rz = rr;
   }
@@ -154,16 +186,31 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(VecArgs a) {
 
 // p = z + beta p; ends the iteration (loop control).
 template <int PK>
-__global__ void __launch_bounds__(kVecThreads) cg_direction_kernel(VecArgs a) {
+__global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
   if (a.st->stop) return;
   const double beta = a.st->beta;
-  FOR_ROWS(i) {
-    double zv;
-    if (PK == PREC_BLOCK) zv = a.z[i];
-    else if (PK == PREC_SCALAR) zv = a.dinv[i] * a.r[i];
-    else zv = a.r[i];
-    a.p[i] = fma(beta, a.p[i], zv);
+  FOR_PAIRS(i2) {
+    const int i = 2 * i2;
+    if (i + 1 < a.n) {
+      double2 zv;
+      if (PK == PREC_BLOCK) {
+        zv = ld2(a.z + i);
+      } else if (PK == PREC_SCALAR) {
+        const double2 d = ld2(a.dinv + i), rv = ld2(a.r + i);
+        zv = make_double2(d.x * rv.x, d.y * rv.y);
+      } else {
+        zv = ld2(a.r + i);
+      }
+      const double2 pv = ld2(a.p + i);
+      st2(a.p + i, fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+    } else {
+      double zv;
+      if (PK == PREC_BLOCK) zv = a.z[i];
+      else if (PK == PREC_SCALAR) zv = a.dinv[i] * a.r[i];
+      else zv = a.r[i];
+      a.p[i] = fma(beta, a.p[i], zv);
+    }
   }
 }
 
@@ -264,6 +311,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
 }
 
 #undef FOR_ROWS
+#undef FOR_PAIRS
 #undef FOR_BLOCK_LANES
 
 }  // namespace
@@ -349,7 +397,7 @@ int vec_grid(const Solver& S) {
                             ? ((S.P->nblocks + (32 / S.P->bs) - 1) / (32 / S.P->bs)) * 32
                             : S.n;
   const int64_t g = (units + kVecThreads - 1) / kVecThreads;
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 4 * sm_count())));
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8 * sm_count())));
 }
 
 Epi spmv_epi(const Solver& S, int mode, const double* u, double* y, int fin, int skip_mode) {

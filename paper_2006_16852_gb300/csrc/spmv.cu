@@ -30,9 +30,12 @@ __device__ __forceinline__ bool epi_skip(const Epi& e) {
 
 __device__ __forceinline__ void epi_row(const Epi& e, int row, double s, double& a0, double& a1) {
   switch (e.mode) {
+    case EPI_COPY:
+      e.y[row] = s;
+      break;
     case EPI_PLAIN: {
       double as = e.alpha * s;
-      e.y[row] = (e.beta == 0.0) ? as : fma(e.beta, e.y[row], as);
+      e.y[row] = e.beta_zero ? as : fma(e.beta, e.y[row], as);
       break;
     }
     case EPI_RESID: {
@@ -55,18 +58,50 @@ __device__ __forceinline__ void epi_row(const Epi& e, int row, double s, double&
   }
 }
 
+// The same epilogue with the mode fixed at compile time (used where register
+// pressure matters: the ELL kernel runs at full occupancy only within 32
+// registers per thread).
+template <int MODE>
+__device__ __forceinline__ void epi_row_t(const Epi& e, int row, double s, double& a0, double& a1) {
+  if (MODE == EPI_COPY) {
+    e.y[row] = s;
+  } else if (MODE == EPI_PLAIN) {
+    double as = e.alpha * s;
+    e.y[row] = e.beta_zero ? as : fma(e.beta, e.y[row], as);
+  } else if (MODE == EPI_RESID) {
+    double b = e.u[row];
+    double r = b - s;
+    e.y[row] = r;
+    a0 = fma(r, r, a0);
+    a1 = fma(b, b, a1);
+  } else if (MODE == EPI_DOT) {
+    e.y[row] = s;
+    a0 = fma(e.u[row], s, a0);
+  } else {
+    e.y[row] = s;
+    a0 = fma(e.u[row], s, a0);
+    a1 = fma(s, s, a1);
+  }
+}
+
 // Grid-wide reduction of (a0, a1) and the scalar step that consumes it.
 __device__ __forceinline__ void epi_finish(const Epi& e, double a0, double a1, double* scratch) {
-  if (e.mode == EPI_PLAIN) return;
+  if (e.mode == EPI_PLAIN || e.mode == EPI_COPY) return;
   double v[2] = {a0, a1}, out[2];
   if (grid_sum<2>(v, e.partials, e.counter, scratch, out)) {
     if (threadIdx.x == 0 && e.st) finalize(e.fin, out, e.st);
   }
 }
 
+// Out-of-line copy for kernels whose row loop must stay within a tight
+// register budget.
+__device__ __noinline__ void epi_finish_ool(const Epi& e, double a0, double a1, double* scratch) {
+  epi_finish(e, a0, a1, scratch);
+}
+
 // Block partials only; a later launch finishes the reduction.
 __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, double* scratch) {
-  if (e.mode == EPI_PLAIN) return;
+  if (e.mode == EPI_PLAIN || e.mode == EPI_COPY) return;
   double v[2] = {a0, a1};
   block_sum<2>(v, scratch);
   if (threadIdx.x == 0) {
@@ -213,7 +248,19 @@ struct EllArgs {
   const double* tail_sum;
 };
 
-__global__ void __launch_bounds__(kEllThreads) spmv_ell_kernel(EllArgs a, Epi e) {
+// 8 blocks of 256 threads per SM (32 registers): full occupancy is what hides
+// the latency of the gathers (measured: 6 blocks/SM ran 10-25 % slower).
+// The reduction epilogues carry two accumulators and a second vector through
+// the loop; they issue their gathers in batches of 4 instead of 8 so that
+// they, too, fit 32 registers and keep 8 blocks per SM.
+template <int MODE>
+struct EllBatch {
+  static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN) ? 8 : 4;
+};
+
+template <int MODE, bool TAIL>
+__global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi e) {
+  constexpr int B = EllBatch<MODE>::value;
   __shared__ double red_scratch[64];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
@@ -223,17 +270,17 @@ __global__ void __launch_bounds__(kEllThreads) spmv_ell_kernel(EllArgs a, Epi e)
     const int32_t* cp = a.col + row;
     const double* vp = a.val + row;
     int j = 0;
-    for (; j + 8 <= a.K; j += 8) {
-      int cc[8];
-      double xv[8], vv[8];
+    for (; j + B <= a.K; j += B) {
+      int cc[B];
+      double xv[B], vv[B];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) cc[u] = __ldg(cp + (j + u) * a.ld);
+      for (int u = 0; u < B; ++u) cc[u] = __ldg(cp + (j + u) * a.ld);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) vv[u] = __ldg(vp + (j + u) * a.ld);
+      for (int u = 0; u < B; ++u) vv[u] = __ldg(vp + (j + u) * a.ld);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+      for (int u = 0; u < B; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < B; ++u)
         if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
     }
     for (; j < a.K; j += 4) {
@@ -249,13 +296,24 @@ __global__ void __launch_bounds__(kEllThreads) spmv_ell_kernel(EllArgs a, Epi e)
       for (int u = 0; u < 4; ++u)
         if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
     }
-    if (a.tail_slot) {
+    if (TAIL) {
       const int t = __ldg(a.tail_slot + row);
       if (t >= 0) s += __ldcg(a.tail_sum + t);
     }
-    epi_row(e, row, s, a0, a1);
+    epi_row_t<MODE>(e, row, s, a0, a1);
   }
-  epi_finish(e, a0, a1, red_scratch);
+  if (MODE != EPI_COPY && MODE != EPI_PLAIN) epi_finish(e, a0, a1, red_scratch);
+}
+
+template <bool TAIL>
+void launch_ell_t(int grid, cudaStream_t s, const EllArgs& a, const Epi& e) {
+  switch (e.mode) {
+    case EPI_COPY: spmv_ell_kernel<EPI_COPY, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+    case EPI_PLAIN: spmv_ell_kernel<EPI_PLAIN, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+    case EPI_RESID: spmv_ell_kernel<EPI_RESID, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+    case EPI_DOT: spmv_ell_kernel<EPI_DOT, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+    default: spmv_ell_kernel<EPI_DOT2, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -474,7 +532,7 @@ __global__ void __launch_bounds__(1024) spmv_merge_fixup_kernel(MergeArgs a, Epi
     }
     epi_row(e, h, v, a0, a1);
   }
-  if (e.mode == EPI_PLAIN) return;
+  if (e.mode == EPI_PLAIN || e.mode == EPI_COPY) return;
   for (int b = threadIdx.x; b < main_grid; b += blockDim.x) {
     a0 += e.partials[2 * b];
     a1 += e.partials[2 * b + 1];
@@ -561,7 +619,7 @@ int bin_grid(int64_t work_warps) {
 }
 
 int ell_grid(int64_t n_rows) {
-  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_ell_kernel), kEllThreads, 0);
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_ell_kernel<EPI_COPY, false>), kEllThreads, 0);
   int64_t need = (n_rows + kEllThreads - 1) / kEllThreads;
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
 }
@@ -587,16 +645,18 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
     case GK_HYB: {
       if (A.format == GK_HYB && A.m_tail > 0) {
         Epi te;
-        te.mode = EPI_PLAIN;
+        te.mode = EPI_COPY;
         te.y = A.tail_sum;
         te.st = e.st;
         te.skip_mode = e.skip_mode;
         te.err = e.err;
         GK_TRY(launch_merge(A.tail, x, te, s));
       }
+      const bool tail = A.format == GK_HYB && A.m_tail > 0;
       EllArgs ea{A.ell_col, A.ell_val, A.ld, static_cast<int>(A.K), static_cast<int>(A.n_rows), x,
-                 A.format == GK_HYB ? A.tail_slot : nullptr, A.tail_sum};
-      spmv_ell_kernel<<<A.grid_ell, kEllThreads, 0, s>>>(ea, e);
+                 tail ? A.tail_slot : nullptr, A.tail_sum};
+      if (tail) launch_ell_t<true>(A.grid_ell, s, ea, e);
+      else launch_ell_t<false>(A.grid_ell, s, ea, e);
       GK_TRY_CUDA(cudaGetLastError());
       return GK_OK;
     }

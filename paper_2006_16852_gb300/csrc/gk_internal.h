@@ -114,6 +114,9 @@ constexpr int kBinRowsMax = 32;    // rows per warp item
 constexpr int kBinShortMax = 32;   // longest "short" row
 constexpr int kBinItemNnz = kBinRowsMax * kBinShortMax;
 constexpr int kEllThreads = 256;
+// Blocks of the merge-path fix-up launch; reduction scratch holds
+// 2 * (max grid + kFixupMaxGrid) doubles.
+constexpr int kFixupMaxGrid = 64;
 
 struct MergePlan {
   int64_t n_rows = 0, nnz = 0, n_tiles = 0;

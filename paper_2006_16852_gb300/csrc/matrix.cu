@@ -337,7 +337,7 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
     A->grid_ell = ell_grid(n_rows);
   }
   A->max_grid = std::max(spmv_max_grid(*A), 4 * sm_count());
-  GK_TRY(dalloc_n(&A->partials, static_cast<size_t>(2 * A->max_grid), bytes));
+  GK_TRY(dalloc_n(&A->partials, static_cast<size_t>(2 * (A->max_grid + kFixupMaxGrid)), bytes));
   GK_TRY_CUDA(cudaStreamSynchronize(s));
   *out = reinterpret_cast<gk_matrix>(hold.release());
   return GK_OK;

@@ -35,45 +35,53 @@ __global__ void jacobi_scalar_kernel(const int32_t* __restrict__ rowptr, const i
   }
 }
 
-// Gauss-Jordan inversion of one diagonal block per warp on the augmented
-// matrix [D | I] held in shared memory (row stride 65 doubles: conflict-free
-// column access).  Pivot: largest |entry| in column k at or below row k,
-// lowest row on ties.  The pivot row is scaled by the reciprocal of the pivot
-// and every other row i is updated w_ij = fma(-w_ik, w_kj, w_ij).  Columns
-// left of and at k are not needed again once step k is done, so only
-// columns j > k are updated: the right half (the inverse) receives exactly
-// the operations of the full elimination.
+// Gauss-Jordan inversion of the diagonal blocks on the augmented matrices
+// [D | I] held in shared memory.  A warp inverts 32/GW blocks at once, one
+// group of GW lanes (GW = the next power of two >= the block size) per
+// block, lane i owning row i; each block's tile has an odd row stride
+// (2 GW + 1 doubles) so column accesses are conflict-free.
+// Pivot: largest |entry| in column k at or below row k, lowest row on ties
+// (xor butterfly inside the group).  The pivot row is scaled by the
+// reciprocal of the pivot and every other row i is updated
+// w_ij = fma(-w_ik, w_kj, w_ij).  Columns left of and at k are never read
+// again once step k is done, so only columns j > k are updated: the right
+// half (the inverse) receives exactly the operations of the full elimination.
 constexpr int kBjWarps = 4;
-constexpr int kBjStride = 65;
-constexpr int kBjWarpDoubles = 32 * kBjStride;
 
+template <int GW>
 __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
     int n, int bs, int nblocks, double* blocks, int* bad) {
   extern __shared__ double bj_smem[];
+  constexpr int G = 32 / GW;
+  constexpr int LD = 2 * GW + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* W = bj_smem + warp * kBjWarpDoubles;
-  for (int blk = blockIdx.x * kBjWarps + warp; blk < nblocks; blk += gridDim.x * kBjWarps) {
+  const int grp = lane / GW, i = lane - grp * GW;
+  double* W = bj_smem + (warp * G + grp) * GW * LD;
+  const int step_blocks = gridDim.x * kBjWarps * G;
+  for (int blk0 = (blockIdx.x * kBjWarps + warp) * G; blk0 < nblocks; blk0 += step_blocks) {
+    const int blk = blk0 + grp;
     const int r0 = blk * bs;
-    const int m = min(bs, n - r0);
+    const int m = blk < nblocks ? min(bs, n - r0) : 0;
     const int wd = 2 * m;
-    for (int idx = lane; idx < 32 * kBjStride; idx += 32) W[idx] = 0.0;
+    for (int idx = i; idx < GW * LD; idx += GW) W[idx] = 0.0;
     __syncwarp();
-    if (lane < m) {
-      const int r = r0 + lane;
+    if (i < m) {
+      const int r = r0 + i;
       for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
         const int c = col[k];
-        if (c >= r0 && c < r0 + m) W[lane * kBjStride + (c - r0)] = val[k];
+        if (c >= r0 && c < r0 + m) W[i * LD + (c - r0)] = val[k];
       }
-      W[lane * kBjStride + m + lane] = 1.0;
+      W[i * LD + m + i] = 1.0;
     }
     __syncwarp();
     bool singular = false;
-    for (int k = 0; k < m; ++k) {
-      double a = (lane >= k && lane < m) ? fabs(W[lane * kBjStride + k]) : -1.0;
-      int idx = lane;
+    for (int k = 0; k < bs; ++k) {
+      const bool live = k < m && !singular;
+      double a = (live && i >= k && i < m) ? fabs(W[i * LD + k]) : -1.0;
+      int idx = i;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = GW / 2; o > 0; o >>= 1) {
         const double a2 = __shfl_xor_sync(0xffffffffu, a, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
         if (a2 > a || (a2 == a && i2 < idx)) {
@@ -81,39 +89,57 @@ __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
           idx = i2;
         }
       }
-      if (!(a > 0.0)) {
-        singular = true;
-        break;
-      }
+      if (live && !(a > 0.0)) singular = true;
+      const bool work = live && !singular;
       const int piv = idx;
       __syncwarp();
-      if (piv != k) {
-        for (int j = k + lane; j < wd; j += 32) {
-          const double t = W[k * kBjStride + j];
-          W[k * kBjStride + j] = W[piv * kBjStride + j];
-          W[piv * kBjStride + j] = t;
+      if (work && piv != k) {
+        for (int j = k + i; j < wd; j += GW) {
+          const double t = W[k * LD + j];
+          W[k * LD + j] = W[piv * LD + j];
+          W[piv * LD + j] = t;
         }
       }
       __syncwarp();
-      const double rcp = 1.0 / W[k * kBjStride + k];
+      const double rcp = work ? 1.0 / W[k * LD + k] : 0.0;
       __syncwarp();
-      for (int j = k + 1 + lane; j < wd; j += 32) W[k * kBjStride + j] = W[k * kBjStride + j] * rcp;
+      if (work)
+        for (int j = k + 1 + i; j < wd; j += GW) W[k * LD + j] = W[k * LD + j] * rcp;
       __syncwarp();
-      if (lane < m && lane != k) {
-        const double f = W[lane * kBjStride + k];
-        for (int j = k + 1; j < wd; ++j)
-          W[lane * kBjStride + j] = fma(-f, W[k * kBjStride + j], W[lane * kBjStride + j]);
+      if (work && i < m && i != k) {
+        const double f = W[i * LD + k];
+        for (int j = k + 1; j < wd; ++j) W[i * LD + j] = fma(-f, W[k * LD + j], W[i * LD + j]);
       }
       __syncwarp();
     }
-    if (singular && lane == 0) atomicMin(bad, blk);
+    if (singular && i == 0) atomicMin(bad, blk);
     const int64_t off = static_cast<int64_t>(blk) * bs * bs;
-    for (int idx = lane; idx < m * m; idx += 32) {
-      const int j = idx / m, i = idx - j * m;
-      blocks[off + idx] = W[i * kBjStride + m + j];
+    for (int e = i; e < m * m; e += GW) {
+      const int j = e / m, ii = e - j * m;
+      blocks[off + e] = W[ii * LD + m + j];
     }
     __syncwarp();
   }
+}
+
+template <int GW>
+int launch_bj_generate(const Matrix* A, int n, int bs, int nblocks, double* blocks, int* bad, cudaStream_t s) {
+  const size_t smem = sizeof(double) * static_cast<size_t>(kBjWarps) * 32 * (2 * GW + 1);
+  cudaFuncSetAttribute(bj_generate_kernel<GW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  const int64_t warps = (nblocks + (32 / GW) - 1) / (32 / GW);
+  const int64_t g = std::min<int64_t>((warps + kBjWarps - 1) / kBjWarps, 16 * static_cast<int64_t>(sm_count()));
+  bj_generate_kernel<GW><<<static_cast<int>(std::max<int64_t>(g, 1)), kBjWarps * 32, smem, s>>>(
+      A->rowptr, A->col, A->val, n, bs, nblocks, blocks, bad);
+  return GK_OK;
+}
+
+int bj_generate(const Matrix* A, int n, int bs, int nblocks, double* blocks, int* bad, cudaStream_t s) {
+  if (bs <= 2) return launch_bj_generate<2>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 4) return launch_bj_generate<4>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 8) return launch_bj_generate<8>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 16) return launch_bj_generate<16>(A, n, bs, nblocks, blocks, bad, s);
+  return launch_bj_generate<32>(A, n, bs, nblocks, blocks, bad, s);
 }
 
 __global__ void scalar_apply_kernel(const double* __restrict__ dinv, const double* __restrict__ r, double* z,
@@ -241,13 +267,8 @@ extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream
       if ((rc = dalloc_n(&P->blocks, static_cast<size_t>(std::max<int64_t>(P->block_elems, 1)),
                          &P->device_bytes)))
         break;
-      const size_t smem = sizeof(double) * kBjWarpDoubles * kBjWarps;
-      cudaFuncSetAttribute(bj_generate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
       if (P->nblocks > 0)
-        bj_generate_kernel<<<grid_for(P->nblocks * 32, kBjWarps * 32), kBjWarps * 32, smem, s>>>(
-            A->rowptr, A->col, A->val, static_cast<int>(P->n), block_size, static_cast<int>(P->nblocks),
-            P->blocks, A->err + 1);
+        bj_generate(A, static_cast<int>(P->n), block_size, static_cast<int>(P->nblocks), P->blocks, A->err + 1, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -561,7 +561,8 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
     if ((rc = dalloc_n(&S->st, 1, by))) break;
     S->grid_vec = vec_grid(*S);
     const int pg = std::max(S->grid_vec, spmv_max_grid(*A));
-    if ((rc = dalloc_n(&S->partials, static_cast<size_t>(2 * pg), by)) || (rc = dalloc_n(&S->counter, 1, by)))
+    if ((rc = dalloc_n(&S->partials, static_cast<size_t>(2 * (pg + kFixupMaxGrid)), by)) ||
+        (rc = dalloc_n(&S->counter, 1, by)))
       break;
     cudaError_t e = cudaMemset(S->counter, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(S->st, 0, sizeof(SolverState));

@@ -338,6 +338,8 @@ struct MergeSmem {
   int32_t head_row[kMergeThreads];
   int32_t carry_row[kMergeThreads];
   int32_t cont[kMergeThreads];
+  double scan_v[kMergeThreads];  // segmented prefix sums of carry_val (long-row tiles)
+  int32_t scan_f[kMergeThreads];
   uint64_t bar;
   double red[64];
 };
@@ -469,6 +471,33 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
       S.cont[t] = 0;
     }
     __syncthreads();
+    // ---- long rows: segmented prefix sums of the threads' partial sums -----
+    // A row much longer than kMergeItems is split over many threads; summing
+    // their pieces one by one would leave the block waiting on one thread.
+    // Tiles touching such a row instead build, in a fixed tree order, the
+    // prefix sums of carry_val within runs of continuation threads (a run
+    // starts at every thread that is not a pure continuation).
+    bool lt = false;
+    for (int r = ti + t; r <= min(ti1, a.n_rows - 1); r += kMergeThreads)
+      lt = lt || (RP(r + 1) - RP(r) >= 4 * kMergeItems);
+    const bool long_tile = __syncthreads_or(lt) != 0;
+    if (long_tile) {
+      S.scan_v[t] = S.carry_val[t];
+      S.scan_f[t] = (t == 0 || !S.cont[t]) ? 1 : 0;
+      __syncthreads();
+      for (int d = 1; d < kMergeThreads; d <<= 1) {
+        double nv = S.scan_v[t];
+        int nf = S.scan_f[t];
+        if (t >= d && !nf) {
+          nv = S.scan_v[t - d] + nv;
+          nf = S.scan_f[t - d];
+        }
+        __syncthreads();
+        S.scan_v[t] = nv;
+        S.scan_f[t] = nf;
+        __syncthreads();
+      }
+    }
     // ---- phase 2: rows whose end lies in this tile, one per thread --------
     if (t == 0) a.head_row[tile] = -1;
     for (int r = ti + t; r < ti1; r += kMergeThreads) {
@@ -477,7 +506,11 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
       if (ds < d0) {
         // the row began in an earlier tile: leave it to the fix-up launch
         double v = S.head_val[t_end];
-        for (int u = t_end - 1; u >= 0; --u) v += S.carry_val[u];
+        if (long_tile) {
+          if (t_end > 0) v += S.scan_v[t_end - 1];
+        } else {
+          for (int u = t_end - 1; u >= 0; --u) v += S.carry_val[u];
+        }
         a.head_val[tile] = v;
         a.head_row[tile] = r;
       } else {
@@ -485,6 +518,8 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
         double v;
         if (t_start == t_end) {
           v = S.ys[r - ti];
+        } else if (long_tile) {
+          v = S.head_val[t_end] + S.scan_v[t_end - 1];
         } else {
           v = S.head_val[t_end];
           for (int u = t_end - 1; u >= t_start; --u) v += S.carry_val[u];
@@ -498,10 +533,14 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
       double cv = 0.0;
       if (tile != a.n_tiles - 1 && tj1 > RP(ti1)) {
         crow = ti1;
-        for (int u = kMergeThreads - 1; u >= 0; --u) {
-          if (S.carry_row[u] != crow) break;
-          cv += S.carry_val[u];
-          if (!S.cont[u]) break;
+        if (long_tile) {
+          cv = S.scan_v[kMergeThreads - 1];
+        } else {
+          for (int u = kMergeThreads - 1; u >= 0; --u) {
+            if (S.carry_row[u] != crow) break;
+            cv += S.carry_val[u];
+            if (!S.cont[u]) break;
+          }
         }
         ccont = (ti1 == ti && tile_mid) ? 1 : 0;
       }
@@ -515,13 +554,17 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
   epi_partial(e, a0, a1, S.red);
 }
 
-// Completes rows that cross tile boundaries and finishes the epilogue's
-// reduction over the main launch's block partials.
-__global__ void __launch_bounds__(1024) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
+// Completes rows that cross tile boundaries (one thread per tile, all tiles
+// in parallel) and finishes the epilogue's reduction: the main launch's
+// block partials are folded into this launch's own fixed-order grid sum, whose
+// block partials live after the main launch's.
+__global__ void __launch_bounds__(256) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
   __shared__ double red_scratch[64];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
-  for (int t = threadIdx.x; t < a.n_tiles; t += blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int t = gt; t < a.n_tiles; t += stride) {
     const int h = a.head_row[t];
     if (h < 0) continue;
     double v = a.head_val[t];
@@ -533,13 +576,13 @@ __global__ void __launch_bounds__(1024) spmv_merge_fixup_kernel(MergeArgs a, Epi
     epi_row(e, h, v, a0, a1);
   }
   if (e.mode == EPI_PLAIN || e.mode == EPI_COPY) return;
-  for (int b = threadIdx.x; b < main_grid; b += blockDim.x) {
-    a0 += e.partials[2 * b];
-    a1 += e.partials[2 * b + 1];
+  for (int b = gt; b < main_grid; b += stride) {
+    a0 += __ldcg(e.partials + 2 * b);
+    a1 += __ldcg(e.partials + 2 * b + 1);
   }
-  double v[2] = {a0, a1};
-  block_sum<2>(v, red_scratch);
-  if (threadIdx.x == 0 && e.st) finalize(e.fin, v, e.st);
+  double v[2] = {a0, a1}, out[2];
+  if (grid_sum<2>(v, e.partials + 2 * main_grid, e.counter, red_scratch, out) && threadIdx.x == 0 && e.st)
+    finalize(e.fin, out, e.st);
 }
 
 // ---------------------------------------------------------------------------
@@ -597,7 +640,8 @@ int launch_merge(const MergePlan& P, const double* x, const Epi& e, cudaStream_t
   MergeArgs m = merge_args(P, x);
   spmv_merge_kernel<<<P.grid, kMergeThreads, sizeof(MergeSmem), s>>>(m, e);
   GK_TRY_CUDA(cudaGetLastError());
-  spmv_merge_fixup_kernel<<<1, 1024, 0, s>>>(m, e, P.grid);
+  const int fg = static_cast<int>(std::min<int64_t>(kFixupMaxGrid, (P.n_tiles + 255) / 256));
+  spmv_merge_fixup_kernel<<<fg, 256, 0, s>>>(m, e, P.grid);
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }

@@ -400,12 +400,13 @@ def run_gpu(args):
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    dom = "spmv_a_csr"
+    dom = "spmv_a_ell"
     dom_ms = statistics.mean(part_ms[dom]) / SPMV_REPS
     dom_bytes = part_bytes[dom][0] // SPMV_REPS
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     tr = NCU_TRAFFIC.get(spmv_source_hash())
-    roofline = {"kernel": "spmv_binned_kernel (CSR-binned SpMV, workload (a))", "bound": "hbm",
+    roofline = {"kernel": "spmv_ell_kernel (ELL SpMV of (a), plain-apply instantiation; the same kernel with "
+                          "the fused dot runs inside the ELL CG solves)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm if hbm else 6800.0, "unit": "GB/s",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
                 "frac": round(achieved / (hbm if hbm else 6800.0), 4),

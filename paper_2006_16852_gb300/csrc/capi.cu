@@ -124,7 +124,7 @@ bool is_host(const void* p) {
 __global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                   int64_t n, double* partials, unsigned int* counter,
                                                   double* result) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   double a[1] = {0.0};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)

@@ -77,12 +77,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-order FP64 reductions.  A block sums per-thread values with an xor
-// butterfly inside each warp and then warp totals in warp order; the grid
-// sums per-block partials in the last block to arrive (an integer ticket
-// decides which block that is, the order of the sum does not depend on it).
-// The result is identical from run to run for a fixed grid and block shape.
+// Fixed-order FP64 reductions.  A block sums its threads' values in one warp
+// (block_sum below); the grid sums per-block partials in the last block to
+// arrive (an integer ticket decides which block that is, the order of the sum
+// does not depend on it).  The result is identical from run to run for a
+// fixed grid and block shape.
 // ---------------------------------------------------------------------------
+
+// Shared scratch (doubles) a reduction of up to two values over a block of up
+// to 256 threads needs.
+constexpr int kRedScratch = 512;
 
 template <int K>
 __device__ __forceinline__ void warp_sum(double (&v)[K]) {
@@ -93,23 +97,29 @@ __device__ __forceinline__ void warp_sum(double (&v)[K]) {
   }
 }
 
-// Sum over the block; the result is valid in thread 0.  scratch: >= 32*K doubles.
+// Sum over the block; the result is valid in thread 0.  Per-thread values go
+// to shared memory and warp 0 alone adds them (lane l sums threads l, l+32,
+// ... in order, then one xor butterfly): an FP64 add tree in every warp would
+// cost the (slow) FP64 pipe about three times as much.
+// scratch: >= K * blockDim.x doubles; blockDim.x a multiple of 32, <= 1024.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
-  warp_sum<K>(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int nt = blockDim.x;
   __syncthreads();
-  if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
-  }
+  for (int k = 0; k < K; ++k) scratch[k * nt + threadIdx.x] = v[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    double w[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double s = scratch[k];
-      for (int w = 1; w < nw; ++w) s += scratch[w * K + k];
-      v[k] = s;
+      w[k] = scratch[k * nt + threadIdx.x];
+      for (int t = threadIdx.x + 32; t < nt; t += 32) w[k] += scratch[k * nt + t];
+    }
+    warp_sum<K>(w);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = w[k];
     }
   }
 }

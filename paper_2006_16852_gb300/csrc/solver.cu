@@ -112,7 +112,7 @@ __device__ __forceinline__ void reduce_finalize(const VecArgs& a, double s0, dou
 // z = M^{-1} r, p = z, rho = r.z; criteria at k = 0.
 template <int PK>
 __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   double rz = 0.0;
   if (PK == PREC_BLOCK) {
     FOR_BLOCK_LANES(L) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
 // x += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); k += 1 and criteria.
 template <int PK>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
   double rz = 0.0, rr = 0.0;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a)
 
 // r^ = r_0, p = v = 0, rho = r^.r; criteria at k = 0.
 __global__ void __launch_bounds__(kVecThreads) bicg_start_kernel(VecArgs a) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   double rho = 0.0;
   FOR_ROWS(i) {
     const double rv = a.r[i];
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
 // s = r - alpha v; s^ = M^{-1} s; ||s||^2 (half-step test).
 template <int PK>
 __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
   double ss = 0.0;
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
 // next rho and beta; ends the iteration.  After a half-step exit only
 // x += alpha p^ and r = s.
 __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
-  __shared__ double scratch[64];
+  __shared__ double scratch[kRedScratch];
   if (a.st->stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
     return;

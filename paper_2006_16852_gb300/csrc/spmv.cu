@@ -175,7 +175,7 @@ struct BinArgs {
 
 __global__ void __launch_bounds__(kBinWarps * 32) spmv_binned_kernel(BinArgs a, Epi e) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_scratch[64];
+  __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* base = smem_raw + warp * kBinWarpBytes;
@@ -261,7 +261,7 @@ struct EllBatch {
 template <int MODE, bool TAIL>
 __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi e) {
   constexpr int B = EllBatch<MODE>::value;
-  __shared__ double red_scratch[64];
+  __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
   const int stride = gridDim.x * blockDim.x;
@@ -341,7 +341,6 @@ struct MergeSmem {
   double scan_v[kMergeThreads];  // segmented prefix sums of carry_val (long-row tiles)
   int32_t scan_f[kMergeThreads];
   uint64_t bar;
-  double red[64];
 };
 
 struct MergeArgs {
@@ -551,7 +550,7 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
 #undef RP
     __syncthreads();
   }
-  epi_partial(e, a0, a1, S.red);
+  epi_partial(e, a0, a1, S.ys);  // ys is free once the tiles are done
 }
 
 // Completes rows that cross tile boundaries (one thread per tile, all tiles
@@ -559,7 +558,7 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
 // block partials are folded into this launch's own fixed-order grid sum, whose
 // block partials live after the main launch's.
 __global__ void __launch_bounds__(256) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
-  __shared__ double red_scratch[64];
+  __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
   const int stride = gridDim.x * blockDim.x;

@@ -74,6 +74,7 @@ extern "C" {
 
 #define GK_CG 0
 #define GK_BICGSTAB 1
+#define GK_IR_CG 2       /* FP64 iterative refinement around an FP32 CG inner solver */
 
 /* Stop reasons (the stopping_status of Section 2.5). */
 #define GK_STOP_NONE 0
@@ -97,11 +98,17 @@ typedef struct gk_solver_s* gk_solver;
  * launches the iterations from the host and reads the stop flag back after
  * every check_every iterations. */
 typedef struct {
-  int64_t max_iters;
+  int64_t max_iters;        /* GK_IR_CG: limit on the total of inner iterations      */
   double reduction_factor;
   int32_t rel_to_b;
   int32_t check_every;
   double time_limit_s;
+  /* GK_IR_CG only: each inner solve stops once its residual is reduced by
+   * max(inner_reduction, tol / (2 ||r||)) (inner_reduction <= 0: 1e-5) or
+   * after inner_max_iters iterations (<= 0: max_iters). */
+  double inner_reduction;
+  int32_t inner_max_iters;
+  int32_t reserved_;
 } gk_criteria;
 
 /* Convergence record of one solve (the Convergence logger of Section 2.6). */
@@ -114,7 +121,19 @@ typedef struct {
   double ref_norm;      /* ref used by the residual criterion                         */
   int32_t stop_reason;  /* GK_STOP_*                                                  */
   int32_t device_error; /* nonzero if a device-side wait timed out                    */
+  int64_t outer_iters;  /* GK_IR_CG: refinement steps (FP64 residuals); else 0        */
 } gk_status;
+
+/* What a solver was built into. */
+typedef struct {
+  int32_t kind;             /* GK_CG, GK_BICGSTAB, GK_IR_CG                       */
+  int32_t inner_format;     /* GK_IR_CG: storage of the FP32 operator copy (GK_ELL */
+                            /* for ELL/HYB matrices, else GK_CSR)                  */
+  int64_t n;
+  int64_t inner_fp16_blocks; /* GK_IR_CG + block Jacobi: blocks stored in FP16   */
+  int64_t inner_fp32_blocks; /* ... and in FP32                                  */
+  int64_t device_bytes;
+} gk_solver_info;
 
 typedef struct {
   int64_t n_rows, n_cols, nnz;
@@ -179,7 +198,15 @@ GK_API int gk_precond_destroy(gk_precond P);
 
 /* ---- solvers (Section 3.1) ---------------------------------------------- */
 /* S_A = generate(A): a CG or BiCGSTAB operator bound to A, optionally
- * preconditioned by P (NULL for none), stopping on *crit. */
+ * preconditioned by P (NULL for none), stopping on *crit.
+ * GK_IR_CG is the iterative refinement of Sections 2.2.3 and 3.1 with a
+ * CG inner solver run in lower precision: the outer loop computes r = b - A x,
+ * its norm and the update x += d in FP64; the inner solve of A d = r runs on
+ * an FP32 copy of A with FP32 vectors and FP32 accumulation, preconditioned
+ * by an FP32 copy of P (scalar Jacobi) or by P's inverse blocks stored per
+ * block in FP16 or FP32 chosen by the block's condition number kappa_1
+ * (Section 3.2's adaptive-precision block Jacobi: FP16 when
+ * kappa_1 * 2^-11 <= 1e-2, each block scaled by a power of two). */
 GK_API int gk_solver_generate(gk_matrix A, gk_precond P, int32_t kind, const gk_criteria* crit,
                        gk_solver* out);
 
@@ -189,6 +216,7 @@ GK_API int gk_solver_generate(gk_matrix A, gk_precond P, int32_t kind, const gk_
  * says which criterion ended the iteration. */
 GK_API int gk_solve(gk_solver S, const void* b, void* x, gk_status* st, void* stream);
 GK_API int gk_solver_destroy(gk_solver S);
+GK_API int gk_solver_get_info(gk_solver S, gk_solver_info* info);
 
 /* ---- reductions ---------------------------------------------------------- */
 /* result[0] = sum_i x_i y_i in FP64 with a fixed, run-to-run reproducible

@@ -83,6 +83,11 @@ def lib():
         L.or_precond_apply.restype = None
         L.or_hyb_width.argtypes = [i64, vp, i64, i64]
         L.or_hyb_width.restype = i64
+        L.or_block_jacobi_precision.argtypes = [i64, vp, vp, vp, ctypes.c_int32, vp, vp, vp]
+        L.or_block_jacobi_precision.restype = None
+        L.or_ir_cg.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp, ctypes.POINTER(_Criteria),
+                               f64, i64, ctypes.POINTER(_Status), ctypes.POINTER(i64)]
+        L.or_ir_cg.restype = ctypes.c_int
         for name in ("or_cg", "or_bicgstab"):
             f = getattr(L, name)
             f.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp,
@@ -233,3 +238,35 @@ def cg(A, b, **kw) -> SolveResult:
 
 def bicgstab(A, b, **kw) -> SolveResult:
     return _solve("or_bicgstab", A, b, **kw)
+
+
+def block_jacobi_precision(A, bs, blocks):
+    """Per-block storage precision (0 FP16, 1 FP32) and kappa_1 of the inverse blocks."""
+    rowptr, col, val = _csr(A)
+    n = rowptr.shape[0] - 1
+    nb = (n + bs - 1) // bs
+    prec = np.zeros(max(nb, 1), dtype=np.uint8)
+    kappa = np.zeros(max(nb, 1))
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    lib().or_block_jacobi_precision(n, _p(rowptr), _p(col), _p(val), bs, _p(blocks), _p(prec), _p(kappa))
+    return prec[:nb], kappa[:nb]
+
+
+def ir_cg(A, b, x0=None, P: Precond | None = None, max_iters=100000, tol=1e-10, rel_to_b=True,
+          inner_reduction=1e-5, inner_max=None):
+    """Mixed-precision iterative refinement; returns (SolveResult, outer steps)."""
+    rowptr, col, val = _csr(A)
+    n = rowptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    crit = _Criteria(int(max_iters), float(tol), 1 if rel_to_b else 0)
+    st = _Status()
+    P = P or Precond()
+    pc = P._c()
+    outer = ctypes.c_int64(0)
+    rc = lib().or_ir_cg(n, _p(rowptr), _p(col), _p(val), ctypes.byref(pc), _p(b), _p(x), ctypes.byref(crit),
+                        float(inner_reduction), int(inner_max or max_iters), ctypes.byref(st), ctypes.byref(outer))
+    if rc != OK:
+        raise RuntimeError(f"or_ir_cg failed: {rc}")
+    return SolveResult(x, st.iters, st.spmvs, st.rel_res, st.rel_res_true, st.ref_norm, st.stop_reason,
+                       None), outer.value

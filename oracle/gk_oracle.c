@@ -406,3 +406,178 @@ int or_bicgstab(int64_t n, const int32_t* rowptr, const int32_t* col, const doub
   free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mixed precision: adaptive block storage and iterative refinement         */
+/* ------------------------------------------------------------------------ */
+
+void or_block_jacobi_precision(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                               int32_t bs, const double* blocks, uint8_t* prec, double* kappa) {
+  int64_t off = 0, b = 0;
+  for (int64_t r0 = 0; r0 < n; r0 += bs, ++b) {
+    int64_t m = (r0 + bs <= n) ? bs : n - r0;
+    double na = 0.0, ni = 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+      /* column j of D: |a_{r0+i, r0+j}| summed over i in increasing order */
+      double cs = 0.0;
+      for (int64_t i = 0; i < m; ++i) {
+        double a = 0.0;
+        for (int64_t k = rowptr[r0 + i]; k < rowptr[r0 + i + 1]; ++k)
+          if (col[k] == r0 + j) a = fabs(val[k]);
+        cs += a;
+      }
+      if (cs > na) na = cs;
+      /* column j of D^{-1} (blocks are row-major here) */
+      double ci = 0.0;
+      for (int64_t i = 0; i < m; ++i) ci += fabs(blocks[off + i * m + j]);
+      if (ci > ni) ni = ci;
+    }
+    double k1 = na * ni;
+    if (kappa) kappa[b] = k1;
+    prec[b] = (k1 <= 1e-2 * 2048.0) ? 0 : 1;
+    off += m * m;
+  }
+}
+
+typedef struct {
+  int32_t kind, bs;
+  float* dinv;      /* scalar Jacobi */
+  float* blocks;    /* block Jacobi, row-major, values as stored (rounded), scaled */
+  float* scale;     /* per block: 2^e */
+} or_precond32;
+
+static void precond32_apply(int64_t n, const or_precond32* P, const float* r, float* z) {
+  if (P->kind == OR_PREC_NONE) {
+    for (int64_t i = 0; i < n; ++i) z[i] = r[i];
+  } else if (P->kind == OR_PREC_SCALAR_JACOBI) {
+    for (int64_t i = 0; i < n; ++i) z[i] = P->dinv[i] * r[i];
+  } else {
+    int64_t bs = P->bs, off = 0, b = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += bs, ++b) {
+      int64_t m = (r0 + bs <= n) ? bs : n - r0;
+      for (int64_t i = 0; i < m; ++i) {
+        float s = 0.0f;
+        for (int64_t j = 0; j < m; ++j) s = fmaf(P->blocks[off + i * m + j], r[r0 + j], s);
+        z[r0 + i] = s * P->scale[b];
+      }
+      off += m * m;
+    }
+  }
+}
+
+static float dotf(int64_t n, const float* x, const float* y) {
+  float s = 0.0f;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+int or_ir_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+             const or_precond* P, const double* b, double* x, const or_criteria* crit,
+             double inner_reduction, int64_t inner_max, or_status* st, int64_t* outer) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  int64_t nnz = rowptr[n];
+  size_t fz = sizeof(float) * (size_t)(n + 1);
+  float *val32 = malloc(sizeof(float) * (size_t)(nnz + 1)), *r = malloc(fz), *p = malloc(fz), *q = malloc(fz),
+        *z = malloc(fz), *d = malloc(fz);
+  double* r64 = malloc(sizeof(double) * (size_t)(n + 1));
+  or_precond32 P32 = {OR_PREC_NONE, 1, NULL, NULL, NULL};
+  for (int64_t k = 0; k < nnz; ++k) val32[k] = (float)val[k];
+  if (P && P->kind == OR_PREC_SCALAR_JACOBI) {
+    P32.kind = OR_PREC_SCALAR_JACOBI;
+    P32.dinv = malloc(fz);
+    for (int64_t i = 0; i < n; ++i) P32.dinv[i] = (float)P->dinv[i];
+  } else if (P && P->kind == OR_PREC_BLOCK_JACOBI) {
+    int64_t bs = P->block_size, nb = (n + bs - 1) / bs, total = or_block_jacobi_size(n, (int32_t)bs);
+    uint8_t* prec = malloc((size_t)nb + 1);
+    P32.kind = OR_PREC_BLOCK_JACOBI;
+    P32.bs = (int32_t)bs;
+    P32.blocks = malloc(sizeof(float) * (size_t)(total + 1));
+    P32.scale = malloc(sizeof(float) * (size_t)(nb + 1));
+    or_block_jacobi_precision(n, rowptr, col, val, (int32_t)bs, P->blocks, prec, NULL);
+    int64_t off = 0, blk = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += bs, ++blk) {
+      int64_t m = (r0 + bs <= n) ? bs : n - r0;
+      double vmax = 0.0;
+      for (int64_t e = 0; e < m * m; ++e) vmax = fmax(vmax, fabs(P->blocks[off + e]));
+      int ex = 0;
+      if (vmax > 0.0) frexp(vmax, &ex);
+      double sc = ldexp(1.0, -ex);
+      P32.scale[blk] = (float)ldexp(1.0, ex);
+      for (int64_t e = 0; e < m * m; ++e) {
+        double v = P->blocks[off + e] * sc;
+        P32.blocks[off + e] = prec[blk] == 0 ? (float)(_Float16)v : (float)v;
+      }
+      off += m * m;
+    }
+    free(prec);
+  }
+  double bnorm = or_norm2(n, b), ref = 0.0, tol = 0.0, rnorm = 0.0;
+  int stop = OR_STOP_NONE;
+  int64_t k_total = 0, steps = 0;
+  for (;;) {
+    residual(n, rowptr, col, val, b, x, r64);
+    st->spmvs += 1;
+    rnorm = or_norm2(n, r64);
+    if (steps == 0) {
+      ref = crit->rel_to_b ? bnorm : rnorm;
+      if (ref == 0.0) ref = 1.0;
+      tol = crit->reduction_factor * ref;
+    }
+    stop = check_stop(rnorm, tol, k_total, crit->max_iters);
+    if (stop != OR_STOP_NONE || steps >= 200) {
+      if (stop == OR_STOP_NONE) stop = OR_STOP_MAX_ITERS;
+      break;
+    }
+    /* inner CG in float on A d = r / ||r|| */
+    double inv = 1.0 / rnorm;
+    for (int64_t i = 0; i < n; ++i) {
+      r[i] = (float)(r64[i] * inv);
+      d[i] = 0.0f;
+    }
+    precond32_apply(n, &P32, r, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    float rho = dotf(n, r, z);
+    double rr0 = dotf(n, r, r);
+    /* the last inner solve only needs the reduction that is still missing */
+    double red = fmax(inner_reduction, 0.5 * tol / rnorm);
+    double tol2 = red * red * rr0;
+    int64_t it = 0;
+    int broke = 0;
+    while (it < inner_max) {
+      for (int64_t i = 0; i < n; ++i) {
+        float s = 0.0f;
+        for (int64_t kk = rowptr[i]; kk < rowptr[i + 1]; ++kk) s = fmaf(val32[kk], p[col[kk]], s);
+        q[i] = s;
+      }
+      float sigma = dotf(n, p, q);
+      if (!isfinite(sigma) || sigma <= 0.0f) { broke = 1; break; }
+      float alpha = (float)((double)rho / (double)sigma);
+      for (int64_t i = 0; i < n; ++i) d[i] = fmaf(alpha, p[i], d[i]);
+      for (int64_t i = 0; i < n; ++i) r[i] = fmaf(-alpha, q[i], r[i]);
+      it += 1;
+      precond32_apply(n, &P32, r, z);
+      float rz = dotf(n, r, z);
+      float rr = dotf(n, r, r);
+      if (!isfinite(rz) || !isfinite(rr)) { broke = 1; break; }
+      if ((double)rr <= tol2) break;
+      float beta = (float)((double)rz / (double)rho);
+      for (int64_t i = 0; i < n; ++i) p[i] = fmaf(beta, p[i], z[i]);
+      rho = rz;
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = fma(rnorm, (double)d[i], x[i]);
+    k_total += it;
+    st->spmvs += it;
+    steps += 1;
+    if (it == 0 || (broke && it <= 1)) { stop = OR_STOP_BREAKDOWN; break; }
+  }
+  st->iters = k_total;
+  st->stop_reason = stop;
+  st->rel_res = rnorm / ref;
+  st->rel_res_true = rnorm / ref;
+  st->ref_norm = ref;
+  if (outer) *outer = steps;
+  free(val32); free(r); free(p); free(q); free(z); free(d); free(r64);
+  free(P32.dinv); free(P32.blocks); free(P32.scale);
+  return OR_OK;
+}

@@ -109,6 +109,27 @@ int or_bicgstab(int64_t n, const int32_t* rowptr, const int32_t* col, const doub
                 const or_precond* P, const double* b, double* x, const or_criteria* crit,
                 or_status* st, double* res_hist);
 
+/* Adaptive-precision block Jacobi (Section 3.2): for every inverse block,
+ * kappa_1 = ||D||_1 ||D^{-1}||_1 (column sums in increasing row order, the
+ * maximum over columns) and the storage precision: 0 = FP16 when
+ * kappa_1 * 2^-11 <= 1e-2, else 1 = FP32.  kappa may be NULL. */
+void or_block_jacobi_precision(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                               int32_t bs, const double* blocks, uint8_t* prec, double* kappa);
+
+/* Iterative refinement with a lower-precision CG inner solver (Sections
+ * 2.2.3 and 3.1): outer r = b - A x, ||r|| and the criteria in FP64; inner CG
+ * on A d = r / ||r|| with float matrix values, float vectors and float
+ * accumulation, stopped when ||r_inner|| <= red * ||r_inner,0|| with
+ * red = max(inner_reduction, tol / (2 ||r||)) -- the reduction still missing --
+ * or after inner_max iterations; then x = x + ||r|| d.  The inner
+ * preconditioner is the float copy of P: scalar Jacobi, or block Jacobi
+ * with each block stored in FP16 or float by or_block_jacobi_precision and
+ * scaled by the power of two that puts its largest magnitude in [0.5, 1).
+ * st->iters counts inner iterations, *outer the refinement steps. */
+int or_ir_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+             const or_precond* P, const double* b, double* x, const or_criteria* crit,
+             double inner_reduction, int64_t inner_max, or_status* st, int64_t* outer);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,14 +26,14 @@ ERR_NAMES = {1: "GK_ERR_ARG", 2: "GK_ERR_DIM", 3: "GK_ERR_DTYPE", 4: "GK_ERR_NOT
 F64, F32 = 0, 1
 FORMATS = {"csr": 0, "csr_merge": 1, "ell": 2, "hyb": 3, "auto": 4}
 FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
-SOLVERS = {"cg": 0, "bicgstab": 1}
+SOLVERS = {"cg": 0, "bicgstab": 1, "ir_cg": 2}
 STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME = range(6)
 
 # every symbol include/gk.h declares
 EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get_info",
            "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
            "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
-           "gk_solver_destroy", "gk_dot", "gk_dot_noalloc")
+           "gk_solver_destroy", "gk_solver_get_info", "gk_dot", "gk_dot_noalloc")
 
 
 class GkError(RuntimeError):
@@ -45,16 +45,24 @@ class GkError(RuntimeError):
 class Criteria(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("reduction_factor", ctypes.c_double),
                 ("rel_to_b", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("time_limit_s", ctypes.c_double)]
+                ("time_limit_s", ctypes.c_double), ("inner_reduction", ctypes.c_double),
+                ("inner_max_iters", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Status(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("spmvs", ctypes.c_int64), ("rel_res", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("ref_norm", ctypes.c_double),
-                ("stop_reason", ctypes.c_int32), ("device_error", ctypes.c_int32)]
+                ("stop_reason", ctypes.c_int32), ("device_error", ctypes.c_int32),
+                ("outer_iters", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SolverInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("inner_format", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("inner_fp16_blocks", ctypes.c_int64), ("inner_fp32_blocks", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -101,6 +109,7 @@ def load(path: str | None = None):
         "gk_solver_generate": [vp, vp, i32, ctypes.POINTER(Criteria), ctypes.POINTER(vp)],
         "gk_solve": [vp, vp, vp, ctypes.POINTER(Status), vp],
         "gk_solver_destroy": [vp],
+        "gk_solver_get_info": [vp, ctypes.POINTER(SolverInfo)],
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
     }
@@ -248,6 +257,7 @@ class SolveStatus:
     ref_norm: float
     stop_reason: int
     device_error: int
+    outer_iters: int
 
 
 class Solver:
@@ -255,15 +265,20 @@ class Solver:
 
     def __init__(self, A: Matrix, P: Precond | None = None, kind: str = "cg", max_iters: int = 1000,
                  reduction_factor: float = 1e-10, rel_to_b: bool = True, check_every: int = 0,
-                 time_limit_s: float = 0.0):
+                 time_limit_s: float = 0.0, inner_reduction: float = 0.0, inner_max_iters: int = 0):
         crit = Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, int(check_every),
-                        float(time_limit_s))
+                        float(time_limit_s), float(inner_reduction), int(inner_max_iters), 0)
         h = ctypes.c_void_p()
         _check(lib().gk_solver_generate(A.handle, P.handle if P is not None else None, SOLVERS[kind],
                                         ctypes.byref(crit), ctypes.byref(h)))
         self.handle = h
         self.n = A.n_rows
         self._keep = (A, P)
+
+    def info(self) -> dict:
+        inf = SolverInfo()
+        _check(lib().gk_solver_get_info(self.handle, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in SolverInfo._fields_}
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -88,8 +88,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 // to 256 threads needs.
 constexpr int kRedScratch = 512;
 
-template <int K>
-__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+template <int K, typename T>
+__device__ __forceinline__ void warp_sum(T (&v)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -102,21 +102,21 @@ __device__ __forceinline__ void warp_sum(double (&v)[K]) {
 // ... in order, then one xor butterfly): an FP64 add tree in every warp would
 // cost the (slow) FP64 pipe about three times as much.
 // scratch: >= K * blockDim.x doubles; blockDim.x a multiple of 32, <= 1024.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
+template <int K, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[K], T* scratch) {
   const int nt = blockDim.x;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) scratch[k * nt + threadIdx.x] = v[k];
   __syncthreads();
   if (threadIdx.x < 32) {
-    double w[K];
+    T w[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       w[k] = scratch[k * nt + threadIdx.x];
       for (int t = threadIdx.x + 32; t < nt; t += 32) w[k] += scratch[k * nt + t];
     }
-    warp_sum<K>(w);
+    warp_sum<K, T>(w);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < K; ++k) v[k] = w[k];
@@ -128,11 +128,11 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
 // in exactly one block (the last to arrive), where thread 0 holds the totals
 // in out[].  partials: >= gridDim.x*K doubles; counter: zero on entry, reset
 // to zero by the last block.
-template <int K>
-__device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsigned int* counter,
-                                         double* scratch, double (&out)[K]) {
+template <int K, typename T>
+__device__ __forceinline__ bool grid_sum(T (&v)[K], T* partials, unsigned int* counter, T* scratch,
+                                         T (&out)[K]) {
   __shared__ unsigned int s_last;
-  block_sum<K>(v, scratch);
+  block_sum<K, T>(v, scratch);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[blockIdx.x * K + k] = v[k];
@@ -143,14 +143,14 @@ __device__ __forceinline__ bool grid_sum(double (&v)[K], double* partials, unsig
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double w[K];
+  T w[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) w[k] = 0.0;
+  for (int k = 0; k < K; ++k) w[k] = T(0);
   for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] += __ldcg(partials + b * K + k);
   }
-  block_sum<K>(w, scratch);
+  block_sum<K, T>(w, scratch);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = w[k];

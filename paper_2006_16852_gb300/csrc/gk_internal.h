@@ -56,6 +56,7 @@ struct SolverState {
   double true_rr;            // ||b - A x||^2 of the final check
   long long iter, max_iters, spmvs;
   long long iter_guard;      // iterations the device-side loop has run
+  long long outer;           // iterative refinement: outer steps taken
   unsigned long long t_start_ns, time_limit_ns;
   int stop;                  // GK_STOP_*
   int half;                  // BiCGSTAB: converged at the half step
@@ -76,6 +77,7 @@ enum Fin : int {
   FIN_BI_OMEGA,     // sums = (s.t, t.t): omega
   FIN_BI_ITER,      // sums = (r^.r, r.r): k += 1, criteria, next rho/beta
   FIN_TRUE_RESID,   // sums = (||b - A x||^2, -): store
+  FIN_IR_RESID,     // sums = (||b - A x||^2, ||b||^2): outer criteria of refinement
 };
 
 // ---------------------------------------------------------------------------
@@ -230,6 +232,39 @@ struct Precond {
 void precond_release(Precond* P);
 
 enum PrecKind : int { PREC_NONE = 0, PREC_SCALAR = 1, PREC_BLOCK = 2 };
+
+struct IrData;
+
+// Solver handle.
+struct Solver {
+  std::atomic<int> refs{1};
+  int device = 0;
+  Matrix* A = nullptr;
+  Precond* P = nullptr;
+  int kind = GK_CG;
+  int pk = PREC_NONE;
+  gk_criteria crit{};
+  int64_t n = 0;
+  int64_t device_bytes = 0;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+  double *rh = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
+  SolverState* st = nullptr;
+  SolverState* h_st = nullptr;  // pinned
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  int grid_vec = 1;
+  cudaStream_t cs = nullptr;  // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  IrData* ir = nullptr;  // GK_IR_CG: the FP32 inner solver
+};
+
+// Mixed-precision iterative refinement (mixed.cu).
+int ir_generate(Solver* S);
+int ir_solve(Solver* S, cudaStream_t s);
+void ir_release(IrData* ir);
+
 
 // z = M^{-1} r as a standalone launch.
 int precond_apply_launch(const Precond* P, const double* r, double* z, cudaStream_t s);

@@ -316,28 +316,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
 
 }  // namespace
 
-struct Solver {
-  std::atomic<int> refs{1};
-  int device = 0;
-  Matrix* A = nullptr;
-  Precond* P = nullptr;
-  int kind = GK_CG;
-  int pk = PREC_NONE;
-  gk_criteria crit{};
-  int64_t n = 0;
-  int64_t device_bytes = 0;
-  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
-  double *rh = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
-  SolverState* st = nullptr;
-  SolverState* h_st = nullptr;  // pinned
-  double* partials = nullptr;
-  unsigned int* counter = nullptr;
-  int grid_vec = 1;
-  cudaStream_t cs = nullptr;  // capture stream
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle cond = 0;
-};
+
 
 namespace {
 
@@ -355,6 +334,7 @@ void solver_release(Solver* S) {
   dfree(S->partials);
   dfree(S->counter);
   if (S->h_st) cudaFreeHost(S->h_st);
+  ir_release(S->ir);
   precond_release(S->P);
   matrix_release(S->A);
   if (prev >= 0) cudaSetDevice(prev);
@@ -522,7 +502,8 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
   Matrix* A = as_matrix(hA);
   Precond* P = as_precond(hP);
   if (!A || !crit) return set_error(GK_ERR_ARG, "gk_solver_generate: NULL matrix or criteria");
-  if (kind != GK_CG && kind != GK_BICGSTAB) return set_error(GK_ERR_ARG, "unknown solver kind %d", kind);
+  if (kind != GK_CG && kind != GK_BICGSTAB && kind != GK_IR_CG)
+    return set_error(GK_ERR_ARG, "unknown solver kind %d", kind);
   if (A->n_rows != A->n_cols) return set_error(GK_ERR_DIM, "gk_solver_generate: matrix is not square");
   if (P && P->n != A->n_rows) return set_error(GK_ERR_DIM, "preconditioner size %lld != %lld",
                                                (long long)P->n, (long long)A->n_rows);
@@ -571,6 +552,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
       rc = cuda_error(e, "solver allocation");
       break;
     }
+    if (kind == GK_IR_CG && (rc = ir_generate(S))) break;
   } while (false);
   if (prev != A->device) cudaSetDevice(prev);
   if (rc != GK_OK) return rc;
@@ -601,7 +583,9 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       rc = cuda_error(e, "gk_solve: copying b and x");
       break;
     }
-    if (S->crit.check_every > 0) {
+    if (S->kind == GK_IR_CG) {
+      if ((rc = ir_solve(S, s))) break;
+    } else if (S->crit.check_every > 0) {
       // host-driven loop: groups of check_every iterations, then a status read
       VecArgs a = vec_args(*S, 0);
       if ((rc = enqueue_setup(*S, s, a))) break;
@@ -653,6 +637,7 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       status->rel_res_true = sqrt(H.true_rr) / H.ref;
       status->stop_reason = H.stop;
       status->device_error = H.err;
+      status->outer_iters = H.outer;
     }
     if (H.err & kErrTimeout) rc = set_error(GK_ERR_TIMEOUT, "gk_solve: a device-side wait timed out");
   } while (false);

@@ -120,6 +120,24 @@ __device__ __forceinline__ void finalize(int fin, const double* s, SolverState* 
       st->spmvs += 1;
       st->true_rr = s[0];
       break;
+    case FIN_IR_RESID: {
+      // iterative refinement: r = b - A x in FP64 after every inner solve
+      st->spmvs += 1;
+      const double rn = sqrt(s[0]);
+      if (st->outer == 0) {
+        st->t_start_ns = global_ns();
+        st->bnorm = sqrt(s[1]);
+        st->rnorm0 = rn;
+        double ref = st->rel_to_b ? st->bnorm : rn;
+        if (ref == 0.0) ref = 1.0;
+        st->ref = ref;
+        st->tol = st->factor * ref;
+      }
+      st->rnorm = rn;
+      st->true_rr = s[0];
+      st->stop = check_stop(st, rn, st->iter);
+      break;
+    }
     default:
       break;
   }

@@ -8,13 +8,16 @@ workload:
   (b) power-law matrix, n = 1,000,000, row lengths Zipf(1.8) capped at 10^4,
       symmetrised and made diagonally dominant (nnz ~ 29M)
 
-  * SpMV x -> A x once in every format: (a) CSR-binned, CSR-merge, ELL, HYB;
-    (b) CSR-merge, HYB, CSR-binned (ELL refuses (b): padding > 8x nnz)
+  * SpMV x -> A x three times back to back in every format: (a) CSR-binned,
+    CSR-merge, ELL, HYB; (b) CSR-merge, HYB, CSR-binned (ELL refuses (b):
+    padding > 8x nnz)
   * preconditioner generation: scalar Jacobi and block Jacobi (bs 8) of (a),
     block Jacobi (bs 4) of (b)
-  * (a) CG to ||r|| <= 1e-10 ||b|| from x0 = 0, b = A x*: plain FP64 CG,
-    Jacobi-CG and block-Jacobi-CG
-  * (b) Jacobi-CG and block-Jacobi BiCGSTAB to 1e-10
+  * (a) CG to ||r|| <= 1e-10 ||b|| from x0 = 0, b = A x*: plain FP64 CG
+    (CSR), Jacobi-CG and block-Jacobi-CG (ELL), and the mixed-precision forms
+    (FP64 refinement around FP32 CG with Jacobi or adaptive FP16/FP32 block
+    Jacobi); "chosen form" = the fastest of the preconditioned/mixed forms
+  * (b) Jacobi-CG and block-Jacobi BiCGSTAB to 1e-10 (HYB)
 
 value = algorithmic bytes of the step / device time of the step (GB/s).
 Inputs are larger than the 129 MB L2 (711 MB and ~371 MB per SpMV).
@@ -97,6 +100,27 @@ def bicgstab_bytes(iters, spmvs, nnz, n, prec="none", bs=1):
     full_it = 2 * spmv_bytes(nnz, n, n) + 16 * n + k1 + k3 + k5
     half_it = spmv_bytes(nnz, n, n) + 8 * n + k1 + k3 + 40 * n
     return setup + full * full_it + half * half_it + resid_bytes(nnz, n)
+
+
+def ir_bytes(inner, outer, nnz, n, prec="none", bs=1, fp16_frac=0.0):
+    """FP64 refinement around an FP32 CG inner solve (GK_IR_CG) on an ELL copy.
+
+    Outer step: r = b - A x in FP64 (SpMV + b), the start of the inner solve
+    (r64 in; r32, d32, p32 out; M), and x += ||r|| d (x in/out, d in).  Inner
+    iteration: FP32 SpMV (8 bytes per entry, x and y in FP32), update (d, p,
+    q, r, M in; d, r out), direction (p, r or z, M in; p out).  Block-Jacobi
+    blocks cost 2 (FP16) or 4 (FP32) bytes per entry."""
+    if prec == "none":
+        pe = 0.0
+    elif prec == "jacobi":
+        pe = 4.0
+    else:
+        pe = bs * (2.0 * fp16_frac + 4.0 * (1.0 - fp16_frac))
+    z_store = 4.0 if prec == "block" else 0.0
+    spmv32 = nnz * 8 + (n + 1) * 4 + n * 4 + n * 4
+    per_inner = spmv32 + (16 + pe + 8 + z_store) * n + (12 + (4 if prec == "jacobi" else 0)) * n
+    per_outer = resid_bytes(nnz, n) + (8 + 12 + pe) * n + 20 * n
+    return int(outer * per_outer + inner * per_inner + resid_bytes(nnz, n))
 
 
 def precond_bytes(nnz, n, bs):
@@ -263,7 +287,18 @@ class GpuStep:
                                 "jacobi", 1, "cg", "hyb"),
             "b_bicgstab_bj4_hyb": (gk.Solver(M[("b", "hyb")], gk.Precond(M[("b", "hyb")], 4), "bicgstab", **crit),
                                    "b", "block", 4, "bicgstab", "hyb"),
+            # mixed precision: FP64 refinement around FP32 CG (adaptive FP16/FP32 blocks)
+            "a_ircg_jacobi_ell": (gk.Solver(M[("a", "ell")], gk.Precond(M[("a", "ell")], 1), "ir_cg", **crit),
+                                  "a", "jacobi", 1, "ir_cg", "ell"),
+            "a_ircg_bj8_ell": (gk.Solver(M[("a", "ell")], gk.Precond(M[("a", "ell")], 8), "ir_cg", **crit),
+                               "a", "block", 8, "ir_cg", "ell"),
         }
+        self.fp16_frac = {}
+        for name, v in self.solvers.items():
+            if v[4] == "ir_cg" and v[2] == "block":
+                inf = v[0].info()
+                tot = inf["inner_fp16_blocks"] + inf["inner_fp32_blocks"]
+                self.fp16_frac[name] = inf["inner_fp16_blocks"] / max(tot, 1)
         self.xsol = {k: torch.zeros(self.na if v[1] == "a" else self.nb, dtype=torch.float64, device=dev)
                      for k, v in self.solvers.items()}
         self.gens = [("a", "csr", 1), ("a", "csr", 8), ("b", "csr_merge", 4)]
@@ -326,6 +361,9 @@ class GpuStep:
             return precond_bytes(self.nnz_of(k), self.n_of(k), bs)
         name, st = tag[1], tag[2]
         S, k, prec, bs, sk, fmt = self.solvers[name]
+        if sk == "ir_cg":
+            return ir_bytes(st.iters, st.outer_iters, self.nnz_of(k), self.n_of(k), prec, bs,
+                            self.fp16_frac.get(name, 0.0))
         if sk == "cg":
             return cg_bytes(st.iters, self.nnz_of(k), self.n_of(k), prec, bs)
         return bicgstab_bytes(st.iters, st.spmvs, self.nnz_of(k), self.n_of(k), prec, bs)
@@ -338,7 +376,14 @@ class GpuStep:
             return 1
         name, st = tag[1], tag[2]
         S, k, prec, bs, sk, fmt = self.solvers[name]
-        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(self.mats[(k, fmt)].info()))
+        info = self.mats[(k, fmt)].info()
+        if sk == "ir_cg":
+            # init; per outer step: FP64 residual SpMV, start, apply; per inner
+            # iteration: FP32 SpMV (+ overflow kernel for HYB), update, direction
+            inner_spmv = 2 if (info["format_name"] == "hyb" and info["tail_rows"] > 0) else 1
+            return (1 + (st.outer_iters + 1) * spmv_launches(info) + 2 * st.outer_iters
+                    + st.iters * (inner_spmv + 2))
+        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(info))
 
 
 def run_gpu(args):
@@ -384,7 +429,7 @@ def run_gpu(args):
 
     # per-part figures from the recorded events
     part_ms, part_bytes, launches = {}, {}, 0
-    iters = {}
+    iters, outers = {}, {}
     for parts in rec:
         for name, e0, e1, tag in parts:
             part_ms.setdefault(name, []).append(e0.elapsed_time(e1))
@@ -392,6 +437,8 @@ def run_gpu(args):
             launches += step.part_launches(tag)
             if tag[0] == "solve":
                 iters[tag[1]] = tag[2].iters
+                if tag[2].outer_iters:
+                    outers[tag[1]] = tag[2].outer_iters
                 if tag[2].stop_reason != gk.STOP_CONVERGED:
                     raise RuntimeError(f"{tag[1]} did not converge: {tag[2]}")
     step_bytes = sum(sum(v) for v in part_bytes.values()) / args.steps
@@ -425,10 +472,13 @@ def run_gpu(args):
         if n.startswith("solve_"):
             s = summary(n)
             s["iters"] = iters[n[6:]]
+            if n[6:] in outers:
+                s["outer_iters"] = outers[n[6:]]
             solves[n[6:]] = s
     precs = {n[8:]: summary(n) for n in part_ms if n.startswith("precond_")}
     plain = solves["a_cg_plain_csr"]["ms"]
-    chosen = min(("a_cg_jacobi_ell", "a_cg_bj8_ell"), key=lambda k: solves[k]["ms"])
+    chosen = min(("a_cg_jacobi_ell", "a_cg_bj8_ell", "a_ircg_jacobi_ell", "a_ircg_bj8_ell"),
+                 key=lambda k: solves[k]["ms"])
 
     # end to end: the same step through the C ABI with pinned host vectors
     host = {}
@@ -475,7 +525,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (129 MB): no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "frac_hbm": round(value / (hbm or 6800.0), 4),
-        "time_to_tol_ms": {"plain_fp64_cg": plain, "chosen_form": chosen, "chosen_ms": solves[chosen]["ms"]},
+        "time_to_tol_ms": {"plain_fp64_cg": plain, "chosen_form": chosen, "chosen_ms": solves[chosen]["ms"],
+                           "speedup_vs_plain": round(plain / solves[chosen]["ms"], 3)},
         "spmv": spmv, "solves": solves, "precond_generate": precs,
         "paper_table2_cg_bytes_plain": table2_cg_bytes(solves["a_cg_plain_csr"]["iters"], step.nnza, step.na),
         "roofline": roofline,

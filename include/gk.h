@@ -218,6 +218,72 @@ GK_API int gk_solve(gk_solver S, const void* b, void* x, gk_status* st, void* st
 GK_API int gk_solver_destroy(gk_solver S);
 GK_API int gk_solver_get_info(gk_solver S, gk_solver_info* info);
 
+/* ---- batched small systems ------------------------------------------------ */
+/* Many independent square systems (the per-right-hand-side / per-system
+ * stopping status of Section 2.5 taken to independent matrices), stored as
+ * one block-diagonal CSR matrix: system s owns rows and columns
+ * [sys_ptr[s], sys_ptr[s+1]) and each of its rows may reference only those
+ * columns, in increasing order without repeats (else GK_ERR_CSR).  Systems
+ * of 1 to 4096 rows are supported (GK_ERR_UNSUPPORTED beyond).  dtype GK_F64
+ * solves in FP64; GK_F32 stores the values in FP32 and solves in FP32 (b and
+ * x stay FP64 in memory).
+ * gk_batch_create: sys_ptr is a host array of n_sys+1 offsets starting at 0;
+ * rowptr (n_rows+1), col and val (nnz) may be host or device memory and are
+ * copied.  The handle owns its device memory; calls on one handle must be
+ * ordered (they share a schedule counter and a status array). */
+typedef struct gk_batch_s* gk_batch;
+
+typedef struct {
+  int32_t iters;
+  int32_t stop_reason;  /* GK_STOP_* per system                              */
+  double rel_res;       /* recurred ||r|| / ||b|| (or / ||r_0||) at exit      */
+} gk_batch_status;
+
+GK_API int gk_batch_create(int64_t n_sys, const int64_t* sys_ptr, int64_t nnz, const int32_t* rowptr,
+                           const int32_t* col, const double* val, int32_t dtype, void* stream, gk_batch* out);
+
+/* Size classes: class c holds the systems of 16*2^c + 1 to 32*2^c rows
+ * (class 0: 1 to 32 rows, ..., class 7: 2049 to 4096 rows). */
+#define GK_BATCH_CLASSES 8
+
+/* Solves every system with CG or BiCGSTAB (kind), scalar Jacobi if
+ * jacobi != 0, in one CUDA graph launch: each size class is one persistent
+ * kernel (the classes run side by side as independent graph branches); a
+ * thread block holds one system at a time with its vectors in shared memory
+ * and takes the class's systems in decreasing size.  Each system's result
+ * depends only on the system, b, x_0 and its class's block size -- not on its
+ * neighbours, the schedule or the run.  b and x are device arrays of n_rows
+ * doubles laid out like the rows; x holds the initial guesses and receives
+ * the solutions.  st (host, nullable) receives n_sys records (the call then
+ * waits for the stream).  crit: max_iters, reduction_factor and rel_to_b
+ * apply to every system; the other fields are ignored.  When a class's
+ * largest system does not fit in one block's shared memory (BiCGSTAB with
+ * Jacobi in FP64 above about 3500 rows) GK_ERR_UNSUPPORTED is returned. */
+GK_API int gk_batch_solve(gk_batch B, int32_t kind, int32_t jacobi, const gk_criteria* crit, const void* b,
+                          void* x, gk_batch_status* st, void* stream);
+
+/* The autotuner: for (kind, jacobi), times every non-empty class alone at
+ * block sizes 32 (one warp per system), 64, 128 and 256, solving for b from
+ * x = 0 into a workspace of the handle, and keeps the fastest size per class
+ * for later gk_batch_solve calls.  threads (nullable, GK_BATCH_CLASSES
+ * entries) receives the chosen sizes (0 for empty classes); times_ms
+ * (nullable, GK_BATCH_CLASSES * 4 entries, class-major) the measured times,
+ * -1 where a size does not fit or the class is empty.  Waits for the stream. */
+GK_API int gk_batch_autotune(gk_batch B, int32_t kind, int32_t jacobi, const gk_criteria* crit, const void* b,
+                             int32_t* threads, double* times_ms, void* stream);
+
+/* Sets the block size per class for (kind, jacobi): GK_BATCH_CLASSES entries
+ * of 32, 64, 128, 256, or 0 for the built-in default (32 up to 64 rows, 64
+ * up to 512, else 128).  GK_ERR_ARG for any other value. */
+GK_API int gk_batch_set_threads(gk_batch B, int32_t kind, int32_t jacobi, const int32_t* threads);
+
+/* Per class (GK_BATCH_CLASSES entries each, all nullable): systems in the
+ * class, rows of its largest system, and the block size (kind, jacobi) will
+ * run it with (0 for empty classes). */
+GK_API int gk_batch_get_info(gk_batch B, int32_t kind, int32_t jacobi, int32_t* counts, int32_t* nmax,
+                             int32_t* threads);
+GK_API int gk_batch_destroy(gk_batch B);
+
 /* ---- reductions ---------------------------------------------------------- */
 /* result[0] = sum_i x_i y_i in FP64 with a fixed, run-to-run reproducible
  * reduction order (per-block trees, then one block over the block partials;

@@ -88,6 +88,11 @@ def lib():
         L.or_ir_cg.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp, ctypes.POINTER(_Criteria),
                                f64, i64, ctypes.POINTER(_Status), ctypes.POINTER(i64)]
         L.or_ir_cg.restype = ctypes.c_int
+        for name in ("or_cg_f32", "or_bicgstab_f32"):
+            f = getattr(L, name)
+            f.argtypes = [i64, vp, vp, vp, ctypes.c_int32, vp, vp, ctypes.POINTER(_Criteria),
+                          ctypes.POINTER(_Status)]
+            f.restype = ctypes.c_int
         for name in ("or_cg", "or_bicgstab"):
             f = getattr(L, name)
             f.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp,
@@ -270,3 +275,60 @@ def ir_cg(A, b, x0=None, P: Precond | None = None, max_iters=100000, tol=1e-10, 
         raise RuntimeError(f"or_ir_cg failed: {rc}")
     return SolveResult(x, st.iters, st.spmvs, st.rel_res, st.rel_res_true, st.ref_norm, st.stop_reason,
                        None), outer.value
+
+
+def _solve_f32(name, A, b, x0=None, jacobi=True, max_iters=1000, tol=1e-6, rel_to_b=True):
+    rowptr, col, val = _csr(A)
+    n = rowptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    crit = _Criteria(int(max_iters), float(tol), 1 if rel_to_b else 0)
+    st = _Status()
+    rc = getattr(lib(), name)(n, _p(rowptr), _p(col), _p(val), 1 if jacobi else 0, _p(b), _p(x),
+                              ctypes.byref(crit), ctypes.byref(st))
+    if rc != OK:
+        raise RuntimeError(f"{name} failed: {rc}")
+    return SolveResult(x, st.iters, st.spmvs, st.rel_res, st.rel_res_true, st.ref_norm, st.stop_reason, None)
+
+
+def cg_f32(A, b, **kw) -> SolveResult:
+    """CG in single precision (float values, vectors and sums)."""
+    return _solve_f32("or_cg_f32", A, b, **kw)
+
+
+def bicgstab_f32(A, b, **kw) -> SolveResult:
+    """BiCGSTAB in single precision (float values, vectors and sums)."""
+    return _solve_f32("or_bicgstab_f32", A, b, **kw)
+
+
+def batch_system(sys_ptr, A, s):
+    """Rows and columns [sys_ptr[s], sys_ptr[s+1]) of a block-diagonal CSR
+    matrix as a CSR triple of its own (columns shifted to start at 0)."""
+    rowptr, col, val = _csr(A)
+    r0, r1 = int(sys_ptr[s]), int(sys_ptr[s + 1])
+    k0, k1 = int(rowptr[r0]), int(rowptr[r1])
+    return ((rowptr[r0:r1 + 1] - k0).astype(np.int32), (col[k0:k1] - r0).astype(np.int32),
+            val[k0:k1].copy())
+
+
+def batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, dtype="f64", systems=None, x0=None, **kw):
+    """Solve the independent systems one after another (each by cg / bicgstab
+    or their FP32 forms).  Returns (x, list of SolveResult) over `systems`
+    (default: all); entries of x outside those systems are left at x0."""
+    n = int(sys_ptr[-1])
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    systems = range(len(sys_ptr) - 1) if systems is None else systems
+    out = []
+    for s in systems:
+        r0, r1 = int(sys_ptr[s]), int(sys_ptr[s + 1])
+        sub = batch_system(sys_ptr, A, s)
+        if dtype == "f32":
+            f = cg_f32 if kind == "cg" else bicgstab_f32
+            res = f(sub, b[r0:r1], x0=x[r0:r1], jacobi=jacobi, **kw)
+        else:
+            P = precond(sub, "jacobi") if jacobi else None
+            f = cg if kind == "cg" else bicgstab
+            res = f(sub, b[r0:r1], x0=x[r0:r1], P=P, **kw)
+        x[r0:r1] = res.x
+        out.append(res)
+    return x, out

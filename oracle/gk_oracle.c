@@ -581,3 +581,171 @@ int or_ir_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
   free(P32.dinv); free(P32.blocks); free(P32.scale);
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Single-precision CG and BiCGSTAB (the batched FP32 solves)                */
+/* ------------------------------------------------------------------------ */
+
+/* Float copies of A's values, b and x_0, and the scalar Jacobi inverse in
+ * float (1 / (float) a_ii).  OR_ERR_SINGULAR when a diagonal is missing or 0. */
+static int f32_setup(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     int32_t jacobi, const double* b, const double* x, float* val32, float* b32,
+                     float* x32, float* dinv) {
+  int64_t nnz = rowptr[n];
+  for (int64_t k = 0; k < nnz; ++k) val32[k] = (float)val[k];
+  for (int64_t i = 0; i < n; ++i) {
+    b32[i] = (float)b[i];
+    x32[i] = (float)x[i];
+  }
+  if (!jacobi) return OR_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    float d = 0.0f;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] == i) d = val32[k];
+    if (d == 0.0f) return OR_ERR_SINGULAR;
+    dinv[i] = 1.0f / d;
+  }
+  return OR_OK;
+}
+
+/* y = A x in float: ordered row sums by fmaf. */
+static void spmvf(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val32,
+                  const float* x, float* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    float s = 0.0f;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fmaf(val32[k], x[col[k]], s);
+    y[i] = s;
+  }
+}
+
+static void jacf(int64_t n, int32_t jacobi, const float* dinv, const float* r, float* z) {
+  for (int64_t i = 0; i < n; ++i) z[i] = jacobi ? dinv[i] * r[i] : r[i];
+}
+
+int or_cg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
+              const double* b, double* x, const or_criteria* crit, or_status* st) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t fz = sizeof(float) * (size_t)(n + 1);
+  float *a32 = malloc(sizeof(float) * (size_t)(rowptr[n] + 1)), *b32 = malloc(fz), *x32 = malloc(fz),
+        *dinv = malloc(fz), *r = malloc(fz), *z = malloc(fz), *p = malloc(fz), *q = malloc(fz);
+  double* work = malloc(sizeof(double) * (size_t)(n + 1));
+  int rc = f32_setup(n, rowptr, col, val, jacobi, b, x, a32, b32, x32, dinv);
+  if (rc == OR_OK) {
+    spmvf(n, rowptr, col, a32, x32, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b32[i] - q[i];
+    st->spmvs = 1;
+    double bnorm = sqrt((double)dotf(n, b32, b32));
+    double rnorm = sqrt((double)dotf(n, r, r));
+    double ref = crit->rel_to_b ? bnorm : rnorm;
+    if (ref == 0.0) ref = 1.0;
+    double tol = crit->reduction_factor * ref;
+    jacf(n, jacobi, dinv, r, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    float rho = dotf(n, r, z);
+    int64_t k = 0;
+    int stop;
+    while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+      spmvf(n, rowptr, col, a32, p, q);
+      st->spmvs += 1;
+      float sigma = dotf(n, p, q);
+      if (!isfinite(sigma)) { stop = OR_STOP_NAN; break; }
+      if (sigma <= 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      float alpha = rho / sigma;
+      for (int64_t i = 0; i < n; ++i) x32[i] = fmaf(alpha, p[i], x32[i]);
+      for (int64_t i = 0; i < n; ++i) r[i] = fmaf(-alpha, q[i], r[i]);
+      k += 1;
+      rnorm = sqrt((double)dotf(n, r, r));
+      jacf(n, jacobi, dinv, r, z);
+      float rho_new = dotf(n, r, z);
+      float beta = rho_new / rho;
+      for (int64_t i = 0; i < n; ++i) p[i] = fmaf(beta, p[i], z[i]);
+      rho = rho_new;
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = (double)x32[i];
+    st->iters = k;
+    st->stop_reason = stop;
+    finish(n, rowptr, col, val, b, x, ref, rnorm, st, work);
+  }
+  free(a32); free(b32); free(x32); free(dinv); free(r); free(z); free(p); free(q); free(work);
+  return rc;
+}
+
+int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
+                    const double* b, double* x, const or_criteria* crit, or_status* st) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t fz = sizeof(float) * (size_t)(n + 1);
+  float *a32 = malloc(sizeof(float) * (size_t)(rowptr[n] + 1)), *b32 = malloc(fz), *x32 = malloc(fz),
+        *dinv = malloc(fz), *r = malloc(fz), *rh = malloc(fz), *p = malloc(fz), *v = malloc(fz),
+        *ph = malloc(fz), *s = malloc(fz), *sh = malloc(fz), *t = malloc(fz);
+  double* work = malloc(sizeof(double) * (size_t)(n + 1));
+  int rc = f32_setup(n, rowptr, col, val, jacobi, b, x, a32, b32, x32, dinv);
+  if (rc == OR_OK) {
+    spmvf(n, rowptr, col, a32, x32, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b32[i] - t[i];
+    st->spmvs = 1;
+    double bnorm = sqrt((double)dotf(n, b32, b32));
+    double rnorm = sqrt((double)dotf(n, r, r));
+    double ref = crit->rel_to_b ? bnorm : rnorm;
+    if (ref == 0.0) ref = 1.0;
+    double tol = crit->reduction_factor * ref;
+    for (int64_t i = 0; i < n; ++i) {
+      rh[i] = r[i];
+      p[i] = 0.0f;
+      v[i] = 0.0f;
+    }
+    float rho_prev = 1.0f, alpha = 1.0f, omega = 1.0f;
+    int64_t k = 0;
+    int stop;
+    while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+      float rho = dotf(n, rh, r);
+      if (!isfinite(rho)) { stop = OR_STOP_NAN; break; }
+      if (rho == 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      float beta = (rho / rho_prev) * (alpha / omega);
+      for (int64_t i = 0; i < n; ++i) p[i] = fmaf(beta, fmaf(-omega, v[i], p[i]), r[i]);
+      jacf(n, jacobi, dinv, p, ph);
+      spmvf(n, rowptr, col, a32, ph, v);
+      st->spmvs += 1;
+      float rhv = dotf(n, rh, v);
+      if (!isfinite(rhv)) { stop = OR_STOP_NAN; break; }
+      if (rhv == 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      alpha = rho / rhv;
+      for (int64_t i = 0; i < n; ++i) s[i] = fmaf(-alpha, v[i], r[i]);
+      double snorm = sqrt((double)dotf(n, s, s));
+      if (isfinite(snorm) && snorm <= tol) {
+        for (int64_t i = 0; i < n; ++i) x32[i] = fmaf(alpha, ph[i], x32[i]);
+        for (int64_t i = 0; i < n; ++i) r[i] = s[i];
+        k += 1;
+        rnorm = snorm;
+        stop = OR_STOP_CONVERGED;
+        break;
+      }
+      jacf(n, jacobi, dinv, s, sh);
+      spmvf(n, rowptr, col, a32, sh, t);
+      st->spmvs += 1;
+      float tt = dotf(n, t, t);
+      float ts = dotf(n, t, s);
+      if (!isfinite(tt) || !isfinite(ts)) { stop = OR_STOP_NAN; break; }
+      if (tt == 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      omega = ts / tt;
+      for (int64_t i = 0; i < n; ++i) x32[i] = fmaf(omega, sh[i], fmaf(alpha, ph[i], x32[i]));
+      for (int64_t i = 0; i < n; ++i) r[i] = fmaf(-omega, t[i], s[i]);
+      rho_prev = rho;
+      k += 1;
+      rnorm = sqrt((double)dotf(n, r, r));
+      if (omega == 0.0f) {
+        stop = check_stop(rnorm, tol, k, crit->max_iters);
+        if (stop == OR_STOP_NONE) stop = OR_STOP_BREAKDOWN;
+        break;
+      }
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = (double)x32[i];
+    st->iters = k;
+    st->stop_reason = stop;
+    finish(n, rowptr, col, val, b, x, ref, rnorm, st, work);
+  }
+  free(a32); free(b32); free(x32); free(dinv); free(r); free(rh); free(p); free(v); free(ph); free(s);
+  free(sh); free(t); free(work);
+  return rc;
+}

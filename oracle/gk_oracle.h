@@ -130,6 +130,17 @@ int or_ir_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
              const or_precond* P, const double* b, double* x, const or_criteria* crit,
              double inner_reduction, int64_t inner_max, or_status* st, int64_t* outer);
 
+/* CG and BiCGSTAB in single precision (the batched FP32 solves): the steps of
+ * or_cg and or_bicgstab with float matrix values, float b, x, vectors and
+ * float sums (in increasing index order), norms sqrt((double) sum); scalar
+ * Jacobi (1 / (float) a_ii) if jacobi != 0, else none.  x is FP64 in memory
+ * (rounded to float on entry); rel_res_true is computed in FP64 on exit.
+ * OR_ERR_SINGULAR if jacobi and a diagonal entry is missing or zero. */
+int or_cg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
+              const double* b, double* x, const or_criteria* crit, or_status* st);
+int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
+                    const double* b, double* x, const or_criteria* crit, or_status* st);
+
 #ifdef __cplusplus
 }
 #endif

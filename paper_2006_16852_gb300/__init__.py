@@ -33,7 +33,11 @@ STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME =
 EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get_info",
            "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
            "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
-           "gk_solver_destroy", "gk_solver_get_info", "gk_dot", "gk_dot_noalloc")
+           "gk_solver_destroy", "gk_solver_get_info", "gk_batch_create", "gk_batch_solve",
+           "gk_batch_autotune", "gk_batch_set_threads", "gk_batch_get_info", "gk_batch_destroy", "gk_dot",
+           "gk_dot_noalloc")
+BATCH_CLASSES = 8
+BATCH_BLOCK_SIZES = (32, 64, 128, 256)
 
 
 class GkError(RuntimeError):
@@ -63,6 +67,10 @@ class SolverInfo(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("inner_format", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("inner_fp16_blocks", ctypes.c_int64), ("inner_fp32_blocks", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class BatchStatus(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("stop_reason", ctypes.c_int32), ("rel_res", ctypes.c_double)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -110,6 +118,12 @@ def load(path: str | None = None):
         "gk_solve": [vp, vp, vp, ctypes.POINTER(Status), vp],
         "gk_solver_destroy": [vp],
         "gk_solver_get_info": [vp, ctypes.POINTER(SolverInfo)],
+        "gk_batch_create": [i64, vp, i64, vp, vp, vp, i32, vp, ctypes.POINTER(vp)],
+        "gk_batch_solve": [vp, i32, i32, ctypes.POINTER(Criteria), vp, vp, vp, vp],
+        "gk_batch_autotune": [vp, i32, i32, ctypes.POINTER(Criteria), vp, vp, vp, vp],
+        "gk_batch_set_threads": [vp, i32, i32, vp],
+        "gk_batch_get_info": [vp, i32, i32, vp, vp, vp],
+        "gk_batch_destroy": [vp],
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
     }
@@ -314,3 +328,80 @@ def dot_noalloc(x, y, result, stream=None):
     _check_vec(y, n, "y")
     _check(lib().gk_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
     return result
+
+
+class Batch:
+    """Independent small systems in one block-diagonal CSR matrix (``sys_ptr``:
+    numpy int64 offsets of the systems' first rows, n_sys + 1 entries)."""
+
+    def __init__(self, sys_ptr, rowptr, col, val, dtype: str = "f64", stream=None):
+        import numpy as np
+        sp = np.ascontiguousarray(np.asarray(sys_ptr, dtype=np.int64))
+        for a, want in ((rowptr, "int32"), (col, "int32"), (val, "float64")):
+            if want not in str(a.dtype):
+                raise GkError(3, f"CSR arrays must be int32/int32/float64, got {a.dtype}")
+        nnz = col.numel() if hasattr(col, "numel") else col.size
+        h = ctypes.c_void_p()
+        _check(lib().gk_batch_create(sp.size - 1, sp.ctypes.data, nnz, _ptr(rowptr), _ptr(col), _ptr(val),
+                                     F32 if dtype == "f32" else F64, _stream(stream, rowptr, col, val),
+                                     ctypes.byref(h)))
+        self.handle = h
+        self.sys_ptr = sp
+        self.n_sys = sp.size - 1
+        self.n_rows = int(sp[-1])
+        self.nnz = nnz
+
+    @staticmethod
+    def _crit(max_iters, reduction_factor, rel_to_b):
+        return Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, 0, 0.0, 0.0, 0, 0)
+
+    def solve(self, b, x, kind: str = "cg", jacobi: bool = True, max_iters: int = 1000,
+              reduction_factor: float = 1e-10, rel_to_b: bool = True, status: bool = True, stream=None):
+        """Solve every system (x: initial guesses in, solutions out).  Returns
+        a dict of numpy arrays (iters, stop_reason, rel_res) when status."""
+        import numpy as np
+        _check_vec(b, self.n_rows, "b")
+        _check_vec(x, self.n_rows, "x")
+        crit = self._crit(max_iters, reduction_factor, rel_to_b)
+        st = (BatchStatus * self.n_sys)() if status else None
+        _check(lib().gk_batch_solve(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.byref(crit),
+                                    _ptr(b), _ptr(x), ctypes.addressof(st) if status else None,
+                                    _stream(stream, b, x)))
+        if not status:
+            return None
+        raw = np.frombuffer(st, dtype=np.dtype([("iters", np.int32), ("stop_reason", np.int32),
+                                                ("rel_res", np.float64)]))
+        return {"iters": raw["iters"].copy(), "stop_reason": raw["stop_reason"].copy(),
+                "rel_res": raw["rel_res"].copy()}
+
+    def autotune(self, b, kind: str = "cg", jacobi: bool = True, max_iters: int = 1000,
+                 reduction_factor: float = 1e-10, rel_to_b: bool = True, stream=None):
+        """Time block sizes 32/64/128/256 per size class and keep the fastest.
+        Returns (chosen sizes per class, {class: {size: ms}}) over non-empty classes."""
+        _check_vec(b, self.n_rows, "b")
+        crit = self._crit(max_iters, reduction_factor, rel_to_b)
+        t = (ctypes.c_int32 * BATCH_CLASSES)()
+        ms = (ctypes.c_double * (4 * BATCH_CLASSES))()
+        _check(lib().gk_batch_autotune(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.byref(crit),
+                                       _ptr(b), ctypes.addressof(t), ctypes.addressof(ms), _stream(stream, b)))
+        chosen = list(t)
+        times = {c: dict(zip(BATCH_BLOCK_SIZES, list(ms)[4 * c:4 * c + 4]))
+                 for c in range(BATCH_CLASSES) if chosen[c]}
+        return chosen, times
+
+    def set_threads(self, threads, kind: str = "cg", jacobi: bool = True):
+        """Block size per size class (0 = built-in default)."""
+        t = (ctypes.c_int32 * BATCH_CLASSES)(*[int(v) for v in threads])
+        _check(lib().gk_batch_set_threads(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.addressof(t)))
+
+    def info(self, kind: str = "cg", jacobi: bool = True) -> dict:
+        cnt, nmax, thr = ((ctypes.c_int32 * BATCH_CLASSES)() for _ in range(3))
+        _check(lib().gk_batch_get_info(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.addressof(cnt),
+                                       ctypes.addressof(nmax), ctypes.addressof(thr)))
+        return {"counts": list(cnt), "nmax": list(nmax), "threads": list(thr)}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.gk_batch_destroy(h)
+            self.handle = None

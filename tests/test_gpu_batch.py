@@ -1,0 +1,241 @@
+"""GPU parity of the batched small-system solves against the oracle solving
+each system on its own (the per-system stopping status of Section 2.5; the
+CG and BiCGSTAB of Section 3.1 with scalar Jacobi, FP64 and FP32).
+
+Each system is summed in a fixed block-tree order on the GPU and
+sequentially in the oracle, so iterates differ by rounding.  Compared per
+system: the stop reason, the iteration count (within 1 for FP64 CG; within
+max(3, 25%) for BiCGSTAB, whose non-monotone residual makes the step at
+which it crosses the target sensitive to rounding -- the oracle's own count
+on these systems moves by up to 21% when b is perturbed by 1e-16 relative
+noise; within 2 + 5% for CG in FP32
+and max(5, 25%) for BiCGSTAB in FP32, where 1e-6 lies near the attainable
+accuracy), the
+recurred and true residuals, and the solution against the
+oracle's to kappa * tol.  What must hold bit for bit on the GPU (a system's
+result not depending on its neighbours, on the schedule or on the run) is
+checked bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(gk, sys_ptr, A, dtype="f64"):
+    return gk.Batch(sys_ptr, to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), dtype=dtype)
+
+
+def _run(gk, sys_ptr, A, b, kind, jacobi, dtype, tol, x0=None, max_iters=1000, B=None):
+    B = B or _batch(gk, sys_ptr, A, dtype)
+    x = to_dev(np.zeros(int(sys_ptr[-1])) if x0 is None else x0)
+    st = B.solve(to_dev(b), x, kind=kind, jacobi=jacobi, reduction_factor=tol, max_iters=max_iters)
+    return st, to_np(x)
+
+
+def _true_rel(orc, sys_ptr, A, b, x):
+    r = b - orc.spmv(A, x)
+    out = []
+    for s in range(len(sys_ptr) - 1):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        nb = np.linalg.norm(b[r0:r1])
+        out.append(np.linalg.norm(r[r0:r1]) / (nb if nb > 0 else 1.0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
+@pytest.mark.parametrize("jacobi", [True, False])
+def test_batch_fp64_matches_oracle(gk, orc, kind, jacobi):
+    sys_ptr, A = W.batch_varcoef2d(48, seed=5)
+    b = W.uniform_vector(int(sys_ptr[-1]), 21)
+    st, x = _run(gk, sys_ptr, A, b, kind, jacobi, "f64", 1e-10)
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=jacobi, tol=1e-10)
+    for s, r in enumerate(res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        slack = 1 if kind == "cg" else max(3, r.iters // 4)
+        assert st["stop_reason"][s] == r.stop_reason == gk.STOP_CONVERGED
+        assert abs(int(st["iters"][s]) - r.iters) <= slack, (s, st["iters"][s], r.iters)
+        assert st["rel_res"][s] <= 1e-10
+        err = np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1])
+        assert err <= 1e-6, (s, err)
+    assert _true_rel(orc, sys_ptr, A, b, x).max() <= 3e-10
+
+
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
+def test_batch_fp32_matches_oracle(gk, orc, kind):
+    sys_ptr, A = W.batch_varcoef2d(48, seed=6)
+    b = W.uniform_vector(int(sys_ptr[-1]), 22)
+    st, x = _run(gk, sys_ptr, A, b, kind, True, "f32", 1e-6)
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, dtype="f32", tol=1e-6)
+    for s, r in enumerate(res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        assert st["stop_reason"][s] == r.stop_reason == gk.STOP_CONVERGED
+        slack = 2 + r.iters // 20 if kind == "cg" else max(5, r.iters // 4)
+        assert abs(int(st["iters"][s]) - r.iters) <= slack, (s, st["iters"][s], r.iters)
+        assert st["rel_res"][s] <= 1e-6
+        err = np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1])
+        assert err <= 2e-3, (s, err)
+    assert _true_rel(orc, sys_ptr, A, b, x).max() <= 1e-4
+
+
+def test_batch_result_independent_of_neighbours_and_runs(gk):
+    """A system's FP64 result is bit-identical whether it is solved with its
+    neighbours or within another batch, and from run to run."""
+    sys_ptr, A = W.batch_varcoef2d(30, seed=5)
+    b = W.uniform_vector(int(sys_ptr[-1]), 23)
+    st1, x1 = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10)
+    st2, x2 = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10)
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(st1["iters"], st2["iters"])
+    # systems 10..19 alone, as a batch of their own
+    k0, k1 = 10, 20
+    r0, r1 = sys_ptr[k0], sys_ptr[k1]
+    rowptr, col, val = A
+    sub_ptr = sys_ptr[k0:k1 + 1] - r0
+    sub = ((rowptr[r0:r1 + 1] - rowptr[r0]).astype(np.int32), (col[rowptr[r0]:rowptr[r1]] - r0).astype(np.int32),
+           val[rowptr[r0]:rowptr[r1]].copy())
+    st3, x3 = _run(gk, sub_ptr, sub, b[r0:r1], "cg", True, "f64", 1e-10)
+    np.testing.assert_array_equal(x3, x1[r0:r1])
+    np.testing.assert_array_equal(st3["iters"], st1["iters"][k0:k1])
+
+
+def test_batch_initial_guess_zero_rhs_and_max_iters(gk, orc):
+    sys_ptr, A = W.batch_varcoef2d(12, seed=8)
+    n = int(sys_ptr[-1])
+    b = W.uniform_vector(n, 24)
+    # b = 0 on system 3: the criterion becomes absolute and x_0 = 0 is exact
+    b[sys_ptr[3]:sys_ptr[4]] = 0.0
+    x0 = 0.1 * W.uniform_vector(n, 25)
+    x0[sys_ptr[3]:sys_ptr[4]] = 0.0
+    st, x = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10, x0=x0)
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, tol=1e-10, x0=x0)
+    assert st["iters"][3] == 0 and st["stop_reason"][3] == gk.STOP_CONVERGED
+    np.testing.assert_array_equal(x[sys_ptr[3]:sys_ptr[4]], 0.0)
+    for s, r in enumerate(res):
+        assert abs(int(st["iters"][s]) - r.iters) <= 1
+    # the Iteration criterion stops every system after exactly 3 steps
+    st, x = _run(gk, sys_ptr, A, b, "bicgstab", True, "f64", 1e-10, max_iters=3)
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind="bicgstab", jacobi=True, tol=1e-10, max_iters=3)
+    for s, r in enumerate(res):
+        if s == 3:
+            continue
+        assert st["iters"][s] == r.iters == 3
+        assert st["stop_reason"][s] == r.stop_reason == gk.STOP_MAX_ITERS
+        assert st["rel_res"][s] == pytest.approx(r.rel_res, rel=1e-8)
+
+
+def test_batch_edge_sizes(gk, orc):
+    """One-row systems, a single system, and the largest supported size."""
+    # 1x1 systems: one step, x = b / a exactly
+    n = 5
+    sys_ptr = np.arange(n + 1, dtype=np.int64)
+    A = (np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.array([2.0, 4.0, 8.0, 0.5, 1.0]))
+    b = np.array([1.0, -3.0, 5.0, 7.0, 0.25])
+    st, x = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10)
+    np.testing.assert_array_equal(x, b / A[2])
+    assert np.all(st["iters"] == 1)
+    # one 64 x 64 system (4096 rows, the maximum)
+    A = W.varcoef2d(np.exp(0.5 * np.random.default_rng(3).standard_normal((64, 64))))
+    sys_ptr = np.array([0, 4096], dtype=np.int64)
+    b = W.uniform_vector(4096, 26)
+    st, x = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10, max_iters=3000)
+    ref = orc.cg(A, b, P=orc.precond(A, "jacobi"), tol=1e-10, max_iters=3000)
+    assert st["stop_reason"][0] == gk.STOP_CONVERGED
+    assert abs(int(st["iters"][0]) - ref.iters) <= max(2, ref.iters // 30)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    # FP64 BiCGSTAB with Jacobi keeps 8 vectors: 4096 rows do not fit
+    B = _batch(gk, sys_ptr, A)
+    with pytest.raises(gk.GkError) as e:
+        B.solve(to_dev(b), to_dev(np.zeros(4096)), kind="bicgstab", jacobi=True)
+    assert e.value.code == 8
+    # ...but the FP32 form does
+    st, x = _run(gk, sys_ptr, A, b, "bicgstab", True, "f32", 1e-6, max_iters=3000)
+    assert st["stop_reason"][0] == gk.STOP_CONVERGED
+
+
+def test_batch_create_rejects_bad_layouts(gk):
+    sys_ptr, A = W.batch_varcoef2d(4, seed=5)
+    rowptr, col, val = A
+    bad = col.copy()
+    bad[rowptr[sys_ptr[1]]] = sys_ptr[1] - 1  # first row of system 1 reaches into system 0
+    with pytest.raises(gk.GkError) as e:
+        _batch(gk, sys_ptr, (rowptr, bad, val))
+    assert e.value.code == 5
+    with pytest.raises(gk.GkError) as e:  # an empty system
+        _batch(gk, np.concatenate([sys_ptr[:2], sys_ptr[1:]]), A)
+    assert e.value.code == 5
+    big = W.poisson2d(65, 64)  # 4160 rows
+    with pytest.raises(gk.GkError) as e:
+        _batch(gk, np.array([0, 4160], dtype=np.int64), big)
+    assert e.value.code == 8
+
+
+def test_batch_autotune(gk, orc):
+    sys_ptr, A = W.batch_varcoef2d(400, seed=5)
+    b = W.uniform_vector(int(sys_ptr[-1]), 27)
+    B = _batch(gk, sys_ptr, A)
+    info = B.info()
+    sizes = np.diff(sys_ptr)
+    for c in range(gk.BATCH_CLASSES):
+        in_c = (sizes > 16 * 2 ** c) & (sizes <= 32 * 2 ** c) if c else sizes <= 32
+        assert info["counts"][c] == int(in_c.sum())
+        assert info["nmax"][c] == (int(sizes[in_c].max()) if in_c.any() else 0)
+    chosen, times = B.autotune(to_dev(b), kind="cg", jacobi=True, reduction_factor=1e-10)
+    assert set(times) == {c for c in range(gk.BATCH_CLASSES) if info["counts"][c]}
+    for c, t in times.items():
+        assert chosen[c] in gk.BATCH_BLOCK_SIZES
+        assert all(v > 0 for v in t.values())
+        assert t[chosen[c]] == min(t.values())
+    assert B.info()["threads"] == chosen
+    st, x = _run(gk, sys_ptr, A, b, "cg", True, "f64", 1e-10, B=B)
+    assert np.all(st["stop_reason"] == gk.STOP_CONVERGED)
+    sample = [0, 77, 199, 399]
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, tol=1e-10, systems=sample)
+    for s, r in zip(sample, res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        assert abs(int(st["iters"][s]) - r.iters) <= 1
+        assert np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1]) <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+def test_batch_every_block_size_matches_oracle(gk, orc, kind, threads):
+    """Each schedule (one warp per system, or 64 to 256 threads) on every
+    class gives the oracle's per-system result within the rounding bounds."""
+    sys_ptr, A = W.batch_varcoef2d(40, seed=9)
+    b = W.uniform_vector(int(sys_ptr[-1]), 29)
+    B = _batch(gk, sys_ptr, A)
+    B.set_threads([threads] * gk.BATCH_CLASSES, kind=kind, jacobi=True)
+    assert set(B.info(kind=kind)["threads"]) <= {0, threads}
+    st, x = _run(gk, sys_ptr, A, b, kind, True, "f64", 1e-10, B=B)
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, tol=1e-10)
+    for s, r in enumerate(res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        slack = 1 if kind == "cg" else max(3, r.iters // 4)
+        assert st["stop_reason"][s] == r.stop_reason == gk.STOP_CONVERGED
+        assert abs(int(st["iters"][s]) - r.iters) <= slack, (s, st["iters"][s], r.iters)
+        err = np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1])
+        assert err <= 1e-6, (s, err)
+    with pytest.raises(gk.GkError):
+        B.set_threads([48] * gk.BATCH_CLASSES)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-6)])
+def test_batch_full_size_sampled(gk, orc, dtype, tol):
+    """10,000 systems, side U{6..32}: every system converges; a sample is
+    checked against the oracle one by one."""
+    sys_ptr, A = W.batch_varcoef2d(10000, seed=5)
+    b = W.uniform_vector(int(sys_ptr[-1]), 28)
+    st, x = _run(gk, sys_ptr, A, b, "cg", True, dtype, tol)
+    assert np.all(st["stop_reason"] == gk.STOP_CONVERGED)
+    assert st["rel_res"].max() <= tol
+    sample = list(np.random.default_rng(0).choice(10000, 12, replace=False))
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, dtype=dtype, tol=tol, systems=sample)
+    for s, r in zip(sample, res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        assert abs(int(st["iters"][s]) - r.iters) <= (1 if dtype == "f64" else 2 + r.iters // 20)
+        err = np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1])
+        assert err <= (1e-6 if dtype == "f64" else 2e-3)

@@ -1,0 +1,129 @@
+"""CPU pins of the batched-solve oracle: the variable-coefficient workload,
+the block-diagonal batch layout, and CG / BiCGSTAB in single precision
+(closed forms, finite termination, agreement with the FP64 solvers)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def test_varcoef2d_constant_coefficient_is_poisson():
+    """With every cell coefficient 1 the harmonic-mean faces are 1 and the
+    boundary faces 1: the operator is the 5-point Poisson stencil."""
+    for nx, ny in ((5, 5), (7, 4)):
+        A = W.varcoef2d(np.ones((ny, nx)))
+        P = W.poisson2d(nx, ny)
+        for a, p in zip(A, P):
+            np.testing.assert_array_equal(a, p)
+
+
+def test_varcoef2d_faces_and_spd():
+    """Off-diagonal a_ij = -2 c_i c_j / (c_i + c_j); a_ii = the sum of the
+    cell's four faces (boundary faces take c_i); symmetric positive definite."""
+    rng = np.random.default_rng(1)
+    coef = np.exp(0.5 * rng.standard_normal((4, 6)))
+    D = W.csr_to_dense(W.varcoef2d(coef))
+    c = coef.ravel()
+    nx = 6
+    i, j = 7, 8  # horizontal neighbours
+    assert D[i, j] == pytest.approx(-2 * c[i] * c[j] / (c[i] + c[j]), rel=1e-15)
+    i, j = 7, 7 + nx  # vertical neighbours
+    assert D[i, j] == pytest.approx(-2 * c[i] * c[j] / (c[i] + c[j]), rel=1e-15)
+    # corner cell 0: two boundary faces (its own coefficient) + two interior faces
+    expect0 = 2 * c[0] - D[0, 1] - D[0, nx]
+    assert D[0, 0] == pytest.approx(expect0, rel=1e-14)
+    np.testing.assert_array_equal(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
+
+
+def test_batch_layout(orc):
+    """Sizes side^2 with side in [6, 32]; every row references only its own
+    system's columns; an extracted system equals its diagonal block."""
+    sys_ptr, A = W.batch_varcoef2d(40, seed=5)
+    sizes = np.diff(sys_ptr)
+    sides = np.sqrt(sizes).round().astype(int)
+    np.testing.assert_array_equal(sides * sides, sizes)
+    assert sides.min() >= 6 and sides.max() <= 32
+    rowptr, col, _ = A
+    sys_of_row = np.repeat(np.arange(40), sizes)
+    rows = np.repeat(np.arange(sys_ptr[-1]), np.diff(rowptr))
+    assert np.all(sys_of_row[col] == sys_of_row[rows])
+    D = W.csr_to_dense(A)
+    for s in (0, 17, 39):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        sub = orc.batch_system(sys_ptr, A, s)
+        np.testing.assert_array_equal(W.csr_to_dense(sub), D[r0:r1, r0:r1])
+
+
+def test_cg_f32_scaled_identity_closed_form(orc):
+    """A = 4 I with Jacobi: z = r/4, q = A p = r exactly, so alpha = 1 and one
+    step gives x = float(b) / 4 exactly."""
+    n = 300
+    b = W.uniform_vector(n, 3)
+    res = orc.cg_f32(W.scaled_identity(n, 4.0), b, jacobi=True, tol=1e-6)
+    assert res.iters == 1 and res.stop_reason == 1
+    np.testing.assert_array_equal(res.x, b.astype(np.float32).astype(np.float64) / 4.0)
+
+
+@pytest.mark.parametrize("f", ["cg_f32", "bicgstab_f32"])
+def test_f32_finite_termination_on_distinct_eigenvalues(orc, f):
+    """A diagonal SPD matrix with 3 distinct eigenvalues: the Krylov space is
+    3-dimensional, so CG ends in at most 3 steps (BiCGSTAB in at most 3
+    half-steps' worth: iteration count <= 3) up to float rounding."""
+    d = np.repeat([1.0, 3.0, 7.0], 50)
+    A = W.diagonal(d)
+    b = W.uniform_vector(d.size, 4)
+    res = getattr(orc, f)(A, b, jacobi=False, tol=1e-5)
+    assert res.stop_reason == 1
+    assert res.iters <= 3
+    np.testing.assert_allclose(res.x, b / d, rtol=5e-5, atol=5e-5)
+
+
+def test_cg_f32_follows_fp64_cg(orc):
+    """On a variable-coefficient system CG in float takes the FP64 solver's
+    iteration count (within 2) to 1e-6 and lands on its solution to about
+    kappa * 1e-6; a dropped term or a wrong sign would not."""
+    rng = np.random.default_rng(7)
+    A = W.varcoef2d(np.exp(0.5 * rng.standard_normal((20, 20))))
+    xs = W.uniform_vector(400, 8)
+    b = orc.spmv(A, xs)
+    r64 = orc.cg(A, b, P=orc.precond(A, "jacobi"), tol=1e-6)
+    r32 = orc.cg_f32(A, b, jacobi=True, tol=1e-6)
+    assert r32.stop_reason == 1 and abs(r32.iters - r64.iters) <= 2
+    assert r32.rel_res <= 1e-6 and r32.rel_res_true <= 2e-5
+    err = np.linalg.norm(r32.x - r64.x) / np.linalg.norm(r64.x)
+    assert err <= 1e-4
+
+
+def test_bicgstab_f32_follows_fp64_bicgstab(orc):
+    """Nonsymmetric convection-diffusion: the float BiCGSTAB matches the FP64
+    one's iteration count within 2 and its solution to 1e-4."""
+    A = W.convdiff2d(16, 0.5)
+    xs = W.uniform_vector(256, 9)
+    b = orc.spmv(A, xs)
+    r64 = orc.bicgstab(A, b, P=orc.precond(A, "jacobi"), tol=1e-6)
+    r32 = orc.bicgstab_f32(A, b, jacobi=True, tol=1e-6)
+    assert r32.stop_reason == 1 and abs(r32.iters - r64.iters) <= 2
+    assert r32.rel_res_true <= 2e-5
+    assert np.linalg.norm(r32.x - xs) / np.linalg.norm(xs) <= 1e-4
+
+
+def test_f32_jacobi_needs_a_diagonal(orc):
+    rowptr = np.array([0, 1, 2], np.int32)
+    col = np.array([1, 0], np.int32)
+    with pytest.raises(RuntimeError):
+        orc.cg_f32((rowptr, col, np.array([1.0, 1.0])), np.ones(2), jacobi=True)
+
+
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
+def test_batch_oracle_solves_each_system(orc, kind):
+    """Every system of a small batch meets the FP64 criterion on its own:
+    ||b_s - A_s x_s|| <= 1e-10 ||b_s|| (up to the recurrence gap)."""
+    sys_ptr, A = W.batch_varcoef2d(6, seed=11)
+    b = W.uniform_vector(int(sys_ptr[-1]), 12)
+    x, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, tol=1e-10)
+    full = b - orc.spmv(A, x)
+    for s, r in enumerate(res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        assert r.stop_reason == 1
+        assert np.linalg.norm(full[r0:r1]) <= 1e-9 * np.linalg.norm(b[r0:r1])

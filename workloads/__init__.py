@@ -12,7 +12,7 @@ import numpy as np
 
 __all__ = [
     "poisson1d", "poisson2d", "stencil27", "powerlaw", "random_csr", "diagonal",
-    "convdiff2d", "uniform_vector", "csr_to_dense", "scaled_identity",
+    "convdiff2d", "uniform_vector", "csr_to_dense", "scaled_identity", "varcoef2d", "batch_varcoef2d",
 ]
 
 
@@ -179,3 +179,60 @@ def csr_to_dense(A, n_cols: int | None = None):
     rows = np.repeat(np.arange(m), np.diff(rowptr))
     D[rows, col] = val
     return D
+
+
+def varcoef2d(coef):
+    """5-point variable-coefficient diffusion on an (ny, nx) grid of cell
+    coefficients: face coefficient = harmonic mean of the two cells, faces on
+    the boundary take the cell's own coefficient (homogeneous Dirichlet);
+    a_ii = sum of the cell's four faces, a_ij = -face.  SPD."""
+    coef = np.asarray(coef, dtype=np.float64)
+    ny, nx = coef.shape
+    n = nx * ny
+    hm = lambda a, b: 2.0 * a * b / (a + b)
+    west = np.empty_like(coef)
+    east = np.empty_like(coef)
+    south = np.empty_like(coef)
+    north = np.empty_like(coef)
+    west[:, 0] = coef[:, 0]
+    west[:, 1:] = hm(coef[:, 1:], coef[:, :-1])
+    east[:, -1] = coef[:, -1]
+    east[:, :-1] = hm(coef[:, :-1], coef[:, 1:])
+    south[0, :] = coef[0, :]
+    south[1:, :] = hm(coef[1:, :], coef[:-1, :])
+    north[-1, :] = coef[-1, :]
+    north[:-1, :] = hm(coef[:-1, :], coef[1:, :])
+    diag = (west + east + south + north).ravel()
+    offs = [(-1, 0), (0, -1), (0, 0), (0, 1), (1, 0)]
+    rowptr, col, _ = _from_offsets((ny, nx), offs, [1.0] * 5)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    delta = col.astype(np.int64) - rows
+    val = np.empty(col.size)
+    val[delta == 0] = diag[rows[delta == 0]]
+    val[delta == -nx] = -south.ravel()[rows[delta == -nx]]
+    val[delta == nx] = -north.ravel()[rows[delta == nx]]
+    val[delta == -1] = -west.ravel()[rows[delta == -1]]
+    val[delta == 1] = -east.ravel()[rows[delta == 1]]
+    return _finish(rowptr, col, val)
+
+
+def batch_varcoef2d(n_sys: int, seed: int = 5, side_lo: int = 6, side_hi: int = 32, sigma: float = 0.5):
+    """Batch of independent 2D variable-coefficient systems: side ~ U{lo..hi},
+    cell coefficients log-normal(0, sigma).  Returns (sys_ptr int64[n_sys+1],
+    block-diagonal CSR triple)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, size=n_sys)
+    rps, cols, vals = [], [], []
+    sys_ptr = np.zeros(n_sys + 1, dtype=np.int64)
+    nnz_off = 0
+    for s, side in enumerate(sides):
+        coef = np.exp(sigma * rng.standard_normal((side, side)))
+        rp, c, v = varcoef2d(coef)
+        r0 = sys_ptr[s]
+        sys_ptr[s + 1] = r0 + side * side
+        rps.append(rp[:-1].astype(np.int64) + nnz_off)
+        cols.append(c.astype(np.int64) + r0)
+        vals.append(v)
+        nnz_off += c.size
+    rowptr = np.concatenate(rps + [np.array([nnz_off])])
+    return sys_ptr, _finish(rowptr, np.concatenate(cols), np.concatenate(vals))

@@ -234,9 +234,12 @@ GK_API int gk_solver_get_info(gk_solver S, gk_solver_info* info);
 typedef struct gk_batch_s* gk_batch;
 
 typedef struct {
-  int32_t iters;
+  int32_t iters;        /* iterations (GK_IR_CG: inner iterations, all steps)  */
   int32_t stop_reason;  /* GK_STOP_* per system                              */
-  double rel_res;       /* recurred ||r|| / ||b|| (or / ||r_0||) at exit      */
+  double rel_res;       /* recurred ||r|| / ||b|| (or / ||r_0||) at exit;
+                           GK_IR_CG: the last FP64 residual                  */
+  int32_t outer_iters;  /* GK_IR_CG: refinement steps; else 0                */
+  int32_t reserved_;
 } gk_batch_status;
 
 GK_API int gk_batch_create(int64_t n_sys, const int64_t* sys_ptr, int64_t nnz, const int32_t* rowptr,
@@ -247,7 +250,13 @@ GK_API int gk_batch_create(int64_t n_sys, const int64_t* sys_ptr, int64_t nnz, c
 #define GK_BATCH_CLASSES 8
 
 /* Solves every system with CG or BiCGSTAB (kind), scalar Jacobi if
- * jacobi != 0, in one CUDA graph launch: each size class is one persistent
+ * jacobi != 0, in one CUDA graph launch.  kind GK_IR_CG (FP64 batches
+ * only) is the iterative refinement of gk_solver_generate per system: FP64
+ * residual, criteria and update on the FP64 values, FP32 CG corrections on
+ * an FP32 copy with the FP64 inverse diagonal rounded to FP32, inner stop
+ * by crit->inner_reduction / inner_max_iters as for gk_solve, at most 200
+ * refinement steps; it reaches FP64 residuals with FP32 inner work.  In
+ * every kind: each size class is one persistent
  * kernel (the classes run side by side as independent graph branches); a
  * thread block holds one system at a time with its vectors in shared memory
  * and takes the class's systems in decreasing size.  Each system's result

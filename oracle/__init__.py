@@ -312,9 +312,11 @@ def batch_system(sys_ptr, A, s):
 
 
 def batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, dtype="f64", systems=None, x0=None, **kw):
-    """Solve the independent systems one after another (each by cg / bicgstab
-    or their FP32 forms).  Returns (x, list of SolveResult) over `systems`
-    (default: all); entries of x outside those systems are left at x0."""
+    """Solve the independent systems one after another (each by cg /
+    bicgstab, their FP32 forms, or ir_cg -- whose results carry the number
+    of refinement steps as `.outer`).  Returns (x, list of SolveResult) over
+    `systems` (default: all); entries of x outside those systems are left at
+    x0."""
     n = int(sys_ptr[-1])
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     systems = range(len(sys_ptr) - 1) if systems is None else systems
@@ -322,7 +324,11 @@ def batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, dtype="f64", systems=None
     for s in systems:
         r0, r1 = int(sys_ptr[s]), int(sys_ptr[s + 1])
         sub = batch_system(sys_ptr, A, s)
-        if dtype == "f32":
+        if kind == "ir_cg":
+            P = precond(sub, "jacobi") if jacobi else None
+            res, outer = ir_cg(sub, b[r0:r1], x0=x[r0:r1], P=P, **kw)
+            res.outer = outer
+        elif dtype == "f32":
             f = cg_f32 if kind == "cg" else bicgstab_f32
             res = f(sub, b[r0:r1], x0=x[r0:r1], jacobi=jacobi, **kw)
         else:

@@ -70,7 +70,8 @@ class SolverInfo(ctypes.Structure):
 
 
 class BatchStatus(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int32), ("stop_reason", ctypes.c_int32), ("rel_res", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int32), ("stop_reason", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("outer_iters", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -352,17 +353,20 @@ class Batch:
         self.nnz = nnz
 
     @staticmethod
-    def _crit(max_iters, reduction_factor, rel_to_b):
-        return Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, 0, 0.0, 0.0, 0, 0)
+    def _crit(max_iters, reduction_factor, rel_to_b, inner_reduction=0.0, inner_max_iters=0):
+        return Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, 0, 0.0,
+                        float(inner_reduction), int(inner_max_iters), 0)
 
     def solve(self, b, x, kind: str = "cg", jacobi: bool = True, max_iters: int = 1000,
-              reduction_factor: float = 1e-10, rel_to_b: bool = True, status: bool = True, stream=None):
-        """Solve every system (x: initial guesses in, solutions out).  Returns
-        a dict of numpy arrays (iters, stop_reason, rel_res) when status."""
+              reduction_factor: float = 1e-10, rel_to_b: bool = True, status: bool = True,
+              inner_reduction: float = 0.0, inner_max_iters: int = 0, stream=None):
+        """Solve every system (x: initial guesses in, solutions out); kind cg,
+        bicgstab or ir_cg.  Returns a dict of numpy arrays (iters,
+        stop_reason, rel_res, outer_iters) when status."""
         import numpy as np
         _check_vec(b, self.n_rows, "b")
         _check_vec(x, self.n_rows, "x")
-        crit = self._crit(max_iters, reduction_factor, rel_to_b)
+        crit = self._crit(max_iters, reduction_factor, rel_to_b, inner_reduction, inner_max_iters)
         st = (BatchStatus * self.n_sys)() if status else None
         _check(lib().gk_batch_solve(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.byref(crit),
                                     _ptr(b), _ptr(x), ctypes.addressof(st) if status else None,
@@ -370,16 +374,17 @@ class Batch:
         if not status:
             return None
         raw = np.frombuffer(st, dtype=np.dtype([("iters", np.int32), ("stop_reason", np.int32),
-                                                ("rel_res", np.float64)]))
-        return {"iters": raw["iters"].copy(), "stop_reason": raw["stop_reason"].copy(),
-                "rel_res": raw["rel_res"].copy()}
+                                                ("rel_res", np.float64), ("outer_iters", np.int32),
+                                                ("reserved_", np.int32)]))
+        return {k: raw[k].copy() for k in ("iters", "stop_reason", "rel_res", "outer_iters")}
 
     def autotune(self, b, kind: str = "cg", jacobi: bool = True, max_iters: int = 1000,
-                 reduction_factor: float = 1e-10, rel_to_b: bool = True, stream=None):
+                 reduction_factor: float = 1e-10, rel_to_b: bool = True, inner_reduction: float = 0.0,
+                 inner_max_iters: int = 0, stream=None):
         """Time block sizes 32/64/128/256 per size class and keep the fastest.
         Returns (chosen sizes per class, {class: {size: ms}}) over non-empty classes."""
         _check_vec(b, self.n_rows, "b")
-        crit = self._crit(max_iters, reduction_factor, rel_to_b)
+        crit = self._crit(max_iters, reduction_factor, rel_to_b, inner_reduction, inner_max_iters)
         t = (ctypes.c_int32 * BATCH_CLASSES)()
         ms = (ctypes.c_double * (4 * BATCH_CLASSES))()
         _check(lib().gk_batch_autotune(self.handle, SOLVERS[kind], 1 if jacobi else 0, ctypes.byref(crit),

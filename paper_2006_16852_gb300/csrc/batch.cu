@@ -52,15 +52,20 @@ struct BatchArgs {
   const int32_t* ell_w;     // per system: ELL width
   const uint16_t* ell_col;  // local column indices
   const void* ell_val;      // values in the solve precision
+  const float* ell_val32;   // FP32 copy of FP64 values (refinement inner solves)
   const double* b;
   double* x;
   gk_batch_status* st;
   unsigned int* next;  // this class's counter
   long long max_iters;
   double factor;
+  double inner_red;          // refinement: inner reduction target
+  long long inner_max;       // refinement: inner iteration limit
   int rel_to_b;
   int k0, count, nmax;
 };
+
+constexpr int kBatchMaxOuter = 200;  // refinement steps per system
 
 // ---------------------------------------------------------------------------
 // Reductions.  The totals of K per-thread values are formed in a fixed order
@@ -144,6 +149,7 @@ __device__ __forceinline__ void sys_finish(const BatchArgs& a, const T* X, int s
     a.st[sys].iters = static_cast<int32_t>(it);
     a.st[sys].stop_reason = stop;
     a.st[sys].rel_res = rnorm / ref;
+    a.st[sys].outer_iters = 0;
   }
 }
 
@@ -370,10 +376,175 @@ __device__ void bicg_system(const BatchArgs& a, T* V, T* red, double* sc, int sy
   sys_finish<T>(a, X, sys, r0, n, it, stop, rnorm, ref);
 }
 
-// Vectors of nmax entries a block keeps in shared memory.
-__host__ __device__ constexpr int batch_nvec(int kind, bool jac) {
-  return kind == GK_CG ? (jac ? 5 : 4) : (jac ? 8 : 6);
+// Iterative refinement (Sections 2.2.3 and 3.1) per system: the residual
+// r = b - A x, its norm, the criteria and the update x = x + ||r|| d in FP64
+// on the FP64 values; the correction d from CG in FP32 on the FP32 copy of A
+// (FP32 vectors and sums) for A d = r / ||r||, stopped once its residual is
+// reduced by max(inner_reduction, tol / (2 ||r||)) or after inner_max
+// iterations.  Jacobi: the FP64 inverse diagonal rounded to FP32.
+// Shared memory: x and r in FP64, then r, p, q (z between the updates), d
+// and the inverse diagonal in FP32.
+template <bool JAC, bool WARP>
+__device__ void ir_system(const BatchArgs& a, unsigned char* smem, double* redd, double* sc, int sys, int r0,
+                          int n) {
+  const SysMat<double> m64 = sys_mat<double>(a, sys, n);
+  const SysMat<float> m32{a.ell_val32 + a.ell_off[sys], m64.col, n, m64.w};
+  const int nm = a.nmax;
+  double* X = reinterpret_cast<double*>(smem);
+  double* R64 = X + nm;
+  float* R = reinterpret_cast<float*>(R64 + nm);
+  float *P = R + nm, *Q = R + 2 * nm, *DX = R + 3 * nm, *D = R + 4 * nm;
+  float* redf = reinterpret_cast<float*>(redd);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    X[i] = a.x[r0 + i];
+    if (JAC) {
+      double d = 0.0;
+      for (int k = 0; k < m64.w; ++k)
+        if (m64.col[k * n + i] == i) {
+          d = m64.val[k * n + i];
+          break;
+        }
+      D[i] = d != 0.0 ? static_cast<float>(1.0 / d) : 1.0f;
+    }
+  }
+  __syncthreads();
+  long long k_total = 0;
+  int steps = 0, stop = GK_STOP_NONE;
+  double rnorm = 0.0, ref = 1.0, tol = 0.0;
+  const int rel_to_b = a.rel_to_b;
+  for (;;) {
+    // FP64 residual and its norm (and ||b|| on the first step)
+    sys_spmv<double>(m64, X, R64);
+    double s2[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double bi = a.b[r0 + i];
+      const double ri = bi - R64[i];
+      R64[i] = ri;
+      s2[0] = fma(ri, ri, s2[0]);
+      s2[1] = fma(bi, bi, s2[1]);
+    }
+    double o[3];
+    const bool first = steps == 0;
+    const double ref_prev = ref;
+    reduce<WARP>(s2, redd, sc, o, [&](double(&t)[2], double(&out)[3]) {
+      const double rn = sqrt(t[0]);
+      double rf = ref_prev;
+      if (first) {
+        rf = rel_to_b ? sqrt(t[1]) : rn;
+        if (rf == 0.0) rf = 1.0;
+      }
+      out[0] = rn;
+      out[1] = rf;
+      out[2] = 1.0 / rn;
+    });
+    rnorm = o[0];
+    ref = o[1];
+    const double inv = o[2];
+    if (first) tol = a.factor * ref;
+    stop = sys_check(rnorm, tol, k_total, a.max_iters);
+    if (stop != GK_STOP_NONE || steps >= kBatchMaxOuter) {
+      if (stop == GK_STOP_NONE) stop = GK_STOP_MAX_ITERS;
+      break;
+    }
+    // FP32 inner CG on A d = r / ||r|| from d = 0
+    float v2[2] = {0.0f, 0.0f};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float ri = static_cast<float>(R64[i] * inv);
+      R[i] = ri;
+      DX[i] = 0.0f;
+      const float z = JAC ? D[i] * ri : ri;
+      P[i] = z;
+      v2[0] = fmaf(ri, z, v2[0]);
+      v2[1] = fmaf(ri, ri, v2[1]);
+    }
+    double oi[2];
+    const double inner_red = a.inner_red;
+    reduce<WARP>(v2, redf, sc, oi, [&](float(&t)[2], double(&out)[2]) {
+      const double red = fmax(inner_red, 0.5 * tol / rnorm);
+      out[0] = static_cast<double>(t[0]);
+      out[1] = red * red * static_cast<double>(t[1]);
+    });
+    float rho = static_cast<float>(oi[0]);
+    const double tol2 = oi[1];
+    long long it = 0;
+    bool broke = false;
+    while (it < a.inner_max) {
+      sys_spmv<float>(m32, P, Q);
+      float sg[1] = {0.0f};
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sg[0] = fmaf(P[i], Q[i], sg[0]);
+      double oa[2];
+      reduce<WARP>(sg, redf, sc, oa, [&](float(&t)[1], double(&out)[2]) {
+        const float sigma = t[0];
+        const bool bad = !isfinite(sigma) || sigma <= 0.0f;
+        out[0] = bad ? 0.0 : static_cast<double>(static_cast<float>(static_cast<double>(rho) / sigma));
+        out[1] = bad ? 1.0 : 0.0;
+      });
+      if (oa[1] != 0.0) {
+        broke = true;
+        break;
+      }
+      const float alpha = static_cast<float>(oa[0]);
+      float v[2] = {0.0f, 0.0f};
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        DX[i] = fmaf(alpha, P[i], DX[i]);
+        const float rn = fmaf(-alpha, Q[i], R[i]);
+        R[i] = rn;
+        const float z = JAC ? D[i] * rn : rn;
+        if (JAC) Q[i] = z;
+        v[0] = fmaf(rn, z, v[0]);
+        v[1] = fmaf(rn, rn, v[1]);
+      }
+      double ob[3];
+      reduce<WARP>(v, redf, sc, ob, [&](float(&t)[2], double(&out)[3]) {
+        // out[2]: 0 go on, 1 broke (not finite), 2 inner target reached
+        const bool bad = !isfinite(t[0]) || !isfinite(t[1]);
+        out[0] = static_cast<double>(t[0]);
+        out[1] = bad ? 0.0 : static_cast<double>(static_cast<float>(static_cast<double>(t[0]) / rho));
+        out[2] = bad ? 1.0 : (static_cast<double>(t[1]) <= tol2 ? 2.0 : 0.0);
+      });
+      ++it;
+      if (ob[2] == 1.0) {
+        broke = true;
+        break;
+      }
+      if (ob[2] == 2.0) break;
+      const float beta = static_cast<float>(ob[1]);
+      rho = static_cast<float>(ob[0]);
+      const float* Z = JAC ? Q : R;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) P[i] = fmaf(beta, P[i], Z[i]);
+      __syncthreads();
+    }
+    // x = x + ||r|| d in FP64
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[i] = fma(rnorm, static_cast<double>(DX[i]), X[i]);
+    __syncthreads();
+    k_total += it;
+    ++steps;
+    if (it == 0 || (broke && it <= 1)) {
+      stop = GK_STOP_BREAKDOWN;
+      break;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.x[r0 + i] = X[i];
+  if (threadIdx.x == 0 && a.st) {
+    a.st[sys].iters = static_cast<int32_t>(k_total);
+    a.st[sys].stop_reason = stop;
+    a.st[sys].rel_res = rnorm / ref;
+    a.st[sys].outer_iters = steps;
+  }
 }
+
+// Shared-memory bytes per row a block keeps for one system.
+__host__ __device__ constexpr int batch_row_bytes(int kind, bool jac, int el) {
+  return kind == GK_CG ? el * (jac ? 5 : 4)
+                       : (kind == GK_BICGSTAB ? el * (jac ? 8 : 6) : 16 + 4 * (jac ? 5 : 4));
+}
+
+// Offset of the reduction scratch (16-byte aligned) behind the vectors.
+__host__ __device__ constexpr size_t batch_red_offset(int kind, bool jac, int el, int nmax) {
+  return (static_cast<size_t>(batch_row_bytes(kind, jac, el)) * nmax + 15) / 16 * 16;
+}
+
 
 template <typename T, int KIND, bool JAC, bool WARP>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
@@ -381,7 +552,8 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
   __shared__ double s_sc[4];
   __shared__ int s_k;
   T* V = reinterpret_cast<T*>(bsm);
-  T* red = V + batch_nvec(KIND, JAC) * a.nmax;
+  unsigned char* redp = bsm + batch_red_offset(KIND, JAC, static_cast<int>(sizeof(T)), a.nmax);
+  T* red = reinterpret_cast<T*>(redp);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_k = static_cast<int>(atomicAdd(a.next, 1u));
@@ -390,8 +562,9 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
     if (k >= a.count) break;
     const int sys = a.order[a.k0 + k];
     const int r0 = a.sys_ptr[sys], n = a.sys_ptr[sys + 1] - r0;
-    if (KIND == GK_CG) cg_system<T, JAC, WARP>(a, V, red, s_sc, sys, r0, n);
-    else bicg_system<T, JAC, WARP>(a, V, red, s_sc, sys, r0, n);
+    if constexpr (KIND == GK_CG) cg_system<T, JAC, WARP>(a, V, red, s_sc, sys, r0, n);
+    else if constexpr (KIND == GK_BICGSTAB) bicg_system<T, JAC, WARP>(a, V, red, s_sc, sys, r0, n);
+    else ir_system<JAC, WARP>(a, bsm, reinterpret_cast<double*>(redp), s_sc, sys, r0, n);
   }
 }
 
@@ -449,6 +622,7 @@ BatchFn pick_t(int kind, bool jac, bool warp) {
 
 BatchFn pick_kernel(int dtype, int kind, bool jac, int threads) {
   const bool warp = threads == 32;
+  if (kind == GK_IR_CG) return jac ? pick_w<double, GK_IR_CG, true>(warp) : pick_w<double, GK_IR_CG, false>(warp);
   return dtype == GK_F32 ? pick_t<float>(kind, jac, warp) : pick_t<double>(kind, jac, warp);
 }
 
@@ -470,10 +644,11 @@ struct Batch {
   int32_t* ell_w = nullptr;
   uint16_t* ell_col = nullptr;
   void* ell_val = nullptr;
+  float* ell_val32 = nullptr;  // FP64 batches: FP32 copy for refinement
   unsigned int* next = nullptr;  // one counter per class
   gk_batch_status* st = nullptr;
   double* xtune = nullptr;
-  int threads[2][2][kBatchClasses] = {};  // [kind][jacobi][class]; 0 = default
+  int threads[3][2][kBatchClasses] = {};  // [kind][jacobi][class]; 0 = default
   int64_t device_bytes = 0;
   cudaGraphExec_t exec = nullptr;  // graph of the last configuration solved
   uint64_t key[8 + kBatchClasses] = {};
@@ -488,7 +663,7 @@ struct ClassPlan {
 };
 
 int class_threads(const Batch& B, int kind, int jac, int c) {
-  const int t = B.threads[kind == GK_CG ? 0 : 1][jac ? 1 : 0][c];
+  const int t = B.threads[kind][jac ? 1 : 0][c];
   return t > 0 ? t : default_threads(c);
 }
 
@@ -498,7 +673,8 @@ int plan_class(const Batch& B, int kind, int jac, int c, int threads, ClassPlan*
   const BatchClass& k = B.cls[c];
   const size_t el = B.dtype == GK_F32 ? 4 : 8;
   p->threads = threads;
-  p->smem = el * (static_cast<size_t>(batch_nvec(kind, jac != 0)) * k.nmax + 2 * static_cast<size_t>(threads)) + 16;
+  const int elk = kind == GK_IR_CG ? 8 : static_cast<int>(el);
+  p->smem = batch_red_offset(kind, jac != 0, elk, k.nmax) + 16 * static_cast<size_t>(threads) + 16;
   p->fn = pick_kernel(B.dtype, kind, jac != 0, threads);
   int smem_max = 0;
   GK_TRY_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, B.device));
@@ -522,6 +698,7 @@ BatchArgs class_args(const Batch& B, const gk_criteria& c, const double* b, doub
   a.ell_w = B.ell_w;
   a.ell_col = B.ell_col;
   a.ell_val = B.ell_val;
+  a.ell_val32 = B.ell_val32;
   a.b = b;
   a.x = x;
   a.st = B.st;
@@ -529,6 +706,8 @@ BatchArgs class_args(const Batch& B, const gk_criteria& c, const double* b, doub
   a.max_iters = c.max_iters;
   a.factor = c.reduction_factor;
   a.rel_to_b = c.rel_to_b;
+  a.inner_red = c.inner_reduction > 0 ? c.inner_reduction : 1e-5;
+  a.inner_max = c.inner_max_iters > 0 ? c.inner_max_iters : std::max<int64_t>(c.max_iters, 1);
   a.k0 = B.cls[cl].k0;
   a.count = B.cls[cl].count;
   a.nmax = B.cls[cl].nmax;
@@ -546,7 +725,8 @@ void batch_release(Batch* B) {
   const int prev = current_device();
   cudaSetDevice(B->device);
   if (B->exec) cudaGraphExecDestroy(B->exec);
-  void* ptrs[] = {B->sys_ptr, B->order, B->ell_off, B->ell_w, B->ell_col, B->ell_val, B->next, B->st, B->xtune};
+  void* ptrs[] = {B->sys_ptr, B->order,  B->ell_off, B->ell_w, B->ell_col, B->ell_val,
+                  B->ell_val32, B->next, B->st,     B->xtune};
   for (void* p : ptrs) dfree(p);
   cudaSetDevice(prev);
   delete B;
@@ -557,7 +737,15 @@ struct BatchDeleter {
 };
 
 int check_kind(int32_t kind) {
-  if (kind != GK_CG && kind != GK_BICGSTAB) return set_error(GK_ERR_ARG, "batch: kind must be GK_CG or GK_BICGSTAB");
+  if (kind != GK_CG && kind != GK_BICGSTAB && kind != GK_IR_CG)
+    return set_error(GK_ERR_ARG, "batch: kind must be GK_CG, GK_BICGSTAB or GK_IR_CG");
+  return GK_OK;
+}
+
+int check_kind(const Batch& B, int32_t kind) {
+  GK_TRY(check_kind(kind));
+  if (kind == GK_IR_CG && B.dtype != GK_F64)
+    return set_error(GK_ERR_ARG, "batch: GK_IR_CG needs an FP64 batch (its residuals use the FP64 values)");
   return GK_OK;
 }
 
@@ -717,6 +905,12 @@ extern "C" int gk_batch_create(int64_t n_sys, const int64_t* sys_ptr, int64_t nn
                                                 static_cast<int>(n_sys), static_cast<double*>(B->ell_val),
                                                 B->ell_col);
   GK_TRY_CUDA(cudaGetLastError());
+  if (dtype == GK_F64) {
+    GK_TRY(dalloc_n(&B->ell_val32, static_cast<size_t>(std::max<int64_t>(total, 1)), by));
+    batch_ell_kernel<float><<<eg, 128, 0, s>>>(B->sys_ptr, d.rowptr, d.col, d.val, B->ell_off, B->ell_w,
+                                               static_cast<int>(n_sys), B->ell_val32, B->ell_col);
+    GK_TRY_CUDA(cudaGetLastError());
+  }
   GK_TRY_CUDA(cudaStreamSynchronize(s));
   *out = reinterpret_cast<gk_batch>(hold.release());
   return GK_OK;
@@ -726,7 +920,7 @@ extern "C" int gk_batch_solve(gk_batch h, int32_t kind, int32_t jacobi, const gk
                               void* x, gk_batch_status* st, void* stream) {
   Batch* B = reinterpret_cast<Batch*>(h);
   if (!B || !crit || !b || !x) return set_error(GK_ERR_ARG, "gk_batch_solve: NULL argument");
-  GK_TRY(check_kind(kind));
+  GK_TRY(check_kind(*B, kind));
   const int prev = current_device();
   if (prev != B->device) cudaSetDevice(B->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -741,6 +935,8 @@ extern "C" int gk_batch_solve(gk_batch h, int32_t kind, int32_t jacobi, const gk
     key[4] = static_cast<uint64_t>(crit->max_iters);
     memcpy(&key[5], &crit->reduction_factor, sizeof(double));
     key[6] = static_cast<uint64_t>(crit->rel_to_b);
+    memcpy(&key[7], &crit->inner_reduction, sizeof(double));
+    key[7] ^= static_cast<uint64_t>(static_cast<uint32_t>(crit->inner_max_iters)) * 0x9E3779B97F4A7C15ull;
     for (int c = 0; c < kBatchClasses; ++c) key[8 + c] = static_cast<uint64_t>(class_threads(*B, kind, jacobi, c));
     if (!B->exec || memcmp(key, B->key, sizeof(key)) != 0) {
       if (B->exec) {
@@ -801,7 +997,7 @@ extern "C" int gk_batch_set_threads(gk_batch h, int32_t kind, int32_t jacobi, co
     if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256)
       return set_error(GK_ERR_ARG, "gk_batch_set_threads: block size %d (0, 32, 64, 128 or 256)", t);
   }
-  for (int c = 0; c < kBatchClasses; ++c) B->threads[kind == GK_CG ? 0 : 1][jacobi ? 1 : 0][c] = threads[c];
+  for (int c = 0; c < kBatchClasses; ++c) B->threads[kind][jacobi ? 1 : 0][c] = threads[c];
   return GK_OK;
 }
 
@@ -822,7 +1018,7 @@ extern "C" int gk_batch_autotune(gk_batch h, int32_t kind, int32_t jacobi, const
                                  int32_t* threads, double* times_ms, void* stream) {
   Batch* B = reinterpret_cast<Batch*>(h);
   if (!B || !crit || !b) return set_error(GK_ERR_ARG, "gk_batch_autotune: NULL argument");
-  GK_TRY(check_kind(kind));
+  GK_TRY(check_kind(*B, kind));
   const int prev = current_device();
   if (prev != B->device) cudaSetDevice(B->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -880,7 +1076,7 @@ extern "C" int gk_batch_autotune(gk_batch h, int32_t kind, int32_t jacobi, const
     }
     if (rc != GK_OK) break;
     for (int c = 0; c < kBatchClasses; ++c) {
-      B->threads[kind == GK_CG ? 0 : 1][jacobi ? 1 : 0][c] = chosen[c];
+      B->threads[kind][jacobi ? 1 : 0][c] = chosen[c];
       if (threads) threads[c] = chosen[c];
     }
   } while (false);

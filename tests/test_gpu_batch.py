@@ -81,6 +81,33 @@ def test_batch_fp32_matches_oracle(gk, orc, kind):
     assert _true_rel(orc, sys_ptr, A, b, x).max() <= 1e-4
 
 
+def test_batch_refinement_matches_oracle(gk, orc):
+    """FP64 refinement around FP32 CG per system: the same number of
+    refinement steps as the oracle (within 1), inner iterations within 10%
+    + 3 per step, the FP64 criterion met on the true residual, and the
+    solution of FP64 CG to kappa * tol."""
+    sys_ptr, A = W.batch_varcoef2d(48, seed=15)
+    b = W.uniform_vector(int(sys_ptr[-1]), 31)
+    for jac in (True, False):
+        st, x = _run(gk, sys_ptr, A, b, "ir_cg", jac, "f64", 1e-10, max_iters=20000)
+        xo, res = orc.batch_solve(sys_ptr, A, b, kind="ir_cg", jacobi=jac, tol=1e-10, max_iters=20000)
+        x64, _ = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=jac, tol=1e-10, max_iters=20000)
+        for s, r in enumerate(res):
+            r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+            assert st["stop_reason"][s] == r.stop_reason == gk.STOP_CONVERGED
+            assert abs(int(st["outer_iters"][s]) - r.outer) <= 1, (s, st["outer_iters"][s], r.outer)
+            assert abs(int(st["iters"][s]) - r.iters) <= r.iters // 10 + 3 * r.outer, (s, st["iters"][s], r.iters)
+            assert st["rel_res"][s] <= 1e-10
+            err = np.linalg.norm(x[r0:r1] - x64[r0:r1]) / np.linalg.norm(x64[r0:r1])
+            assert err <= 1e-6, (s, err)
+        assert _true_rel(orc, sys_ptr, A, b, x).max() <= 1e-10
+    # refinement needs the FP64 values: an FP32 batch refuses it
+    B32 = _batch(gk, sys_ptr, A, "f32")
+    with pytest.raises(gk.GkError) as e:
+        B32.solve(to_dev(b), to_dev(np.zeros(int(sys_ptr[-1]))), kind="ir_cg")
+    assert e.value.code == 1
+
+
 def test_batch_result_independent_of_neighbours_and_runs(gk):
     """A system's FP64 result is bit-identical whether it is solved with its
     neighbours or within another batch, and from run to run."""

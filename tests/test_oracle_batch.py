@@ -48,11 +48,15 @@ def test_batch_layout(orc):
     sys_of_row = np.repeat(np.arange(40), sizes)
     rows = np.repeat(np.arange(sys_ptr[-1]), np.diff(rowptr))
     assert np.all(sys_of_row[col] == sys_of_row[rows])
-    D = W.csr_to_dense(A)
+    rowptr, col, val = A
     for s in (0, 17, 39):
         r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        D = np.zeros((r1 - r0, int(sys_ptr[-1])))
+        for r in range(r0, r1):
+            D[r - r0, col[rowptr[r]:rowptr[r + 1]]] = val[rowptr[r]:rowptr[r + 1]]
         sub = orc.batch_system(sys_ptr, A, s)
-        np.testing.assert_array_equal(W.csr_to_dense(sub), D[r0:r1, r0:r1])
+        np.testing.assert_array_equal(W.csr_to_dense(sub), D[:, r0:r1])
+        assert not D[:, :r0].any() and not D[:, r1:].any()
 
 
 def test_cg_f32_scaled_identity_closed_form(orc):
@@ -127,3 +131,18 @@ def test_batch_oracle_solves_each_system(orc, kind):
         r0, r1 = sys_ptr[s], sys_ptr[s + 1]
         assert r.stop_reason == 1
         assert np.linalg.norm(full[r0:r1]) <= 1e-9 * np.linalg.norm(b[r0:r1])
+
+
+def test_batch_oracle_refinement_reaches_fp64_residual(orc):
+    """Refinement with FP32 inner solves reaches the FP64 criterion on every
+    system in a few steps, and lands on the FP64 CG solution to kappa*tol."""
+    sys_ptr, A = W.batch_varcoef2d(5, seed=13)
+    b = W.uniform_vector(int(sys_ptr[-1]), 14)
+    x, res = orc.batch_solve(sys_ptr, A, b, kind="ir_cg", jacobi=True, tol=1e-10)
+    x64, _ = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, tol=1e-10)
+    full = b - orc.spmv(A, x)
+    for s, r in enumerate(res):
+        r0, r1 = sys_ptr[s], sys_ptr[s + 1]
+        assert r.stop_reason == 1 and 2 <= r.outer <= 6
+        assert np.linalg.norm(full[r0:r1]) <= 1e-10 * np.linalg.norm(b[r0:r1])
+        assert np.linalg.norm(x[r0:r1] - x64[r0:r1]) <= 1e-6 * np.linalg.norm(x64[r0:r1])

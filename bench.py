@@ -20,6 +20,11 @@ workload:
   * (b) Jacobi-CG and block-Jacobi BiCGSTAB to 1e-10 (HYB)
 
 value = algorithmic bytes of the step / device time of the step (GB/s).
+
+Beside the step (not part of its value) the line carries "batched": 10,000
+small variable-coefficient systems solved per system in one graph launch
+(FP64 CG / BiCGSTAB / refinement to 1e-10, FP32 CG / BiCGSTAB to 1e-6), with
+solves/s and the time against plain FP64 CG on the block-diagonal matrix.
 Inputs are larger than the 129 MB L2 (711 MB and ~371 MB per SpMV).
 """
 from __future__ import annotations
@@ -386,6 +391,110 @@ class GpuStep:
         return solve_launches(sk, st.iters, st.spmvs, spmv_launches(info))
 
 
+# ---------------------------------------------------------------------------
+# batched small systems (reported beside the step, not part of its value)
+# ---------------------------------------------------------------------------
+
+BATCH_WORKLOAD = ("10,000 independent SPD systems, 2D 5-point variable-coefficient diffusion (cell coefficients "
+                  "log-normal sigma=0.5, harmonic-mean faces, Dirichlet), grid side U{6..32} (n 36..1024), seed 5; "
+                  "b uniform[-1,1], x0 = 0")
+# nominal FP64 rate of a GB300 (the batched FP64 solves are bound by the FP64 pipe)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def batch_fp64_flops(kind, jac, iters, nnz_s, n_s):
+    """FP64 flops (2 per fused multiply-add) of the batched FP64 solves: per
+    CG iteration a row costs its nonzeros + 7 FMA-class operations with Jacobi
+    (sigma, x, r, z, r.z, r.r, p) or + 6 without; BiCGSTAB: 2 SpMVs + 14 (+2
+    with Jacobi); plus the initial residual."""
+    per_row = {"cg": 7 if jac else 6, "bicgstab": 16 if jac else 14}[kind]
+    spmvs = 2 if kind == "bicgstab" else 1
+    return 2.0 * float(np.sum(iters * (spmvs * nnz_s + per_row * n_s) + nnz_s + 2 * n_s))
+
+
+def run_batched(dev, reps=3, n_sys=10000):
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    sys_ptr, A = W.batch_varcoef2d(n_sys, seed=5)
+    n = int(sys_ptr[-1])
+    rowptr = A[0]
+    nnz_s = (rowptr[sys_ptr[1:]] - rowptr[sys_ptr[:-1]]).astype(np.float64)
+    n_s = np.diff(sys_ptr).astype(np.float64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dA = [t(a) for a in A]
+    b = t(W.uniform_vector(n, 28))
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    forms = {}
+    launches = {}
+    Bs = {"f64": gk.Batch(sys_ptr, *dA, dtype="f64"), "f32": gk.Batch(sys_ptr, *dA, dtype="f32")}
+    cfgs = [("fp64_cg_jacobi", "f64", "cg", 1e-10), ("fp64_bicgstab_jacobi", "f64", "bicgstab", 1e-10),
+            ("fp64_ir_cg_jacobi", "f64", "ir_cg", 1e-10), ("fp32_cg_jacobi", "f32", "cg", 1e-6),
+            ("fp32_bicgstab_jacobi", "f32", "bicgstab", 1e-6)]
+    for name, dt, kind, tol in cfgs:
+        B = Bs[dt]
+        chosen, _ = B.autotune(b, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000)
+        x.zero_()
+        st = B.solve(b, x, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000)
+        ms = timed(lambda: B.solve(b, x, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000,
+                                   status=False))
+        f = {"ms": round(ms, 3), "solves_per_s": round(n_sys / (ms * 1e-3)), "tol": tol,
+             "converged": int((st["stop_reason"] == gk.STOP_CONVERGED).sum()),
+             "iters_mean": round(float(st["iters"].mean()), 2), "iters_max": int(st["iters"].max()),
+             "block_sizes_per_class": chosen}
+        if kind == "ir_cg":
+            f["outer_mean"] = round(float(st["outer_iters"].mean()), 3)
+        if dt == "f64" and kind != "ir_cg":
+            fl = batch_fp64_flops(kind, True, st["iters"].astype(np.float64), nnz_s, n_s)
+            f["fp64_tflops"] = round(fl / (ms * 1e-3) / 1e12, 4)
+        forms[name] = f
+        launches[name] = sum(1 for c in chosen if c)
+    # plain FP64 CG through the unbatched path on the block-diagonal matrix
+    # (ELL, one global criterion ||r|| <= 1e-10 ||b||)
+    M = gk.Matrix(*dA, fmt="ell")
+    S = gk.Solver(M, None, "cg", max_iters=20000, reduction_factor=1e-10)
+    x.zero_()
+    st = gk.solve(S, b, x)
+    plain_ms = timed(lambda: gk.solve(S, b, x))
+    r = torch.zeros_like(b)
+    gk.apply(M, x, r)
+    r = (b - r).cpu().numpy()
+    bh = b.cpu().numpy()
+    seg = lambda v: np.sqrt(np.add.reduceat(v * v, sys_ptr[:-1]))
+    per_sys = seg(r) / seg(bh)
+    chosen_form = min(("fp64_cg_jacobi", "fp64_bicgstab_jacobi", "fp64_ir_cg_jacobi"), key=lambda k: forms[k]["ms"])
+    cg64 = forms["fp64_cg_jacobi"]
+    ach = cg64["fp64_tflops"]
+    return {
+        "workload": BATCH_WORKLOAD, "n_sys": n_sys, "rows": n, "nnz": int(A[1].size),
+        "timing": "CUDA events around each gk_batch_solve graph launch, median of %d, inputs resident" % reps,
+        "forms": forms,
+        "time_to_tol_ms": {"plain_fp64_cg_unbatched": round(plain_ms, 3), "plain_iters": st.iters,
+                           "plain_per_system_rel_res_max": float(per_sys.max()),
+                           "chosen_form": chosen_form, "chosen_ms": forms[chosen_form]["ms"],
+                           "speedup_vs_plain": round(plain_ms / forms[chosen_form]["ms"], 2)},
+        "roofline": {"kernel": "batch_kernel<double, CG, Jacobi> (one block per system, FP64)", "bound": "alu",
+                     "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "peak_source": "nominal GB300 FP64 rate", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                     "traffic": None},
+        "gpu_launches_per_solve": launches,
+    }
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -535,6 +644,8 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
     }
+    if not args.no_batched:
+        out["batched"] = run_batched(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -685,6 +796,8 @@ def main():
     ap.add_argument("--impl", choices=["gk", "reference"], default="gk")
     ap.add_argument("--small", action="store_true", help="small matrices (quick checks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched small-system solves")
+    ap.add_argument("--batched-only", action="store_true", help="only the batched small-system solves")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
     ap.add_argument("--spmv-only", metavar="MAT:FMT", default=None,
                     help="only time repeated applies of matrix a|b in one format (profiling aid)")
@@ -697,7 +810,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.spmv_only:
+    if args.batched_only:
+        import torch
+        import paper_2006_16852_gb300 as gk
+        gk.load()
+        out = run_batched(torch.device("cuda:0"))
+    elif args.spmv_only:
         out = run_spmv_only(args)
     elif args.solve_only:
         out = run_solve_only(args)

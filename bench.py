@@ -52,7 +52,7 @@ WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point sten
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel per launch on workload (a); valid only while spmv.cu is the
 # file it was measured on (sha256 prefix).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"099ac26c568ff1d0": 711961600}
 
 # back-to-back applies per format and matrix in one step (the per-launch time
 # of the roofline is their average)
@@ -412,7 +412,11 @@ def batch_fp64_flops(kind, jac, iters, nnz_s, n_s):
     return 2.0 * float(np.sum(iters * (spmvs * nnz_s + per_row * n_s) + nnz_s + 2 * n_s))
 
 
-def run_batched(dev, reps=3, n_sys=10000):
+BATCH_FORMS = ("fp64_cg_jacobi", "fp64_bicgstab_jacobi", "fp64_ir_cg_jacobi", "fp32_cg_jacobi",
+               "fp32_bicgstab_jacobi")
+
+
+def run_batched(dev, reps=3, n_sys=10000, only=None, tune=True, plain=True):
     import torch
     import paper_2006_16852_gb300 as gk
     import workloads as W
@@ -446,8 +450,13 @@ def run_batched(dev, reps=3, n_sys=10000):
             ("fp64_ir_cg_jacobi", "f64", "ir_cg", 1e-10), ("fp32_cg_jacobi", "f32", "cg", 1e-6),
             ("fp32_bicgstab_jacobi", "f32", "bicgstab", 1e-6)]
     for name, dt, kind, tol in cfgs:
+        if only and name not in only:
+            continue
         B = Bs[dt]
-        chosen, _ = B.autotune(b, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000)
+        if tune:
+            chosen, _ = B.autotune(b, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000)
+        else:
+            chosen = B.info(kind=kind)["threads"]
         x.zero_()
         st = B.solve(b, x, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000)
         ms = timed(lambda: B.solve(b, x, kind=kind, jacobi=True, reduction_factor=tol, max_iters=20000,
@@ -463,6 +472,11 @@ def run_batched(dev, reps=3, n_sys=10000):
             f["fp64_tflops"] = round(fl / (ms * 1e-3) / 1e12, 4)
         forms[name] = f
         launches[name] = sum(1 for c in chosen if c)
+    out = {"workload": BATCH_WORKLOAD, "n_sys": n_sys, "rows": n, "nnz": int(A[1].size),
+           "timing": "CUDA events around each gk_batch_solve graph launch, median of %d, inputs resident" % reps,
+           "forms": forms, "gpu_launches_per_solve": launches}
+    if not plain or "fp64_cg_jacobi" not in forms:
+        return out
     # plain FP64 CG through the unbatched path on the block-diagonal matrix
     # (ELL, one global criterion ||r|| <= 1e-10 ||b||)
     M = gk.Matrix(*dA, fmt="ell")
@@ -476,13 +490,11 @@ def run_batched(dev, reps=3, n_sys=10000):
     bh = b.cpu().numpy()
     seg = lambda v: np.sqrt(np.add.reduceat(v * v, sys_ptr[:-1]))
     per_sys = seg(r) / seg(bh)
-    chosen_form = min(("fp64_cg_jacobi", "fp64_bicgstab_jacobi", "fp64_ir_cg_jacobi"), key=lambda k: forms[k]["ms"])
+    chosen_form = min((k for k in ("fp64_cg_jacobi", "fp64_bicgstab_jacobi", "fp64_ir_cg_jacobi") if k in forms),
+                      key=lambda k: forms[k]["ms"])
     cg64 = forms["fp64_cg_jacobi"]
     ach = cg64["fp64_tflops"]
-    return {
-        "workload": BATCH_WORKLOAD, "n_sys": n_sys, "rows": n, "nnz": int(A[1].size),
-        "timing": "CUDA events around each gk_batch_solve graph launch, median of %d, inputs resident" % reps,
-        "forms": forms,
+    out.update({
         "time_to_tol_ms": {"plain_fp64_cg_unbatched": round(plain_ms, 3), "plain_iters": st.iters,
                            "plain_per_system_rel_res_max": float(per_sys.max()),
                            "chosen_form": chosen_form, "chosen_ms": forms[chosen_form]["ms"],
@@ -491,8 +503,8 @@ def run_batched(dev, reps=3, n_sys=10000):
                      "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "peak_source": "nominal GB300 FP64 rate", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
                      "traffic": None},
-        "gpu_launches_per_solve": launches,
-    }
+    })
+    return out
 
 
 def run_gpu(args):
@@ -798,6 +810,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched small-system solves")
     ap.add_argument("--batched-only", action="store_true", help="only the batched small-system solves")
+    ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
+    ap.add_argument("--batch-forms", default=None, help="--batched-only: comma list of " + ", ".join(BATCH_FORMS))
+    ap.add_argument("--batch-no-tune", action="store_true",
+                    help="--batched-only: default block sizes instead of the autotuner")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
     ap.add_argument("--spmv-only", metavar="MAT:FMT", default=None,
                     help="only time repeated applies of matrix a|b in one format (profiling aid)")
@@ -814,7 +830,9 @@ def main():
         import torch
         import paper_2006_16852_gb300 as gk
         gk.load()
-        out = run_batched(torch.device("cuda:0"))
+        out = run_batched(torch.device("cuda:0"), n_sys=args.batch_systems,
+                          only=args.batch_forms.split(",") if args.batch_forms else None,
+                          tune=not args.batch_no_tune, plain=not args.batch_forms)
     elif args.spmv_only:
         out = run_spmv_only(args)
     elif args.solve_only:

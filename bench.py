@@ -21,7 +21,11 @@ workload:
 
 value = algorithmic bytes of the step / device time of the step (GB/s).
 
-Beside the step (not part of its value) the line carries "batched": 10,000
+Beside the step (not part of its value) the line carries "mixed": the
+mixed-precision workload (7-point variable-coefficient diffusion on 256^3,
+log-normal sigma 1) solved to 1e-12 by plain FP64 CG and by FP64 refinement
+around FP32 CG with Jacobi or adaptive FP16/FP32 block Jacobi; and
+"batched": 10,000
 small variable-coefficient systems solved per system in one graph launch
 (FP64 CG / BiCGSTAB / refinement to 1e-10, FP32 CG / BiCGSTAB to 1e-6), with
 solves/s and the time against plain FP64 CG on the block-diagonal matrix.
@@ -507,6 +511,74 @@ def run_batched(dev, reps=3, n_sys=10000, only=None, tune=True, plain=True):
     return out
 
 
+# ---------------------------------------------------------------------------
+# mixed precision at its own workload (reported beside the step)
+# ---------------------------------------------------------------------------
+
+MIXED_WORKLOAD = ("7-point variable-coefficient diffusion on a {s}^3 grid (n={n:,}, nnz={nnz:,}), cell "
+                  "coefficients log-normal sigma=1 i.i.d. (seed 4), harmonic-mean faces, Dirichlet; b uniform[-1,1] "
+                  "(seed 7), x0 = 0, ||r|| <= 1e-12 ||b||")
+
+
+def run_mixed(dev, side=256, tol=1e-12):
+    """Plain FP64 CG against FP64 refinement around FP32 CG (Jacobi or
+    adaptive FP16/FP32 block Jacobi of 8, 16, 32) on the mixed-precision
+    workload; one warm-up solve and one timed solve per form."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    A = W.varcoef3d(side, sigma=1.0, seed=4)
+    n, nnz = A[0].size - 1, A[1].size
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dA = [t(a) for a in A]
+    del A
+    b = t(W.uniform_vector(n, 7))
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    M = gk.Matrix(*dA, fmt="ell")
+    del dA
+    crit = dict(max_iters=200000, reduction_factor=tol)
+    forms = {"plain_fp64_cg": (None, "cg"), "fp64_cg_bj16": (16, "cg"), "ir_cg_jacobi": (1, "ir_cg"),
+             "ir_cg_bj8": (8, "ir_cg"), "ir_cg_bj16": (16, "ir_cg"), "ir_cg_bj32": (32, "ir_cg")}
+    out = {}
+    for name, (bs, kind) in forms.items():
+        P = gk.Precond(M, bs) if bs else None
+        S = gk.Solver(M, P, kind, **crit)
+        ms = []
+        for _ in range(2):
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, b, x)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        if st.stop_reason != gk.STOP_CONVERGED:
+            raise RuntimeError(f"mixed {name} did not converge: {st}")
+        prec = "none" if not bs else ("jacobi" if bs == 1 else "block")
+        f = {"ms": round(ms[-1], 2), "iters": st.iters, "rel_res_true": st.rel_res_true}
+        if kind == "ir_cg":
+            inf = S.info()
+            tot = inf["inner_fp16_blocks"] + inf["inner_fp32_blocks"]
+            frac = inf["inner_fp16_blocks"] / tot if tot else 0.0
+            f["outer_iters"] = st.outer_iters
+            if tot:
+                f["fp16_block_fraction"] = round(frac, 4)
+            by = ir_bytes(st.iters, st.outer_iters, nnz, n, prec, bs or 1, frac)
+        else:
+            by = cg_bytes(st.iters, nnz, n, prec, bs or 1)
+        f["GB/s"] = round(by / (ms[-1] * 1e-3) / 1e9, 1)
+        out[name] = f
+        del S, P
+    plain = out["plain_fp64_cg"]["ms"]
+    chosen = min((k for k in out if k != "plain_fp64_cg"), key=lambda k: out[k]["ms"])
+    return {"workload": MIXED_WORKLOAD.format(s=side, n=n, nnz=nnz),
+            "timing": "CUDA events around gk_solve (device-side graph loop), second of two solves, inputs resident",
+            "forms": out,
+            "time_to_tol_ms": {"plain_fp64_cg": plain, "chosen_form": chosen, "chosen_ms": out[chosen]["ms"],
+                               "speedup_vs_plain": round(plain / out[chosen]["ms"], 3)}}
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -658,6 +730,8 @@ def run_gpu(args):
     }
     if not args.no_batched:
         out["batched"] = run_batched(dev)
+    if not args.no_mixed:
+        out["mixed"] = run_mixed(dev, side=args.mixed_side)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -810,6 +884,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched small-system solves")
     ap.add_argument("--batched-only", action="store_true", help="only the batched small-system solves")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision workload")
+    ap.add_argument("--mixed-only", action="store_true", help="only the mixed-precision workload")
+    ap.add_argument("--mixed-side", type=int, default=256, help="grid side of the mixed-precision workload")
     ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
     ap.add_argument("--batch-forms", default=None, help="--batched-only: comma list of " + ", ".join(BATCH_FORMS))
     ap.add_argument("--batch-no-tune", action="store_true",
@@ -826,7 +903,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.batched_only:
+    if args.mixed_only:
+        import torch
+        import paper_2006_16852_gb300 as gk
+        gk.load()
+        out = run_mixed(torch.device("cuda:0"), side=args.mixed_side)
+    elif args.batched_only:
         import torch
         import paper_2006_16852_gb300 as gk
         gk.load()

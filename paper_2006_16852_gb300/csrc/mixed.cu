@@ -80,7 +80,8 @@ __global__ void to_float_kernel(const double* __restrict__ in, float* __restrict
 
 // One warp per block: kappa_1 = ||D||_1 ||D^{-1}||_1 (column sums in
 // increasing row order, maximum over columns), the storage precision, the
-// power-of-two scale, and the scaled copy.
+// power-of-two scale, and the scaled copy -- stored row-major (entry (i, j)
+// at i * m + j) so that a lane reads its row with vector loads.
 __global__ void __launch_bounds__(128) bj_adapt_kernel(const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ col,
                                                        const double* __restrict__ val,
@@ -127,28 +128,80 @@ __global__ void __launch_bounds__(128) bj_adapt_kernel(const int32_t* __restrict
       bscale[blk] = static_cast<float>(ldexp(1.0, e));
     }
     for (int idx = lane; idx < m * m; idx += 32) {
-      const double v = inv[off + idx] * sc;
-      if (half) blk16[off + idx] = __double2half(v);
-      else blk32[off + idx] = static_cast<float>(v);
+      const double v = inv[off + idx] * sc;  // column-major source: idx = j * m + i
+      const int j = idx / m, i = idx - j * m;
+      const int64_t o = off + static_cast<int64_t>(i) * m + j;
+      if (half) blk16[o] = __double2half(v);
+      else blk32[o] = static_cast<float>(v);
     }
     __syncwarp();
   }
 }
 
-// z_i = bscale * sum_j D'(i, j) r_j for the lane's block (FP32 arithmetic).
+// z_i = bscale * sum_j D'(i, j) r_j for the lane's block (FP32 arithmetic,
+// increasing j).  BS > 0: the block size known at compile time -- a full
+// block's row is fetched with 16-byte (FP32) or 8/16-byte (FP16) loads, all
+// issued before the sum; BS = 0: any block size, one load per entry.  The
+// loads may diverge; the shuffles that hand r_j around are executed by every
+// lane of the warp.
+template <int BS>
 __device__ __forceinline__ float bj_apply32(const IrData& a, const BjLane& L, int bs, float r_mine) {
-  float z = 0.0f;
-  const int64_t off = static_cast<int64_t>(L.blk) * bs * bs;
-  const bool h = L.active && a.prec[L.blk] == 0;
-  for (int j = 0; j < bs; ++j) {
-    const float rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
-    if (L.active && j < L.m) {
-      const int64_t o = off + static_cast<int64_t>(j) * L.m + L.i;
-      const float dv = h ? __half2float(a.blk16[o]) : a.blk32[o];
-      z = fmaf(dv, rj, z);
+  if constexpr (BS == 0) {
+    float z = 0.0f;
+    const int64_t off = static_cast<int64_t>(L.blk) * bs * bs + static_cast<int64_t>(L.i) * L.m;
+    const bool h = L.active && a.prec[L.blk] == 0;
+    for (int j = 0; j < bs; ++j) {
+      const float rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
+      if (L.active && j < L.m) {
+        const float dv = h ? __half2float(a.blk16[off + j]) : a.blk32[off + j];
+        z = fmaf(dv, rj, z);
+      }
     }
+    return L.active ? z * a.bscale[L.blk] : 0.0f;
+  } else {
+    float dv[BS];
+#pragma unroll
+    for (int j = 0; j < BS; ++j) dv[j] = 0.0f;
+    if (L.active) {
+      const int64_t off = static_cast<int64_t>(L.blk) * BS * BS + static_cast<int64_t>(L.i) * L.m;
+      const bool h = a.prec[L.blk] == 0;
+      if (L.m == BS && h && BS % 8 == 0) {
+        const uint4* src = reinterpret_cast<const uint4*>(a.blk16 + off);
+#pragma unroll
+        for (int k = 0; k < BS / 8; ++k) {
+          const uint4 u = __ldg(src + k);
+          const unsigned int w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+            dv[8 * k + 2 * q] = f.x;
+            dv[8 * k + 2 * q + 1] = f.y;
+          }
+        }
+      } else if (L.m == BS && !h && BS % 4 == 0) {
+        const float4* src = reinterpret_cast<const float4*>(a.blk32 + off);
+#pragma unroll
+        for (int k = 0; k < BS / 4; ++k) {
+          const float4 f = __ldg(src + k);
+          dv[4 * k] = f.x;
+          dv[4 * k + 1] = f.y;
+          dv[4 * k + 2] = f.z;
+          dv[4 * k + 3] = f.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+          if (j < L.m) dv[j] = h ? __half2float(a.blk16[off + j]) : a.blk32[off + j];
+      }
+    }
+    float z = 0.0f;
+#pragma unroll
+    for (int j = 0; j < BS; ++j) {
+      const float rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
+      if (j < L.m) z = fmaf(dv[j], rj, z);
+    }
+    return L.active ? z * a.bscale[L.blk] : 0.0f;
   }
-  return L.active ? z * a.bscale[L.blk] : 0.0f;
 }
 
 // --------------------------------------------------------------------------
@@ -285,7 +338,7 @@ __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_csr_kernel(const int32_
     for (BjLane L = bj_lane(w_ * bpw_, lane_, a.bs, a.n, a.nblocks), *once_ = &L; once_; once_ = nullptr)
 
 // r = r64 / ||r64||, d = 0, z = M^{-1} r, p = z, rho = r.z, rr0 = r.r.
-template <int PK>
+template <int PK, int BS>
 __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d) {
   __shared__ float scratch[kRedScratch];
   const double inv = 1.0 / a.st->rnorm;
@@ -298,7 +351,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d
         d.r[L.row] = rv;
         d.d[L.row] = 0.0f;
       }
-      const float zz = bj_apply32(d, L, a.bs, rv);
+      const float zz = bj_apply32<BS>(d, L, a.bs, rv);
       if (L.active) {
         d.p[L.row] = zz;
         rz = fmaf(rv, zz, rz);
@@ -332,7 +385,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d
 }
 
 // d += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); inner criteria.
-template <int PK>
+template <int PK, int BS>
 __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData d) {
   __shared__ float scratch[kRedScratch];
   if (d.ist->done) return;
@@ -346,7 +399,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData 
         rn = fmaf(-alpha, d.q[L.row], d.r[L.row]);
         d.r[L.row] = rn;
       }
-      const float zz = bj_apply32(d, L, a.bs, rn);
+      const float zz = bj_apply32<BS>(d, L, a.bs, rn);
       if (L.active) {
         d.z[L.row] = zz;
         rz = fmaf(rn, zz, rz);
@@ -487,13 +540,19 @@ int ir_spmv(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
   return GK_OK;
 }
 
-#define IR_LAUNCH_PK(kern, s, a, d)                                                    \
-  do {                                                                                 \
-    if (pk == PREC_BLOCK) kern<PREC_BLOCK><<<(d).grid, kIrThreads, 0, s>>>(a, d);     \
-    else if (pk == PREC_SCALAR) kern<PREC_SCALAR><<<(d).grid, kIrThreads, 0, s>>>(a, d); \
-    else kern<PREC_NONE><<<(d).grid, kIrThreads, 0, s>>>(a, d);                        \
-    GK_TRY_CUDA(cudaGetLastError());                                                   \
+// Block-Jacobi kernels with the block size as a template argument where it
+// is one of the common sizes (vectorised, unrolled apply), else generic.
+#define IR_LAUNCH_BS(kern, bs, grid, s, a, d)                                      \
+  do {                                                                             \
+    switch (bs) {                                                                  \
+      case 4: kern<PREC_BLOCK, 4><<<grid, kIrThreads, 0, s>>>(a, d); break;       \
+      case 8: kern<PREC_BLOCK, 8><<<grid, kIrThreads, 0, s>>>(a, d); break;       \
+      case 16: kern<PREC_BLOCK, 16><<<grid, kIrThreads, 0, s>>>(a, d); break;     \
+      case 32: kern<PREC_BLOCK, 32><<<grid, kIrThreads, 0, s>>>(a, d); break;     \
+      default: kern<PREC_BLOCK, 0><<<grid, kIrThreads, 0, s>>>(a, d); break;      \
+    }                                                                              \
   } while (0)
+
 
 // The inner solve and the update of x as one graph:
 // start -> WHILE(cond) { SpMV; update; direction } -> apply.
@@ -506,9 +565,9 @@ int ir_build_graph(Solver& S, IrData& d) {
   GK_TRY_CUDA(cudaStreamBeginCaptureToGraph(d.cs, d.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int rc = GK_OK;
   do {
-    if (pk == PREC_BLOCK) ir_start_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-    else if (pk == PREC_SCALAR) ir_start_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-    else ir_start_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
+    if (pk == PREC_BLOCK) IR_LAUNCH_BS(ir_start_kernel, a.bs, d.grid, d.cs, a, d);
+    else if (pk == PREC_SCALAR) ir_start_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
+    else ir_start_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
     cudaError_t e = cudaGetLastError();
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
@@ -541,13 +600,13 @@ int ir_build_graph(Solver& S, IrData& d) {
     int brc = ir_spmv(S, d, a, d.cs);
     if (brc == GK_OK) {
       if (pk == PREC_BLOCK) {
-        ir_update_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
+        IR_LAUNCH_BS(ir_update_kernel, a.bs, d.grid, d.cs, a, d);
         ir_direction_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
       } else if (pk == PREC_SCALAR) {
-        ir_update_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
+        ir_update_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
         ir_direction_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
       } else {
-        ir_update_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
+        ir_update_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
         ir_direction_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
       }
     }

@@ -84,3 +84,46 @@ def test_ir_edge_cases(gk, orc):
     s1, _, _ = _gk_ir(gk, A, b, "csr", 1, inner_reduction=1e-2)
     s2, _, _ = _gk_ir(gk, A, b, "csr", 1, inner_reduction=1e-6)
     assert s1.stop_reason == s2.stop_reason == gk.STOP_CONVERGED and s1.outer_iters > s2.outer_iters
+
+
+@pytest.mark.parametrize("bs", [8, 16, 32])
+def test_ir_varcoef3d_adaptive_blocks_to_1e12(gk, orc, bs):
+    """The mixed-precision workload's operator (7-point, log-normal sigma = 1
+    coefficients) at 24^3: refinement with adaptive FP16/FP32 block Jacobi to
+    1e-12 -- the oracle's FP16/FP32 split exactly, its number of refinement
+    steps within 1, and the FP64 criterion met on the true residual."""
+    A = W.varcoef3d(24, sigma=1.0, seed=4)
+    n = A[0].size - 1
+    xs = W.uniform_vector(n, 3)
+    b = orc.spmv(A, xs)
+    st, x, info = _gk_ir(gk, A, b, "ell", bs, max_iters=100000, reduction_factor=1e-12)
+    P = orc.precond(A, "block_jacobi", bs)
+    prec, _ = orc.block_jacobi_precision(A, bs, P.blocks)
+    ref, outer = orc.ir_cg(A, b, P=P, tol=1e-12, max_iters=100000)
+    assert info["inner_fp16_blocks"] == int((prec == 0).sum()) > 0
+    assert info["inner_fp32_blocks"] == int((prec == 1).sum())
+    assert st.stop_reason == gk.STOP_CONVERGED == ref.stop_reason
+    assert abs(st.outer_iters - outer) <= 1, (st.outer_iters, outer)
+    assert abs(st.iters - ref.iters) <= max(5, ref.iters // 8), (st.iters, ref.iters)
+    r = b - orc.spmv(A, x)
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(x - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+
+
+def test_ir_varcoef3d_full_size(gk, orc):
+    """The mixed-precision workload at its full size (256^3, n = 16,777,216,
+    nnz = 117,047,296), refinement with adaptive block Jacobi (bs 16) to
+    1e-12: the FP16/FP32 decisions of all 1,048,576 blocks equal the
+    oracle's, and the oracle's FP64 SpMV confirms the residual."""
+    A = W.varcoef3d(256, sigma=1.0, seed=4)
+    n = A[0].size - 1
+    assert n == 16_777_216 and A[1].size == 117_047_296
+    b = W.uniform_vector(n, 7)
+    st, x, info = _gk_ir(gk, A, b, "ell", 16, max_iters=200000, reduction_factor=1e-12)
+    P = orc.precond(A, "block_jacobi", 16)
+    prec, _ = orc.block_jacobi_precision(A, 16, P.blocks)
+    assert info["inner_fp16_blocks"] == int((prec == 0).sum())
+    assert info["inner_fp32_blocks"] == int((prec == 1).sum())
+    assert st.stop_reason == gk.STOP_CONVERGED
+    r = b - orc.spmv(A, x)
+    assert np.linalg.norm(r) <= 1.2e-12 * np.linalg.norm(b)

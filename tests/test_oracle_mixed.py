@@ -80,3 +80,34 @@ def test_ir_more_outer_steps_when_inner_is_loose(orc):
     # outer loop still converges
     capped, o3 = orc.ir_cg(A, b, inner_reduction=1e-12, inner_max=40)
     assert capped.stop_reason == orc.STOP_CONVERGED and o3 > o1
+
+
+def test_varcoef3d_unit_coefficients_is_poisson7():
+    """Unit cell coefficients give the 7-point Poisson stencil (6 on the
+    diagonal, -1 per neighbour, Dirichlet)."""
+    A = W.varcoef3d_from(np.ones((3, 4, 5)))
+    offs = [(-1, 0, 0), (0, -1, 0), (0, 0, -1), (0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0)]
+    P = W._from_offsets((3, 4, 5), offs, [-1, -1, -1, 6, -1, -1, -1])
+    for a, p in zip(A, P):
+        np.testing.assert_array_equal(a, p)
+
+
+def test_varcoef3d_faces_and_spd():
+    """a_ij = -2 c_i c_j / (c_i + c_j) for face neighbours along each axis;
+    a_ii = the six faces with boundary faces carrying c_i; symmetric positive
+    definite; the 256^3 size of the mixed-precision workload has
+    7 n - 6 * 256^2 nonzeros."""
+    rng = np.random.default_rng(2)
+    coef = np.exp(rng.standard_normal((3, 4, 5)))
+    D = W.csr_to_dense(W.varcoef3d_from(coef))
+    c = coef.ravel()
+    hm = lambda a, b: 2 * a * b / (a + b)
+    i = 1 * 20 + 2 * 5 + 3  # interior cell (z=1, y=2, x=3)
+    for j in (i - 1, i + 1, i - 5, i + 5, i - 20, i + 20):
+        assert D[i, j] == pytest.approx(-hm(c[i], c[j]), rel=1e-15)
+    assert D[i, i] == pytest.approx(-(D[i].sum() - D[i, i]), rel=1e-14)  # interior: diag = sum of faces
+    # corner cell 0: three boundary faces (c_0) + three interior faces
+    assert D[0, 0] == pytest.approx(3 * c[0] - (D[0, 1] + D[0, 5] + D[0, 20]), rel=1e-14)
+    np.testing.assert_array_equal(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
+    assert 7 * 256 ** 3 - 6 * 256 ** 2 == 117_047_296

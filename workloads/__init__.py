@@ -13,6 +13,7 @@ import numpy as np
 __all__ = [
     "poisson1d", "poisson2d", "stencil27", "powerlaw", "random_csr", "diagonal",
     "convdiff2d", "uniform_vector", "csr_to_dense", "scaled_identity", "varcoef2d", "batch_varcoef2d",
+    "varcoef3d", "varcoef3d_from",
 ]
 
 
@@ -236,3 +237,74 @@ def batch_varcoef2d(n_sys: int, seed: int = 5, side_lo: int = 6, side_hi: int = 
         nnz_off += c.size
     rowptr = np.concatenate(rps + [np.array([nnz_off])])
     return sys_ptr, _finish(rowptr, np.concatenate(cols), np.concatenate(vals))
+
+
+def varcoef3d_from(coef):
+    """7-point variable-coefficient diffusion on an (nz, ny, nx) grid of cell
+    coefficients (slowest axis first): the face between two cells carries the
+    harmonic mean of their coefficients, a face on the grid boundary the
+    cell's own coefficient (homogeneous Dirichlet); a_ii = the sum of the
+    cell's six faces, a_ij = -face.  SPD.  Built one stencil offset at a time
+    so that a 256^3 grid needs little more memory than the matrix."""
+    c = np.asarray(coef, dtype=np.float64)
+    shape = c.shape
+    n = c.size
+    hm = lambda a, b: 2.0 * a * b / (a + b)
+    # faces[(axis, side)]: coefficient of the face towards the neighbour at
+    # offset side (-1 or +1) along axis, per cell
+    faces = {}
+    for ax in range(3):
+        lo = np.empty_like(c)
+        hi = np.empty_like(c)
+        sl = lambda a, b: tuple(slice(a, b) if d == ax else slice(None) for d in range(3))
+        inner = hm(c[sl(1, None)], c[sl(None, -1)])
+        lo[sl(1, None)] = inner
+        lo[sl(0, 1)] = c[sl(0, 1)]
+        hi[sl(None, -1)] = inner
+        hi[sl(-1, None)] = c[sl(-1, None)]
+        faces[(ax, -1)] = lo.ravel()
+        faces[(ax, 1)] = hi.ravel()
+    diag = sum(faces.values())
+    strides = (shape[1] * shape[2], shape[2], 1)
+    # offsets in increasing column order
+    offs = [(0, -1), (1, -1), (2, -1), None, (2, 1), (1, 1), (0, 1)]
+    coords = [np.arange(shape[d]).reshape([-1 if e == d else 1 for e in range(3)]) for d in range(3)]
+    masks = []
+    for off in offs:
+        if off is None:
+            masks.append(None)
+            continue
+        ax, sd = off
+        ok = (coords[ax] + sd >= 0) & (coords[ax] + sd < shape[ax])
+        masks.append(np.broadcast_to(ok, shape).ravel())
+    lens = np.ones(n, dtype=np.int64)
+    for m in masks:
+        if m is not None:
+            lens += m
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    pos = rowptr[:-1].copy()
+    rows = np.arange(n, dtype=np.int64)
+    for off, m in zip(offs, masks):
+        if off is None:
+            col[pos] = rows
+            val[pos] = diag
+            pos += 1
+            continue
+        ax, sd = off
+        idx = np.flatnonzero(m)
+        col[pos[idx]] = idx + sd * strides[ax]
+        val[pos[idx]] = -faces[off][idx]
+        pos[idx] += 1
+    return _finish(rowptr, col, val)
+
+
+def varcoef3d(nx: int, sigma: float = 1.0, seed: int = 4):
+    """varcoef3d_from on an nx^3 grid with i.i.d. log-normal(0, sigma) cell
+    coefficients (the mixed-precision workload: nx = 256, sigma = 1)."""
+    rng = np.random.default_rng(seed)
+    coef = np.exp(sigma * rng.standard_normal((nx, nx, nx)))
+    return varcoef3d_from(coef)

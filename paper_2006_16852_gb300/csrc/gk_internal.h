@@ -222,7 +222,7 @@ struct Precond {
   int bs = 1;
   int64_t nblocks = 0;
   double* dinv = nullptr;    // scalar Jacobi: 1/a_ii
-  double* blocks = nullptr;  // block Jacobi: inverse blocks, each column-major
+  double* blocks = nullptr;  // block Jacobi: inverse blocks, each row-major
   int64_t block_elems = 0;
   double* stage_in = nullptr;
   double* stage_out = nullptr;

@@ -80,8 +80,8 @@ __global__ void to_float_kernel(const double* __restrict__ in, float* __restrict
 
 // One warp per block: kappa_1 = ||D||_1 ||D^{-1}||_1 (column sums in
 // increasing row order, maximum over columns), the storage precision, the
-// power-of-two scale, and the scaled copy -- stored row-major (entry (i, j)
-// at i * m + j) so that a lane reads its row with vector loads.
+// power-of-two scale, and the scaled copy (row-major like the FP64 blocks:
+// entry (i, j) at i * m + j, so that a lane reads its row with vector loads).
 __global__ void __launch_bounds__(128) bj_adapt_kernel(const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ col,
                                                        const double* __restrict__ val,
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(128) bj_adapt_kernel(const int32_t* __restrict
     double na = 0.0, ni = 0.0, vmax = 0.0;
     if (lane < m) {
       for (int i = 0; i < m; ++i) na += T[i][lane];
-      for (int i = 0; i < m; ++i) {
-        const double v = fabs(inv[off + static_cast<int64_t>(lane) * m + i]);
+      for (int i = 0; i < m; ++i) {  // column `lane` of the row-major inverse
+        const double v = fabs(inv[off + static_cast<int64_t>(i) * m + lane]);
         ni += v;
         vmax = fmax(vmax, v);
       }
@@ -127,12 +127,10 @@ __global__ void __launch_bounds__(128) bj_adapt_kernel(const int32_t* __restrict
       prec[blk] = half ? 0 : 1;
       bscale[blk] = static_cast<float>(ldexp(1.0, e));
     }
-    for (int idx = lane; idx < m * m; idx += 32) {
-      const double v = inv[off + idx] * sc;  // column-major source: idx = j * m + i
-      const int j = idx / m, i = idx - j * m;
-      const int64_t o = off + static_cast<int64_t>(i) * m + j;
-      if (half) blk16[o] = __double2half(v);
-      else blk32[o] = static_cast<float>(v);
+    for (int idx = lane; idx < m * m; idx += 32) {  // row-major in and out
+      const double v = inv[off + idx] * sc;
+      if (half) blk16[off + idx] = __double2half(v);
+      else blk32[off + idx] = static_cast<float>(v);
     }
     __syncwarp();
   }

@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
     }
     if (singular && i == 0) atomicMin(bad, blk);
     const int64_t off = static_cast<int64_t>(blk) * bs * bs;
-    for (int e = i; e < m * m; e += GW) {
-      const int j = e / m, ii = e - j * m;
+    for (int e = i; e < m * m; e += GW) {  // row-major: e = ii * m + j
+      const int ii = e / m, j = e - ii * m;
       blocks[off + e] = W[ii * LD + m + j];
     }
     __syncwarp();
@@ -149,6 +149,7 @@ __global__ void scalar_apply_kernel(const double* __restrict__ dinv, const doubl
     z[i] = dinv[i] * r[i];
 }
 
+template <int BS>
 __global__ void bj_apply_kernel(const double* __restrict__ blocks, int n, int bs, int nblocks,
                                 const double* __restrict__ r, double* z) {
   const int lane = threadIdx.x & 31;
@@ -157,25 +158,8 @@ __global__ void bj_apply_kernel(const double* __restrict__ blocks, int n, int bs
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * bpw < nblocks; w += nw) {
     const BjLane L = bj_lane(w * bpw, lane, bs, n, nblocks);
     const double rm = L.active ? r[L.row] : 0.0;
-    const double zz = bj_apply_lane(blocks, L, bs, rm);
+    const double zz = bj_apply_lane<BS>(blocks, L, bs, rm);
     if (L.active) z[L.row] = zz;
-  }
-}
-
-// Row-major, concatenated copy of the column-major device blocks (the layout
-// of gk_precond_get_blocks).
-__global__ void bj_export_kernel(const double* __restrict__ blocks, int n, int bs, int nblocks, double* out) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t total = static_cast<int64_t>(nblocks - 1) * bs * bs +
-                        static_cast<int64_t>(n - (nblocks - 1) * bs) * (n - (nblocks - 1) * bs);
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t blk = e / (static_cast<int64_t>(bs) * bs);
-    const int64_t off = blk * bs * bs;
-    const int64_t rem = static_cast<int64_t>(n) - blk * bs;
-    const int m = static_cast<int>(rem < bs ? rem : bs);
-    const int idx = static_cast<int>(e - off);
-    const int i = idx / m, j = idx - i * m;
-    out[e] = blocks[off + static_cast<int64_t>(j) * m + i];
   }
 }
 
@@ -218,8 +202,11 @@ int precond_apply_launch(const Precond* P, const double* r, double* z, cudaStrea
   } else {
     const int bpw = 32 / P->bs;
     const int64_t warps = (P->nblocks + bpw - 1) / bpw;
-    bj_apply_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(P->blocks, static_cast<int>(P->n), P->bs,
-                                                              static_cast<int>(P->nblocks), r, z);
+#define GK_BJ_APPLY(BS)                                                                                   \
+  bj_apply_kernel<BS><<<grid_for(warps * 32, 256), 256, 0, s>>>(P->blocks, static_cast<int>(P->n), P->bs, \
+                                                                static_cast<int>(P->nblocks), r, z)
+    GK_BJ_DISPATCH(P->bs, GK_BJ_APPLY);
+#undef GK_BJ_APPLY
   }
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
@@ -321,26 +308,15 @@ extern "C" int gk_precond_get_blocks(gk_precond h, double* out, int64_t n_out, v
   if (prev != P->device) cudaSetDevice(P->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = GK_OK;
-  double* tmp = nullptr;
   do {
-    if (P->bs == 1) {
-      if (cudaMemcpyAsync(out, P->dinv, sizeof(double) * total, cudaMemcpyDefault, s) != cudaSuccess) {
-        rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
-        break;
-      }
-    } else {
-      if ((rc = dalloc_n(&tmp, static_cast<size_t>(total), nullptr))) break;
-      bj_export_kernel<<<grid_for(total, 256), 256, 0, s>>>(P->blocks, static_cast<int>(P->n), P->bs,
-                                                            static_cast<int>(P->nblocks), tmp);
-      if (cudaGetLastError() != cudaSuccess ||
-          cudaMemcpyAsync(out, tmp, sizeof(double) * total, cudaMemcpyDefault, s) != cudaSuccess) {
-        rc = cuda_error(cudaGetLastError(), "export blocks");
-        break;
-      }
+    // the device layout is the exported one: row-major blocks, concatenated
+    const double* src = P->bs == 1 ? P->dinv : P->blocks;
+    if (cudaMemcpyAsync(out, src, sizeof(double) * total, cudaMemcpyDefault, s) != cudaSuccess) {
+      rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
+      break;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "sync");
   } while (false);
-  dfree(tmp);
   if (prev != P->device) cudaSetDevice(prev);
   return rc;
 }

@@ -37,18 +37,64 @@ __device__ __forceinline__ BjLane bj_lane(int warp_block0, int lane, int bs, int
 }
 
 // z_i = sum_j Dinv(i, j) r_j for the lane's block, with the r_j held by the
-// lanes of the block's group; blocks are stored column-major, block k at
-// offset k * bs * bs.  Sum in increasing j via fma, the order of the CPU
-// reference.  Every lane of the warp must call it.
+// lanes of the block's group; blocks are stored row-major (entry (i, j) at
+// i * m + j), block k at offset k * bs * bs.  Sum in increasing j via fma,
+// the order of the CPU reference.  BS > 0: the block size known at compile
+// time -- a full block's row is fetched with 16-byte loads, all issued before
+// the sum; BS = 0: any block size.  The loads may diverge; every lane of the
+// warp executes the shuffles.
+template <int BS>
 __device__ __forceinline__ double bj_apply_lane(const double* __restrict__ blocks, const BjLane& L, int bs,
                                                 double r_mine) {
-  double z = 0.0;
-  const int64_t off = static_cast<int64_t>(L.blk) * bs * bs;
-  for (int j = 0; j < bs; ++j) {
-    const double rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
-    if (L.active && j < L.m) z = fma(__ldg(blocks + off + static_cast<int64_t>(j) * L.m + L.i), rj, z);
+  if constexpr (BS == 0) {
+    double z = 0.0;
+    const int64_t off = static_cast<int64_t>(L.blk) * bs * bs + static_cast<int64_t>(L.i) * L.m;
+    for (int j = 0; j < bs; ++j) {
+      const double rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
+      if (L.active && j < L.m) z = fma(__ldg(blocks + off + j), rj, z);
+    }
+    return z;
+  } else {
+    double dv[BS];
+#pragma unroll
+    for (int j = 0; j < BS; ++j) dv[j] = 0.0;
+    if (L.active) {
+      const int64_t off = static_cast<int64_t>(L.blk) * BS * BS + static_cast<int64_t>(L.i) * L.m;
+      if (L.m == BS && BS % 2 == 0) {
+        const double2* src = reinterpret_cast<const double2*>(blocks + off);
+#pragma unroll
+        for (int k = 0; k < BS / 2; ++k) {
+          const double2 v = __ldg(src + k);
+          dv[2 * k] = v.x;
+          dv[2 * k + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+          if (j < L.m) dv[j] = __ldg(blocks + off + j);
+      }
+    }
+    double z = 0.0;
+#pragma unroll
+    for (int j = 0; j < BS; ++j) {
+      const double rj = __shfl_sync(0xffffffffu, r_mine, (L.base + j) & 31);
+      if (L.active && j < L.m) z = fma(dv[j], rj, z);
+    }
+    return z;
   }
-  return z;
 }
+
+// Calls body<BS>() with BS = bs for the block sizes that have a compiled,
+// vectorised apply, else BS = 0.
+#define GK_BJ_DISPATCH(bs, CALL) \
+  do {                           \
+    switch (bs) {                \
+      case 4: CALL(4); break;    \
+      case 8: CALL(8); break;    \
+      case 16: CALL(16); break;  \
+      case 32: CALL(32); break;  \
+      default: CALL(0); break;   \
+    }                            \
+  } while (0)
 
 }  // namespace gk

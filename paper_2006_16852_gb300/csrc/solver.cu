@@ -110,14 +110,14 @@ __device__ __forceinline__ void reduce_finalize(const VecArgs& a, double s0, dou
 // ---- CG --------------------------------------------------------------------
 
 // z = M^{-1} r, p = z, rho = r.z; criteria at k = 0.
-template <int PK>
+template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
   __shared__ double scratch[kRedScratch];
   double rz = 0.0;
   if (PK == PREC_BLOCK) {
     FOR_BLOCK_LANES(L) {
       const double rm = L.active ? a.r[L.row] : 0.0;
-      const double zz = bj_apply_lane(a.blocks, L, a.bs, rm);
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, rm);
       if (L.active) {
         a.p[L.row] = zz;
         rz = fma(rm, zz, rz);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
 }
 
 // x += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); k += 1 and criteria.
-template <int PK>
+template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
   __shared__ double scratch[kRedScratch];
   if (a.st->stop) return;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_updat
         rn = fma(-alpha, a.q[L.row], a.r[L.row]);
         a.r[L.row] = rn;
       }
-      const double zz = bj_apply_lane(a.blocks, L, a.bs, rn);
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, rn);
       if (L.active) {
         a.z[L.row] = zz;
         rz = fma(rn, zz, rz);
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_start_kernel(VecArgs a) {
 }
 
 // p = r + beta (p - omega v); p^ = M^{-1} p.
-template <int PK>
+template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
   if (a.st->stop) return;
   const double beta = a.st->beta, omega = a.st->omega;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
         pn = fma(beta, fma(-omega, a.q[L.row], a.p[L.row]), a.r[L.row]);
         a.p[L.row] = pn;
       }
-      const double zz = bj_apply_lane(a.blocks, L, a.bs, pn);
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, pn);
       if (L.active) a.ph[L.row] = zz;
     }
   } else {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
 }
 
 // s = r - alpha v; s^ = M^{-1} s; ||s||^2 (half-step test).
-template <int PK>
+template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
   __shared__ double scratch[kRedScratch];
   if (a.st->stop) return;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
         a.s[L.row] = sn;
         ss = fma(sn, sn, ss);
       }
-      const double zz = bj_apply_lane(a.blocks, L, a.bs, sn);
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, sn);
       if (L.active) a.sh[L.row] = zz;
     }
   } else {
@@ -394,6 +394,26 @@ Epi spmv_epi(const Solver& S, int mode, const double* u, double* y, int fin, int
   return e;
 }
 
+// As LAUNCH_PK for kernels that apply block Jacobi: the block size becomes
+// a template argument where a vectorised apply is compiled for it.
+#define LAUNCH_PK_BS(kern, grid, s, args)                                                       \
+  do {                                                                                          \
+    if (S.pk == PREC_BLOCK) {                                                                   \
+      switch (S.P->bs) {                                                                        \
+        case 4: kern<PREC_BLOCK, 4><<<grid, kVecThreads, 0, s>>>(args); break;                 \
+        case 8: kern<PREC_BLOCK, 8><<<grid, kVecThreads, 0, s>>>(args); break;                 \
+        case 16: kern<PREC_BLOCK, 16><<<grid, kVecThreads, 0, s>>>(args); break;               \
+        case 32: kern<PREC_BLOCK, 32><<<grid, kVecThreads, 0, s>>>(args); break;               \
+        default: kern<PREC_BLOCK, 0><<<grid, kVecThreads, 0, s>>>(args); break;                \
+      }                                                                                         \
+    } else if (S.pk == PREC_SCALAR) {                                                           \
+      kern<PREC_SCALAR, 0><<<grid, kVecThreads, 0, s>>>(args);                                  \
+    } else {                                                                                    \
+      kern<PREC_NONE, 0><<<grid, kVecThreads, 0, s>>>(args);                                    \
+    }                                                                                           \
+    GK_TRY_CUDA(cudaGetLastError());                                                            \
+  } while (0)
+
 #define LAUNCH_PK(kern, grid, s, args)                                                          \
   do {                                                                                          \
     if (S.pk == PREC_BLOCK) kern<PREC_BLOCK><<<grid, kVecThreads, 0, s>>>(args);               \
@@ -410,7 +430,7 @@ int enqueue_setup(const Solver& S, cudaStream_t s, const VecArgs& a) {
   GK_TRY_CUDA(cudaGetLastError());
   GK_TRY(spmv_launch(*S.A, S.x, spmv_epi(S, EPI_RESID, S.b, S.r, FIN_SETUP_RESID, 0), s));
   if (S.kind == GK_CG) {
-    LAUNCH_PK(cg_start_kernel, S.grid_vec, s, a);
+    LAUNCH_PK_BS(cg_start_kernel, S.grid_vec, s, a);
   } else {
     bicg_start_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
     GK_TRY_CUDA(cudaGetLastError());
@@ -421,14 +441,14 @@ int enqueue_setup(const Solver& S, cudaStream_t s, const VecArgs& a) {
 int enqueue_iteration(const Solver& S, cudaStream_t s, const VecArgs& a) {
   if (S.kind == GK_CG) {
     GK_TRY(spmv_launch(*S.A, S.p, spmv_epi(S, EPI_DOT, S.p, S.q, FIN_CG_SIGMA, 1), s));
-    LAUNCH_PK(cg_update_kernel, S.grid_vec, s, a);
+    LAUNCH_PK_BS(cg_update_kernel, S.grid_vec, s, a);
     LAUNCH_PK(cg_direction_kernel, S.grid_vec, s, a);
   } else {
     const double* ph = (S.pk == PREC_NONE) ? S.p : S.ph;
     const double* sh = (S.pk == PREC_NONE) ? S.s : S.sh;
-    LAUNCH_PK(bicg_dir_kernel, S.grid_vec, s, a);
+    LAUNCH_PK_BS(bicg_dir_kernel, S.grid_vec, s, a);
     GK_TRY(spmv_launch(*S.A, ph, spmv_epi(S, EPI_DOT, S.rh, S.q, FIN_BI_RHV, 1), s));
-    LAUNCH_PK(bicg_s_kernel, S.grid_vec, s, a);
+    LAUNCH_PK_BS(bicg_s_kernel, S.grid_vec, s, a);
     GK_TRY(spmv_launch(*S.A, sh, spmv_epi(S, EPI_DOT2, S.s, S.t, FIN_BI_OMEGA, 2), s));
     bicg_update_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
     GK_TRY_CUDA(cudaGetLastError());

@@ -293,6 +293,63 @@ GK_API int gk_batch_get_info(gk_batch B, int32_t kind, int32_t jacobi, int32_t* 
                              int32_t* threads);
 GK_API int gk_batch_destroy(gk_batch B);
 
+/* ---- learned warm start -------------------------------------------------- */
+/* Not in the paper: a convolutional network that predicts the initial guess
+ * x0 of a variable-coefficient diffusion solve on an H x W grid (natural
+ * row-major ordering) from the log-coefficient field g (one value per grid
+ * point) and the right-hand side b; zero-start CG remains the reference the
+ * prediction is judged against.  Six 3x3 convolutions with dilations
+ * dilations[0..5] and zero padding, channels 2 -> 32 -> 32 -> 32 -> 32 -> 32
+ * -> 1, ReLU between layers.  Input (B, 2, H, W) float = [g, b / rms(b)];
+ * output (B, 1, H, W) float = x / (rms(b) * out_scale).  Parameters: one
+ * float vector, per layer the weights (out, in, 3, 3) then the biases.
+ * Training runs in FP32 (deterministic reductions, Adam with beta1 0.9,
+ * beta2 0.999, eps 1e-8); inference in BF16 (weights, biases, activations)
+ * with FP32 products and sums.  All array arguments are device memory unless
+ * said otherwise; calls on one handle must be ordered (shared scratch). */
+typedef struct gk_wsnet_s* gk_wsnet;
+
+/* batch_max: largest batch of the training / forward calls; dilations: 6
+ * values in 1..64.  GK_ERR_UNSUPPORTED when a gradient kernel's shared
+ * memory (about 4 * (32 W + 96 (W + 2 d)) bytes) exceeds the device's. */
+GK_API int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const int32_t* dilations, gk_wsnet* out);
+GK_API int gk_wsnet_num_params(gk_wsnet N, int64_t* n);
+/* params: host or device floats; resets Adam's moments and step count. */
+GK_API int gk_wsnet_set_params(gk_wsnet N, const float* params, void* stream);
+GK_API int gk_wsnet_get_params(gk_wsnet N, float* params, void* stream);
+/* Training loss: 0 (default) the mean squared error over all outputs; 1 the
+ * energy norm (1 / N) sum_p e_p (A e)_p of e = output - target, with A the
+ * 5-point variable-coefficient operator of each sample (cell coefficients
+ * exp(input channel 0), faces the harmonic mean of the two cells, a boundary
+ * face the cell's own coefficient) -- the norm CG's error decreases in. */
+GK_API int gk_wsnet_set_loss(gk_wsnet N, int32_t kind);
+/* FP32 forward of B inputs x (B, 2, H, W) into y (B, 1, H, W). */
+GK_API int gk_wsnet_forward(gk_wsnet N, int32_t B, const float* x, float* y, void* stream);
+/* The training loss against target (B, 1, H, W) and its gradient for every
+ * parameter, without an update; loss and grads: host or device,
+ * nullable.  Waits for the stream. */
+GK_API int gk_wsnet_gradients(gk_wsnet N, int32_t B, const float* x, const float* target, float* loss,
+                              float* grads, void* stream);
+/* One Adam step on the batch; loss (host or device, nullable) receives the
+ * batch loss before the step (asynchronously: synchronize the stream before
+ * reading a host value). */
+GK_API int gk_wsnet_train_step(gk_wsnet N, int32_t B, const float* x, const float* target, float lr,
+                               float* loss, void* stream);
+/* BF16 inference of B inputs into y (B, 1, H, W) float. */
+GK_API int gk_wsnet_infer_bf16(gk_wsnet N, int32_t B, const float* x, float* y, void* stream);
+/* Network input of one problem from FP64 g and b (H W each) into feat
+ * (2 H W floats) and, when x (FP64 solution) is given, the training target
+ * x / (rms(b) * out_scale) into target (H W floats). */
+GK_API int gk_wsnet_features(gk_wsnet N, const double* g, const double* b, const double* x, double out_scale,
+                             float* feat, float* target, void* stream);
+/* The warm start of one problem: features, BF16 inference, x0 = prediction
+ * * rms(b) * out_scale in FP64; when A (nullable) is given, x0 is then scaled
+ * by alpha = (x0 . b) / (x0 . A x0), the multiple of the prediction closest to
+ * the solution in the A-norm (for SPD A never farther than x = 0). */
+GK_API int gk_wsnet_warm_start(gk_wsnet N, gk_matrix A, const double* g, const double* b, double out_scale,
+                               double* x0, void* stream);
+GK_API int gk_wsnet_destroy(gk_wsnet N);
+
 /* ---- reductions ---------------------------------------------------------- */
 /* result[0] = sum_i x_i y_i in FP64 with a fixed, run-to-run reproducible
  * reduction order (per-block trees, then one block over the block partials;

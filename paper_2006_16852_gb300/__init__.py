@@ -34,8 +34,11 @@ EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get
            "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
            "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
            "gk_solver_destroy", "gk_solver_get_info", "gk_batch_create", "gk_batch_solve",
-           "gk_batch_autotune", "gk_batch_set_threads", "gk_batch_get_info", "gk_batch_destroy", "gk_dot",
-           "gk_dot_noalloc")
+           "gk_batch_autotune", "gk_batch_set_threads", "gk_batch_get_info", "gk_batch_destroy",
+           "gk_wsnet_create", "gk_wsnet_num_params", "gk_wsnet_set_params", "gk_wsnet_get_params",
+           "gk_wsnet_set_loss",
+           "gk_wsnet_forward", "gk_wsnet_gradients", "gk_wsnet_train_step", "gk_wsnet_infer_bf16",
+           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc")
 BATCH_CLASSES = 8
 BATCH_BLOCK_SIZES = (32, 64, 128, 256)
 
@@ -125,6 +128,18 @@ def load(path: str | None = None):
         "gk_batch_set_threads": [vp, i32, i32, vp],
         "gk_batch_get_info": [vp, i32, i32, vp, vp, vp],
         "gk_batch_destroy": [vp],
+        "gk_wsnet_create": [i32, i32, i32, vp, ctypes.POINTER(vp)],
+        "gk_wsnet_num_params": [vp, ctypes.POINTER(i64)],
+        "gk_wsnet_set_params": [vp, vp, vp],
+        "gk_wsnet_get_params": [vp, vp, vp],
+        "gk_wsnet_set_loss": [vp, i32],
+        "gk_wsnet_forward": [vp, i32, vp, vp, vp],
+        "gk_wsnet_gradients": [vp, i32, vp, vp, vp, vp, vp],
+        "gk_wsnet_train_step": [vp, i32, vp, vp, ctypes.c_float, vp, vp],
+        "gk_wsnet_infer_bf16": [vp, i32, vp, vp, vp],
+        "gk_wsnet_features": [vp, vp, vp, vp, f64, vp, vp, vp],
+        "gk_wsnet_warm_start": [vp, vp, vp, vp, f64, vp, vp],
+        "gk_wsnet_destroy": [vp],
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
     }
@@ -409,4 +424,91 @@ class Batch:
         h = getattr(self, "handle", None)
         if h and _lib is not None:
             _lib.gk_batch_destroy(h)
+            self.handle = None
+
+
+WSNET_DILATIONS = (1, 2, 4, 8, 16, 32)
+
+
+class WsNet:
+    """The warm-start network (see gk_wsnet_* in include/gk.h).  Tensors are
+    torch CUDA float32 (inputs (B, 2, H, W), outputs (B, 1, H, W)); parameter
+    vectors are numpy float32 on the host."""
+
+    def __init__(self, H: int, W: int, batch_max: int = 16, dilations=WSNET_DILATIONS):
+        d = (ctypes.c_int32 * 6)(*[int(v) for v in dilations])
+        h = ctypes.c_void_p()
+        _check(lib().gk_wsnet_create(int(H), int(W), int(batch_max), ctypes.addressof(d), ctypes.byref(h)))
+        self.handle = h
+        self.H, self.W, self.batch_max = int(H), int(W), int(batch_max)
+        self.dilations = tuple(int(v) for v in dilations)
+        n = ctypes.c_int64()
+        _check(lib().gk_wsnet_num_params(h, ctypes.byref(n)))
+        self.nparams = n.value
+
+    def set_params(self, params, stream=None):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.nparams:
+            raise GkError(2, f"expected {self.nparams} parameters, got {p.size}")
+        _check(lib().gk_wsnet_set_params(self.handle, p.ctypes.data, _stream(stream)))
+
+    def set_loss(self, kind: str):
+        """'mse' or 'energy' (the A-norm of the error)."""
+        _check(lib().gk_wsnet_set_loss(self.handle, {"mse": 0, "energy": 1}[kind]))
+
+    def get_params(self, stream=None):
+        import numpy as np
+        p = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().gk_wsnet_get_params(self.handle, p.ctypes.data, _stream(stream)))
+        return p
+
+    def _bx(self, x):
+        if x.dim() != 4 or tuple(x.shape[1:]) != (2, self.H, self.W) or x.dtype.__str__() != "torch.float32":
+            raise GkError(2, f"input must be float32 (B, 2, {self.H}, {self.W}), got {tuple(x.shape)} {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("input must be contiguous")
+        return x.shape[0]
+
+    def forward(self, x, y, stream=None):
+        B = self._bx(x)
+        _check(lib().gk_wsnet_forward(self.handle, B, _ptr(x), _ptr(y), _stream(stream, x, y)))
+        return y
+
+    def gradients(self, x, target, stream=None):
+        """(loss, flat gradient as numpy float32)."""
+        import numpy as np
+        B = self._bx(x)
+        loss = ctypes.c_float()
+        g = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().gk_wsnet_gradients(self.handle, B, _ptr(x), _ptr(target), ctypes.addressof(loss), g.ctypes.data,
+                                        _stream(stream, x, target)))
+        return loss.value, g
+
+    def train_step(self, x, target, lr: float, loss_out=None, stream=None):
+        """One Adam step; loss_out: optional device float32 tensor of one element."""
+        B = self._bx(x)
+        _check(lib().gk_wsnet_train_step(self.handle, B, _ptr(x), _ptr(target), float(lr),
+                                         _ptr(loss_out) if loss_out is not None else None,
+                                         _stream(stream, x, target)))
+
+    def infer_bf16(self, x, y, stream=None):
+        B = self._bx(x)
+        _check(lib().gk_wsnet_infer_bf16(self.handle, B, _ptr(x), _ptr(y), _stream(stream, x, y)))
+        return y
+
+    def features(self, g, b, feat, x=None, target=None, out_scale: float = 1.0, stream=None):
+        _check(lib().gk_wsnet_features(self.handle, _ptr(g), _ptr(b), _ptr(x), float(out_scale), _ptr(feat),
+                                       _ptr(target), _stream(stream, g, b)))
+
+    def warm_start(self, g, b, x0, out_scale: float, A: Matrix | None = None, stream=None):
+        """x0 = the network's prediction (scaled by the A-norm-optimal factor when A is given)."""
+        _check(lib().gk_wsnet_warm_start(self.handle, A.handle if A is not None else None, _ptr(g), _ptr(b),
+                                         float(out_scale), _ptr(x0), _stream(stream, g, b, x0)))
+        return x0
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.gk_wsnet_destroy(h)
             self.handle = None

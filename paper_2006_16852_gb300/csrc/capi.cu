@@ -149,24 +149,6 @@ int dot_grid() { return 4 * sm_count(); }
 
 using namespace gk;
 
-namespace {
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) {
-      cudaGetLastError();
-      prev = -1;
-    }
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-}  // namespace
-
 extern "C" const char* gk_last_error(void) { return gk::g_last_error.c_str(); }
 
 extern "C" int32_t gk_version(void) { return 100; }

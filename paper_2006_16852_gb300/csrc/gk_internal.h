@@ -44,6 +44,24 @@ void dfree(void* p);
 int sm_count();
 int current_device();
 
+// Makes `dev` current for the lifetime of the guard, then restores the
+// caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // device-side solver state (one per solver handle; also used by gk_dot)
 // ---------------------------------------------------------------------------

@@ -308,3 +308,126 @@ def varcoef3d(nx: int, sigma: float = 1.0, seed: int = 4):
     rng = np.random.default_rng(seed)
     coef = np.exp(sigma * rng.standard_normal((nx, nx, nx)))
     return varcoef3d_from(coef)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: diffusion with a random coefficient field
+# ---------------------------------------------------------------------------
+
+def grf_field(side: int, seed, n_modes: int = 16, corr: float = 0.1, sigma: float = 1.0):
+    """Gaussian random field on the cell centres ((i + 1) / (side + 1)) of a
+    side x side grid: a sum of n_modes cosines with wave vectors drawn from
+    N(0, (1 / (2 pi corr))^2 I) and uniform phases, amplitude
+    sigma * sqrt(2 / n_modes) -- a random-feature field with variance
+    sigma^2 and squared-exponential correlation of length corr.  Each cosine
+    is evaluated in separated form, cos(u + v) = cos u cos v - sin u sin v."""
+    rng = np.random.default_rng(seed)
+    k = rng.normal(0.0, 1.0 / (2.0 * np.pi * corr), size=(n_modes, 2))
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    t = (np.arange(side) + 1.0) / (side + 1.0)
+    u = 2.0 * np.pi * k[:, 0:1] * t[None, :] + phi[:, None]   # (modes, x)
+    v = 2.0 * np.pi * k[:, 1:2] * t[None, :]                  # (modes, y)
+    g = np.cos(v).T @ np.cos(u) - np.sin(v).T @ np.sin(u)     # (y, x)
+    return sigma * np.sqrt(2.0 / n_modes) * g
+
+
+def gaussian_bumps(side: int, seed, n_bumps: int = 4):
+    """Source term: n_bumps Gaussian bumps with centres U[0.1, 0.9]^2, widths
+    U[0.03, 0.08] and amplitudes U[-1, 1] on the cell centres (each bump the
+    outer product of its two 1D profiles)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.1, 0.9, size=(n_bumps, 2))
+    w = rng.uniform(0.03, 0.08, size=n_bumps)
+    a = rng.uniform(-1.0, 1.0, size=n_bumps)
+    t = (np.arange(side) + 1.0) / (side + 1.0)
+    px = np.exp(-((t[None, :] - c[:, 0:1]) ** 2) / (2.0 * w[:, None] ** 2))  # (bumps, x)
+    py = np.exp(-((t[None, :] - c[:, 1:2]) ** 2) / (2.0 * w[:, None] ** 2))  # (bumps, y)
+    return (py * a[:, None]).T @ px
+
+
+def grf_problem(side: int, index: int, base_seed: int = 6):
+    """Problem `index` of the learned-warm-start family: g = GRF (16 modes,
+    correlation 0.1, sigma 1), cell coefficients exp(g), the 5-point
+    variable-coefficient operator of varcoef2d, b = h^2 f with f four
+    Gaussian bumps (h = 1 / (side + 1)).  Returns (g, A, b); g and b are
+    (side, side) / (side^2,) float64."""
+    g = grf_field(side, (base_seed, index, 0))
+    f = gaussian_bumps(side, (base_seed, index, 1))
+    A = varcoef2d(np.exp(g))
+    h = 1.0 / (side + 1.0)
+    return g, A, (h * h) * f.ravel()
+
+
+_PATTERN_CACHE = {}
+
+
+def _varcoef2d_pattern(side: int):
+    """CSR pattern of the 5-point stencil on a side x side grid and, per
+    stencil position (south, west, centre, east, north), the entry indices
+    and the rows they belong to."""
+    if side not in _PATTERN_CACHE:
+        offs = [(-1, 0), (0, -1), (0, 0), (0, 1), (1, 0)]
+        rowptr, col, _ = _from_offsets((side, side), offs, [1.0] * 5)
+        rows = np.repeat(np.arange(side * side), np.diff(rowptr))
+        delta = col.astype(np.int64) - rows
+        pos = {d: (np.flatnonzero(delta == d), rows[delta == d]) for d in (-side, -1, 0, 1, side)}
+        _PATTERN_CACHE[side] = (rowptr, col, pos)
+    return _PATTERN_CACHE[side]
+
+
+def varcoef2d_values(coef):
+    """Values of varcoef2d(coef) on the fixed pattern of its grid (the same
+    numbers as varcoef2d, without rebuilding the pattern)."""
+    coef = np.asarray(coef, dtype=np.float64)
+    side = coef.shape[0]
+    rowptr, col, pos = _varcoef2d_pattern(side)
+    hm = lambda a, b: 2.0 * a * b / (a + b)
+    west = np.empty_like(coef)
+    east = np.empty_like(coef)
+    south = np.empty_like(coef)
+    north = np.empty_like(coef)
+    west[:, 0] = coef[:, 0]
+    west[:, 1:] = hm(coef[:, 1:], coef[:, :-1])
+    east[:, -1] = coef[:, -1]
+    east[:, :-1] = hm(coef[:, :-1], coef[:, 1:])
+    south[0, :] = coef[0, :]
+    south[1:, :] = hm(coef[1:, :], coef[:-1, :])
+    north[-1, :] = coef[-1, :]
+    north[:-1, :] = hm(coef[:-1, :], coef[1:, :])
+    val = np.empty(col.size)
+    for d, face in ((-side, south), (side, north), (-1, west), (1, east)):
+        idx, rows = pos[d]
+        val[idx] = -face.ravel()[rows]
+    idx, rows = pos[0]
+    val[idx] = (west + east + south + north).ravel()[rows]
+    return val
+
+
+_STACK_CACHE = {}
+
+
+def grf_stack(side: int, indices, base_seed: int = 6):
+    """Problems `indices` of the learned-warm-start family stacked as one
+    block-diagonal system: returns (g (S, side, side), b (S, side^2), CSR of
+    the block-diagonal matrix).  Each block equals grf_problem's matrix.  The
+    stacked pattern and the output buffers are cached per (side, S) and reused
+    by the next call of the same shape (copy what must outlive it)."""
+    rowptr, col, _ = _varcoef2d_pattern(side)
+    n, nnz = side * side, col.size
+    S = len(indices)
+    key = (side, S)
+    if key not in _STACK_CACHE:
+        if S * nnz >= 2 ** 31:
+            raise ValueError("stack too large for int32 indices")
+        rp = np.empty(S * n + 1, dtype=np.int32)
+        rp[:-1].reshape(S, n)[:] = rowptr[None, :-1] + (nnz * np.arange(S, dtype=np.int32))[:, None]
+        rp[-1] = S * nnz
+        cl = (col[None, :] + (n * np.arange(S, dtype=np.int32))[:, None]).ravel()
+        _STACK_CACHE[key] = (rp, cl, np.empty((S, side, side)), np.empty((S, n)), np.empty((S, nnz)))
+    rp, cl, gs, bs, vals = _STACK_CACHE[key]
+    h = 1.0 / (side + 1.0)
+    for k, i in enumerate(indices):
+        gs[k] = grf_field(side, (base_seed, int(i), 0))
+        bs[k] = (h * h) * gaussian_bumps(side, (base_seed, int(i), 1)).ravel()
+        vals[k] = varcoef2d_values(np.exp(gs[k]))
+    return gs, bs, (rp, cl, vals.reshape(-1))

@@ -75,6 +75,9 @@ extern "C" {
 #define GK_CG 0
 #define GK_BICGSTAB 1
 #define GK_IR_CG 2       /* FP64 iterative refinement around an FP32 CG inner solver */
+#define GK_FCG 3         /* flexible CG (Polak-Ribiere beta)                          */
+#define GK_CGS 4         /* conjugate gradient squared                                */
+#define GK_GMRES 5       /* restarted GMRES, right preconditioning                    */
 
 /* Stop reasons (the stopping_status of Section 2.5). */
 #define GK_STOP_NONE 0
@@ -108,7 +111,9 @@ typedef struct {
    * after inner_max_iters iterations (<= 0: max_iters). */
   double inner_reduction;
   int32_t inner_max_iters;
-  int32_t reserved_;
+  /* GK_GMRES only: the restart length m, Arnoldi vectors kept per cycle
+   * (<= 0: 30; at most 128). */
+  int32_t krylov_dim;
 } gk_criteria;
 
 /* Convergence record of one solve (the Convergence logger of Section 2.6). */
@@ -197,8 +202,18 @@ GK_API int gk_precond_get_blocks(gk_precond P, double* out, int64_t n_out, void*
 GK_API int gk_precond_destroy(gk_precond P);
 
 /* ---- solvers (Section 3.1) ---------------------------------------------- */
-/* S_A = generate(A): a CG or BiCGSTAB operator bound to A, optionally
- * preconditioned by P (NULL for none), stopping on *crit.
+/* S_A = generate(A): a Krylov solver operator bound to A -- CG, BiCGSTAB,
+ * FCG, CGS or restarted GMRES (Section 3.1) -- optionally preconditioned by
+ * P (NULL for none), stopping on *crit.
+ * GK_FCG: CG with beta = z_{k+1}.(r_{k+1} - r_k) / (r_k.z_k) (Notay's
+ * flexible CG; equal to CG for a fixed preconditioner in exact arithmetic).
+ * GK_CGS: Sonneveld's CGS in the Templates form with r^ = r_0 (two SpMVs per
+ * iteration; breakdown when r^.r or r^.v^ vanishes).
+ * GK_GMRES: GMRES(m), m = crit->krylov_dim, right-preconditioned (A M^{-1}),
+ * Arnoldi with classical Gram-Schmidt applied twice, Givens rotations; an
+ * Arnoldi step is one iteration and its rotated residual |g_{j+1}| is the
+ * norm the criteria see; every cycle ends with x += M^{-1} V y and a fresh
+ * true residual.
  * GK_IR_CG is the iterative refinement of Sections 2.2.3 and 3.1 with a
  * CG inner solver run in lower precision: the outer loop computes r = b - A x,
  * its norm and the update x += d in FP64; the inner solve of A d = r runs on

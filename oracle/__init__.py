@@ -93,7 +93,10 @@ def lib():
             f.argtypes = [i64, vp, vp, vp, ctypes.c_int32, vp, vp, ctypes.POINTER(_Criteria),
                           ctypes.POINTER(_Status)]
             f.restype = ctypes.c_int
-        for name in ("or_cg", "or_bicgstab"):
+        L.or_gmres.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp, ctypes.POINTER(_Criteria),
+                               ctypes.c_int32, ctypes.POINTER(_Status), vp]
+        L.or_gmres.restype = ctypes.c_int
+        for name in ("or_cg", "or_bicgstab", "or_cgs", "or_fcg"):
             f = getattr(L, name)
             f.argtypes = [i64, vp, vp, vp, ctypes.POINTER(_Precond), vp, vp,
                           ctypes.POINTER(_Criteria), ctypes.POINTER(_Status), vp]
@@ -243,6 +246,35 @@ def cg(A, b, **kw) -> SolveResult:
 
 def bicgstab(A, b, **kw) -> SolveResult:
     return _solve("or_bicgstab", A, b, **kw)
+
+
+def cgs(A, b, **kw) -> SolveResult:
+    return _solve("or_cgs", A, b, **kw)
+
+
+def fcg(A, b, **kw) -> SolveResult:
+    return _solve("or_fcg", A, b, **kw)
+
+
+def gmres(A, b, x0=None, P: Precond | None = None, max_iters=1000, tol=1e-10, rel_to_b=True, krylov_dim=30,
+          history=False) -> SolveResult:
+    """Restarted GMRES(krylov_dim) with right preconditioning."""
+    rowptr, col, val = _csr(A)
+    n = rowptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    crit = _Criteria(int(max_iters), float(tol), 1 if rel_to_b else 0)
+    st = _Status()
+    P = P or Precond()
+    pc = P._c()
+    hist = np.full(int(max_iters) + 2, np.nan) if history else None
+    rc = lib().or_gmres(n, _p(rowptr), _p(col), _p(val), ctypes.byref(pc), _p(b), _p(x), ctypes.byref(crit),
+                        int(krylov_dim), ctypes.byref(st), _p(hist))
+    if rc != OK:
+        raise RuntimeError(f"or_gmres failed: {rc}")
+    if hist is not None:
+        hist = hist[: st.iters + 1]
+    return SolveResult(x, st.iters, st.spmvs, st.rel_res, st.rel_res_true, st.ref_norm, st.stop_reason, hist)
 
 
 def block_jacobi_precision(A, bs, blocks):

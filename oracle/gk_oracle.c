@@ -749,3 +749,228 @@ int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const 
   free(sh); free(t); free(work);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* CGS, FCG and restarted GMRES (the rest of Section 3.1's Krylov family)    */
+/* ------------------------------------------------------------------------ */
+
+/* Preconditioned CGS (Sonneveld 1989, in the form of Barrett et al.,
+ * "Templates", 1994), shadow residual r^ = r_0:
+ *   rho = r^.r;  first step: u = r, p = u;  else beta = rho / rho_prev,
+ *   u = r + beta q, p = u + beta (q + beta p)
+ *   p^ = M^{-1} p;  v^ = A p^;  alpha = rho / (r^.v^);  q = u - alpha v^
+ *   u^ = M^{-1} (u + q);  x = x + alpha u^;  q^ = A u^;  r = r - alpha q^
+ * rho = 0 or r^.v^ = 0 are breakdowns. */
+int or_cgs(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+           const double* b, double* x, const or_criteria* crit, or_status* st, double* res_hist) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t sz = sizeof(double) * (size_t)(n + 1);
+  double *r = malloc(sz), *rh = malloc(sz), *u = malloc(sz), *p = malloc(sz), *q = malloc(sz),
+         *ph = malloc(sz), *vh = malloc(sz), *uh = malloc(sz), *t = malloc(sz);
+  residual(n, rowptr, col, val, b, x, r);
+  st->spmvs = 1;
+  double bnorm = or_norm2(n, b), rnorm = or_norm2(n, r);
+  double ref = crit->rel_to_b ? bnorm : rnorm;
+  if (ref == 0.0) ref = 1.0;
+  double tol = crit->reduction_factor * ref;
+  for (int64_t i = 0; i < n; ++i) {
+    rh[i] = r[i];
+    q[i] = 0.0;
+    p[i] = 0.0;
+  }
+  double rho_prev = 1.0;
+  int64_t k = 0;
+  int stop;
+  if (res_hist) res_hist[0] = rnorm / ref;
+  while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+    double rho = or_dot(n, rh, r);
+    if (!is_finite(rho)) { stop = OR_STOP_NAN; break; }
+    if (rho == 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    if (k == 0) {
+      for (int64_t i = 0; i < n; ++i) {
+        u[i] = r[i];
+        p[i] = u[i];
+      }
+    } else {
+      double beta = rho / rho_prev;
+      for (int64_t i = 0; i < n; ++i) {
+        u[i] = fma(beta, q[i], r[i]);
+        p[i] = fma(beta, fma(beta, p[i], q[i]), u[i]);
+      }
+    }
+    or_precond_apply(n, P, p, ph);
+    or_csr_spmv(n, rowptr, col, val, ph, 1.0, 0.0, vh);
+    st->spmvs += 1;
+    double rv = or_dot(n, rh, vh);
+    if (!is_finite(rv)) { stop = OR_STOP_NAN; break; }
+    if (rv == 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    double alpha = rho / rv;
+    for (int64_t i = 0; i < n; ++i) {
+      q[i] = fma(-alpha, vh[i], u[i]);
+      t[i] = u[i] + q[i];
+    }
+    or_precond_apply(n, P, t, uh);
+    for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, uh[i], x[i]);
+    or_csr_spmv(n, rowptr, col, val, uh, 1.0, 0.0, t);
+    st->spmvs += 1;
+    for (int64_t i = 0; i < n; ++i) r[i] = fma(-alpha, t[i], r[i]);
+    rho_prev = rho;
+    k += 1;
+    rnorm = or_norm2(n, r);
+    if (res_hist) res_hist[k] = rnorm / ref;
+  }
+  st->iters = k;
+  st->stop_reason = stop;
+  finish(n, rowptr, col, val, b, x, ref, rnorm, st, t);
+  free(r); free(rh); free(u); free(p); free(q); free(ph); free(vh); free(uh); free(t);
+  return OR_OK;
+}
+
+/* Flexible CG (Notay 2000; the Polak-Ribiere form of beta):
+ *   as CG, but beta = z_{k+1}.(r_{k+1} - r_k) / (r_k.z_k), with
+ *   r_{k+1} - r_k = -alpha q.  For a fixed SPD preconditioner it equals CG in
+ *   exact arithmetic; it tolerates a preconditioner that varies. */
+int or_fcg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+           const double* b, double* x, const or_criteria* crit, or_status* st, double* res_hist) {
+  if (n < 0 || !crit || !st) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t sz = sizeof(double) * (size_t)(n + 1);
+  double *r = malloc(sz), *z = malloc(sz), *p = malloc(sz), *q = malloc(sz), *t = malloc(sz);
+  residual(n, rowptr, col, val, b, x, r);
+  st->spmvs = 1;
+  double bnorm = or_norm2(n, b), rnorm = or_norm2(n, r);
+  double ref = crit->rel_to_b ? bnorm : rnorm;
+  if (ref == 0.0) ref = 1.0;
+  double tol = crit->reduction_factor * ref;
+  or_precond_apply(n, P, r, z);
+  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  double rho = or_dot(n, r, z);
+  int64_t k = 0;
+  int stop;
+  if (res_hist) res_hist[0] = rnorm / ref;
+  while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+    or_csr_spmv(n, rowptr, col, val, p, 1.0, 0.0, q);
+    st->spmvs += 1;
+    double sigma = or_dot(n, p, q);
+    if (!is_finite(sigma)) { stop = OR_STOP_NAN; break; }
+    if (sigma <= 0.0) { stop = OR_STOP_BREAKDOWN; break; }
+    double alpha = rho / sigma;
+    for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, p[i], x[i]);
+    for (int64_t i = 0; i < n; ++i) r[i] = fma(-alpha, q[i], r[i]);
+    k += 1;
+    rnorm = or_norm2(n, r);
+    if (res_hist) res_hist[k] = rnorm / ref;
+    or_precond_apply(n, P, r, z);
+    for (int64_t i = 0; i < n; ++i) t[i] = -alpha * q[i];
+    double rho_t = or_dot(n, z, t);
+    double rho_new = or_dot(n, r, z);
+    double beta = rho_t / rho;
+    for (int64_t i = 0; i < n; ++i) p[i] = fma(beta, p[i], z[i]);
+    rho = rho_new;
+  }
+  st->iters = k;
+  st->stop_reason = stop;
+  finish(n, rowptr, col, val, b, x, ref, rnorm, st, q);
+  free(r); free(z); free(p); free(q); free(t);
+  return OR_OK;
+}
+
+/* Restarted GMRES(m) (Saad and Schultz 1986) with right preconditioning:
+ * the Arnoldi process on A M^{-1} with modified Gram-Schmidt, Givens
+ * rotations on the Hessenberg matrix, the residual estimate |g_{j+1}| as the
+ * criterion's norm after every step, and at the end of a cycle (m steps or
+ * the criterion met) x = x + M^{-1} V y with y from H y = g; the next cycle
+ * starts from the true residual.  One Arnoldi step counts as one iteration.
+ * A zero h_{j+1,j} (lucky breakdown) ends the cycle. */
+int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+             const double* b, double* x, const or_criteria* crit, int32_t m, or_status* st, double* res_hist) {
+  if (n < 0 || !crit || !st || m < 1) return OR_ERR_ARG;
+  memset(st, 0, sizeof(*st));
+  size_t sz = sizeof(double) * (size_t)(n + 1);
+  double* V = malloc(sz * (size_t)(m + 1));
+  double *w = malloc(sz), *z = malloc(sz), *r = malloc(sz);
+  double* H = calloc((size_t)(m + 1) * (size_t)m, sizeof(double)); /* H[i * m + j] */
+  double *cs = malloc(sizeof(double) * (size_t)m), *sn = malloc(sizeof(double) * (size_t)m);
+  double *g = malloc(sizeof(double) * (size_t)(m + 1)), *y = malloc(sizeof(double) * (size_t)m);
+  residual(n, rowptr, col, val, b, x, r);
+  st->spmvs = 1;
+  double bnorm = or_norm2(n, b), rnorm = or_norm2(n, r);
+  double ref = crit->rel_to_b ? bnorm : rnorm;
+  if (ref == 0.0) ref = 1.0;
+  double tol = crit->reduction_factor * ref;
+  int64_t k = 0;
+  int stop = OR_STOP_NONE;
+  if (res_hist) res_hist[0] = rnorm / ref;
+  while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
+    /* one cycle */
+    double beta = rnorm;
+    for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int j = 0, steps = 0;
+    int cycle_stop = 0;
+    for (j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * (size_t)(n + 1);
+      double* vn = V + (size_t)(j + 1) * (size_t)(n + 1);
+      or_precond_apply(n, P, vj, z);
+      or_csr_spmv(n, rowptr, col, val, z, 1.0, 0.0, w);
+      st->spmvs += 1;
+      for (int i = 0; i <= j; ++i) {
+        double* vi = V + (size_t)i * (size_t)(n + 1);
+        double h = or_dot(n, w, vi);
+        H[i * m + j] = h;
+        for (int64_t l = 0; l < n; ++l) w[l] = fma(-h, vi[l], w[l]);
+      }
+      double hn = or_norm2(n, w);
+      H[(j + 1) * m + j] = hn;
+      if (hn != 0.0)
+        for (int64_t l = 0; l < n; ++l) vn[l] = w[l] / hn;
+      /* previous rotations on column j, then a new one for (j, j+1) */
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[j * m + j], c = H[(j + 1) * m + j];
+      double d = hypot(a, c);
+      cs[j] = d != 0.0 ? a / d : 1.0;
+      sn[j] = d != 0.0 ? c / d : 0.0;
+      H[j * m + j] = d;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k += 1;
+      steps = j + 1;
+      rnorm = fabs(g[j + 1]);
+      if (res_hist) res_hist[k] = rnorm / ref;
+      if (check_stop(rnorm, tol, k, crit->max_iters) != OR_STOP_NONE || hn == 0.0) {
+        cycle_stop = 1;
+        break;
+      }
+    }
+    (void)cycle_stop;
+    /* y = H^{-1} g (upper triangular, steps x steps), x += M^{-1} V y */
+    for (int i = steps - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < steps; ++l) s = fma(-H[i * m + l], y[l], s);
+      y[i] = s / H[i * m + i];
+    }
+    for (int64_t l = 0; l < n; ++l) {
+      double s = 0.0;
+      for (int i = 0; i < steps; ++i) s = fma(V[(size_t)i * (size_t)(n + 1) + l], y[i], s);
+      w[l] = s;
+    }
+    or_precond_apply(n, P, w, z);
+    for (int64_t l = 0; l < n; ++l) x[l] += z[l];
+    residual(n, rowptr, col, val, b, x, r);
+    st->spmvs += 1;
+    rnorm = or_norm2(n, r);
+    if (!is_finite(rnorm)) { stop = OR_STOP_NAN; break; }
+  }
+  st->iters = k;
+  st->stop_reason = stop;
+  finish(n, rowptr, col, val, b, x, ref, rnorm, st, w);
+  free(V); free(w); free(z); free(r); free(H); free(cs); free(sn); free(g); free(y);
+  return OR_OK;
+}

@@ -130,6 +130,22 @@ int or_ir_cg(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
              const or_precond* P, const double* b, double* x, const or_criteria* crit,
              double inner_reduction, int64_t inner_max, or_status* st, int64_t* outer);
 
+/* Preconditioned CGS (Section 3.1; Sonneveld 1989, Templates form). */
+int or_cgs(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+           const double* b, double* x, const or_criteria* crit, or_status* st, double* res_hist);
+
+/* Flexible CG (Section 3.1; Notay 2000): beta = z_{k+1}.(r_{k+1} - r_k) / rho_k. */
+int or_fcg(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+           const double* b, double* x, const or_criteria* crit, or_status* st, double* res_hist);
+
+/* Restarted GMRES(m) with right preconditioning (Section 3.1; Saad and
+ * Schultz 1986): modified Gram-Schmidt Arnoldi, Givens rotations, the
+ * rotated residual |g_{j+1}| as the criterion's norm after every Arnoldi step
+ * (one iteration each); every cycle ends with x += M^{-1} V y and restarts
+ * from the true residual, which the criterion is checked on again. */
+int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const or_precond* P,
+             const double* b, double* x, const or_criteria* crit, int32_t m, or_status* st, double* res_hist);
+
 /* CG and BiCGSTAB in single precision (the batched FP32 solves): the steps of
  * or_cg and or_bicgstab with float matrix values, float b, x, vectors and
  * float sums (in increasing index order), norms sqrt((double) sum); scalar

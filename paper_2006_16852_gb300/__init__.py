@@ -26,7 +26,7 @@ ERR_NAMES = {1: "GK_ERR_ARG", 2: "GK_ERR_DIM", 3: "GK_ERR_DTYPE", 4: "GK_ERR_NOT
 F64, F32 = 0, 1
 FORMATS = {"csr": 0, "csr_merge": 1, "ell": 2, "hyb": 3, "auto": 4}
 FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
-SOLVERS = {"cg": 0, "bicgstab": 1, "ir_cg": 2}
+SOLVERS = {"cg": 0, "bicgstab": 1, "ir_cg": 2, "fcg": 3, "cgs": 4, "gmres": 5}
 STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME = range(6)
 
 # every symbol include/gk.h declares
@@ -53,7 +53,7 @@ class Criteria(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int64), ("reduction_factor", ctypes.c_double),
                 ("rel_to_b", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("time_limit_s", ctypes.c_double), ("inner_reduction", ctypes.c_double),
-                ("inner_max_iters", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("inner_max_iters", ctypes.c_int32), ("krylov_dim", ctypes.c_int32)]
 
 
 class Status(ctypes.Structure):
@@ -291,13 +291,15 @@ class SolveStatus:
 
 
 class Solver:
-    """CG or BiCGSTAB operator S_A bound to A (Section 3.1)."""
+    """Krylov solver operator S_A bound to A (Section 3.1): kind cg, bicgstab,
+    fcg, cgs, gmres, or ir_cg (mixed-precision refinement)."""
 
     def __init__(self, A: Matrix, P: Precond | None = None, kind: str = "cg", max_iters: int = 1000,
                  reduction_factor: float = 1e-10, rel_to_b: bool = True, check_every: int = 0,
-                 time_limit_s: float = 0.0, inner_reduction: float = 0.0, inner_max_iters: int = 0):
+                 time_limit_s: float = 0.0, inner_reduction: float = 0.0, inner_max_iters: int = 0,
+                 krylov_dim: int = 0):
         crit = Criteria(int(max_iters), float(reduction_factor), 1 if rel_to_b else 0, int(check_every),
-                        float(time_limit_s), float(inner_reduction), int(inner_max_iters), 0)
+                        float(time_limit_s), float(inner_reduction), int(inner_max_iters), int(krylov_dim))
         h = ctypes.c_void_p()
         _check(lib().gk_solver_generate(A.handle, P.handle if P is not None else None, SOLVERS[kind],
                                         ctypes.byref(crit), ctypes.byref(h)))

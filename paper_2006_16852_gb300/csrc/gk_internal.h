@@ -96,6 +96,11 @@ enum Fin : int {
   FIN_BI_ITER,      // sums = (r^.r, r.r): k += 1, criteria, next rho/beta
   FIN_TRUE_RESID,   // sums = (||b - A x||^2, -): store
   FIN_IR_RESID,     // sums = (||b - A x||^2, ||b||^2): outer criteria of refinement
+  FIN_FCG_ITER,     // sums = (r.z, r.r, z.q): k += 1, criteria, flexible beta
+  FIN_CGS_START,    // sums = (r^.r): criteria at k = 0, first rho
+  FIN_CGS_ALPHA,    // sums = (r^.v^): alpha
+  FIN_CGS_ITER,     // sums = (r^.r, r.r): k += 1, criteria, next rho and beta
+  FIN_GMRES_RESID,  // sums = (||b - A x||^2, -): the true residual after a GMRES cycle
 };
 
 // ---------------------------------------------------------------------------
@@ -252,6 +257,7 @@ void precond_release(Precond* P);
 enum PrecKind : int { PREC_NONE = 0, PREC_SCALAR = 1, PREC_BLOCK = 2 };
 
 struct IrData;
+struct GmresData;
 
 // Solver handle.
 struct Solver {
@@ -276,12 +282,18 @@ struct Solver {
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   IrData* ir = nullptr;  // GK_IR_CG: the FP32 inner solver
+  GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
 };
 
 // Mixed-precision iterative refinement (mixed.cu).
 int ir_generate(Solver* S);
 int ir_solve(Solver* S, cudaStream_t s);
 void ir_release(IrData* ir);
+
+// Restarted GMRES (gmres.cu).
+int gmres_generate(Solver* S);
+int gmres_solve(Solver* S, cudaStream_t s);
+void gmres_release(GmresData* d);
 
 
 // z = M^{-1} r as a standalone launch.

@@ -1,7 +1,7 @@
 // solver.cu -- the Krylov solver operators S_A (Section 3.1): preconditioned
-// CG (Listing 1) and BiCGSTAB (Listing 3), generated from a matrix, an
-// optional Jacobi preconditioner and combined stopping criteria
-// (Section 2.5).
+// CG (Listing 1), BiCGSTAB (Listing 3), flexible CG and CGS, generated from
+// a matrix, an optional Jacobi preconditioner and combined stopping criteria
+// (Section 2.5).  Restarted GMRES lives in gmres.cu.
 //
 // One iteration is a few fused kernels: each SpMV carries the dot product
 // that follows it, and each vector update carries the preconditioner apply
@@ -34,7 +34,7 @@ struct VecArgs {
   int bs, nblocks;
   const double* b;
   double *x, *r, *p, *q, *z;        // CG (q doubles as BiCGSTAB's v)
-  double *rh, *ph, *s, *sh, *t;     // BiCGSTAB
+  double *rh, *ph, *s, *sh, *t;     // BiCGSTAB; CGS: s = u, sh = u^, t = v^ then q^
   SolverState* st;
   double* partials;
   unsigned int* counter;
@@ -107,6 +107,12 @@ __device__ __forceinline__ void reduce_finalize(const VecArgs& a, double s0, dou
   }
 }
 
+__device__ __forceinline__ void reduce_finalize3(const VecArgs& a, double s0, double s1, double s2, int fin,
+                                                 double* scratch) {
+  double v[3] = {s0, s1, s2}, out[3];
+  if (grid_sum<3>(v, a.partials, a.counter, scratch, out) && threadIdx.x == 0) finalize(fin, out, a.st);
+}
+
 // ---- CG --------------------------------------------------------------------
 
 // z = M^{-1} r, p = z, rho = r.z; criteria at k = 0.
@@ -135,12 +141,12 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
 }
 
 // x += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); k += 1 and criteria.
-template <int PK, int BS = 0>
-__global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
-  __shared__ double scratch[kRedScratch];
+// FLEX (flexible CG): also z.q, for beta = -alpha z.q / rho.
+template <int PK, int BS, bool FLEX>
+__device__ __forceinline__ void cg_update_body(const VecArgs& a, double* scratch) {
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
-  double rz = 0.0, rr = 0.0;
+  double rz = 0.0, rr = 0.0, zq = 0.0;
   if (PK == PREC_BLOCK) {
     FOR_BLOCK_LANES(L) {
       double rn = 0.0;
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_updat
         a.z[L.row] = zz;
         rz = fma(rn, zz, rz);
         rr = fma(rn, rn, rr);
+        if (FLEX) zq = fma(zz, a.q[L.row], zq);
       }
     }
   } else {
@@ -170,6 +177,13 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_updat
           const double2 d = ld2(a.dinv + i);
           rz = fma(r0, d.x * r0, rz);
           rz = fma(r1, d.y * r1, rz);
+          if (FLEX) {
+            zq = fma(d.x * r0, qv.x, zq);
+            zq = fma(d.y * r1, qv.y, zq);
+          }
+        } else if (FLEX) {
+          zq = fma(r0, qv.x, zq);
+          zq = fma(r1, qv.y, zq);
         }
       } else {
         a.x[i] = fma(alpha, a.p[i], a.x[i]);
@@ -177,11 +191,25 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_updat
         a.r[i] = rn;
         rr = fma(rn, rn, rr);
         if (PK == PREC_SCALAR) rz = fma(rn, a.dinv[i] * rn, rz);
+        if (FLEX) zq = fma(PK == PREC_SCALAR ? a.dinv[i] * rn : rn, a.q[i], zq);
       }
     }
     if (PK == PREC_NONE) rz = rr;
   }
-  reduce_finalize(a, rz, rr, FIN_CG_ITER, scratch, false);
+  if (FLEX) reduce_finalize3(a, rz, rr, zq, FIN_FCG_ITER, scratch);
+  else reduce_finalize(a, rz, rr, FIN_CG_ITER, scratch, false);
+}
+
+template <int PK, int BS = 0>
+__global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
+  __shared__ double scratch[kRedScratch];
+  cg_update_body<PK, BS, false>(a, scratch);
+}
+
+template <int PK, int BS = 0>
+__global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) fcg_update_kernel(VecArgs a) {
+  __shared__ double scratch[kRedScratch];
+  cg_update_body<PK, BS, true>(a, scratch);
 }
 
 // p = z + beta p; ends the iteration (loop control).
@@ -310,6 +338,104 @@ __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
   reduce_finalize(a, rho, rr, FIN_BI_ITER, scratch, true);
 }
 
+// ---- CGS ---------------------------------------------------------------------
+
+// r^ = r_0, p = q = 0, rho = r^.r; criteria at k = 0.
+__global__ void __launch_bounds__(kVecThreads) cgs_start_kernel(VecArgs a) {
+  __shared__ double scratch[kRedScratch];
+  double rho = 0.0;
+  FOR_ROWS(i) {
+    const double rv = a.r[i];
+    a.rh[i] = rv;
+    a.p[i] = 0.0;
+    a.q[i] = 0.0;
+    rho = fma(rv, rv, rho);
+  }
+  reduce_finalize(a, rho, 0.0, FIN_CGS_START, scratch, false);
+}
+
+// u = r (first step) or r + beta q; p = u (first step) or u + beta (q + beta p);
+// p^ = M^{-1} p.
+template <int PK, int BS = 0>
+__global__ void __launch_bounds__(kVecThreads) cgs_dir_kernel(VecArgs a) {
+  if (a.st->stop) return;
+  const bool first = a.st->iter == 0;
+  const double beta = a.st->beta;
+  if (PK == PREC_BLOCK) {
+    FOR_BLOCK_LANES(L) {
+      double pn = 0.0;
+      if (L.active) {
+        const double rv = a.r[L.row];
+        const double un = first ? rv : fma(beta, a.q[L.row], rv);
+        pn = first ? un : fma(beta, fma(beta, a.p[L.row], a.q[L.row]), un);
+        a.s[L.row] = un;
+        a.p[L.row] = pn;
+      }
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, pn);
+      if (L.active) a.ph[L.row] = zz;
+    }
+  } else {
+    FOR_ROWS(i) {
+      const double rv = a.r[i];
+      const double un = first ? rv : fma(beta, a.q[i], rv);
+      const double pn = first ? un : fma(beta, fma(beta, a.p[i], a.q[i]), un);
+      a.s[i] = un;
+      a.p[i] = pn;
+      if (PK == PREC_SCALAR) a.ph[i] = a.dinv[i] * pn;
+    }
+  }
+}
+
+// q = u - alpha v^; u^ = M^{-1} (u + q); x += alpha u^.
+template <int PK, int BS = 0>
+__global__ void __launch_bounds__(kVecThreads) cgs_q_kernel(VecArgs a) {
+  if (a.st->stop) return;
+  const double alpha = a.st->alpha;
+  if (PK == PREC_BLOCK) {
+    FOR_BLOCK_LANES(L) {
+      double w = 0.0;
+      if (L.active) {
+        const double qn = fma(-alpha, a.t[L.row], a.s[L.row]);
+        a.q[L.row] = qn;
+        w = a.s[L.row] + qn;
+      }
+      const double uh = bj_apply_lane<BS>(a.blocks, L, a.bs, w);
+      if (L.active) {
+        a.sh[L.row] = uh;
+        a.x[L.row] = fma(alpha, uh, a.x[L.row]);
+      }
+    }
+  } else {
+    FOR_ROWS(i) {
+      const double qn = fma(-alpha, a.t[i], a.s[i]);
+      a.q[i] = qn;
+      const double w = a.s[i] + qn;
+      const double uh = PK == PREC_SCALAR ? a.dinv[i] * w : w;
+      a.sh[i] = uh;
+      a.x[i] = fma(alpha, uh, a.x[i]);
+    }
+  }
+}
+
+// r -= alpha q^; (r^.r, r.r); k += 1, criteria, next rho and beta; ends the
+// iteration.
+__global__ void __launch_bounds__(kVecThreads) cgs_update_kernel(VecArgs a) {
+  __shared__ double scratch[kRedScratch];
+  if (a.st->stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
+    return;
+  }
+  const double alpha = a.st->alpha;
+  double rho = 0.0, rr = 0.0;
+  FOR_ROWS(i) {
+    const double rn = fma(-alpha, a.t[i], a.r[i]);
+    a.r[i] = rn;
+    rho = fma(a.rh[i], rn, rho);
+    rr = fma(rn, rn, rr);
+  }
+  reduce_finalize(a, rho, rr, FIN_CGS_ITER, scratch, true);
+}
+
 #undef FOR_ROWS
 #undef FOR_PAIRS
 #undef FOR_BLOCK_LANES
@@ -335,6 +461,7 @@ void solver_release(Solver* S) {
   dfree(S->counter);
   if (S->h_st) cudaFreeHost(S->h_st);
   ir_release(S->ir);
+  gmres_release(S->gm);
   precond_release(S->P);
   matrix_release(S->A);
   if (prev >= 0) cudaSetDevice(prev);
@@ -429,8 +556,11 @@ int enqueue_setup(const Solver& S, cudaStream_t s, const VecArgs& a) {
                                      c.rel_to_b, tl);
   GK_TRY_CUDA(cudaGetLastError());
   GK_TRY(spmv_launch(*S.A, S.x, spmv_epi(S, EPI_RESID, S.b, S.r, FIN_SETUP_RESID, 0), s));
-  if (S.kind == GK_CG) {
+  if (S.kind == GK_CG || S.kind == GK_FCG) {
     LAUNCH_PK_BS(cg_start_kernel, S.grid_vec, s, a);
+  } else if (S.kind == GK_CGS) {
+    cgs_start_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    GK_TRY_CUDA(cudaGetLastError());
   } else {
     bicg_start_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
     GK_TRY_CUDA(cudaGetLastError());
@@ -439,10 +569,19 @@ int enqueue_setup(const Solver& S, cudaStream_t s, const VecArgs& a) {
 }
 
 int enqueue_iteration(const Solver& S, cudaStream_t s, const VecArgs& a) {
-  if (S.kind == GK_CG) {
+  if (S.kind == GK_CG || S.kind == GK_FCG) {
     GK_TRY(spmv_launch(*S.A, S.p, spmv_epi(S, EPI_DOT, S.p, S.q, FIN_CG_SIGMA, 1), s));
-    LAUNCH_PK_BS(cg_update_kernel, S.grid_vec, s, a);
+    if (S.kind == GK_CG) LAUNCH_PK_BS(cg_update_kernel, S.grid_vec, s, a);
+    else LAUNCH_PK_BS(fcg_update_kernel, S.grid_vec, s, a);
     LAUNCH_PK(cg_direction_kernel, S.grid_vec, s, a);
+  } else if (S.kind == GK_CGS) {
+    const double* ph = (S.pk == PREC_NONE) ? S.p : S.ph;
+    LAUNCH_PK_BS(cgs_dir_kernel, S.grid_vec, s, a);
+    GK_TRY(spmv_launch(*S.A, ph, spmv_epi(S, EPI_DOT, S.rh, S.t, FIN_CGS_ALPHA, 1), s));
+    LAUNCH_PK_BS(cgs_q_kernel, S.grid_vec, s, a);
+    GK_TRY(spmv_launch(*S.A, S.sh, spmv_epi(S, EPI_COPY, nullptr, S.t, FIN_NONE, 1), s));
+    cgs_update_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    GK_TRY_CUDA(cudaGetLastError());
   } else {
     const double* ph = (S.pk == PREC_NONE) ? S.p : S.ph;
     const double* sh = (S.pk == PREC_NONE) ? S.s : S.sh;
@@ -457,7 +596,7 @@ int enqueue_iteration(const Solver& S, cudaStream_t s, const VecArgs& a) {
 }
 
 int enqueue_final(const Solver& S, cudaStream_t s) {
-  double* scratch = (S.kind == GK_CG) ? S.q : S.t;
+  double* scratch = (S.kind == GK_CG || S.kind == GK_FCG) ? S.q : S.t;
   return spmv_launch(*S.A, S.x, spmv_epi(S, EPI_RESID, S.b, scratch, FIN_TRUE_RESID, 0), s);
 }
 
@@ -522,7 +661,8 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
   Matrix* A = as_matrix(hA);
   Precond* P = as_precond(hP);
   if (!A || !crit) return set_error(GK_ERR_ARG, "gk_solver_generate: NULL matrix or criteria");
-  if (kind != GK_CG && kind != GK_BICGSTAB && kind != GK_IR_CG)
+  if (kind != GK_CG && kind != GK_BICGSTAB && kind != GK_IR_CG && kind != GK_FCG && kind != GK_CGS &&
+      kind != GK_GMRES)
     return set_error(GK_ERR_ARG, "unknown solver kind %d", kind);
   if (A->n_rows != A->n_cols) return set_error(GK_ERR_DIM, "gk_solver_generate: matrix is not square");
   if (P && P->n != A->n_rows) return set_error(GK_ERR_DIM, "preconditioner size %lld != %lld",
@@ -551,7 +691,13 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
         (rc = alloc_vec(&S->r, S->n, by)) || (rc = alloc_vec(&S->p, S->n, by)) ||
         (rc = alloc_vec(&S->q, S->n, by)))
       break;
-    if (kind == GK_CG && S->pk == PREC_BLOCK && (rc = alloc_vec(&S->z, S->n, by))) break;
+    if ((kind == GK_CG || kind == GK_FCG) && S->pk == PREC_BLOCK && (rc = alloc_vec(&S->z, S->n, by))) break;
+    if (kind == GK_CGS) {
+      if ((rc = alloc_vec(&S->rh, S->n, by)) || (rc = alloc_vec(&S->s, S->n, by)) ||
+          (rc = alloc_vec(&S->t, S->n, by)) || (rc = alloc_vec(&S->sh, S->n, by)))
+        break;
+      if (S->pk != PREC_NONE && (rc = alloc_vec(&S->ph, S->n, by))) break;
+    }
     if (kind == GK_BICGSTAB) {
       if ((rc = alloc_vec(&S->rh, S->n, by)) || (rc = alloc_vec(&S->s, S->n, by)) ||
           (rc = alloc_vec(&S->t, S->n, by)))
@@ -562,7 +708,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
     if ((rc = dalloc_n(&S->st, 1, by))) break;
     S->grid_vec = vec_grid(*S);
     const int pg = std::max(S->grid_vec, spmv_max_grid(*A));
-    if ((rc = dalloc_n(&S->partials, static_cast<size_t>(2 * (pg + kFixupMaxGrid)), by)) ||
+    if ((rc = dalloc_n(&S->partials, static_cast<size_t>(3 * (pg + kFixupMaxGrid)), by)) ||
         (rc = dalloc_n(&S->counter, 1, by)))
       break;
     cudaError_t e = cudaMemset(S->counter, 0, sizeof(unsigned int));
@@ -573,6 +719,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
       break;
     }
     if (kind == GK_IR_CG && (rc = ir_generate(S))) break;
+    if (kind == GK_GMRES && (rc = gmres_generate(S))) break;
   } while (false);
   if (prev != A->device) cudaSetDevice(prev);
   if (rc != GK_OK) return rc;
@@ -605,6 +752,8 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
     }
     if (S->kind == GK_IR_CG) {
       if ((rc = ir_solve(S, s))) break;
+    } else if (S->kind == GK_GMRES) {
+      if ((rc = gmres_solve(S, s))) break;
     } else if (S->crit.check_every > 0) {
       // host-driven loop: groups of check_every iterations, then a status read
       VecArgs a = vec_args(*S, 0);

@@ -37,6 +37,7 @@ __device__ __forceinline__ void bicg_new_rho(SolverState* st, double rho) {
   }
 }
 
+// s: the sums of the reduction (two, or three for FIN_FCG_ITER).
 __device__ __forceinline__ void finalize(int fin, const double* s, SolverState* st) {
   st->red[0] = s[0];
   st->red[1] = s[1];
@@ -116,6 +117,55 @@ __device__ __forceinline__ void finalize(int fin, const double* s, SolverState* 
       if (stop == GK_STOP_NONE) bicg_new_rho(st, s[0]);
       break;
     }
+    case FIN_FCG_ITER: {
+      // beta = z_{k+1}.(r_{k+1} - r_k) / rho_k with r_{k+1} - r_k = -alpha q
+      st->iter += 1;
+      st->rnorm = sqrt(s[1]);
+      st->stop = check_stop(st, st->rnorm, st->iter);
+      st->beta = (-st->alpha * s[2]) / st->rho;
+      st->rho = s[0];
+      break;
+    }
+    case FIN_CGS_START:
+      st->stop = check_stop(st, st->rnorm, 0);
+      if (st->stop == GK_STOP_NONE) {
+        if (!isfinite(s[0])) st->stop = GK_STOP_NAN;
+        else if (s[0] == 0.0) st->stop = GK_STOP_BREAKDOWN;
+        else st->rho = s[0];
+      }
+      break;
+    case FIN_CGS_ALPHA: {
+      st->spmvs += 1;
+      const double rv = s[0];
+      if (!isfinite(rv)) st->stop = GK_STOP_NAN;
+      else if (rv == 0.0) st->stop = GK_STOP_BREAKDOWN;
+      else st->alpha = st->rho / rv;
+      break;
+    }
+    case FIN_CGS_ITER: {
+      st->spmvs += 1;
+      st->iter += 1;
+      st->rnorm = sqrt(s[1]);
+      st->stop = check_stop(st, st->rnorm, st->iter);
+      if (st->stop == GK_STOP_NONE) {
+        const double rho = s[0];
+        if (!isfinite(rho)) {
+          st->stop = GK_STOP_NAN;
+        } else if (rho == 0.0) {
+          st->stop = GK_STOP_BREAKDOWN;
+        } else {
+          st->beta = rho / st->rho;
+          st->rho_prev = st->rho;
+          st->rho = rho;
+        }
+      }
+      break;
+    }
+    case FIN_GMRES_RESID:
+      st->spmvs += 1;
+      st->rnorm = sqrt(s[0]);
+      st->true_rr = s[0];
+      break;
     case FIN_TRUE_RESID:
       st->spmvs += 1;
       st->true_rr = s[0];

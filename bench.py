@@ -25,7 +25,8 @@ Beside the step (not part of its value) the line carries "mixed": the
 mixed-precision workload (7-point variable-coefficient diffusion on 256^3,
 log-normal sigma 1) solved to 1e-12 by plain FP64 CG and by FP64 refinement
 around FP32 CG with Jacobi or adaptive FP16/FP32 block Jacobi; and
-"batched": 10,000
+"learned": CG to 1e-10 on held-out 256x256 random-coefficient diffusion
+problems from the trained network's x0 and from zero; and "batched": 10,000
 small variable-coefficient systems solved per system in one graph launch
 (FP64 CG / BiCGSTAB / refinement to 1e-10, FP32 CG / BiCGSTAB to 1e-6), with
 solves/s and the time against plain FP64 CG on the block-diagonal matrix.
@@ -579,6 +580,81 @@ def run_mixed(dev, side=256, tol=1e-12):
                                "speedup_vs_plain": round(plain / out[chosen]["ms"], 3)}}
 
 
+# ---------------------------------------------------------------------------
+# learned warm start (reported beside the step)
+# ---------------------------------------------------------------------------
+
+LEARNED_WORKLOAD = ("2D diffusion on a 256x256 grid (n=65,536), cell coefficients exp(GRF), GRF a sum of 16 random "
+                    "Fourier modes (correlation length 0.1, sigma 1), source 4 Gaussian bumps (seeds (6, i, .)); "
+                    "held-out problems i >= 1,000,000; Jacobi-CG to ||r|| <= 1e-10 ||b||")
+# FP32 FMA issue rate of a GB300: 152 SMs x 128 lanes x 2 flops at 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_learned(dev, problems=8):
+    import torch
+    import paper_2006_16852_gb300 as gk
+    from paper_2006_16852_gb300 import learned as LN
+    path = os.path.join(LN.DATA_DIR, "wsnet_256.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights at paper_2006_16852_gb300/data/wsnet_256.npz"}
+    net, scale, meta = LN.load(path)
+    idx = range(1_000_000, 1_000_000 + problems)
+    res = LN.evaluate(net, idx, scale)
+    summ = LN.summarize(res)
+    # plain FP64 CG (no preconditioner, zero start) on the same problems
+    import workloads as W
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    plain_ms, plain_it = 0.0, 0
+    stream = torch.cuda.current_stream(dev)
+    for i in idx:
+        g, A, b = W.grf_problem(net.H, i)
+        M = gk.Matrix(*[t(a) for a in A], fmt="ell")
+        S = gk.Solver(M, None, "cg", max_iters=50000, reduction_factor=1e-10)
+        bd = t(b)
+        for _ in range(2):
+            x = torch.zeros_like(bd)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, bd, x)
+            e1.record(stream)
+            e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        plain_it += st.iters
+    # BF16 inference kernel alone (one problem)
+    feat = torch.zeros((1, 2, net.H, net.W), dtype=torch.float32, device=dev)
+    y = torch.zeros((1, 1, net.H, net.W), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        net.infer_bf16(feat, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        net.infer_bf16(feat, y)
+    e1.record(stream)
+    e1.synchronize()
+    inf_ms = e0.elapsed_time(e1) / reps
+    macs = net.H * net.W * sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
+    tfl = 2.0 * macs / (inf_ms * 1e-3) / 1e12
+    best = "warm" if summ["ms_warm"] < summ["ms_zero"] else "zero"
+    return {
+        "workload": LEARNED_WORKLOAD, "network": {"layers": 6, "width": 32, "dilations": list(net.dilations),
+                                                  "weights": "BF16 (trained in FP32)", "params": net.nparams},
+        "training": {k: meta[k] for k in ("samples", "epochs", "batch", "lr", "loss", "data_seconds",
+                                          "train_seconds", "loss_history") if k in meta},
+        "eval": summ,
+        "time_to_tol_ms": {"plain_fp64_cg": round(plain_ms, 3), "plain_iters": plain_it,
+                           "jacobi_cg_zero_start": summ["ms_zero"], "jacobi_cg_learned_start": summ["ms_warm"],
+                           "chosen_form": "jacobi_cg_" + ("learned" if best == "warm" else "zero") + "_start",
+                           "speedup_vs_plain": round(plain_ms / min(summ["ms_warm"], summ["ms_zero"]), 3),
+                           "learned_vs_zero_start": round(summ["ms_zero"] / summ["ms_warm"], 4)},
+        "inference": {"kernel": "conv_fwd_kernel (BF16 in, FP32 accumulate, CUDA cores)", "ms": round(inf_ms, 4),
+                      "tflops": round(tfl, 2), "bound": "alu", "peak": round(FP32_PEAK_TFLOPS, 1),
+                      "peak_source": "FP32 FMA issue rate (152 SMs x 128 x 2 x 2.07 GHz)",
+                      "frac": round(tfl / FP32_PEAK_TFLOPS, 4)},
+    }
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -732,6 +808,8 @@ def run_gpu(args):
         out["batched"] = run_batched(dev)
     if not args.no_mixed:
         out["mixed"] = run_mixed(dev, side=args.mixed_side)
+    if not args.no_learned:
+        out["learned"] = run_learned(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -887,6 +965,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision workload")
     ap.add_argument("--mixed-only", action="store_true", help="only the mixed-precision workload")
     ap.add_argument("--mixed-side", type=int, default=256, help="grid side of the mixed-precision workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--learned-only", action="store_true", help="only the learned warm start")
     ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
     ap.add_argument("--batch-forms", default=None, help="--batched-only: comma list of " + ", ".join(BATCH_FORMS))
     ap.add_argument("--batch-no-tune", action="store_true",
@@ -903,7 +983,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.mixed_only:
+    if args.learned_only:
+        import torch
+        import paper_2006_16852_gb300 as gk
+        gk.load()
+        out = run_learned(torch.device("cuda:0"))
+    elif args.mixed_only:
         import torch
         import paper_2006_16852_gb300 as gk
         gk.load()

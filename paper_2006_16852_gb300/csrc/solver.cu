@@ -107,6 +107,7 @@ __device__ __forceinline__ void reduce_finalize(const VecArgs& a, double s0, dou
   }
 }
 
+// scratch: >= 3 * blockDim.x doubles.
 __device__ __forceinline__ void reduce_finalize3(const VecArgs& a, double s0, double s1, double s2, int fin,
                                                  double* scratch) {
   double v[3] = {s0, s1, s2}, out[3];
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_updat
 
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) fcg_update_kernel(VecArgs a) {
-  __shared__ double scratch[kRedScratch];
+  __shared__ double scratch[3 * kVecThreads];  // a three-value block reduction
   cg_update_body<PK, BS, true>(a, scratch);
 }
 

@@ -8,6 +8,7 @@ orchestrates calls (every arithmetic step runs in the library's kernels, the
 problems come from ``workloads``)."""
 from __future__ import annotations
 
+import ast
 import math
 import os
 import time
@@ -223,6 +224,6 @@ def load(path: str, batch_max: int = 1):
     side = int(z["side"])
     net = gk.WsNet(side, side, batch_max, tuple(int(v) for v in z["dilations"]))
     net.set_params(z["params"])
-    return net, float(z["out_scale"]), z["meta"].item()
+    return net, float(z["out_scale"]), ast.literal_eval(str(z["meta"]))
 if __name__ == "__main__":
     main()

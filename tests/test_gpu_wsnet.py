@@ -168,3 +168,26 @@ def test_warm_start_against_zero_start(gk, orc):
     gk.solve(S, to_dev(b), x)
     r = b - orc.spmv(A, to_np(x))
     assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(b)
+
+
+def test_committed_network_on_held_out_problems(gk, orc):
+    """The trained 256 x 256 network shipped with the package: on held-out
+    problems its x0 is closer to the solution than zero in the A-norm, and
+    CG from it meets the criterion (checked with the oracle's SpMV)."""
+    import os
+    from paper_2006_16852_gb300 import learned as LN
+    path = os.path.join(LN.DATA_DIR, "wsnet_256.npz")
+    net, scale, meta = LN.load(path)
+    assert meta["samples"] == 20000 and net.dilations == tuple(meta["dilations"])
+    res = LN.evaluate(net, [1_000_100, 1_000_101], scale)
+    for i, r in zip((1_000_100, 1_000_101), res):
+        assert r["x0_energy_error"] < 0.6
+        assert r["warm"]["stop_reason"] == gk.STOP_CONVERGED
+    g, A, b = W.grf_problem(256, 1_000_100)
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="ell")
+    S = gk.Solver(M, gk.Precond(M, 1), "cg", max_iters=20000, reduction_factor=1e-10)
+    x = to_dev(np.zeros(65536))
+    net.warm_start(to_dev(g.reshape(-1)), to_dev(b), x, scale, A=M)
+    gk.solve(S, to_dev(b), x)
+    r = b - orc.spmv(A, to_np(x))
+    assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(b)

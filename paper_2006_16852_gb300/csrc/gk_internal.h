@@ -134,10 +134,12 @@ struct Epi {
 constexpr int kMergeThreads = 128;
 constexpr int kMergeItems = 16;  // merge-path items (row ends + nonzeros) per thread
 constexpr int kMergeTile = kMergeThreads * kMergeItems;
-constexpr int kBinWarps = 8;       // warps per block of the binned kernel (one block per SM)
-constexpr int kBinRowsMax = 32;    // rows per warp item
-constexpr int kBinShortMax = 32;   // longest "short" row
-constexpr int kBinItemNnz = kBinRowsMax * kBinShortMax;
+// GK_CSR: rows of up to kSliceMaxLen entries go to length-sorted slices of 32
+// rows; longer rows are summed one warp per row, beyond kBlockRowLen one
+// thread block per row.
+constexpr int kSliceMaxLen = 256;
+constexpr int kBlockRowLen = 4096;
+constexpr int kSliceThreads = 256;
 constexpr int kEllThreads = 256;
 // Blocks of the merge-path fix-up launch; reduction scratch holds
 // 2 * (max grid + kFixupMaxGrid) doubles.
@@ -170,13 +172,20 @@ struct Matrix {
   int32_t* col = nullptr;
   double* val = nullptr;
   std::vector<int32_t> h_rowptr;  // host copy of the row pointers (planning)
-  // GK_CSR: warp items of short rows and the list of long rows
-  int32_t* item_r0 = nullptr;
-  int32_t* item_r1 = nullptr;
-  int64_t n_items = 0;
-  int32_t* long_rows = nullptr;
-  int64_t n_long = 0;
-  int grid_bin = 0;
+  // GK_CSR: rows sorted by decreasing length.  Rows of <= kSliceMaxLen
+  // entries in slices of 32 rows, each slice column-major (entry k of lane l
+  // at sl_off[c] + 32 k + l) and padded to its longest row with column -1;
+  // the rest by length: mid rows (warp per row), big rows (block per row).
+  int32_t* sl_perm = nullptr;   // [n_sell] the row of each slice lane
+  int64_t* sl_off = nullptr;    // [n_slices + 1]
+  int32_t* sl_col = nullptr;
+  double* sl_val = nullptr;
+  int64_t n_sell = 0, n_slices = 0, sl_entries = 0;
+  int32_t* mid_rows = nullptr;
+  int64_t n_mid = 0;
+  int32_t* big_rows = nullptr;
+  int64_t n_big = 0;
+  int grid_sl = 0;
   // GK_CSR_MERGE
   MergePlan merge;
   // GK_ELL / GK_HYB
@@ -211,7 +220,7 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s);
 int spmv_max_grid(const Matrix& A);
 // Persistent grid sizes of the SpMV kernels for a given amount of work.
 int merge_grid(int64_t n_tiles);
-int bin_grid(int64_t work_warps);
+int sliced_grid(int64_t warp_items, int64_t big_rows);
 int ell_grid(int64_t n_rows);
 
 // Format construction (matrix.cu).

@@ -105,25 +105,46 @@ struct MatrixDeleter {
   void operator()(Matrix* m) const { matrix_release(m); }
 };
 
-// Efficiency of the binned kernel's FP64 pipe: stored entries over the DFMA
-// lane slots its warps issue (a warp item issues 32 x its longest row; a
-// long row 32 x ceil(len/32) plus its butterfly).
-double binned_efficiency(const std::vector<int32_t>& rp, int64_t n) {
+// Fill the length-sorted slices: one thread per (slice, lane); entry k of
+// the lane's row at off[c] + 32 k + lane, padding with column -1 and 0.
+__global__ void slice_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, const int32_t* __restrict__ perm,
+                                  const int64_t* __restrict__ off, int64_t n_slices, int64_t n_sell,
+                                  int32_t* __restrict__ scol, double* __restrict__ sval) {
+  const int64_t total = n_slices * 32;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = t >> 5;
+    const int lane = static_cast<int>(t & 31);
+    const int64_t o0 = off[c];
+    const int L = static_cast<int>((off[c + 1] - o0) >> 5);
+    const int row = t < n_sell ? perm[t] : -1;
+    const int k0 = row >= 0 ? rowptr[row] : 0;
+    const int len = row >= 0 ? rowptr[row + 1] - k0 : 0;
+    for (int k = 0; k < L; ++k) {
+      const int64_t d = o0 + 32 * static_cast<int64_t>(k) + lane;
+      scol[d] = k < len ? col[k0 + k] : -1;
+      sval[d] = k < len ? val[k0 + k] : 0.0;
+    }
+  }
+}
+
+// Stored entries over the DFMA lane slots the GK_CSR kernel issues (slices:
+// 32 x their longest row; a mid row 32 x ceil(len / 32) plus its butterfly;
+// a big row 256 x ceil(len / 256)).
+double sliced_efficiency(const std::vector<int32_t>& rp, int64_t n) {
+  std::vector<int64_t> cnt(kSliceMaxLen + 1, 0);
   double slots = 0.0, nnz = static_cast<double>(rp[n]);
-  int64_t i = 0;
-  while (i < n) {
-    int64_t len = rp[i + 1] - rp[i];
-    if (len > kBinShortMax) {
-      slots += 32.0 * ((len + 31) / 32) + 160.0;
-      ++i;
-      continue;
-    }
-    int64_t start = i, mx = 0;
-    while (i < n && i - start < kBinRowsMax && rp[i + 1] - rp[i] <= kBinShortMax) {
-      mx = std::max<int64_t>(mx, rp[i + 1] - rp[i]);
-      ++i;
-    }
-    slots += 32.0 * std::max<int64_t>(mx, 1);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t len = rp[i + 1] - rp[i];
+    if (len <= kSliceMaxLen) cnt[len] += 1;
+    else if (len <= kBlockRowLen) slots += 32.0 * ((len + 31) / 32) + 160.0;
+    else slots += 256.0 * ((len + 255) / 256) + 256.0;
+  }
+  int64_t in_slice = 0;  // rows placed so far, longest first
+  for (int64_t L = kSliceMaxLen; L >= 0; --L) {
+    for (int64_t r = 0; r < cnt[L]; ++r, ++in_slice)
+      if ((in_slice & 31) == 0) slots += 32.0 * static_cast<double>(L);
   }
   return slots > 0 ? nnz / slots : 1.0;
 }
@@ -162,7 +183,7 @@ void matrix_release(Matrix* A) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(A->device);
-  void* ptrs[] = {A->rowptr, A->col, A->val, A->item_r0, A->item_r1, A->long_rows,
+  void* ptrs[] = {A->rowptr, A->col, A->val, A->sl_perm, A->sl_off, A->sl_col, A->sl_val, A->mid_rows, A->big_rows,
                   A->merge.tile_i, A->merge.tile_j, A->merge.head_val, A->merge.head_row,
                   A->merge.carry_val, A->merge.carry_row, A->merge.cont, A->ell_col, A->ell_val,
                   A->tail_rows, A->tail_rowptr, A->tail_col, A->tail_val, A->tail_slot, A->tail_sum,
@@ -246,28 +267,55 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
 
   // ---- format ------------------------------------------------------------------
   int fmt = format;
-  if (fmt == GK_AUTO) fmt = (binned_efficiency(rp, n_rows) >= 0.75) ? GK_CSR : GK_CSR_MERGE;
+  if (fmt == GK_AUTO) fmt = (sliced_efficiency(rp, n_rows) >= 0.75) ? GK_CSR : GK_CSR_MERGE;
   A->format = fmt;
   if (fmt == GK_CSR) {
-    std::vector<int32_t> r0s, r1s, longs;
-    int64_t i = 0;
-    while (i < n_rows) {
-      if (rp[i + 1] - rp[i] > kBinShortMax) {
-        longs.push_back(static_cast<int32_t>(i));
-        ++i;
-        continue;
-      }
-      int64_t start = i;
-      while (i < n_rows && i - start < kBinRowsMax && rp[i + 1] - rp[i] <= kBinShortMax) ++i;
-      r0s.push_back(static_cast<int32_t>(start));
-      r1s.push_back(static_cast<int32_t>(i));
+    // counting sort by decreasing length (ties: increasing row index)
+    std::vector<int64_t> cnt(kSliceMaxLen + 2, 0);
+    std::vector<int32_t> mid, big;
+    for (int64_t i = 0; i < n_rows; ++i) {
+      const int64_t len = rp[i + 1] - rp[i];
+      if (len <= kSliceMaxLen) cnt[kSliceMaxLen - len + 1] += 1;
+      else if (len <= kBlockRowLen) mid.push_back(static_cast<int32_t>(i));
+      else big.push_back(static_cast<int32_t>(i));
     }
-    A->n_items = static_cast<int64_t>(r0s.size());
-    A->n_long = static_cast<int64_t>(longs.size());
-    GK_TRY(upload(&A->item_r0, r0s, 0, bytes, s));
-    GK_TRY(upload(&A->item_r1, r1s, 0, bytes, s));
-    GK_TRY(upload(&A->long_rows, longs, 0, bytes, s));
-    A->grid_bin = bin_grid(std::max(A->n_items, A->n_long));
+    for (int64_t L = 1; L <= kSliceMaxLen + 1; ++L) cnt[L] += cnt[L - 1];
+    const int64_t n_sell = cnt[kSliceMaxLen + 1];
+    std::vector<int32_t> perm(static_cast<size_t>(n_sell));
+    for (int64_t i = 0; i < n_rows; ++i) {
+      const int64_t len = rp[i + 1] - rp[i];
+      if (len <= kSliceMaxLen) perm[cnt[kSliceMaxLen - len]++] = static_cast<int32_t>(i);
+    }
+    auto by_len = [&](int32_t x, int32_t y) {
+      const int64_t lx = rp[x + 1] - rp[x], ly = rp[y + 1] - rp[y];
+      return lx != ly ? lx > ly : x < y;
+    };
+    std::sort(mid.begin(), mid.end(), by_len);
+    std::sort(big.begin(), big.end(), by_len);
+    const int64_t n_slices = (n_sell + 31) / 32;
+    std::vector<int64_t> off(static_cast<size_t>(n_slices + 1), 0);
+    for (int64_t c = 0; c < n_slices; ++c) {
+      const int32_t r = perm[static_cast<size_t>(c * 32)];  // the slice's longest row
+      off[c + 1] = off[c] + 32 * static_cast<int64_t>(rp[r + 1] - rp[r]);
+    }
+    A->n_sell = n_sell;
+    A->n_slices = n_slices;
+    A->sl_entries = off[n_slices];
+    A->n_mid = static_cast<int64_t>(mid.size());
+    A->n_big = static_cast<int64_t>(big.size());
+    GK_TRY(upload(&A->sl_perm, perm, 0, bytes, s));
+    GK_TRY(upload(&A->sl_off, off, 0, bytes, s));
+    GK_TRY(upload(&A->mid_rows, mid, 0, bytes, s));
+    GK_TRY(upload(&A->big_rows, big, 0, bytes, s));
+    GK_TRY(dalloc_n(&A->sl_col, static_cast<size_t>(std::max<int64_t>(A->sl_entries, 1)), bytes));
+    GK_TRY(dalloc_n(&A->sl_val, static_cast<size_t>(std::max<int64_t>(A->sl_entries, 1)), bytes));
+    if (n_slices > 0) {
+      slice_fill_kernel<<<grid1d(n_slices * 32, 256), 256, 0, s>>>(A->rowptr, A->col, A->val, A->sl_perm,
+                                                                   A->sl_off, n_slices, n_sell, A->sl_col,
+                                                                   A->sl_val);
+      GK_TRY_CUDA(cudaGetLastError());
+    }
+    A->grid_sl = sliced_grid(A->n_mid + A->n_slices, A->n_big);
   } else if (fmt == GK_CSR_MERGE) {
     GK_TRY(build_merge_plan(A->merge, n_rows, nnz, A->rowptr, A->col, A->val, bytes, s));
   } else {  // GK_ELL, GK_HYB
@@ -354,8 +402,8 @@ extern "C" int gk_matrix_get_info(gk_matrix h, gk_matrix_info* info) {
   info->ell_width = (A->format == GK_ELL || A->format == GK_HYB) ? A->K : 0;
   info->tail_rows = A->m_tail;
   info->tail_nnz = A->tail_nnz;
-  info->short_items = A->n_items;
-  info->long_rows = A->n_long;
+  info->short_items = A->n_slices;
+  info->long_rows = A->n_mid + A->n_big;
   info->tiles = A->merge.n_tiles;
   info->device_bytes = A->device_bytes;
   info->spmv_bytes = A->nnz * 12 + (A->n_rows + 1) * 4 + A->n_cols * 8 + A->n_rows * 8;

@@ -110,125 +110,110 @@ __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, 
   }
 }
 
-// Sequential row sum s = fma(v_k, x_{c_k}, s) over k in [k0, k1) of staged
-// values/indices, with the gathers of x issued in batches so that several are
-// in flight per lane; the fma order is unchanged (increasing k).
-__device__ __forceinline__ double row_sum_staged(const double* __restrict__ v, const int32_t* __restrict__ c,
-                                                 int k0, int k1, const double* __restrict__ x) {
-  double s = 0.0;
-  int k = k0;
-  for (; k + 8 <= k1; k += 8) {
-    int cc[8];
-    double xv[8], vv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) cc[u] = c[k + u];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = __ldg(x + cc[u]);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) vv[u] = v[k + u];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s = fma(vv[u], xv[u], s);
-  }
-  for (; k < k1; k += 4) {
-    double xv[4], vv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool in = k + u < k1;
-      xv[u] = in ? __ldg(x + c[k + u]) : 0.0;
-      vv[u] = in ? v[k + u] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (k + u < k1) s = fma(vv[u], xv[u], s);
-  }
-  return s;
-}
-
 // ---------------------------------------------------------------------------
-// GK_CSR: rows binned by length.
-// Short rows (<= 32 entries) are grouped into warp items of up to 32
-// consecutive rows; a warp bulk-copies the item's values and column indices
-// into its own shared-memory stage (TMA, one mbarrier per warp) and each lane
-// sums one row sequentially -- the same fma order as the CPU reference, so
-// these rows are bit-identical to it.  Long rows are processed one per warp
-// with coalesced loads and an xor-butterfly sum.
+// GK_CSR: rows binned by length.  The plan sorts the rows by decreasing
+// length.  Rows of up to kSliceMaxLen entries form slices of 32 consecutive
+// (in that order) rows stored column-major and padded to the slice's longest
+// row -- so neighbouring lanes have nearly equal work and their loads of
+// values and indices are coalesced; each lane sums its row sequentially in
+// CSR order, bit-identical to the CPU reference.  Longer rows are summed one
+// warp per row (coalesced loads, xor butterfly), and rows beyond kBlockRowLen
+// entries one thread block per row, so that no row holds up the launch.
 // ---------------------------------------------------------------------------
 
-constexpr int kBinStage = kBinItemNnz + 8;
-constexpr int kBinValBytes = kBinStage * 8;
-constexpr int kBinColBytes = kBinStage * 4;
-constexpr int kBinWarpBytes = kBinValBytes + kBinColBytes + 16;
-static_assert(kBinWarpBytes % 16 == 0, "warp stage must keep 16-byte alignment");
-constexpr int kBinSmem = kBinWarps * kBinWarpBytes;
+template <int MODE>
+struct EllBatchOf {
+  static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN) ? 8 : 4;
+};
 
-struct BinArgs {
+struct SliceArgs {
   const int32_t* rowptr;
   const int32_t* col;
   const double* val;
-  const int32_t* item_r0;
-  const int32_t* item_r1;
-  int n_items;
-  const int32_t* long_rows;
-  int n_long;
+  const int32_t* perm;
+  const int64_t* off;
+  const int32_t* scol;
+  const double* sval;
+  int n_sell, n_slices;
+  const int32_t* mid;
+  int n_mid;
+  const int32_t* big;
+  int n_big;
   const double* x;
 };
 
-__global__ void __launch_bounds__(kBinWarps * 32) spmv_binned_kernel(BinArgs a, Epi e) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int MODE>
+__global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs a, Epi e) {
+  constexpr int B = EllBatchOf<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
+  __shared__ double row_scratch[kRedScratch];
   if (epi_skip(e)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* base = smem_raw + warp * kBinWarpBytes;
-  double* val_s = reinterpret_cast<double*>(base);
-  int32_t* col_s = reinterpret_cast<int32_t*>(base + kBinValBytes);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + kBinValBytes + kBinColBytes);
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
   double a0 = 0.0, a1 = 0.0;
-  uint32_t phase = 0;
-  bool ok = true;
-  const int gw = blockIdx.x * kBinWarps + warp, nwarps = gridDim.x * kBinWarps;
-  for (int it = gw; ok && it < a.n_items; it += nwarps) {
-    const int r0 = __ldg(a.item_r0 + it), r1 = __ldg(a.item_r1 + it);
-    const int k0 = __ldg(a.rowptr + r0), k1 = __ldg(a.rowptr + r1);
-    const int ka = k0 & ~3, kb = (k1 + 3) & ~3;
-    const uint32_t nb = static_cast<uint32_t>(kb - ka);
-    const int row = r0 + lane;
-    int kk0 = 0, kk1 = 0;
-    if (row < r1) {
-      kk0 = __ldg(a.rowptr + row) - ka;
-      kk1 = __ldg(a.rowptr + row + 1) - ka;
-    }
-    if (nb > 0) {
-      if (lane == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, nb * 12u);
-        bulk_g2s(val_s, a.val + ka, nb * 8u, bar);
-        bulk_g2s(col_s, a.col + ka, nb * 4u, bar);
-      }
-      bool w = mbar_wait(bar, phase, e.err);
-      phase ^= 1u;
-      ok = __all_sync(0xffffffffu, w);
-    }
-    if (ok && row < r1) {
-      const double s = row_sum_staged(val_s, col_s, kk0, kk1, a.x);
-      epi_row(e, row, s, a0, a1);
-    }
-    __syncwarp();
-  }
-  for (int lr = gw; ok && lr < a.n_long; lr += nwarps) {
-    const int row = __ldg(a.long_rows + lr);
+  // rows beyond kBlockRowLen entries: one block each
+  for (int v = blockIdx.x; v < a.n_big; v += gridDim.x) {
+    const int row = __ldg(a.big + v);
     const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
-    double s = 0.0;
-    for (int k = k0 + lane; k < k1; k += 32) s = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) epi_row(e, row, s, a0, a1);
+    double sm[1] = {0.0};
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) sm[0] = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), sm[0]);
+    block_sum<1, double>(sm, row_scratch);
+    if (threadIdx.x == 0) epi_row_t<MODE>(e, row, sm[0], a0, a1);
+    __syncthreads();
   }
-  epi_finish(e, a0, a1, red_scratch);
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_items = a.n_mid + a.n_slices;
+  for (int it = gw; it < n_items; it += nw) {
+    if (it < a.n_mid) {
+      const int row = __ldg(a.mid + it);
+      const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+      double s = 0.0;
+      int k = k0 + lane;
+      for (; k + 96 < k1; k += 128) {
+        int cc[4];
+        double vv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cc[u] = __ldg(a.col + k + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vv[u] = __ldg(a.val + k + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = __ldg(a.x + cc[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s = fma(vv[u], xv[u], s);
+      }
+      for (; k < k1; k += 32) s = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) epi_row_t<MODE>(e, row, s, a0, a1);
+    } else {
+      const int c = it - a.n_mid;
+      const int base = c * 32 + lane;
+      const int64_t o0 = __ldg(a.off + c);
+      const int L = static_cast<int>((__ldg(a.off + c + 1) - o0) >> 5);
+      const int32_t* cp = a.scol + o0 + lane;
+      const double* vp = a.sval + o0 + lane;
+      double s = 0.0;
+      int j = 0;
+      for (; j + B <= L; j += B) {
+        int cc[B];
+        double vv[B], xv[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) cc[u] = __ldg(cp + (j + u) * 32);
+#pragma unroll
+        for (int u = 0; u < B; ++u) vv[u] = __ldg(vp + (j + u) * 32);
+#pragma unroll
+        for (int u = 0; u < B; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+          if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
+      }
+      for (; j < L; ++j) {
+        const int cc = __ldg(cp + j * 32);
+        if (cc >= 0) s = fma(__ldg(vp + j * 32), __ldg(a.x + cc), s);
+      }
+      if (base < a.n_sell) epi_row_t<MODE>(e, __ldg(a.perm + base), s, a0, a1);
+    }
+  }
+  if (MODE != EPI_COPY && MODE != EPI_PLAIN) epi_finish(e, a0, a1, red_scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -607,8 +592,6 @@ bool g_attr_done[64] = {};
 int ensure_attributes() {
   int dev = current_device();
   if (dev >= 0 && dev < 64 && g_attr_done[dev]) return GK_OK;
-  GK_TRY_CUDA(cudaFuncSetAttribute(spmv_binned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kBinSmem));
   GK_TRY_CUDA(cudaFuncSetAttribute(spmv_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sizeof(MergeSmem)));
   if (dev >= 0 && dev < 64) g_attr_done[dev] = true;
@@ -654,10 +637,9 @@ int merge_grid(int64_t n_tiles) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, n_tiles)));
 }
 
-int bin_grid(int64_t work_warps) {
-  if (ensure_attributes() != GK_OK) return 1;
-  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_binned_kernel), kBinWarps * 32, kBinSmem);
-  int64_t need = (work_warps + kBinWarps - 1) / kBinWarps;
+int sliced_grid(int64_t warp_items, int64_t big_rows) {
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_RESID>), kSliceThreads, 0);
+  int64_t need = std::max<int64_t>((warp_items + kSliceThreads / 32 - 1) / (kSliceThreads / 32), big_rows);
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
 }
 
@@ -668,7 +650,7 @@ int ell_grid(int64_t n_rows) {
 }
 
 int spmv_max_grid(const Matrix& A) {
-  return std::max({A.grid_bin, A.grid_ell, A.merge.grid, 1});
+  return std::max({A.grid_sl, A.grid_ell, A.merge.grid, 1});
 }
 
 int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) {
@@ -676,9 +658,16 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
   if (A.n_rows == 0) return GK_OK;
   switch (A.format) {
     case GK_CSR: {
-      BinArgs b{A.rowptr, A.col, A.val, A.item_r0, A.item_r1, static_cast<int>(A.n_items),
-                A.long_rows, static_cast<int>(A.n_long), x};
-      spmv_binned_kernel<<<A.grid_bin, kBinWarps * 32, kBinSmem, s>>>(b, e);
+      SliceArgs b{A.rowptr, A.col, A.val, A.sl_perm, A.sl_off, A.sl_col, A.sl_val, static_cast<int>(A.n_sell),
+                  static_cast<int>(A.n_slices), A.mid_rows, static_cast<int>(A.n_mid), A.big_rows,
+                  static_cast<int>(A.n_big), x};
+      switch (e.mode) {
+        case EPI_COPY: spmv_sliced_kernel<EPI_COPY><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+        case EPI_PLAIN: spmv_sliced_kernel<EPI_PLAIN><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+        case EPI_RESID: spmv_sliced_kernel<EPI_RESID><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+        case EPI_DOT: spmv_sliced_kernel<EPI_DOT><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+        default: spmv_sliced_kernel<EPI_DOT2><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+      }
       GK_TRY_CUDA(cudaGetLastError());
       return GK_OK;
     }

@@ -224,6 +224,7 @@ struct IrArgs {
   const double* r64;
   SolverState* st;
   cudaGraphConditionalHandle cond;
+  int use_cond;  // 0: launched from the host (no graph loop to re-arm)
 };
 
 __device__ __forceinline__ void inner_alpha(InnerState* ist, float sigma) {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_direction_kernel(IrArgs a, IrDa
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const InnerState* s = d.ist;
     const bool more = !s->done && s->it < s->max_it + 2;
-    cudaGraphSetConditional(a.cond, more ? 1u : 0u);
+    if (a.use_cond) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
   }
   if (d.ist->done) return;
   const float beta = static_cast<float>(d.ist->beta);
@@ -495,6 +496,7 @@ IrArgs ir_args(const Solver& S, const IrData& d) {
   a.r64 = S.r;
   a.st = S.st;
   a.cond = d.cond;
+  a.use_cond = 1;
   return a;
 }
 
@@ -554,19 +556,42 @@ int ir_spmv(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
 
 // The inner solve and the update of x as one graph:
 // start -> WHILE(cond) { SpMV; update; direction } -> apply.
+int ir_enqueue_start(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
+  if (S.pk == PREC_BLOCK) IR_LAUNCH_BS(ir_start_kernel, a.bs, d.grid, s, a, d);
+  else if (S.pk == PREC_SCALAR) ir_start_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  else ir_start_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
+// One inner CG iteration: FP32 SpMV (with p.q), update, direction.
+int ir_enqueue_inner(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
+  GK_TRY(ir_spmv(S, d, a, s));
+  if (S.pk == PREC_BLOCK) {
+    IR_LAUNCH_BS(ir_update_kernel, a.bs, d.grid, s, a, d);
+    ir_direction_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  } else if (S.pk == PREC_SCALAR) {
+    ir_update_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
+    ir_direction_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  } else {
+    ir_update_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
+    ir_direction_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  }
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
 int ir_build_graph(Solver& S, IrData& d) {
   if (!d.cs) GK_TRY_CUDA(cudaStreamCreateWithFlags(&d.cs, cudaStreamNonBlocking));
   GK_TRY_CUDA(cudaGraphCreate(&d.graph, 0));
   GK_TRY_CUDA(cudaGraphConditionalHandleCreate(&d.cond, d.graph, 1, cudaGraphCondAssignDefault));
   const IrArgs a = ir_args(S, d);
-  const int pk = S.pk;
   GK_TRY_CUDA(cudaStreamBeginCaptureToGraph(d.cs, d.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   int rc = GK_OK;
   do {
-    if (pk == PREC_BLOCK) IR_LAUNCH_BS(ir_start_kernel, a.bs, d.grid, d.cs, a, d);
-    else if (pk == PREC_SCALAR) ir_start_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-    else ir_start_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-    cudaError_t e = cudaGetLastError();
+    rc = ir_enqueue_start(S, d, a, d.cs);
+    if (rc != GK_OK) break;
+    cudaError_t e = cudaSuccess;
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -595,19 +620,7 @@ int ir_build_graph(Solver& S, IrData& d) {
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
     cudaGraph_t body = np.conditional.phGraph_out[0];
     GK_TRY_CUDA(cudaStreamBeginCaptureToGraph(d.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int brc = ir_spmv(S, d, a, d.cs);
-    if (brc == GK_OK) {
-      if (pk == PREC_BLOCK) {
-        IR_LAUNCH_BS(ir_update_kernel, a.bs, d.grid, d.cs, a, d);
-        ir_direction_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-      } else if (pk == PREC_SCALAR) {
-        ir_update_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-        ir_direction_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-      } else {
-        ir_update_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-        ir_direction_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, d.cs>>>(a, d);
-      }
-    }
+    int brc = ir_enqueue_inner(S, d, a, d.cs);
     e = cudaStreamEndCapture(d.cs, &captured);
     if (brc != GK_OK) return brc;
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture (inner body)");
@@ -704,7 +717,8 @@ int ir_generate(Solver* S) {
 
 int ir_solve(Solver* S, cudaStream_t s) {
   IrData& d = *S->ir;
-  if (!d.exec) GK_TRY(ir_build_graph(*S, d));
+  const bool host_loop = S->crit.check_every > 0;
+  if (!host_loop && !d.exec) GK_TRY(ir_build_graph(*S, d));
   const gk_criteria& c = S->crit;
   const unsigned long long tl = c.time_limit_s > 0 ? static_cast<unsigned long long>(c.time_limit_s * 1e9) : 0ull;
   ir_init_kernel<<<1, 1, 0, s>>>(S->st, c.reduction_factor, static_cast<long long>(c.max_iters), c.rel_to_b, tl);
@@ -729,7 +743,25 @@ int ir_solve(Solver* S, cudaStream_t s) {
       GK_TRY_CUDA(cudaMemcpyAsync(&S->st->stop, &stop, sizeof(int), cudaMemcpyHostToDevice, s));
       break;
     }
-    GK_TRY_CUDA(cudaGraphLaunch(d.exec, s));
+    if (!host_loop) {
+      GK_TRY_CUDA(cudaGraphLaunch(d.exec, s));
+      continue;
+    }
+    // the inner solve launched from the host, its state read every
+    // check_every iterations (same kernels as the graph's loop body)
+    IrArgs a = ir_args(*S, d);
+    a.use_cond = 0;
+    GK_TRY(ir_enqueue_start(*S, d, a, s));
+    for (int64_t done = 0;;) {
+      for (int i = 0; i < S->crit.check_every; ++i) GK_TRY(ir_enqueue_inner(*S, d, a, s));
+      done += S->crit.check_every;
+      InnerState h;
+      GK_TRY_CUDA(cudaMemcpyAsync(&h, d.ist, sizeof(InnerState), cudaMemcpyDeviceToHost, s));
+      GK_TRY_CUDA(cudaStreamSynchronize(s));
+      if (h.done || h.it >= h.max_it + 2 || done > h.max_it + 2) break;
+    }
+    ir_apply_kernel<<<d.grid, kIrThreads, 0, s>>>(a, d);
+    GK_TRY_CUDA(cudaGetLastError());
   }
   return GK_OK;
 }

@@ -127,3 +127,16 @@ def test_ir_varcoef3d_full_size(gk, orc):
     assert st.stop_reason == gk.STOP_CONVERGED
     r = b - orc.spmv(A, x)
     assert np.linalg.norm(r) <= 1.2e-12 * np.linalg.norm(b)
+
+
+def test_ir_host_loop_equals_graph_loop(gk, orc):
+    """The refinement launched from the host (check_every > 0) runs the same
+    kernels as the device-controlled graph loop: bit-identical results."""
+    A = W.stencil27(20)
+    n = A[0].size - 1
+    b = orc.spmv(A, W.uniform_vector(n, 4))
+    for prec in (1, 8):
+        s1, x1, _ = _gk_ir(gk, A, b, "ell", prec, max_iters=20000, reduction_factor=1e-10)
+        s2, x2, _ = _gk_ir(gk, A, b, "ell", prec, max_iters=20000, reduction_factor=1e-10, check_every=7)
+        assert s1.iters == s2.iters and s1.outer_iters == s2.outer_iters
+        np.testing.assert_array_equal(x1, x2)

@@ -57,7 +57,7 @@ WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point sten
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel per launch on workload (a); valid only while the ELL
 # kernel's source (spmv_source_hash) is the one it was measured on.
-NCU_TRAFFIC = {"8f0479bcad827b53": 711961600}
+NCU_TRAFFIC = {"8f0479bcad827b53": {"copy": 711961600}}
 
 # back-to-back applies per format and matrix in one step (the per-launch time
 # of the roofline is their average)
@@ -285,6 +285,7 @@ class GpuStep:
         self.x = {"a": t(inp["xa"]), "b": t(inp["xb"])}
         self.y = {"a": torch.zeros(self.na, dtype=torch.float64, device=dev),
                   "b": torch.zeros(self.nb, dtype=torch.float64, device=dev)}
+        self.dot_out = torch.zeros(1, dtype=torch.float64, device=dev)
         # right-hand sides b = A x* (computed by the library on the device)
         self.rhs = {}
         for k, xs in (("a", inp["xs_a"]), ("b", inp["xs_b"])):
@@ -344,6 +345,14 @@ class GpuStep:
                     gk.apply(M, host["x" + k], host["y" + k])
             e1.record(self.stream)
             parts.append((f"spmv_{k}_{f}", e0, e1, ("spmv", k, M)))
+        # the SpMV with the fused dot of the CG steps (the step's dominant
+        # kernel), on (a) in ELL; device vectors in both modes
+        e0, e1 = ev(), ev()
+        e0.record(self.stream)
+        for _ in range(SPMV_REPS):
+            gk.apply_dot(self.mats[("a", "ell")], self.x["a"], self.y["a"], self.rhs["a"], self.dot_out)
+        e1.record(self.stream)
+        parts.append(("spmvdot_a_ell", e0, e1, ("spmvdot", "a", self.mats[("a", "ell")])))
         for k, f, bs in self.gens:
             e0, e1 = ev(), ev()
             e0.record(self.stream)
@@ -373,6 +382,9 @@ class GpuStep:
         if kind == "spmv":
             k = tag[1]
             return SPMV_REPS * spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k))
+        if kind == "spmvdot":
+            k = tag[1]
+            return SPMV_REPS * (spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k)) + 8 * self.n_of(k))
         if kind == "precond":
             k, bs = tag[1], tag[2]
             return precond_bytes(self.nnz_of(k), self.n_of(k), bs)
@@ -387,7 +399,7 @@ class GpuStep:
 
     def part_launches(self, tag):
         kind = tag[0]
-        if kind == "spmv":
+        if kind in ("spmv", "spmvdot"):
             return SPMV_REPS * spmv_launches(tag[2].info())
         if kind == "precond":
             return 1
@@ -723,26 +735,28 @@ def run_gpu(args):
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    dom = "spmv_a_ell"
+    dom = "spmvdot_a_ell"
     dom_ms = statistics.mean(part_ms[dom]) / SPMV_REPS
     dom_bytes = part_bytes[dom][0] // SPMV_REPS
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    tr = NCU_TRAFFIC.get(spmv_source_hash())
-    roofline = {"kernel": "spmv_ell_kernel (ELL SpMV of (a), plain-apply instantiation; the same kernel with "
-                          "the fused dot runs inside the ELL CG solves)", "bound": "hbm",
+    tr = NCU_TRAFFIC.get(spmv_source_hash(), {}).get("dot")
+    roofline = {"kernel": "spmv_ell_kernel<EPI_DOT> (ELL SpMV of (a) with the fused dot product: the kernel "
+                          "that dominates the step inside the ELL CG solves, timed through gk_apply_dot)",
+                "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm if hbm else 6800.0, "unit": "GB/s",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
                 "frac": round(achieved / (hbm if hbm else 6800.0), 4),
                 "traffic": tr, "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
 
     def summary(name):
-        reps = SPMV_REPS if name.startswith("spmv_") else 1
+        reps = SPMV_REPS if name.startswith("spmv") else 1
         ms = statistics.median(part_ms[name]) / reps
         by = part_bytes[name][0] / reps
         return {"ms": round(ms, 4), "GB/s": round(by / (ms * 1e-3) / 1e9, 1),
                 "frac_hbm": round(by / (ms * 1e-3) / 1e9 / (hbm or 6800.0), 3)}
 
     spmv = {n[5:]: summary(n) for n in part_ms if n.startswith("spmv_")}
+    spmv["a_ell_fused_dot"] = summary("spmvdot_a_ell")
     solves = {}
     for n in part_ms:
         if n.startswith("solve_"):
@@ -897,7 +911,9 @@ def run_spmv_only(args):
     import paper_2006_16852_gb300 as gk
     import workloads as W
     gk.load()
-    mat, fmt = args.spmv_only.split(":")
+    parts = args.spmv_only.split(":")
+    mat, fmt = parts[0], parts[1]
+    dot = len(parts) > 2 and parts[2] == "dot"
     if mat == "a":
         A = W.stencil27(128 if not args.small else 32)
     else:
@@ -906,17 +922,19 @@ def run_spmv_only(args):
     t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
     M = gk.Matrix(t(A[0]), t(A[1]), t(A[2]), fmt=fmt)
     x, y = t(W.uniform_vector(n, 2)), torch.zeros(n, dtype=torch.float64, device="cuda")
+    u, res = t(W.uniform_vector(n, 3)), torch.zeros(1, dtype=torch.float64, device="cuda")
+    op = (lambda: gk.apply_dot(M, x, y, u, res)) if dot else (lambda: gk.apply(M, x, y))
     for _ in range(args.warmup):
-        gk.apply(M, x, y)
+        op()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.steps):
-        gk.apply(M, x, y)
+        op()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    by = spmv_bytes(A[1].size, n, n)
+    by = spmv_bytes(A[1].size, n, n) + (8 * n if dot else 0)
     return {"spmv_only": args.spmv_only, "ms": round(ms, 4), "GB/s": round(by / ms / 1e6, 1),
             "info": M.info()}
 
@@ -979,8 +997,9 @@ def main():
     ap.add_argument("--batch-no-tune", action="store_true",
                     help="--batched-only: default block sizes instead of the autotuner")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CG in cpu_baseline")
-    ap.add_argument("--spmv-only", metavar="MAT:FMT", default=None,
-                    help="only time repeated applies of matrix a|b in one format (profiling aid)")
+    ap.add_argument("--spmv-only", metavar="MAT:FMT[:dot]", default=None,
+                    help="only time repeated applies of matrix a|b in one format, with ':dot' the apply "
+                         "with the fused dot product of the Krylov steps (profiling aid)")
     ap.add_argument("--solve-only", metavar="MAT:FMT:PREC:KIND", default=None,
                     help="only time repeated solves of one configuration (profiling aid)")
     ap.add_argument("--host-loop", type=int, default=0, metavar="K",

@@ -182,6 +182,15 @@ GK_API int gk_apply(gk_matrix A, const void* b, void* x, void* stream);
  * read x (BLAS convention), so gk_apply == gk_apply_adv(1, A, b, 0, x). */
 GK_API int gk_apply_adv(double alpha, gk_matrix A, const void* b, double beta, void* x, void* stream);
 
+/* x = A b and result[0] = u . x in one pass: the SpMV with the fused dot
+ * product every Krylov iteration uses (Section 7.4 on fusing the reductions
+ * of Krylov solvers into the kernels that produce their operands).  A square;
+ * b, x, u, result: device memory; the sum's order is fixed (per-row products
+ * accumulated per thread, then the block and grid reductions of gk_dot), so
+ * the result is reproducible run to run.  Calls on one matrix must be ordered
+ * (they share the matrix's reduction scratch). */
+GK_API int gk_apply_dot(gk_matrix A, const double* b, double* x, const double* u, double* result, void* stream);
+
 /* ---- preconditioners (Section 3.2) -------------------------------------- */
 /* Jacobi preconditioner P_A = M^{-1} generated from A (square).
  * block_size 1: scalar Jacobi, M = diag(A).  block_size 2..32: block Jacobi

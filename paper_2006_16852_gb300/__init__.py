@@ -31,7 +31,7 @@ STOP_NONE, STOP_CONVERGED, STOP_MAX_ITERS, STOP_BREAKDOWN, STOP_NAN, STOP_TIME =
 
 # every symbol include/gk.h declares
 EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get_info",
-           "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_precond_generate", "gk_precond_apply",
+           "gk_matrix_destroy", "gk_apply", "gk_apply_adv", "gk_apply_dot", "gk_precond_generate", "gk_precond_apply",
            "gk_precond_get_blocks", "gk_precond_destroy", "gk_solver_generate", "gk_solve",
            "gk_solver_destroy", "gk_solver_get_info", "gk_batch_create", "gk_batch_solve",
            "gk_batch_autotune", "gk_batch_set_threads", "gk_batch_get_info", "gk_batch_destroy",
@@ -114,6 +114,7 @@ def load(path: str | None = None):
         "gk_matrix_destroy": [vp],
         "gk_apply": [vp, vp, vp, vp],
         "gk_apply_adv": [f64, vp, vp, f64, vp, vp],
+        "gk_apply_dot": [vp, vp, vp, vp, vp, vp],
         "gk_precond_generate": [vp, i32, vp, ctypes.POINTER(vp)],
         "gk_precond_apply": [vp, vp, vp, vp],
         "gk_precond_get_blocks": [vp, vp, i64, vp],
@@ -231,6 +232,15 @@ def apply(A: Matrix, b, x, stream=None):
     _check_vec(x, A.n_rows, "x")
     _check(lib().gk_apply(A.handle, _ptr(b), _ptr(x), _stream(stream, b, x)))
     return x
+
+
+def apply_dot(A: Matrix, b, x, u, result, stream=None):
+    """x = A b and result[0] = u . x in one fused pass (device tensors)."""
+    _check_vec(b, A.n_cols, "b")
+    _check_vec(x, A.n_rows, "x")
+    _check_vec(u, A.n_rows, "u")
+    _check(lib().gk_apply_dot(A.handle, _ptr(b), _ptr(x), _ptr(u), _ptr(result), _stream(stream, b, x, u)))
+    return result
 
 
 def apply_adv(alpha: float, A: Matrix, b, beta: float, x, stream=None):

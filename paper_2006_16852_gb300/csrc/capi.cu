@@ -178,6 +178,41 @@ extern "C" int gk_apply(gk_matrix h, const void* b, void* x, void* stream) {
   return gk_apply_adv(1.0, h, b, 0.0, x, stream);
 }
 
+extern "C" int gk_apply_dot(gk_matrix h, const double* b, double* x, const double* u, double* result,
+                            void* stream) {
+  Matrix* A = as_matrix(h);
+  if (!A || !b || !x || !u || !result) return set_error(GK_ERR_ARG, "gk_apply_dot: NULL argument");
+  if (b == x) return set_error(GK_ERR_ARG, "gk_apply_dot: b and x must not alias");
+  if (is_host(b) || is_host(x) || is_host(u) || is_host(result))
+    return set_error(GK_ERR_NOT_DEVICE, "gk_apply_dot: vectors and result must be device memory");
+  if (A->n_rows != A->n_cols) return set_error(GK_ERR_DIM, "gk_apply_dot: matrix is not square");
+  DeviceGuard g(A->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!A->dot_st) {
+    GK_TRY(dalloc_n(&A->dot_st, 1, &A->device_bytes));
+    GK_TRY_CUDA(cudaMemsetAsync(A->dot_st, 0, sizeof(SolverState), s));
+  }
+  if (A->n_rows == 0) {
+    GK_TRY_CUDA(cudaMemsetAsync(result, 0, sizeof(double), s));
+    return GK_OK;
+  }
+  // the SpMV's EPI_DOT epilogue of the Krylov steps: x = A b and u.x in one
+  // pass, the fixed-order sum left in dot_st->red[0] by the last block
+  Epi e;
+  e.mode = EPI_DOT;
+  e.fin = FIN_NONE;
+  e.u = u;
+  e.y = x;
+  e.st = A->dot_st;
+  e.skip_mode = 0;
+  e.partials = A->partials;
+  e.counter = A->counter;
+  e.err = A->err;
+  GK_TRY(spmv_launch(*A, b, e, s));
+  GK_TRY_CUDA(cudaMemcpyAsync(result, &A->dot_st->red[0], sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return GK_OK;
+}
+
 extern "C" int gk_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {
   if (n < 0 || !result || (n > 0 && (!x || !y))) return set_error(GK_ERR_ARG, "gk_dot: bad argument");
   if (is_host(x) || is_host(y) || is_host(result))

@@ -206,6 +206,7 @@ struct Matrix {
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   int* err = nullptr;
+  SolverState* dot_st = nullptr;  // gk_apply_dot: receives the fused sum
   double* stage_in = nullptr;   // host-vector staging
   double* stage_out = nullptr;
   int max_grid = 0;             // partials hold max_grid * 2 doubles

@@ -189,7 +189,7 @@ void matrix_release(Matrix* A) {
                   A->tail_rows, A->tail_rowptr, A->tail_col, A->tail_val, A->tail_slot, A->tail_sum,
                   A->tail.tile_i, A->tail.tile_j, A->tail.head_val, A->tail.head_row,
                   A->tail.carry_val, A->tail.carry_row, A->tail.cont, A->partials, A->counter,
-                  A->err, A->stage_in, A->stage_out};
+                  A->err, A->dot_st, A->stage_in, A->stage_out};
   for (void* p : ptrs) dfree(p);
   if (prev >= 0) cudaSetDevice(prev);
   delete A;

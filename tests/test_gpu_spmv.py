@@ -174,3 +174,26 @@ def test_full_size_sampled_rows(gk, orc, big_mats, fmt, which):
 @pytest.fixture(scope="module")
 def big_mats():
     return {"stencil27_128": W.stencil27(128), "powerlaw_1M": W.powerlaw(1_000_000, seed=3)}
+
+
+@pytest.mark.parametrize("fmt", ["csr", "csr_merge", "ell", "hyb"])
+def test_apply_dot_fuses_the_dot(gk, orc, fmt):
+    """x = A b equals gk_apply bit for bit, and result = u . x within the
+    rounding of a length-n dot product; run to run bit-identical."""
+    import torch
+    A = W.poisson2d(70)
+    n = 4900
+    b, u = W.uniform_vector(n, 1), W.uniform_vector(n, 2)
+    M = _gk_matrix(gk, A, fmt)
+    x1 = to_dev(np.zeros(n))
+    x2 = to_dev(np.zeros(n))
+    r = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    gk.apply(M, to_dev(b), x1)
+    gk.apply_dot(M, to_dev(b), x2, to_dev(u), r[0:1])
+    gk.apply_dot(M, to_dev(b), x2, to_dev(u), r[1:2])
+    np.testing.assert_array_equal(to_np(x1), to_np(x2))
+    rv = to_np(r)
+    assert rv[0] == rv[1]
+    x = to_np(x2)
+    ref = float(np.dot(u, x))
+    assert abs(rv[0] - ref) <= 1e-13 * float(np.dot(np.abs(u), np.abs(x)))

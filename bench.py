@@ -674,6 +674,54 @@ def run_learned(dev, problems=8):
     }
 
 
+# ---------------------------------------------------------------------------
+# the rest of the Krylov family (reported beside the step)
+# ---------------------------------------------------------------------------
+
+KRYLOV_WORKLOAD = ("nonsymmetric 2D convection-diffusion (first-order upwind, wind 0.5) on a 1024x1024 grid "
+                   "(n=1,048,576, nnz=5,238,784) and the 27-point stencil on 128^3 for the symmetric methods; "
+                   "x* uniform[-1,1], b = A x*, x0 = 0, ||r|| <= 1e-10 ||b||, scalar Jacobi, ELL")
+
+
+def run_krylov(dev):
+    """Time to 1e-10 of every Krylov method on a matrix it applies to."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    mats = {"convdiff1024": W.convdiff2d(1024, 0.5), "stencil27_128": W.stencil27(128)}
+    runs = [("convdiff1024", "bicgstab", {}), ("convdiff1024", "cgs", {}), ("convdiff1024", "gmres", {"krylov_dim": 30}),
+            ("stencil27_128", "cg", {}), ("stencil27_128", "fcg", {}), ("stencil27_128", "gmres", {"krylov_dim": 30})]
+    built = {}
+    for name, A in mats.items():
+        n = A[0].size - 1
+        M = gk.Matrix(*[t(a) for a in A], fmt="ell")
+        b = torch.zeros(n, dtype=torch.float64, device=dev)
+        gk.apply(M, t(W.uniform_vector(n, 11)), b)
+        built[name] = (M, gk.Precond(M, 1), b, A[1].size, n)
+    for name, kind, extra in runs:
+        M, P, b, nnz, n = built[name]
+        S = gk.Solver(M, P, kind, max_iters=20000, reduction_factor=1e-10, **extra)
+        for rep_ in range(2):
+            x = torch.zeros_like(b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, b, x)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        rec = {"ms": round(ms, 3), "iters": st.iters, "spmvs": st.spmvs, "rel_res_true": st.rel_res_true,
+               "converged": st.stop_reason == gk.STOP_CONVERGED,
+               "ms_per_spmv": round(ms / max(st.spmvs, 1), 4)}
+        if kind in ("cg", "fcg"):
+            rec["GB/s_cg_model"] = round(cg_bytes(st.iters, nnz, n, "jacobi", 1) / (ms * 1e-3) / 1e9, 1)
+        out[f"{name}_{kind}"] = rec
+    return {"workload": KRYLOV_WORKLOAD, "timing": "CUDA events around gk_solve, the second of two solves",
+            "solves": out}
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -831,6 +879,8 @@ def run_gpu(args):
         out["mixed"] = run_mixed(dev, side=args.mixed_side)
     if not args.no_learned:
         out["learned"] = run_learned(dev)
+    if not args.no_krylov:
+        out["krylov"] = run_krylov(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -991,6 +1041,8 @@ def main():
     ap.add_argument("--mixed-only", action="store_true", help="only the mixed-precision workload")
     ap.add_argument("--mixed-side", type=int, default=256, help="grid side of the mixed-precision workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--no-krylov", action="store_true", help="skip the FCG / CGS / GMRES section")
+    ap.add_argument("--krylov-only", action="store_true", help="only the FCG / CGS / GMRES section")
     ap.add_argument("--learned-only", action="store_true", help="only the learned warm start")
     ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
     ap.add_argument("--batch-forms", default=None, help="--batched-only: comma list of " + ", ".join(BATCH_FORMS))
@@ -1009,7 +1061,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.learned_only:
+    if args.krylov_only:
+        import torch
+        import paper_2006_16852_gb300 as gk
+        gk.load()
+        out = run_krylov(torch.device("cuda:0"))
+    elif args.learned_only:
         import torch
         import paper_2006_16852_gb300 as gk
         gk.load()

@@ -722,6 +722,53 @@ def run_krylov(dev):
             "solves": out}
 
 
+# ---------------------------------------------------------------------------
+# latency of one iteration on the small configuration (reported beside the step)
+# ---------------------------------------------------------------------------
+
+LATENCY_WORKLOAD = ("Poisson-2D 64x64 (n=4,096, nnz=20,224; L2-resident), x* uniform[-1,1] (seed 1), b = A x*, "
+                    "x0 = 0, ||r|| <= 1e-10 ||b||")
+
+
+def run_latency(dev):
+    """Per-iteration time of CG on the small Poisson problem, where every
+    kernel is latency-bound: the whole solve as one graph whose loop the GPU
+    controls (check_every 0) against a host-driven loop that reads the status
+    after every iteration (check_every 1, the paper's host-side check) or
+    after every 10."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    A = W.poisson2d(64)
+    n = 4096
+    out = {}
+    for fmt in ("csr", "ell"):
+        M = gk.Matrix(*[t(a) for a in A], fmt=fmt)
+        b = torch.zeros(n, dtype=torch.float64, device=dev)
+        gk.apply(M, t(W.uniform_vector(n, 1)), b)
+        for prec in (0, 1):
+            P = gk.Precond(M, 1) if prec else None
+            for every in (0, 1, 10):
+                S = gk.Solver(M, P, "cg", max_iters=5000, reduction_factor=1e-10, check_every=every)
+                best = None
+                for _ in range(5):
+                    x = torch.zeros_like(b)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = gk.solve(S, b, x)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+                key = f"{fmt}_{'jacobi' if prec else 'plain'}_{'graph' if every == 0 else 'host%d' % every}"
+                out[key] = {"ms": round(best, 4), "iters": st.iters, "us_per_iter": round(1e3 * best / max(st.iters, 1), 3),
+                            "rel_res_true": st.rel_res_true}
+    return {"workload": LATENCY_WORKLOAD, "timing": "CUDA events around gk_solve, best of 5",
+            "paper_host_overhead_us_per_iter": [1.0, 1.5], "solves": out}
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -881,6 +928,8 @@ def run_gpu(args):
         out["learned"] = run_learned(dev)
     if not args.no_krylov:
         out["krylov"] = run_krylov(dev)
+    if not args.no_latency:
+        out["latency"] = run_latency(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -1043,6 +1092,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
     ap.add_argument("--no-krylov", action="store_true", help="skip the FCG / CGS / GMRES section")
     ap.add_argument("--krylov-only", action="store_true", help="only the FCG / CGS / GMRES section")
+    ap.add_argument("--no-latency", action="store_true", help="skip the per-iteration latency section")
+    ap.add_argument("--latency-only", action="store_true", help="only the per-iteration latency section")
     ap.add_argument("--learned-only", action="store_true", help="only the learned warm start")
     ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
     ap.add_argument("--batch-forms", default=None, help="--batched-only: comma list of " + ", ".join(BATCH_FORMS))
@@ -1061,11 +1112,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gk" and not args.small:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.krylov_only:
+    if args.krylov_only or args.latency_only:
         import torch
         import paper_2006_16852_gb300 as gk
         gk.load()
-        out = run_krylov(torch.device("cuda:0"))
+        run = run_krylov if args.krylov_only else run_latency
+        out = run(torch.device("cuda:0"))
     elif args.learned_only:
         import torch
         import paper_2006_16852_gb300 as gk

@@ -640,21 +640,31 @@ def run_learned(dev, problems=8):
             e1.synchronize()
         plain_ms += e0.elapsed_time(e1)
         plain_it += st.iters
-    # BF16 inference kernel alone (one problem)
-    feat = torch.zeros((1, 2, net.H, net.W), dtype=torch.float32, device=dev)
-    y = torch.zeros((1, 1, net.H, net.W), dtype=torch.float32, device=dev)
-    for _ in range(3):
-        net.infer_bf16(feat, y)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    e0.record(stream)
-    for _ in range(reps):
-        net.infer_bf16(feat, y)
-    e1.record(stream)
-    e1.synchronize()
-    inf_ms = e0.elapsed_time(e1) / reps
+    # BF16 inference alone: one problem (the warm start's case) and a batch
+    # of 64 (enough tiles for every SM)
     macs = net.H * net.W * sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
-    tfl = 2.0 * macs / (inf_ms * 1e-3) / 1e12
+    inf = {}
+    bnet, _, _ = LN.load(path, batch_max=64)
+    for B, nt in ((1, net), (64, bnet)):
+        feat = torch.zeros((B, 2, net.H, net.W), dtype=torch.float32, device=dev)
+        feat[:, 0].normal_()
+        feat[:, 1].normal_()
+        y = torch.zeros((B, 1, net.H, net.W), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            nt.infer_bf16(feat, y)
+        nt.check()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            nt.infer_bf16(feat, y)
+        e1.record(stream)
+        e1.synchronize()
+        nt.check()
+        ms = e0.elapsed_time(e1) / reps
+        inf[B] = (ms, 2.0 * B * macs / (ms * 1e-3) / 1e12)
+    bf16_peak = peaks().get("bf16_tflops")
+    inf_ms, tfl = inf[1]
     best = "warm" if summ["ms_warm"] < summ["ms_zero"] else "zero"
     return {
         "workload": LEARNED_WORKLOAD, "network": {"layers": 6, "width": 32, "dilations": list(net.dilations),
@@ -667,10 +677,14 @@ def run_learned(dev, problems=8):
                            "chosen_form": "jacobi_cg_" + ("learned" if best == "warm" else "zero") + "_start",
                            "speedup_vs_plain": round(plain_ms / min(summ["ms_warm"], summ["ms_zero"]), 3),
                            "learned_vs_zero_start": round(summ["ms_zero"] / summ["ms_warm"], 4)},
-        "inference": {"kernel": "conv_fwd_kernel (BF16 in, FP32 accumulate, CUDA cores)", "ms": round(inf_ms, 4),
-                      "tflops": round(tfl, 2), "bound": "alu", "peak": round(FP32_PEAK_TFLOPS, 1),
-                      "peak_source": "FP32 FMA issue rate (152 SMs x 128 x 2 x 2.07 GHz)",
-                      "frac": round(tfl / FP32_PEAK_TFLOPS, 4)},
+        "inference": {"kernel": "conv_tc_kernel (tcgen05.mma BF16 x BF16 -> FP32 in tensor memory) for the four "
+                                "32->32 layers (98 % of the flops); first and last layer on the CUDA cores",
+                      "ms": round(inf_ms, 4), "tflops": round(tfl, 2), "bound": "tensor",
+                      "peak": bf16_peak, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                      "frac": round(tfl / bf16_peak, 5) if bf16_peak else None,
+                      "batch64": {"ms": round(inf[64][0], 4), "tflops": round(inf[64][1], 2),
+                                  "frac": round(inf[64][1] / bf16_peak, 5) if bf16_peak else None},
+                      "cuda_core_fp32_issue_peak_tflops": round(FP32_PEAK_TFLOPS, 1)},
     }
 
 
@@ -1038,6 +1052,32 @@ def run_spmv_only(args):
             "info": M.info()}
 
 
+def run_infer_only(args):
+    """Repeated BF16 inferences of the committed network on a batch (for
+    profiler captures of the tensor-core convolution)."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    from paper_2006_16852_gb300 import learned as LN
+    gk.load()
+    B = args.infer_only
+    net, _, _ = LN.load(os.path.join(LN.DATA_DIR, "wsnet_256.npz"), batch_max=B)
+    x = torch.randn((B, 2, net.H, net.W), dtype=torch.float32, device="cuda")
+    y = torch.zeros((B, 1, net.H, net.W), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        net.infer_bf16(x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        net.infer_bf16(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    net.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    macs = net.H * net.W * sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
+    return {"infer_only": B, "ms": round(ms, 4), "TFLOP/s": round(2.0 * B * macs / (ms * 1e-3) / 1e12, 2)}
+
+
 def run_solve_only(args):
     """Repeated solves of one configuration MAT:FMT:PREC:KIND, e.g. a:ell:1:cg
     (PREC = 0 none, 1 scalar Jacobi, 2..32 block Jacobi), for profiling."""
@@ -1093,6 +1133,8 @@ def main():
     ap.add_argument("--no-krylov", action="store_true", help="skip the FCG / CGS / GMRES section")
     ap.add_argument("--krylov-only", action="store_true", help="only the FCG / CGS / GMRES section")
     ap.add_argument("--no-latency", action="store_true", help="skip the per-iteration latency section")
+    ap.add_argument("--infer-only", type=int, default=0, metavar="B",
+                    help="only BF16 inferences of the committed network on a batch of B (profiling)")
     ap.add_argument("--latency-only", action="store_true", help="only the per-iteration latency section")
     ap.add_argument("--learned-only", action="store_true", help="only the learned warm start")
     ap.add_argument("--batch-systems", type=int, default=10000, help="--batched-only: number of systems")
@@ -1137,6 +1179,8 @@ def main():
                           tune=not args.batch_no_tune, plain=not args.batch_forms)
     elif args.spmv_only:
         out = run_spmv_only(args)
+    elif args.infer_only:
+        out = run_infer_only(args)
     elif args.solve_only:
         out = run_solve_only(args)
     else:

@@ -359,8 +359,16 @@ GK_API int gk_wsnet_gradients(gk_wsnet N, int32_t B, const float* x, const float
  * reading a host value). */
 GK_API int gk_wsnet_train_step(gk_wsnet N, int32_t B, const float* x, const float* target, float lr,
                                float* loss, void* stream);
-/* BF16 inference of B inputs into y (B, 1, H, W) float. */
+/* BF16 inference of B inputs into y (B, 1, H, W) float.  The four 32 -> 32
+ * layers run on the tensor cores (tcgen05.mma, BF16 operands, FP32
+ * accumulator in tensor memory), the first and last layer on the CUDA cores
+ * with FP32 sums; activations between layers are BF16.  Asynchronous: a
+ * device-side wait that gave up is reported by gk_wsnet_check. */
 GK_API int gk_wsnet_infer_bf16(gk_wsnet N, int32_t B, const float* x, float* y, void* stream);
+/* Waits for the stream; GK_ERR_TIMEOUT (and the flag cleared) if a
+ * tensor-core completion wait of an inference since the last check gave up
+ * (its outputs are then incomplete), else GK_OK. */
+GK_API int gk_wsnet_check(gk_wsnet N, void* stream);
 /* Network input of one problem from FP64 g and b (H W each) into feat
  * (2 H W floats) and, when x (FP64 solution) is given, the training target
  * x / (rms(b) * out_scale) into target (H W floats). */

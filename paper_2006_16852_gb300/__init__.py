@@ -38,6 +38,7 @@ EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get
            "gk_wsnet_create", "gk_wsnet_num_params", "gk_wsnet_set_params", "gk_wsnet_get_params",
            "gk_wsnet_set_loss",
            "gk_wsnet_forward", "gk_wsnet_gradients", "gk_wsnet_train_step", "gk_wsnet_infer_bf16",
+           "gk_wsnet_check",
            "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc")
 BATCH_CLASSES = 8
 BATCH_BLOCK_SIZES = (32, 64, 128, 256)
@@ -138,6 +139,7 @@ def load(path: str | None = None):
         "gk_wsnet_gradients": [vp, i32, vp, vp, vp, vp, vp],
         "gk_wsnet_train_step": [vp, i32, vp, vp, ctypes.c_float, vp, vp],
         "gk_wsnet_infer_bf16": [vp, i32, vp, vp, vp],
+        "gk_wsnet_check": [vp, vp],
         "gk_wsnet_features": [vp, vp, vp, vp, f64, vp, vp, vp],
         "gk_wsnet_warm_start": [vp, vp, vp, vp, f64, vp, vp],
         "gk_wsnet_destroy": [vp],
@@ -508,6 +510,11 @@ class WsNet:
         B = self._bx(x)
         _check(lib().gk_wsnet_infer_bf16(self.handle, B, _ptr(x), _ptr(y), _stream(stream, x, y)))
         return y
+
+    def check(self, stream=None):
+        """Waits for the stream; raises GkError (GK_ERR_TIMEOUT) if a
+        tensor-core completion wait of an inference gave up."""
+        _check(lib().gk_wsnet_check(self.handle, _stream(stream)))
 
     def features(self, g, b, feat, x=None, target=None, out_scale: float = 1.0, stream=None):
         _check(lib().gk_wsnet_features(self.handle, _ptr(g), _ptr(b), _ptr(x), float(out_scale), _ptr(feat),

@@ -13,7 +13,8 @@
 // (data gradients as a forward convolution with flipped, transposed weights;
 // weight gradients as per-block partial sums reduced in a fixed order), Adam.
 // Inference: weights, biases and activations in BF16, products formed in FP32
-// (exact for BF16 operands) and summed in FP32.
+// (exact for BF16 operands) and summed in FP32; the four 32 -> 32 layers run
+// on the tensor cores (tcgen05.mma, accumulator in tensor memory).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,13 +35,10 @@ constexpr int kConvThreads = 256;
 constexpr int kWgradRows = 4;  // image rows per weight-gradient block
 
 __device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename T>
 __device__ __forceinline__ T from_f(float v);
 template <>
 __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
 enum ConvMode { CONV_LINEAR = 0, CONV_RELU = 1, CONV_MASK = 2 };
 
@@ -387,6 +385,299 @@ __global__ void scale_kernel(double* __restrict__ x0, const double* __restrict__
     x0[i] *= a;
 }
 
+// ---------------------------------------------------------------------------
+// BF16 inference on the tensor cores.  Activations are NHWC BF16 between the
+// layers (a pixel's 32 channels are 64 contiguous bytes).  The 32 -> 32
+// layers run as an implicit GEMM on tcgen05: a tile is 128 consecutive
+// pixels of one image row (M = 128), N = 32 output channels, K = 9 taps x 32
+// input channels, issued as 18 MMAs of K = 16 (BF16 operands, FP32
+// accumulator in tensor memory).  For each kernel row ky the block stages
+// the input row y + d (ky - 1) from x0 - d to x0 + 127 + d once (zeros
+// outside the image); the three taps kx of that row are the same staged
+// window read from slot kx d on, so the MMA's A operand is the window with a
+// start address shifted by kx d rows.  Operands are K-major without
+// swizzling: a core matrix is 8 rows x 16 bytes (8 channels); rows of a
+// matrix are 16 bytes apart and its 8-channel chunks LBO bytes apart.  The
+// first layer (2 input channels) and the last (1 output channel) have no
+// GEMM worth the name and run on the CUDA cores, reading and writing NHWC.
+// ---------------------------------------------------------------------------
+
+constexpr int kTcThreads = 128;                 // 4 warps: one TMEM lane quarter each
+constexpr int kTcTile = 128;                    // pixels per tile (MMA M)
+constexpr int kTcWin = kTcTile + 2 * 64;        // staged window: dilation <= 64
+constexpr uint32_t kTcChunkA = kTcWin * 16;     // bytes between 8-channel chunks of a window
+constexpr uint32_t kTcChunkB = 32 * 16;         // bytes between 8-channel chunks of a tap's weights
+constexpr int kTcPacked = 9 * 4 * 32 * 8;       // packed BF16 weights of one 32 -> 32 layer
+constexpr int kTcMidLayers = kLayers - 2;
+
+struct TcSmem {
+  __nv_bfloat16 a[3 * 4 * kTcWin * 8];  // [ky][chunk][slot][8 channels]
+  __nv_bfloat16 b[kTcPacked];           // [tap][chunk][out][8 channels]
+  float bias[32];
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
+// 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N / 8 in bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
+// (K-direction) byte offset / 16 (bits 16-29), stride (M/N-direction) byte
+// offset / 16 (bits 32-45), the fixed version bits 46-48 = 0b001, no
+// swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of the warp's 32 TMEM lanes (lane = pixel).
+__device__ __forceinline__ void tc_load32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return l | (h << 16);
+}
+
+// One 32 -> 32 layer with ReLU: x, y NHWC BF16 (B, H, W, 32); wp the packed
+// weights [tap][chunk][out][8]; bias BF16.  Persistent over tiles; err gets
+// kErrTimeout if an MMA completion wait gives up.
+__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                             const __nv_bfloat16* __restrict__ wp,
+                                                             const __nv_bfloat16* __restrict__ bias, int B, int H,
+                                                             int W, int dil, __nv_bfloat16* __restrict__ y,
+                                                             int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int i = t; i < kTcPacked / 8; i += kTcThreads)
+    reinterpret_cast<uint4*>(S.b)[i] = __ldg(reinterpret_cast<const uint4*>(wp) + i);
+  if (t < 32) S.bias[t] = __bfloat162float(bias[t]);
+  if (t == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&S.tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t a_base = smem_u32(S.a), b_base = smem_u32(S.b);
+  const int tiles_x = (W + kTcTile - 1) / kTcTile;
+  const int n_tiles = B * H * tiles_x;
+  const int nslot = kTcTile + 2 * dil;
+  uint32_t phase = 0;
+  bool pending = false;  // an MMA group whose completion was not observed
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int row = tile / tiles_x;  // b * H + yy
+    const int x0 = (tile - row * tiles_x) * kTcTile;
+    const int yy = row % H;
+    const int64_t img = static_cast<int64_t>(row - yy) * W;  // first pixel of this sample
+    // stage the three input rows (one pixel's 4 chunks per thread and step)
+    for (int idx = t; idx < 3 * nslot; idx += kTcThreads) {
+      const int ky = idx / nslot, s = idx - ky * nslot;
+      const int ys = yy + dil * (ky - 1), xs = x0 - dil + s;
+      uint4 v[4] = {};
+      if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
+        const uint4* src = reinterpret_cast<const uint4*>(x + (img + static_cast<int64_t>(ys) * W + xs) * 32);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = __ldg(src + c);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(S.a)[(ky * 4 + c) * kTcWin + s] = v[c];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      uint32_t acc = 0;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t aa = a_base + ((ky * 4 + 2 * h) * kTcWin + kx * dil) * 16;
+            const uint32_t bb = b_base + ((ky * 3 + kx) * 4 + 2 * h) * kTcChunkB;
+            tc_mma(tmem, tc_desc(aa, kTcChunkA, 128), tc_desc(bb, kTcChunkB, 128), acc);
+            acc = 1;
+          }
+      tc_commit(&S.bar);
+    }
+    pending = true;
+    const bool ok = __syncthreads_and(mbar_wait(&S.bar, phase, err));
+    if (!ok) break;
+    pending = false;
+    phase ^= 1u;
+    tc_fence_after();
+    float v[32];
+    tc_load32(tmem + (static_cast<uint32_t>(warp * 32) << 16), v);
+    const int px = x0 + warp * 32 + lane;
+    if (px < W) {
+      uint4* dst = reinterpret_cast<uint4*>(y + (img + static_cast<int64_t>(yy) * W + px) * 32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = fmaxf(v[c * 8 + e] + S.bias[c * 8 + e], 0.0f);
+        dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                            pack_bf16x2(o[6], o[7]));
+      }
+    }
+  }
+  // an MMA whose completion was not seen is waited for once more (bounded)
+  // before its accumulator's tensor memory is released
+  if (pending) mbar_wait(&S.bar, phase, err);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  }
+}
+
+// Packs the 32 -> 32 layers' FP32 weights (out, in, 3, 3) into the MMA's B
+// layout [tap][chunk][out][8 channels], rounded to BF16.
+__global__ void pack_tc_kernel(const float* __restrict__ p, int64_t off0, int64_t stride,
+                               __nv_bfloat16* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kTcMidLayers * kTcPacked) return;
+  const int l = i / kTcPacked, r = i - l * kTcPacked;
+  const int e = r & 7, o = (r >> 3) & 31, kc = (r >> 8) & 3, tap = r >> 10;
+  const int c = kc * 8 + e;
+  out[i] = __float2bfloat16_rn(p[off0 + l * stride + (o * 32 + c) * 9 + tap]);
+}
+
+// The first layer (2 -> 32, ReLU): x NCHW BF16 (B, 2, H, W), y NHWC BF16.
+// Weights and bias are the BF16 parameter copy.
+__global__ void __launch_bounds__(256) conv_first_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                              const __nv_bfloat16* __restrict__ w,
+                                                              const __nv_bfloat16* __restrict__ bias, int H, int W,
+                                                              int dil, __nv_bfloat16* __restrict__ y) {
+  __shared__ __align__(16) float ws[18 * 32];
+  __shared__ float bs[32];
+  for (int idx = threadIdx.x; idx < 18 * 32; idx += blockDim.x) {
+    const int ct = idx >> 5, o = idx & 31;
+    ws[idx] = __bfloat162float(w[o * 18 + ct]);
+  }
+  if (threadIdx.x < 32) bs[threadIdx.x] = __bfloat162float(bias[threadIdx.x]);
+  __syncthreads();
+  const int HW = H * W;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= HW) return;
+  const int b = blockIdx.y;
+  const int i = p / W, j = p - i * W;
+  float acc[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) acc[o] = 0.0f;
+  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * 2 * HW;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int ii = i + dil * (ky - 1), jj = j + dil * (kx - 1);
+        const float v =
+            (ii >= 0 && ii < H && jj >= 0 && jj < W) ? __bfloat162float(xb[static_cast<int64_t>(c) * HW + ii * W + jj])
+                                                     : 0.0f;
+        const float4* wr = reinterpret_cast<const float4*>(ws + (c * 9 + ky * 3 + kx) * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 wv = wr[q];
+          acc[4 * q] = fmaf(wv.x, v, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(wv.y, v, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(wv.z, v, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(wv.w, v, acc[4 * q + 3]);
+        }
+      }
+  uint4* dst = reinterpret_cast<uint4*>(y + (static_cast<int64_t>(b) * HW + p) * 32);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o[e] = fmaxf(acc[c * 8 + e] + bs[c * 8 + e], 0.0f);
+    dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                        pack_bf16x2(o[6], o[7]));
+  }
+}
+
+// The last layer (32 -> 1, linear): x NHWC BF16, y FP32 (B, 1, H, W).
+__global__ void __launch_bounds__(256) conv_last_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                             const __nv_bfloat16* __restrict__ w,
+                                                             const __nv_bfloat16* __restrict__ bias, int H, int W,
+                                                             int dil, float* __restrict__ y) {
+  __shared__ float ws[9 * 32];  // [tap][c]
+  for (int idx = threadIdx.x; idx < 9 * 32; idx += blockDim.x) {
+    const int tap = idx >> 5, c = idx & 31;
+    ws[idx] = __bfloat162float(w[c * 9 + tap]);
+  }
+  __syncthreads();
+  const int HW = H * W;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= HW) return;
+  const int b = blockIdx.y;
+  const int i = p / W, j = p - i * W;
+  float acc = 0.0f;
+  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * HW * 32;
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      const int ii = i + dil * (ky - 1), jj = j + dil * (kx - 1);
+      if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(xb + (static_cast<int64_t>(ii) * W + jj) * 32);
+      const float* wr = ws + (ky * 3 + kx) * 32;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 q = __ldg(src + c);
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          acc = fmaf(wr[c * 8 + 2 * e], __uint_as_float(u[e] << 16), acc);
+          acc = fmaf(wr[c * 8 + 2 * e + 1], __uint_as_float(u[e] & 0xFFFF0000u), acc);
+        }
+      }
+    }
+  y[static_cast<int64_t>(b) * HW + p] = acc + __bfloat162float(bias[0]);
+}
+
 int ew_grid(int64_t n) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sm_count())));
 }
@@ -408,7 +699,10 @@ struct WsNet {
   bool bf_stale = true;
   float* act[kLayers + 1] = {};  // act[0] unused (the caller's input); act[l + 1] = layer l output
   float* dbuf[2] = {};           // data-gradient ping-pong
-  __nv_bfloat16* hbf[3] = {};    // inference: input copy + ping-pong activations
+  __nv_bfloat16* hbf[3] = {};    // inference: input copy (NCHW) + ping-pong activations (NHWC)
+  __nv_bfloat16* wtc = nullptr;  // the 32 -> 32 layers' weights in the tensor-core layout
+  int* err = nullptr;            // device-side wait that gave up (kErrTimeout)
+  int tc_grid = 0;               // resident tensor-core conv blocks (all SMs)
   float* partials = nullptr;
   int64_t partial_floats = 0;
   float* chunk = nullptr;  // kReduceChunks x the largest stride
@@ -430,7 +724,7 @@ void wsnet_release(WsNet* N) {
   cudaSetDevice(N->device);
   void* ptrs[] = {N->p,      N->g,      N->m,        N->v,     N->wflip,   N->pbf,  N->dbuf[0],
                   N->dbuf[1], N->hbf[0], N->hbf[1],   N->hbf[2], N->partials, N->chunk, N->red,
-                  N->counter, N->dred,   N->dcounter, N->scal,  N->feat,     N->ax};
+                  N->counter, N->dred,   N->dcounter, N->scal,  N->feat,     N->ax,      N->wtc, N->err};
   for (void* q : ptrs) dfree(q);
   for (int l = 1; l <= kLayers; ++l) dfree(N->act[l]);
   cudaSetDevice(prev);
@@ -546,24 +840,31 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
   if (N.bf_stale) {
     to_bf16_kernel<<<ew_grid(N.nparams), 256, 0, s>>>(N.p, N.pbf, N.nparams);
     GK_TRY_CUDA(cudaGetLastError());
+    pack_tc_kernel<<<(kTcMidLayers * kTcPacked + 255) / 256, 256, 0, s>>>(N.p, N.off_w[1], N.off_w[2] - N.off_w[1],
+                                                                          N.wtc);
+    GK_TRY_CUDA(cudaGetLastError());
     N.bf_stale = false;
   }
   const int64_t nin = static_cast<int64_t>(B) * 2 * N.H * N.W;
   to_bf16_kernel<<<ew_grid(nin), 256, 0, s>>>(x, N.hbf[0], nin);
   GK_TRY_CUDA(cudaGetLastError());
-  const __nv_bfloat16* in = N.hbf[0];
-  for (int l = 0; l < kLayers; ++l) {
-    const __nv_bfloat16* w = N.pbf + N.off_w[l];
-    const __nv_bfloat16* bb = N.pbf + N.off_b[l];
-    if (l < kLayers - 1) {
-      __nv_bfloat16* out = N.hbf[1 + (l & 1)];
-      GK_TRY((forward_layer<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(l, in, w, bb, B, N.H, N.W, N.dil[l], out,
-                                                                           s)));
-      in = out;
-    } else {
-      GK_TRY((forward_layer<__nv_bfloat16, __nv_bfloat16, float>(l, in, w, bb, B, N.H, N.W, N.dil[l], y, s)));
-    }
+  const dim3 pg((N.H * N.W + 255) / 256, B);
+  conv_first_nhwc_kernel<<<pg, 256, 0, s>>>(N.hbf[0], N.pbf + N.off_w[0], N.pbf + N.off_b[0], N.H, N.W, N.dil[0],
+                                            N.hbf[1]);
+  GK_TRY_CUDA(cudaGetLastError());
+  const int64_t tiles = static_cast<int64_t>(B) * N.H * ((N.W + kTcTile - 1) / kTcTile);
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, N.tc_grid)));
+  const __nv_bfloat16* in = N.hbf[1];
+  for (int l = 1; l < kLayers - 1; ++l) {
+    __nv_bfloat16* out = N.hbf[1 + (l & 1)];
+    conv_tc_kernel<<<grid, kTcThreads, sizeof(TcSmem), s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B,
+                                                             N.H, N.W, N.dil[l], out, N.err);
+    GK_TRY_CUDA(cudaGetLastError());
+    in = out;
   }
+  conv_last_nhwc_kernel<<<pg, 256, 0, s>>>(in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H,
+                                           N.W, N.dil[kLayers - 1], y);
+  GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
 
@@ -612,6 +913,16 @@ extern "C" int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const in
   GK_TRY(dalloc_n(&N->hbf[0], static_cast<size_t>(batch_max) * 2 * img, by));
   GK_TRY(dalloc_n(&N->hbf[1], big, by));
   GK_TRY(dalloc_n(&N->hbf[2], big, by));
+  GK_TRY(dalloc_n(&N->wtc, static_cast<size_t>(kTcMidLayers) * kTcPacked, by));
+  GK_TRY(dalloc_n(&N->err, 1, by));
+  GK_TRY_CUDA(cudaMemset(N->err, 0, sizeof(int)));
+  GK_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(sizeof(TcSmem))));
+  {
+    int per_sm = 0;
+    GK_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tc_kernel, kTcThreads, sizeof(TcSmem)));
+    N->tc_grid = std::max(1, per_sm) * sm_count();
+  }
   // weight-gradient slots: the largest layer's count
   int64_t pf = 0;
   const int64_t blocks = static_cast<int64_t>((H + kWgradRows - 1) / kWgradRows) * batch_max;
@@ -727,6 +1038,22 @@ extern "C" int gk_wsnet_infer_bf16(gk_wsnet h, int32_t B, const float* x, float*
   if (!x || !y) return set_error(GK_ERR_ARG, "gk_wsnet_infer_bf16: NULL argument");
   DeviceGuard dg(N->device);
   return infer_bf16(*N, B, x, y, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gk_wsnet_check(gk_wsnet h, void* stream) {
+  WsNet* N = reinterpret_cast<WsNet*>(h);
+  if (!N) return set_error(GK_ERR_ARG, "gk_wsnet_check: NULL handle");
+  DeviceGuard dg(N->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int e = 0;
+  GK_TRY_CUDA(cudaMemcpyAsync(&e, N->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GK_TRY_CUDA(cudaStreamSynchronize(s));
+  if (e != 0) {
+    GK_TRY_CUDA(cudaMemsetAsync(N->err, 0, sizeof(int), s));
+    GK_TRY_CUDA(cudaStreamSynchronize(s));
+    return set_error(GK_ERR_TIMEOUT, "gk_wsnet_check: a tensor-core completion wait gave up");
+  }
+  return GK_OK;
 }
 
 extern "C" int gk_wsnet_features(gk_wsnet h, const double* g, const double* b, const double* x, double out_scale,

@@ -113,12 +113,43 @@ def test_bf16_inference_matches_oracle(gk):
     x, _ = _data(2, 24, 20)
     y = to_dev(np.zeros((2, 1, 24, 20), dtype=np.float32))
     net.infer_bf16(to_dev(x), y)
+    net.check()
     ref = ON.infer_bf16(params, x.astype(np.float64), DIL)
     got = to_np(y)
     assert np.linalg.norm(got - ref) <= 1e-2 * np.linalg.norm(ref)
     full, _ = ON.forward(params, x.astype(np.float64), DIL)
     # and BF16 stays close to the FP64 network
     assert np.linalg.norm(got - full) <= 5e-2 * np.linalg.norm(full)
+
+
+@pytest.mark.parametrize("H,W_,B,dil", [(5, 300, 3, (1, 64, 3, 64, 2, 1)), (9, 128, 2, (2, 1, 7, 16, 5, 3)),
+                                         (3, 1, 1, (1, 1, 1, 1, 1, 1)), (1, 257, 1, (1, 64, 64, 64, 64, 1))])
+def test_bf16_inference_tiles_and_edges(gk, H, W_, B, dil):
+    """The tensor-core layers over several 128-pixel tiles per image row,
+    a ragged last tile, a one-pixel-wide and a one-row image, and dilations
+    up to 64 (the staged window's full width, taps falling outside the
+    image on both sides), per element against the oracle's BF16 inference:
+    an element may differ by the BF16 rounding of its inputs, so the bound
+    is 2 % of the output's scale plus 1 % of the element."""
+    net = gk.WsNet(H, W_, B, dil)
+    params = ON.init_params(5)
+    net.set_params(ON.flatten(params).astype(np.float32))
+    p32 = ON.unflatten(ON.flatten(params).astype(np.float32).astype(np.float64))
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((B, 2, H, W_)).astype(np.float32)
+    y = to_dev(np.full((B, 1, H, W_), np.nan, dtype=np.float32))
+    net.infer_bf16(to_dev(x), y)
+    net.check()
+    got = to_np(y)
+    ref = ON.infer_bf16(p32, x.astype(np.float64), dil)
+    assert np.all(np.isfinite(got))
+    scale = np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= 2e-2 * scale + 1e-2 * np.abs(ref))
+    assert np.linalg.norm(got - ref) <= 1e-2 * np.linalg.norm(ref)
+    # run to run identical
+    y2 = to_dev(np.zeros((B, 1, H, W_), dtype=np.float32))
+    net.infer_bf16(to_dev(x), y2)
+    np.testing.assert_array_equal(to_np(y2), got)
 
 
 def test_features_and_targets(gk):

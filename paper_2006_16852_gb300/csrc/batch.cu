@@ -681,8 +681,7 @@ int plan_class(const Batch& B, int kind, int jac, int c, int threads, ClassPlan*
   if (p->smem + 64 > static_cast<size_t>(smem_max))
     return set_error(GK_ERR_UNSUPPORTED, "batch: a %d-row system needs %zu bytes of shared memory (max %d)", k.nmax,
                      p->smem, smem_max);
-  GK_TRY_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(p->fn),
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p->smem)));
+  GK_TRY(set_smem(reinterpret_cast<const void*>(p->fn), p->smem));
   int per_sm = 0;
   GK_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->fn, threads, p->smem));
   if (per_sm < 1) return set_error(GK_ERR_UNSUPPORTED, "batch: no block of %d threads fits an SM", threads);

@@ -56,6 +56,13 @@ int current_device() {
   return d;
 }
 
+int set_smem(const void* fn, size_t smem) {
+  GK_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  GK_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   static_cast<int>(cudaSharedmemCarveoutMaxShared)));
+  return GK_OK;
+}
+
 int sm_count() {
   static int cache[64] = {};
   int d = current_device();

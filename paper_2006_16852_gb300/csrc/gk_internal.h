@@ -44,6 +44,16 @@ void dfree(void* p);
 int sm_count();
 int current_device();
 
+// Lets kernel `fn` use `smem` bytes of dynamic shared memory and asks for
+// the largest shared-memory carveout, so that as many of its blocks fit an
+// SM as its shared memory allows (with the default carveout the occupancy
+// query and the launch may settle for fewer).
+int set_smem(const void* fn, size_t smem);
+template <typename F>
+int set_smem(F* fn, size_t smem) {
+  return set_smem(reinterpret_cast<const void*>(fn), smem);
+}
+
 // Makes `dev` current for the lifetime of the guard, then restores the
 // caller's device.
 struct DeviceGuard {

@@ -125,8 +125,7 @@ __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
 template <int GW>
 int launch_bj_generate(const Matrix* A, int n, int bs, int nblocks, double* blocks, int* bad, cudaStream_t s) {
   const size_t smem = sizeof(double) * static_cast<size_t>(kBjWarps) * 32 * (2 * GW + 1);
-  cudaFuncSetAttribute(bj_generate_kernel<GW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
+  GK_TRY(set_smem(bj_generate_kernel<GW>, smem));
   const int64_t warps = (nblocks + (32 / GW) - 1) / (32 / GW);
   const int64_t g = std::min<int64_t>((warps + kBjWarps - 1) / kBjWarps, 16 * static_cast<int64_t>(sm_count()));
   bj_generate_kernel<GW><<<static_cast<int>(std::max<int64_t>(g, 1)), kBjWarps * 32, smem, s>>>(

@@ -592,8 +592,7 @@ bool g_attr_done[64] = {};
 int ensure_attributes() {
   int dev = current_device();
   if (dev >= 0 && dev < 64 && g_attr_done[dev]) return GK_OK;
-  GK_TRY_CUDA(cudaFuncSetAttribute(spmv_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(MergeSmem)));
+  GK_TRY(set_smem(spmv_merge_kernel, sizeof(MergeSmem)));
   if (dev >= 0 && dev < 64) g_attr_done[dev] = true;
   return GK_OK;
 }

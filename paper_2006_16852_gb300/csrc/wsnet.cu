@@ -764,8 +764,7 @@ template <int CIN, int COUT>
 int launch_wgrad(const WsNet& N, const float* x, const float* dy, int B, int dil, float* grads, cudaStream_t s) {
   using S = WgradShape<CIN, COUT>;
   const size_t smem = wgrad_smem(CIN, COUT, N.W, dil);
-  GK_TRY_CUDA(cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(smem)));
+  GK_TRY(set_smem(conv_wgrad_kernel<CIN, COUT>, smem));
   const dim3 grid((N.H + kWgradRows - 1) / kWgradRows, B);
   const int64_t nslots = static_cast<int64_t>(grid.x) * grid.y;
   if (nslots * S::STRIDE > N.partial_floats) return set_error(GK_ERR_UNSUPPORTED, "wsnet: gradient scratch too small");
@@ -916,12 +915,16 @@ extern "C" int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const in
   GK_TRY(dalloc_n(&N->wtc, static_cast<size_t>(kTcMidLayers) * kTcPacked, by));
   GK_TRY(dalloc_n(&N->err, 1, by));
   GK_TRY_CUDA(cudaMemset(N->err, 0, sizeof(int)));
-  GK_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(sizeof(TcSmem))));
+  GK_TRY(set_smem(conv_tc_kernel, sizeof(TcSmem)));
   {
-    int per_sm = 0;
-    GK_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tc_kernel, kTcThreads, sizeof(TcSmem)));
-    N->tc_grid = std::max(1, per_sm) * sm_count();
+    // resident blocks per SM: shared memory is the limit (registers, warps
+    // and the 512 tensor-memory columns allow 16 blocks of 32 columns); the
+    // occupancy query has been seen to report 1 for this kernel where 3 fit
+    int smem_sm = 0, reserved = 0;
+    GK_TRY_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, N->device));
+    GK_TRY_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, N->device));
+    const int per_sm = static_cast<int>(smem_sm / (sizeof(TcSmem) + static_cast<size_t>(reserved)));
+    N->tc_grid = std::max(1, std::min(per_sm, 16)) * sm_count();
   }
   // weight-gradient slots: the largest layer's count
   int64_t pf = 0;

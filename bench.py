@@ -1080,7 +1080,9 @@ def run_infer_only(args):
 
 def run_solve_only(args):
     """Repeated solves of one configuration MAT:FMT:PREC:KIND, e.g. a:ell:1:cg
-    (PREC = 0 none, 1 scalar Jacobi, 2..32 block Jacobi), for profiling."""
+    (MAT a = 27-point 128^3, b = power-law 10^6, c = convection-diffusion
+    1024^2; PREC = 0 none, 1 scalar Jacobi, 2..32 block Jacobi), for
+    profiling."""
     import torch
     import paper_2006_16852_gb300 as gk
     import workloads as W
@@ -1089,6 +1091,8 @@ def run_solve_only(args):
     prec = int(prec)
     if mat == "a":
         A = W.stencil27(128 if not args.small else 32)
+    elif mat == "c":
+        A = W.convdiff2d(1024 if not args.small else 128, 0.5)
     else:
         A = W.powerlaw(1_000_000 if not args.small else 20000, seed=3)
     n = A[0].size - 1

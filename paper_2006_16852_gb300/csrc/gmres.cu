@@ -3,10 +3,13 @@
 //
 // One cycle: V_0 = r / ||r||, g = ||r|| e_1; for j = 0 .. m-1 an Arnoldi
 // step w = A M^{-1} V_j orthogonalised against V_0..V_j by classical
-// Gram-Schmidt applied twice (each pass: all the dot products in one launch,
-// then one update launch), h_{j+1,j} = ||w||, V_{j+1} = w / h_{j+1,j}, the
-// previous Givens rotations applied to the new column of H and a new one
-// that zeroes h_{j+1,j}; |g_{j+1}| is the residual norm the criteria see.
+// Gram-Schmidt applied twice (each pass: all the dot products in one launch
+// whose last block also sums them, then one update launch), h_{j+1,j} =
+// ||w||, V_{j+1} = w / h_{j+1,j} (with M^{-1} V_{j+1} for the next step in
+// the same pass), the previous Givens rotations applied to the new column
+// of H and a new one that zeroes h_{j+1,j}; |g_{j+1}| is the residual norm
+// the criteria see.  On a GB300 the 4 (j+1) n FP64 multiply-adds of the two
+// passes, not the bytes, bound a step.
 // The cycle ends when the criteria are met, after m steps, or when
 // h_{j+1,j} = 0; then y = H^{-1} g, x += M^{-1} V y and r = b - A x is
 // recomputed (its norm is checked again at the start of the next cycle).
@@ -26,6 +29,7 @@ namespace gk {
 
 constexpr int kGmresMaxDim = 128;
 constexpr int kGmresThreads = 256;
+constexpr int kDotThreads = 256;  // the dot-product sweep
 
 struct GmresState {
   double H[(kGmresMaxDim + 1) * kGmresMaxDim];  // H[i * m + j]
@@ -44,11 +48,12 @@ struct GmresData {
   double* V = nullptr;     // (m + 1) * ldv
   double* w = nullptr;
   double* z = nullptr;     // M^{-1} V_j, then V y
-  double* dot_part = nullptr;  // (m + 1) x dot_grid partial dot products
-  int dot_grid = 1;
+  double* dot_part = nullptr;  // (m + 1) x dot_grid partial dot products, then m + 1 coefficients
+  int dot_grid = 1;            // blocks of the dot-product launch
+  int grid = 1;                // blocks of the orthogonalisation launch
   GmresState* gs = nullptr;
   double* part = nullptr;  // norm reduction partials
-  unsigned int* counter = nullptr;
+  unsigned int* counter = nullptr;   // [0] norm reduction, [1] dot products
   cudaStream_t cs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -73,10 +78,12 @@ struct GmArgs {
   GmresState* gs;
   SolverState* st;
   double* dot_part;
-  int dot_grid;
+  double* coef;  // this pass's coefficients h_i (after the (m + 1) x dot_grid partials)
   double* part;
   unsigned int* counter;
+  unsigned int* dcounter;
   cudaGraphConditionalHandle cond;
+  int host;  // 1: host-driven steps (no conditional node; a step after the cycle's end does nothing)
 };
 
 #define GM_FOR_ROWS(i) \
@@ -120,31 +127,76 @@ __global__ void __launch_bounds__(kGmresThreads) gm_precond_kernel(GmArgs a) {
   }
 }
 
-// Partial sums of V_i . w for i <= j: block (bx, i) sums the rows of its
-// grid-stride share; one block row of the grid per Arnoldi vector.
-__global__ void __launch_bounds__(kGmresThreads) gm_dots_kernel(GmArgs a) {
-  __shared__ double scratch[kRedScratch];
-  const int i = blockIdx.y;
-  if (i > a.gs->j) return;
-  const double* v = a.V + static_cast<int64_t>(i) * a.ldv;
-  double sum[1] = {0.0};
-  GM_FOR_ROWS(r) sum[0] = fma(v[r], a.w[r], sum[0]);
-  block_sum<1, double>(sum, scratch);
-  if (threadIdx.x == 0) a.dot_part[static_cast<int64_t>(i) * a.dot_grid + blockIdx.x] = sum[0];
-}
-
-// h_i = sum of the partials in block order; H(i, j) += h_i (the first pass
-// sets it).  One thread per i.
-__global__ void gm_collect_kernel(GmArgs a) {
+// h_i = V_i . w for every i <= j in one sweep: chunks of 8 vectors, each
+// chunk's FP64 partial sums per block (w is re-read per chunk, from L2); the
+// last block to arrive sums the block partials of every i in block order
+// (warp k takes i = k, k + 8, ...: lane l adds partials l, l + 32, ... into
+// four interleaved sums so that four loads are in flight, then the four
+// sums and one butterfly) and stores this pass's coefficients and H(i, j)
+// (the first pass sets it, the second adds).
+__global__ void __launch_bounds__(kDotThreads) gm_dots_kernel(GmArgs a) {
+  __shared__ double scratch[8 * kDotThreads];
+  __shared__ unsigned int s_last;
   GmresState* s = a.gs;
+  if (a.host && s->end) return;
   const int j = s->j;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    double h = 0.0;
-    for (int b = 0; b < a.dot_grid; ++b) h += a.dot_part[static_cast<int64_t>(i) * a.dot_grid + b];
-    a.dot_part[static_cast<int64_t>(a.m + 1) * a.dot_grid + i] = h;  // this pass's coefficients
-    if (s->pass == 0) s->H[i * a.m + j] = h;
-    else s->H[i * a.m + j] += h;
+  const int G = gridDim.x;
+  for (int c0 = 0; c0 <= j; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+    GM_FOR_ROWS(r) {
+      const double wr = a.w[r];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (c0 + k <= j) acc[k] = fma(a.V[static_cast<int64_t>(c0 + k) * a.ldv + r], wr, acc[k]);
+    }
+    // block sums of the 8 values, warp k summing value k (lane l adds
+    // threads l, l + 32, ... in order, then one butterfly): block_sum's
+    // order, but eight warps share the slow FP64 adds instead of one
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) scratch[k * kDotThreads + threadIdx.x] = acc[k];
+    __syncthreads();
+    const int wk = threadIdx.x >> 5, lk = threadIdx.x & 31;
+    if (wk < 8 && c0 + wk <= j) {
+      double v = scratch[wk * kDotThreads + lk];
+      for (int u = lk + 32; u < kDotThreads; u += 32) v += scratch[wk * kDotThreads + u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lk == 0) a.dot_part[static_cast<int64_t>(c0 + wk) * G + blockIdx.x] = v;
+    }
   }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(a.dcounter, 1u);
+    s_last = (t == static_cast<unsigned int>(G) - 1u) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j; i += kDotThreads / 32) {
+    const double* p = a.dot_part + static_cast<int64_t>(i) * G;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      v0 += __ldcg(p + b);
+      v1 += __ldcg(p + b + 32);
+      v2 += __ldcg(p + b + 64);
+      v3 += __ldcg(p + b + 96);
+    }
+    for (; b < G; b += 32) v0 += __ldcg(p + b);
+    double v = (v0 + v1) + (v2 + v3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      a.coef[i] = v;
+      if (s->pass == 0) s->H[i * a.m + j] = v;
+      else s->H[i * a.m + j] += v;
+    }
+  }
+  if (threadIdx.x == 0) *a.dcounter = 0u;
 }
 
 // w -= sum_{i <= j} h_i V_i; on the second pass also ||w||^2 (the last block
@@ -153,10 +205,10 @@ __global__ void __launch_bounds__(kGmresThreads) gm_orth_kernel(GmArgs a) {
   __shared__ double scratch[kRedScratch];
   __shared__ double hs[kGmresMaxDim + 1];
   GmresState* s = a.gs;
+  if (a.host && s->end) return;
   const int j = s->j;
   const bool last = s->pass == 1;
-  const double* h = a.dot_part + static_cast<int64_t>(a.m + 1) * a.dot_grid;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = h[i];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = a.coef[i];
   __syncthreads();
   double nn[1] = {0.0};
   GM_FOR_ROWS(r) {
@@ -174,61 +226,103 @@ __global__ void __launch_bounds__(kGmresThreads) gm_orth_kernel(GmArgs a) {
 }
 
 // h_{j+1,j} = ||w||; Givens rotations; residual estimate and criteria;
-// whether the cycle goes on (re-arms the WHILE node).
-__global__ void gm_step_kernel(GmArgs a) {
+// whether the cycle goes on (re-arms the WHILE node).  One warp: column j
+// of H and the previous rotations are staged in shared memory by all lanes,
+// lane 0 applies the rotations there, all lanes write the column back.
+__global__ void __launch_bounds__(32) gm_step_kernel(GmArgs a) {
+  __shared__ double col[kGmresMaxDim + 1], cs[kGmresMaxDim], sn[kGmresMaxDim];
   GmresState* s = a.gs;
+  if (a.host && s->end) return;
   SolverState* st = a.st;
-  const int m = a.m, j = s->j;
+  const int m = a.m, j = s->j, lane = threadIdx.x;
   double* H = s->H;
-  const double hn = s->hn;
-  H[(j + 1) * m + j] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double x0 = H[i * m + j], x1 = H[(i + 1) * m + j];
-    H[i * m + j] = s->cs[i] * x0 + s->sn[i] * x1;
-    H[(i + 1) * m + j] = -s->sn[i] * x0 + s->cs[i] * x1;
+  for (int i = lane; i <= j; i += 32) col[i] = H[i * m + j];
+  for (int i = lane; i < j; i += 32) {
+    cs[i] = s->cs[i];
+    sn[i] = s->sn[i];
   }
-  const double x0 = H[j * m + j], x1 = H[(j + 1) * m + j];
-  const double d = hypot(x0, x1);
-  s->cs[j] = d != 0.0 ? x0 / d : 1.0;
-  s->sn[j] = d != 0.0 ? x1 / d : 0.0;
-  H[j * m + j] = d;
-  H[(j + 1) * m + j] = 0.0;
-  s->g[j + 1] = -s->sn[j] * s->g[j];
-  s->g[j] = s->cs[j] * s->g[j];
-  st->iter += 1;
-  st->spmvs += 1;
-  st->iter_guard += 1;
-  st->rnorm = fabs(s->g[j + 1]);
-  const int stop = check_stop(st, st->rnorm, st->iter);
-  s->steps = j + 1;
-  s->end = (stop != GK_STOP_NONE || j + 1 >= m || hn == 0.0 || !isfinite(hn)) ? 1 : 0;
-  if (!isfinite(hn) || !isfinite(st->rnorm)) st->stop = GK_STOP_NAN;
-  cudaGraphSetConditional(a.cond, s->end ? 0u : 1u);
+  __syncwarp();
+  if (lane == 0) {
+    const double hn = s->hn;
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double x0 = col[i], x1 = col[i + 1];
+      col[i] = cs[i] * x0 + sn[i] * x1;
+      col[i + 1] = -sn[i] * x0 + cs[i] * x1;
+    }
+    const double x0 = col[j], x1 = col[j + 1];
+    const double d = hypot(x0, x1);
+    const double c = d != 0.0 ? x0 / d : 1.0, sj = d != 0.0 ? x1 / d : 0.0;
+    s->cs[j] = c;
+    s->sn[j] = sj;
+    col[j] = d;
+    col[j + 1] = 0.0;
+    const double gj = s->g[j];
+    s->g[j + 1] = -sj * gj;
+    s->g[j] = c * gj;
+    st->iter += 1;
+    st->spmvs += 1;
+    st->iter_guard += 1;
+    st->rnorm = fabs(s->g[j + 1]);
+    const int stop = check_stop(st, st->rnorm, st->iter);
+    s->steps = j + 1;
+    s->end = (stop != GK_STOP_NONE || j + 1 >= m || hn == 0.0 || !isfinite(hn)) ? 1 : 0;
+    if (!isfinite(hn) || !isfinite(st->rnorm)) st->stop = GK_STOP_NAN;
+    if (!s->end) s->j = j + 1;
+    if (!a.host) cudaGraphSetConditional(a.cond, s->end ? 0u : 1u);
+  }
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) H[i * m + j] = col[i];
 }
 
-// V_{j+1} = w / h_{j+1,j} unless the cycle ends; then j += 1.
+// Unless the cycle ends: V_{j+1} = w / h_{j+1,j} and z = M^{-1} V_{j+1}
+// for the next step (the step kernel has advanced j already).
+template <int PK, int BS>
 __global__ void __launch_bounds__(kGmresThreads) gm_next_kernel(GmArgs a) {
   GmresState* s = a.gs;
-  if (!s->end) {
-    const double inv = 1.0 / s->hn;
-    double* vn = a.V + static_cast<int64_t>(s->j + 1) * a.ldv;
-    GM_FOR_ROWS(i) vn[i] = a.w[i] * inv;
+  if (s->end) return;
+  const double inv = 1.0 / s->hn;
+  double* vn = a.V + static_cast<int64_t>(s->j) * a.ldv;
+  if (PK == PREC_BLOCK) {
+    GM_FOR_BLOCK_LANES(L) {
+      const double v = L.active ? a.w[L.row] * inv : 0.0;
+      if (L.active) vn[L.row] = v;
+      const double zz = bj_apply_lane<BS>(a.blocks, L, a.bs, v);
+      if (L.active) a.z[L.row] = zz;
+    }
+  } else {
+    GM_FOR_ROWS(i) {
+      const double v = a.w[i] * inv;
+      vn[i] = v;
+      a.z[i] = PK == PREC_SCALAR ? a.dinv[i] * v : v;
+    }
   }
 }
 
-__global__ void gm_advance_kernel(GmArgs a) {
-  if (!a.gs->end) a.gs->j += 1;
-}
-
-// y = H^{-1} g (back substitution over the steps taken).
-__global__ void gm_solve_kernel(GmArgs a) {
+// y = H^{-1} g (back substitution over the steps taken): the block stages
+// the k x k upper triangle and g in shared memory (dynamic, k * k + k
+// doubles), thread 0 substitutes row by row from there.
+__global__ void __launch_bounds__(256) gm_solve_kernel(GmArgs a) {
+  extern __shared__ double sh[];
   GmresState* s = a.gs;
   const int m = a.m, k = s->steps;
-  for (int i = k - 1; i >= 0; --i) {
-    double v = s->g[i];
-    for (int l = i + 1; l < k; ++l) v = fma(-s->H[i * m + l], s->y[l], v);
-    s->y[i] = v / s->H[i * m + i];
+  double* hk = sh;          // hk[i * k + l] = H(i, l)
+  double* gy = sh + k * k;  // g, then y
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx / k, l = idx - (idx / k) * k;
+    hk[idx] = l >= i ? s->H[i * m + l] : 0.0;
   }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) gy[i] = s->g[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double v = gy[i];
+      for (int l = i + 1; l < k; ++l) v = fma(-hk[i * k + l], gy[l], v);
+      gy[i] = v / hk[i * k + i];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) s->y[i] = gy[i];
 }
 
 // z = V y.
@@ -283,12 +377,16 @@ GmArgs gm_args(const Solver& S, const GmresData& d) {
   a.gs = d.gs;
   a.st = S.st;
   a.dot_part = d.dot_part;
-  a.dot_grid = d.dot_grid;
+  a.coef = d.dot_part + static_cast<int64_t>(d.m + 1) * d.dot_grid;
   a.part = d.part;
   a.counter = d.counter;
+  a.dcounter = d.counter + 1;
   a.cond = d.cond;
+  a.host = 0;
   return a;
 }
+
+size_t gm_solve_smem(const GmresData& d) { return sizeof(double) * (static_cast<size_t>(d.m) * d.m + d.m); }
 
 int gm_grid(const Solver& S) {
   const int64_t units = (S.pk == PREC_BLOCK) ? ((S.P->nblocks + (32 / S.P->bs) - 1) / (32 / S.P->bs)) * 32 : S.n;
@@ -328,25 +426,19 @@ Epi gm_epi(const Solver& S, int mode, const double* u, double* y, int fin) {
   return e;
 }
 
-// One Arnoldi step (the WHILE body).
+// One Arnoldi step (the WHILE body); z = M^{-1} V_j is ready on entry.
 int gm_enqueue_step(const Solver& S, const GmresData& d, const GmArgs& a, cudaStream_t s) {
   const int grid = gm_grid(S);
-  GM_LAUNCH_PK(gm_precond_kernel, grid, s, a);
   GK_TRY(spmv_launch(*S.A, d.z, gm_epi(S, EPI_COPY, nullptr, d.w, FIN_NONE), s));
   for (int pass = 0; pass < 2; ++pass) {
-    gm_dots_kernel<<<dim3(d.dot_grid, d.m + 1), kGmresThreads, 0, s>>>(a);
+    gm_dots_kernel<<<d.dot_grid, kDotThreads, 0, s>>>(a);
     GK_TRY_CUDA(cudaGetLastError());
-    gm_collect_kernel<<<1, 128, 0, s>>>(a);
-    GK_TRY_CUDA(cudaGetLastError());
-    gm_orth_kernel<<<d.dot_grid, kGmresThreads, 0, s>>>(a);
+    gm_orth_kernel<<<d.grid, kGmresThreads, 0, s>>>(a);
     GK_TRY_CUDA(cudaGetLastError());
   }
-  gm_step_kernel<<<1, 1, 0, s>>>(a);
+  gm_step_kernel<<<1, 32, 0, s>>>(a);
   GK_TRY_CUDA(cudaGetLastError());
-  gm_next_kernel<<<grid, kGmresThreads, 0, s>>>(a);
-  GK_TRY_CUDA(cudaGetLastError());
-  gm_advance_kernel<<<1, 1, 0, s>>>(a);
-  GK_TRY_CUDA(cudaGetLastError());
+  GM_LAUNCH_PK(gm_next_kernel, grid, s, a);
   return GK_OK;
 }
 
@@ -363,6 +455,13 @@ int gm_build_graph(Solver& S, GmresData& d) {
   do {
     gm_begin_kernel<<<grid, kGmresThreads, 0, d.cs>>>(a);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      rc = [&]() -> int {
+        GM_LAUNCH_PK(gm_precond_kernel, grid, d.cs, a);
+        return GK_OK;
+      }();
+      if (rc != GK_OK) break;
+    }
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -381,7 +480,7 @@ int gm_build_graph(Solver& S, GmresData& d) {
       break;
     }
     body = np.conditional.phGraph_out[0];
-    gm_solve_kernel<<<1, 1, 0, d.cs>>>(a);
+    gm_solve_kernel<<<1, 256, gm_solve_smem(d), d.cs>>>(a);
     gm_combine_kernel<<<grid, kGmresThreads, 0, d.cs>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -424,17 +523,19 @@ int gmres_generate(Solver* S) {
   if (m > kGmresMaxDim) return set_error(GK_ERR_ARG, "GMRES: krylov_dim %d (at most %d)", m, kGmresMaxDim);
   d->m = m;
   d->ldv = (S->n + 31) / 32 * 32;
-  d->dot_grid = std::max(1, std::min<int>(2 * sm_count(), static_cast<int>((S->n + kGmresThreads - 1) / kGmresThreads)));
+  d->grid = std::max(1, std::min<int>(4 * sm_count(), static_cast<int>((S->n + kGmresThreads - 1) / kGmresThreads)));
+  d->dot_grid = std::max(1, std::min<int>(4 * sm_count(), static_cast<int>((S->n + kDotThreads - 1) / kDotThreads)));
   int64_t* by = &d->bytes;
   int rc = GK_OK;
   do {
     if ((rc = dalloc_n(&d->V, static_cast<size_t>((m + 1) * d->ldv), by)) ||
         (rc = dalloc_n(&d->w, static_cast<size_t>(d->ldv), by)) || (rc = dalloc_n(&d->z, static_cast<size_t>(d->ldv), by)) ||
-        (rc = dalloc_n(&d->dot_part, static_cast<size_t>((m + 2) * d->dot_grid + m + 2), by)) ||
-        (rc = dalloc_n(&d->gs, 1, by)) || (rc = dalloc_n(&d->part, static_cast<size_t>(d->dot_grid + 2), by)) ||
-        (rc = dalloc_n(&d->counter, 1, by)))
+        (rc = dalloc_n(&d->dot_part, static_cast<size_t>((m + 1) * d->dot_grid + m + 2), by)) ||
+        (rc = dalloc_n(&d->gs, 1, by)) || (rc = dalloc_n(&d->part, static_cast<size_t>(d->grid + 2), by)) ||
+        (rc = dalloc_n(&d->counter, 2, by)))
       break;
-    cudaError_t e = cudaMemset(d->counter, 0, sizeof(unsigned int));
+    if ((rc = set_smem(gm_solve_kernel, gm_solve_smem(*d))) != GK_OK) break;
+    cudaError_t e = cudaMemset(d->counter, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(d->gs, 0, sizeof(GmresState));
     if (e != cudaSuccess) rc = cuda_error(e, "GMRES allocation");
   } while (false);
@@ -447,9 +548,36 @@ int gmres_generate(Solver* S) {
   return GK_OK;
 }
 
+// A cycle launched kernel by kernel (check_every > 0): the Arnoldi steps in
+// groups of check_every, each group followed by a read of the cycle's end
+// flag; the same kernels as the graph, for profilers that cannot see
+// kernels under a conditional node.
+int gm_host_cycle(Solver& S, GmresData& d, cudaStream_t s) {
+  GmArgs a = gm_args(S, d);
+  a.host = 1;
+  const int grid = gm_grid(S);
+  gm_begin_kernel<<<grid, kGmresThreads, 0, s>>>(a);
+  GK_TRY_CUDA(cudaGetLastError());
+  GM_LAUNCH_PK(gm_precond_kernel, grid, s, a);
+  const int every = std::max(1, S.crit.check_every);
+  for (int done = 0; done < d.m;) {
+    for (int k = 0; k < every && done < d.m; ++k, ++done) GK_TRY(gm_enqueue_step(S, d, a, s));
+    int end = 0;
+    GK_TRY_CUDA(cudaMemcpyAsync(&end, &d.gs->end, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GK_TRY_CUDA(cudaStreamSynchronize(s));
+    if (end) break;
+  }
+  gm_solve_kernel<<<1, 256, gm_solve_smem(d), s>>>(a);
+  gm_combine_kernel<<<grid, kGmresThreads, 0, s>>>(a);
+  GK_TRY_CUDA(cudaGetLastError());
+  GM_LAUNCH_PK(gm_update_kernel, grid, s, a);
+  return spmv_launch(*S.A, S.x, gm_epi(S, EPI_RESID, S.b, S.r, FIN_GMRES_RESID), s);
+}
+
 int gmres_solve(Solver* S, cudaStream_t s) {
   GmresData& d = *S->gm;
-  if (!d.exec) GK_TRY(gm_build_graph(*S, d));
+  const bool host = S->crit.check_every > 0;
+  if (!host && !d.exec) GK_TRY(gm_build_graph(*S, d));
   const gk_criteria& c = S->crit;
   const unsigned long long tl = c.time_limit_s > 0 ? static_cast<unsigned long long>(c.time_limit_s * 1e9) : 0ull;
   gm_init_kernel<<<1, 1, 0, s>>>(S->st, c.reduction_factor, static_cast<long long>(c.max_iters), c.rel_to_b, tl);
@@ -462,7 +590,8 @@ int gmres_solve(Solver* S, cudaStream_t s) {
     GK_TRY_CUDA(cudaMemcpyAsync(S->h_st, S->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     GK_TRY_CUDA(cudaStreamSynchronize(s));
     if (S->h_st->stop != GK_STOP_NONE) break;
-    GK_TRY_CUDA(cudaGraphLaunch(d.exec, s));
+    if (host) GK_TRY(gm_host_cycle(*S, d, s));
+    else GK_TRY_CUDA(cudaGraphLaunch(d.exec, s));
   }
   // the true residual of the result, as the other solvers report it
   return spmv_launch(*S->A, S->x, gm_epi(*S, EPI_RESID, S->b, d.w, FIN_TRUE_RESID), s);

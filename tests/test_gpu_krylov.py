@@ -105,3 +105,20 @@ def test_gmres_krylov_dim_limit(gk):
     M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]))
     with pytest.raises(gk.GkError):
         gk.Solver(M, None, "gmres", krylov_dim=129)
+
+
+@pytest.mark.parametrize("every", [1, 7])
+@pytest.mark.parametrize("prec", [None, 1, 4])
+def test_gmres_host_driven_steps_identical(gk, prec, every):
+    """The host-driven cycle (check_every > 0: the same kernels launched one
+    by one, the end flag read after every `every` steps) gives the graph's
+    result bit for bit, including restarts and the iteration count."""
+    A = W.convdiff2d(40, 0.5)
+    n = A[0].size - 1
+    b = W.uniform_vector(n, 8)
+    st0, x0 = _solve(gk, A, b, "gmres", "ell", prec, max_iters=3000, reduction_factor=1e-10, krylov_dim=12)
+    st1, x1 = _solve(gk, A, b, "gmres", "ell", prec, max_iters=3000, reduction_factor=1e-10, krylov_dim=12,
+                     check_every=every)
+    assert st0.stop_reason == st1.stop_reason == gk.STOP_CONVERGED
+    assert st0.iters == st1.iters and st0.spmvs == st1.spmvs and st0.iters > 12
+    np.testing.assert_array_equal(x0, x1)

@@ -95,11 +95,15 @@ typedef struct gk_solver_s* gk_solver;
  * stops the iteration.  ResidualNormReduction: ||r_k||_2 <= reduction_factor
  * * ref with ref = ||b||_2 if rel_to_b != 0, else ||r_0||_2.  Iteration:
  * k >= max_iters.  Time: wall time > time_limit_s (<= 0 disables it).
- * check_every <= 0 (the default) runs the whole solve as one CUDA graph whose
- * loop is controlled on the device (the criteria, Time included, are
- * evaluated by the GPU after every iteration); check_every > 0 instead
- * launches the iterations from the host and reads the stop flag back after
- * every check_every iterations. */
+ * check_every <= 0 runs the whole solve as one CUDA graph whose loop is
+ * controlled on the device (the criteria, Time included, are evaluated by
+ * the GPU after every iteration); check_every > 0 instead launches the
+ * iterations from the host and reads the stop flag back after every
+ * check_every iterations.  check_every == 0 (the default) additionally lets
+ * GK_CG without a preconditioner or with scalar Jacobi on up to 32,768 rows
+ * and without a Time criterion run as ONE launch of a 16-CTA thread-block
+ * cluster (the direction vector in distributed shared memory, the phases
+ * separated by cluster barriers); check_every < 0 always takes the graph. */
 typedef struct {
   int64_t max_iters;        /* GK_IR_CG: limit on the total of inner iterations      */
   double reduction_factor;
@@ -127,7 +131,13 @@ typedef struct {
   int32_t stop_reason;  /* GK_STOP_*                                                  */
   int32_t device_error; /* nonzero if a device-side wait timed out                    */
   int64_t outer_iters;  /* GK_IR_CG: refinement steps (FP64 residuals); else 0        */
+  int32_t form;         /* how the iteration ran: GK_FORM_*                           */
+  int32_t reserved_;
 } gk_status;
+
+#define GK_FORM_GRAPH 0    /* one CUDA graph, loop controlled on the device            */
+#define GK_FORM_HOST 1     /* iterations launched from the host (check_every > 0)      */
+#define GK_FORM_CLUSTER 2  /* one launch of a 16-CTA thread-block cluster (small CG)   */
 
 /* What a solver was built into. */
 typedef struct {

@@ -1,0 +1,366 @@
+// cluster_cg.cu -- the whole preconditioned CG solve (Section 3.1, with the
+// criteria of Section 2.5) of a small system in ONE launch: a thread-block
+// cluster of 16 CTAs on 16 SMs, the search direction p distributed over the
+// CTAs' shared memory and read across the cluster (distributed shared
+// memory) by the SpMV, the other vectors in registers of the thread that
+// owns the row, and the cluster's hardware barrier between the phases.
+//
+// Small systems are latency-bound: the graph form spends a few microseconds
+// per kernel launch and per grid-wide reduction, three times per iteration,
+// while the arithmetic of a 4,096-row iteration is about 40,000 FP64
+// multiply-adds.  Here an iteration costs three cluster barriers and the
+// FP64 work spread over 16 SMs.
+//
+// Rows: CTA c owns rows [c L, (c + 1) L), L = 2^lg >= n / 16; thread t owns
+// the CTA's rows t, t + 256, ..., (RPT of them).  An iteration:
+//   q = A p (CSR, each row summed in increasing column order as the oracle's
+//       ordered SpMV), sigma = p.q                                -> barrier
+//   alpha = rho / sigma; x += alpha p; r -= alpha q; z = M^{-1} r;
+//   rho' = r.z, ||r||^2                                           -> barrier
+//   criteria; beta = rho' / rho; p = z + beta p                   -> barrier
+// Every reduction: a fixed per-thread order, fixed butterflies within the
+// CTA, then the 16 CTA partials added in one fixed butterfly by every CTA --
+// all CTAs get bit-identical totals, so their stop decisions (and barrier
+// counts) agree.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "gk_device.cuh"
+#include "gk_internal.h"
+#include "solver_state.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gk {
+namespace {
+
+constexpr int kClCtas = 16;
+constexpr int kClThreads = 256;
+// rows per thread: n <= 16 * 256 * 8 = 32,768.  The FP64 work of an
+// iteration grows with n / 16 per SM here but with n / 152 in the graph form:
+// measured 7.1 us per iteration at n = 4,096 (graph 21.7 us), but ~29 us at
+// n = 65,536 (graph ~23 us); 32,768 rows is below the crossing.
+constexpr int kClMaxRpt = 8;
+
+struct ClusterArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* b;
+  double* x;
+  const double* dinv;
+  SolverState* st;
+  int n;
+  int lg;  // rows per CTA = 2^lg
+};
+
+// Partial sums published by each CTA (one slot per phase, so that a slot is
+// never rewritten before every CTA has read it: between the read of a slot
+// and its next write lies a barrier that the reader passes only after it).
+struct ClSlots {
+  double setup[2];  // ||r0||^2, ||b||^2
+  double start[1];  // r.z
+  double sigma[1];  // p.q
+  double iter[2];   // r.z, r.r
+};
+
+// Sum of v over the cluster, broadcast to the block in tot: a butterfly in
+// every warp (all warps at once), the 8 warp sums in a 3-level butterfly in
+// warp 0, the CTA's sum published in `slot`, the cluster barrier, then the
+// 16 CTA sums in a 4-level butterfly over lanes 0..15 -- 12 dependent FP64
+// adds in all, which on this GPU's slow FP64 pipe is what a reduction costs.
+template <int K>
+__device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)[K], double (*wsum)[K],
+                                              double* slot, double* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum<K, double>(v);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) wsum[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = lane < kClThreads / 32 ? wsum[lane][k] : 0.0;
+#pragma unroll
+    for (int o = kClThreads / 64; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) slot[k] = s[k];
+    }
+  }
+  cl.sync();
+  if (warp == 0) {
+    // lane q < 16 reads CTA q's sum; every CTA adds the same values in the
+    // same order
+    const double* rs = cl.map_shared_rank(slot, lane & (kClCtas - 1));
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = rs[k];
+#pragma unroll
+    for (int o = kClCtas / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) tot[k] = s[k];
+    }
+  }
+  __syncthreads();
+}
+
+template <int PK, int RPT>
+__global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
+  extern __shared__ double p_loc[];  // this CTA's slice of p (2^lg values)
+  __shared__ double* p_of[kClCtas];  // every CTA's slice, as seen from here
+  __shared__ ClSlots slots;
+  __shared__ double wsum[kClThreads / 32][2];
+  __shared__ double tot[2];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int t = threadIdx.x;
+  const int L = 1 << a.lg;
+  const int mask = L - 1;
+  if (t < kClCtas) p_of[t] = cl.map_shared_rank(p_loc, t);
+  const int row0 = rank * L;
+  SolverState* st = a.st;
+  const double factor = st->factor;
+  const long long max_iters = st->max_iters;
+  const int rel_to_b = st->rel_to_b;
+
+  double x[RPT], r[RPT], d[RPT];
+  bool own[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int l = t + u * kClThreads;
+    const int i = row0 + l;
+    own[u] = l < L && i < a.n;
+    x[u] = own[u] ? a.x[i] : 0.0;
+    d[u] = (PK == PREC_SCALAR && own[u]) ? a.dinv[i] : 1.0;
+    if (l < L) p_loc[l] = x[u];
+  }
+  cl.sync();  // p = x0 everywhere
+
+  // q_i = sum_k val_k p[col_k] in increasing k (p read across the cluster;
+  // the CTA's own slice directly); entries in groups of 4 so that their
+  // loads are in flight together
+  auto gather = [&](int c) {
+    const int o = c >> a.lg;
+    return o == rank ? p_loc[c & mask] : p_of[o][c & mask];
+  };
+  auto row_apply = [&](int i) {
+    double s = 0.0;
+    const int k1 = __ldg(a.rowptr + i + 1);
+    int k = __ldg(a.rowptr + i);
+    for (; k + 4 <= k1; k += 4) {
+      int c[4];
+      double v[4], pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(a.col + k + u);
+        v[u] = __ldg(a.val + k + u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = gather(c[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
+    }
+    for (; k < k1; ++k) s = fma(__ldg(a.val + k), gather(__ldg(a.col + k)), s);
+    return s;
+  };
+
+  // r0 = b - A x0; ||r0||, ||b||: the reference and the tolerance
+  {
+    double v[2] = {0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const int i = row0 + t + u * kClThreads;
+      const double bi = a.b[i];
+      r[u] = bi - row_apply(i);
+      v[0] = fma(r[u], r[u], v[0]);
+      v[1] = fma(bi, bi, v[1]);
+    }
+    cluster_total<2>(cl, v, wsum, slots.setup, tot);
+  }
+  const double rnorm0 = sqrt(tot[0]), bnorm = sqrt(tot[1]);
+  double ref = rel_to_b ? bnorm : rnorm0;
+  if (ref == 0.0) ref = 1.0;
+  const double tol = factor * ref;
+  double rnorm = rnorm0;
+  long long iter = 0, spmvs = 1;
+  int stop;
+  double rho, alpha = 1.0, beta = 0.0;
+  // z0 = M^{-1} r0, p0 = z0, rho = r0.z0
+  {
+    double v[1] = {0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int l = t + u * kClThreads;
+      if (!own[u]) continue;
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      p_loc[l] = z;
+      v[0] = fma(r[u], z, v[0]);
+    }
+    cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.start, tot);
+    rho = tot[0];
+  }
+  // the criteria at k = 0, in the order of check_stop (no Time criterion
+  // here: this form is chosen only without one)
+  auto criteria = [&](double rn, long long k) {
+    if (!isfinite(rn)) return GK_STOP_NAN;
+    if (rn <= tol) return GK_STOP_CONVERGED;
+    if (k >= max_iters) return GK_STOP_MAX_ITERS;
+    return GK_STOP_NONE;
+  };
+  stop = criteria(rnorm, 0);
+  while (stop == GK_STOP_NONE) {
+    double q[RPT];
+    {
+      double v[1] = {0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        q[u] = 0.0;
+        if (!own[u]) continue;
+        const int l = t + u * kClThreads;
+        q[u] = row_apply(row0 + l);
+        v[0] = fma(p_loc[l], q[u], v[0]);
+      }
+      cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.sigma, tot);
+    }
+    spmvs += 1;
+    const double sigma = tot[0];
+    if (!isfinite(sigma)) stop = GK_STOP_NAN;
+    else if (sigma <= 0.0) stop = GK_STOP_BREAKDOWN;
+    if (stop != GK_STOP_NONE) break;
+    alpha = rho / sigma;
+    {
+      double v[2] = {0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        if (!own[u]) continue;
+        const int l = t + u * kClThreads;
+        x[u] = fma(alpha, p_loc[l], x[u]);
+        r[u] = fma(-alpha, q[u], r[u]);
+        const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+        v[0] = fma(r[u], z, v[0]);
+        v[1] = fma(r[u], r[u], v[1]);
+      }
+      cluster_total<2>(cl, v, wsum, slots.iter, tot);
+    }
+    iter += 1;
+    rnorm = sqrt(tot[1]);
+    stop = criteria(rnorm, iter);
+    beta = tot[0] / rho;
+    rho = tot[0];
+    if (stop != GK_STOP_NONE) break;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const int l = t + u * kClThreads;
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      p_loc[l] = fma(beta, p_loc[l], z);
+    }
+    cl.sync();  // the new p everywhere before the next SpMV
+  }
+#pragma unroll
+  for (int u = 0; u < RPT; ++u)
+    if (own[u]) a.x[row0 + t + u * kClThreads] = x[u];
+  if (rank == 0 && t == 0) {
+    st->rnorm = rnorm;
+    st->rnorm0 = rnorm0;
+    st->bnorm = bnorm;
+    st->ref = ref;
+    st->tol = tol;
+    st->rho = rho;
+    st->alpha = alpha;
+    st->beta = beta;
+    st->iter = iter;
+    st->iter_guard = iter;
+    st->spmvs = spmvs;
+    st->stop = stop;
+  }
+  // no CTA may leave while others can still read its shared memory
+  cl.sync();
+}
+
+using ClKernel = void (*)(ClusterArgs);
+
+template <int PK>
+ClKernel pick_rpt(int rpt) {
+  switch (rpt) {
+    case 1: return cg_cluster_kernel<PK, 1>;
+    case 2: return cg_cluster_kernel<PK, 2>;
+    case 4: return cg_cluster_kernel<PK, 4>;
+    default: return cg_cluster_kernel<PK, 8>;
+  }
+}
+
+ClKernel pick(int pk, int rpt) { return pk == PREC_SCALAR ? pick_rpt<PREC_SCALAR>(rpt) : pick_rpt<PREC_NONE>(rpt); }
+
+cudaLaunchConfig_t launch_config(int lg, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClCtas, 1, 1);
+  cfg.blockDim = dim3(kClThreads, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(double) << lg;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+}  // namespace
+
+int cluster_cg_plan(Solver* S) {
+  S->cl_lg = -1;
+  if (S->kind != GK_CG || S->pk == PREC_BLOCK) return GK_OK;
+  const int64_t n = S->n;
+  if (n < 1 || n > static_cast<int64_t>(kClCtas) * kClThreads * kClMaxRpt) return GK_OK;
+  int lg = 0;
+  while ((static_cast<int64_t>(kClCtas) << lg) < n) ++lg;
+  const int rpt = std::max(1, (1 << lg) / kClThreads);
+  ClKernel k = pick(S->pk, rpt);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return GK_OK;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = launch_config(lg, nullptr, attr);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return GK_OK;
+  }
+  S->cl_lg = lg;
+  S->cl_rpt = rpt;
+  return GK_OK;
+}
+
+int cluster_cg_solve(Solver* S, cudaStream_t s) {
+  ClusterArgs a;
+  a.rowptr = S->A->rowptr;
+  a.col = S->A->col;
+  a.val = S->A->val;
+  a.b = S->b;
+  a.x = S->x;
+  a.dinv = S->P ? S->P->dinv : nullptr;
+  a.st = S->st;
+  a.n = static_cast<int>(S->n);
+  a.lg = S->cl_lg;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = launch_config(S->cl_lg, s, attr);
+  GK_TRY_CUDA(cudaLaunchKernelEx(&cfg, pick(S->pk, S->cl_rpt), a));
+  return GK_OK;
+}
+
+}  // namespace gk

@@ -303,12 +303,21 @@ struct Solver {
   cudaGraphConditionalHandle cond = 0;
   IrData* ir = nullptr;  // GK_IR_CG: the FP32 inner solver
   GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
+  int cl_lg = -1;           // GK_CG small-system form: rows per CTA = 2^cl_lg (-1: not available)
+  int cl_rpt = 1;           // ... rows per thread
 };
 
 // Mixed-precision iterative refinement (mixed.cu).
 int ir_generate(Solver* S);
 int ir_solve(Solver* S, cudaStream_t s);
 void ir_release(IrData* ir);
+
+// CG of a small system in one thread-block cluster (cluster_cg.cu): the plan
+// (sets cl_lg >= 0 when the form applies and a 16-CTA cluster can run) and
+// the solve (one launch; the state is left as the graph form leaves it
+// before its final true-residual check).
+int cluster_cg_plan(Solver* S);
+int cluster_cg_solve(Solver* S, cudaStream_t s);
 
 // Restarted GMRES (gmres.cu).
 int gmres_generate(Solver* S);

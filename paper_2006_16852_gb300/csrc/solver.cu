@@ -721,6 +721,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
     }
     if (kind == GK_IR_CG && (rc = ir_generate(S))) break;
     if (kind == GK_GMRES && (rc = gmres_generate(S))) break;
+    if (kind == GK_CG && (rc = cluster_cg_plan(S))) break;
   } while (false);
   if (prev != A->device) cudaSetDevice(prev);
   if (rc != GK_OK) return rc;
@@ -736,6 +737,7 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
   if (prev != S->device) cudaSetDevice(S->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = GK_OK;
+  int form = S->crit.check_every > 0 ? GK_FORM_HOST : GK_FORM_GRAPH;
   do {
     if (S->n == 0) {
       if (status) {
@@ -755,6 +757,19 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       if ((rc = ir_solve(S, s))) break;
     } else if (S->kind == GK_GMRES) {
       if ((rc = gmres_solve(S, s))) break;
+    } else if (S->kind == GK_CG && S->cl_lg >= 0 && S->crit.check_every == 0 && !(S->crit.time_limit_s > 0)) {
+      // small system: the whole iteration in one thread-block cluster
+      const gk_criteria& c = S->crit;
+      solver_init_kernel<<<1, 1, 0, s>>>(S->st, c.reduction_factor, static_cast<long long>(c.max_iters), c.rel_to_b,
+                                         0ull);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        rc = cuda_error(e, "gk_solve: state init");
+        break;
+      }
+      if ((rc = cluster_cg_solve(S, s))) break;
+      if ((rc = enqueue_final(*S, s))) break;
+      form = GK_FORM_CLUSTER;
     } else if (S->crit.check_every > 0) {
       // host-driven loop: groups of check_every iterations, then a status read
       VecArgs a = vec_args(*S, 0);
@@ -808,6 +823,8 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       status->stop_reason = H.stop;
       status->device_error = H.err;
       status->outer_iters = H.outer;
+      status->form = form;
+      status->reserved_ = 0;
     }
     if (H.err & kErrTimeout) rc = set_error(GK_ERR_TIMEOUT, "gk_solve: a device-side wait timed out");
   } while (false);

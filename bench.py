@@ -746,8 +746,9 @@ LATENCY_WORKLOAD = ("Poisson-2D 64x64 (n=4,096, nnz=20,224; L2-resident), x* uni
 
 def run_latency(dev):
     """Per-iteration time of CG on the small Poisson problem, where every
-    kernel is latency-bound: the whole solve as one graph whose loop the GPU
-    controls (check_every 0) against a host-driven loop that reads the status
+    kernel is latency-bound: the default form (one launch of a 16-CTA
+    thread-block cluster), the whole solve as one graph whose loop the GPU
+    controls (check_every -1), and host-driven loops that read the status
     after every iteration (check_every 1, the paper's host-side check) or
     after every 10."""
     import torch
@@ -758,13 +759,15 @@ def run_latency(dev):
     A = W.poisson2d(64)
     n = 4096
     out = {}
+    names = {0: "default", -1: "graph", 1: "host1", 10: "host10"}
+    forms = {gk.FORM_GRAPH: "graph", gk.FORM_HOST: "host", gk.FORM_CLUSTER: "cluster"}
     for fmt in ("csr", "ell"):
         M = gk.Matrix(*[t(a) for a in A], fmt=fmt)
         b = torch.zeros(n, dtype=torch.float64, device=dev)
         gk.apply(M, t(W.uniform_vector(n, 1)), b)
         for prec in (0, 1):
             P = gk.Precond(M, 1) if prec else None
-            for every in (0, 1, 10):
+            for every in (0, -1, 1, 10):
                 S = gk.Solver(M, P, "cg", max_iters=5000, reduction_factor=1e-10, check_every=every)
                 best = None
                 for _ in range(5):
@@ -776,9 +779,9 @@ def run_latency(dev):
                     e1.synchronize()
                     ms = e0.elapsed_time(e1)
                     best = ms if best is None else min(best, ms)
-                key = f"{fmt}_{'jacobi' if prec else 'plain'}_{'graph' if every == 0 else 'host%d' % every}"
-                out[key] = {"ms": round(best, 4), "iters": st.iters, "us_per_iter": round(1e3 * best / max(st.iters, 1), 3),
-                            "rel_res_true": st.rel_res_true}
+                key = f"{fmt}_{'jacobi' if prec else 'plain'}_{names[every]}"
+                out[key] = {"form": forms.get(st.form, st.form), "ms": round(best, 4), "iters": st.iters,
+                            "us_per_iter": round(1e3 * best / max(st.iters, 1), 3), "rel_res_true": st.rel_res_true}
     return {"workload": LATENCY_WORKLOAD, "timing": "CUDA events around gk_solve, best of 5",
             "paper_host_overhead_us_per_iter": [1.0, 1.5], "solves": out}
 

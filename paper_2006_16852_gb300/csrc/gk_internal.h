@@ -141,8 +141,8 @@ struct Epi {
 // ---------------------------------------------------------------------------
 // matrix handle
 // ---------------------------------------------------------------------------
-constexpr int kMergeThreads = 128;
-constexpr int kMergeItems = 16;  // merge-path items (row ends + nonzeros) per thread
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 8;  // merge-path items (row ends + nonzeros) per thread
 constexpr int kMergeTile = kMergeThreads * kMergeItems;
 // GK_CSR: rows of up to kSliceMaxLen entries go to length-sorted slices of 32
 // rows; longer rows are summed one warp per row, beyond kBlockRowLen one

@@ -314,8 +314,10 @@ void launch_ell_t(int grid, cudaStream_t s, const EllArgs& a, const Epi& e) {
 
 constexpr int kMergeStage = kMergeTile + 8;
 struct MergeSmem {
-  double val[kMergeStage];
-  double ys[kMergeTile];
+  union {
+    double val[kMergeStage];  // the tile's values (bulk copy), until every thread holds its own
+    double ys[kMergeTile];    // then the sums of rows that end inside one thread's items
+  };
   double head_val[kMergeThreads];
   double carry_val[kMergeThreads];
   int32_t rp[kMergeStage];
@@ -383,12 +385,16 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
     const bool tile_mid = tj > RP(ti);
     // ---- phase 1: each thread walks its items ----------------------------
     // The thread's items are the row ends and entries between merge
-    // diagonals dt and dte: entries [k, k_end) and the ends of rows
+    // diagonals dt and dte: entries [k, k + cnt) and the ends of rows
     // [row, row_end).  Its (at most kMergeItems) values and gathered x are
-    // loaded first, with static register indices, then the walk consumes a
-    // row end whenever the next entry lies past it.
+    // loaded first, with static register indices; after a barrier the value
+    // buffer takes the row sums, and the walk consumes a row end whenever
+    // the next entry lies past it.
     const int dt = d0 + t * kMergeItems;
-    if (dt < d1) {
+    const bool active = dt < d1;
+    int row = 0, k = 0, row_end = 0, cnt = 0;
+    double vv[kMergeItems], xv[kMergeItems];
+    if (active) {
       const int dte = min(dt + kMergeItems, d1);
       int lo = max(ti, dt - tj1), hi = min(ti1, dt - tj);
       while (lo < hi) {
@@ -402,24 +408,28 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
         if (RP(mid + 1) <= dte - mid - 1) lo2 = mid + 1;
         else hi2 = mid;
       }
-      int row = lo;
-      const int k = dt - lo;
-      const int row_end = lo2, cnt = (dte - lo2) - k;
-      double vv[kMergeItems], xv[kMergeItems];
+      row = lo;
+      k = dt - lo;
+      row_end = lo2;
+      cnt = (dte - lo2) - k;
+    }
 #pragma unroll
-      for (int u = 0; u < kMergeItems; ++u) {
-        const bool in = u < cnt;
-        vv[u] = in ? S.val[k + u - ja] : 0.0;
-        xv[u] = in ? __ldg(a.x + S.col[k + u - ja]) : 0.0;
-      }
+    for (int u = 0; u < kMergeItems; ++u) {
+      const bool in = u < cnt;
+      vv[u] = in ? S.val[k + u - ja] : 0.0;
+      xv[u] = in ? __ldg(a.x + S.col[k + u - ja]) : 0.0;
+    }
+    __syncthreads();
+    if (active) {
       const bool mid_row = k > RP(row);
       bool first = true;
       int head = -1;
       double sum = 0.0;
+      int next_end = cnt > 0 ? RP(row + 1) : 0;  // end of the current row, kept in a register
 #pragma unroll
       for (int u = 0; u < kMergeItems; ++u) {
         if (u < cnt) {
-          while (RP(row + 1) <= k + u) {
+          while (next_end <= k + u) {
             if (first && mid_row) {
               S.head_val[t] = sum;
               head = row;
@@ -429,6 +439,7 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
             first = false;
             sum = 0.0;
             ++row;
+            next_end = RP(row + 1);
           }
           sum = fma(vv[u], xv[u], sum);
         }
@@ -533,6 +544,8 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
       a.cont[tile] = ccont;
     }
 #undef RP
+    // the next tile's bulk copy (async proxy) overwrites the row sums (ys)
+    fence_proxy_async_smem();
     __syncthreads();
   }
   epi_partial(e, a0, a1, S.ys);  // ys is free once the tiles are done

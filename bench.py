@@ -760,7 +760,7 @@ def run_latency(dev):
     n = 4096
     out = {}
     names = {0: "default", -1: "graph", 1: "host1", 10: "host10"}
-    forms = {gk.FORM_GRAPH: "graph", gk.FORM_HOST: "host", gk.FORM_CLUSTER: "cluster"}
+    forms = {gk.FORM_GRAPH: "graph", gk.FORM_HOST: "host", gk.FORM_CLUSTER: "cluster", gk.FORM_GRID: "grid"}
     for fmt in ("csr", "ell"):
         M = gk.Matrix(*[t(a) for a in A], fmt=fmt)
         b = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -782,7 +782,30 @@ def run_latency(dev):
                 key = f"{fmt}_{'jacobi' if prec else 'plain'}_{names[every]}"
                 out[key] = {"form": forms.get(st.form, st.form), "ms": round(best, 4), "iters": st.iters,
                             "us_per_iter": round(1e3 * best / max(st.iters, 1), 3), "rel_res_true": st.rel_res_true}
-    return {"workload": LATENCY_WORKLOAD, "timing": "CUDA events around gk_solve, best of 5",
+    # a mid-size system: the default form is the cooperative grid
+    A2 = W.poisson2d(256)
+    M2 = gk.Matrix(*[t(a) for a in A2], fmt="csr")
+    b2 = torch.zeros(65536, dtype=torch.float64, device=dev)
+    gk.apply(M2, t(W.uniform_vector(65536, 1)), b2)
+    P2 = gk.Precond(M2, 1)
+    for every in (0, -1):
+        S = gk.Solver(M2, P2, "cg", max_iters=5000, reduction_factor=1e-10, check_every=every)
+        best = None
+        for _ in range(3):
+            x = torch.zeros_like(b2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, b2, x)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[f"poisson256_jacobi_{names[every]}"] = {"form": forms.get(st.form, st.form), "ms": round(best, 4),
+                                                    "iters": st.iters,
+                                                    "us_per_iter": round(1e3 * best / max(st.iters, 1), 3),
+                                                    "rel_res_true": st.rel_res_true}
+    return {"workload": LATENCY_WORKLOAD + "; and Poisson-2D 256x256 (n=65,536) with Jacobi for the mid-size form",
+            "timing": "CUDA events around gk_solve, best of 5 (3 for 256x256)",
             "paper_host_overhead_us_per_iter": [1.0, 1.5], "solves": out}
 
 

@@ -100,10 +100,12 @@ typedef struct gk_solver_s* gk_solver;
  * the GPU after every iteration); check_every > 0 instead launches the
  * iterations from the host and reads the stop flag back after every
  * check_every iterations.  check_every == 0 (the default) additionally lets
- * GK_CG without a preconditioner or with scalar Jacobi on up to 32,768 rows
- * and without a Time criterion run as ONE launch of a 16-CTA thread-block
+ * GK_CG without a preconditioner or with scalar Jacobi and without a Time
+ * criterion run as ONE launch: up to 32,768 rows a 16-CTA thread-block
  * cluster (the direction vector in distributed shared memory, the phases
- * separated by cluster barriers); check_every < 0 always takes the graph. */
+ * separated by cluster barriers); from 32,769 to 262,144 rows, when no row
+ * has more than 64 entries, a cooperative grid of one CTA per SM (grid-wide
+ * barriers in global memory).  check_every < 0 always takes the graph. */
 typedef struct {
   int64_t max_iters;        /* GK_IR_CG: limit on the total of inner iterations      */
   double reduction_factor;
@@ -138,6 +140,7 @@ typedef struct {
 #define GK_FORM_GRAPH 0    /* one CUDA graph, loop controlled on the device            */
 #define GK_FORM_HOST 1     /* iterations launched from the host (check_every > 0)      */
 #define GK_FORM_CLUSTER 2  /* one launch of a 16-CTA thread-block cluster (small CG)   */
+#define GK_FORM_GRID 3     /* one cooperative launch, grid-wide barriers (mid-size CG) */
 
 /* What a solver was built into. */
 typedef struct {

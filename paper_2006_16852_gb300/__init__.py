@@ -304,7 +304,7 @@ class SolveStatus:
     reserved_: int = 0
 
 
-FORM_GRAPH, FORM_HOST, FORM_CLUSTER = 0, 1, 2
+FORM_GRAPH, FORM_HOST, FORM_CLUSTER, FORM_GRID = 0, 1, 2, 3
 
 
 class Solver:

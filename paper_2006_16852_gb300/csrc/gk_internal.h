@@ -305,6 +305,10 @@ struct Solver {
   GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
   int cl_lg = -1;           // GK_CG small-system form: rows per CTA = 2^cl_lg (-1: not available)
   int cl_rpt = 1;           // ... rows per thread
+  int gr_grid = 0;          // GK_CG mid-size form: CTAs of the cooperative launch (0: not available)
+  int gr_rpt = 1, gr_rows = 0;
+  double* gr_part = nullptr;        // its per-CTA partial sums
+  unsigned int* gr_sync = nullptr;  // its barrier words
 };
 
 // Mixed-precision iterative refinement (mixed.cu).
@@ -318,6 +322,11 @@ void ir_release(IrData* ir);
 // before its final true-residual check).
 int cluster_cg_plan(Solver* S);
 int cluster_cg_solve(Solver* S, cudaStream_t s);
+
+// CG of a mid-size system (32,769 .. 262,144 rows, rows of at most 64
+// entries) in one cooperative launch with grid-wide barriers (grid_cg.cu).
+int grid_cg_plan(Solver* S);
+int grid_cg_solve(Solver* S, cudaStream_t s);
 
 // Restarted GMRES (gmres.cu).
 int gmres_generate(Solver* S);

@@ -1,0 +1,379 @@
+// grid_cg.cu -- the whole preconditioned CG solve (Section 3.1, criteria of
+// Section 2.5) of a mid-size system in ONE cooperative launch: one CTA per
+// SM, every CTA resident for the whole solve, the phases separated by
+// grid-wide barriers in global memory.
+//
+// Between 32,768 rows (the cluster form's limit) and a few hundred thousand,
+// an iteration of the graph form is still bound by launch and reduction
+// latency (~20 us for three launches) rather than by its bytes or FP64
+// work.  Here an iteration is three grid barriers plus the work spread over
+// all 152 SMs.
+//
+// Rows: CTA b owns rows [b R, (b + 1) R), thread t the CTA's rows t, t + 256,
+// ...; x, r, q and the Jacobi diagonal of a row stay in the owning thread's
+// registers, p lives in global memory (L2) because the SpMV reads it at
+// arbitrary columns.  An iteration:
+//   q = A p (CSR rows, each summed in increasing column order as the
+//       oracle's ordered SpMV), sigma = p.q                 -> barrier
+//   alpha = rho / sigma; x += alpha p; r -= alpha q; z = M^{-1} r;
+//   rho' = r.z, ||r||^2                                     -> barrier
+//   criteria; beta = rho' / rho; p = z + beta p              -> barrier
+// A reduction: each CTA's sum (fixed butterflies) is stored in its slot, the
+// barrier, then every CTA adds all the slots in one fixed order -- all CTAs
+// hold bit-identical totals and take identical stop decisions, so they pass
+// the same number of barriers.  Every barrier wait is bounded: a wait that
+// gives up sets the error bit and an abort flag that ends every other
+// CTA's waits at once, so the launch always returns.
+#include <algorithm>
+#include <vector>
+
+#include "gk_device.cuh"
+#include "gk_internal.h"
+#include "solver_state.cuh"
+
+namespace gk {
+namespace {
+
+constexpr int kGrThreads = 256;
+constexpr int kGrMaxRpt = 8;
+constexpr int64_t kGrMinRows = 32769;    // below: the cluster form
+constexpr int64_t kGrMaxRows = 262144;   // above: the graph form's SpMV kernels win
+constexpr int kGrMaxRowLen = 64;         // one thread per row: no long rows
+
+struct GridArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* b;
+  double* x;
+  double* p;
+  const double* dinv;
+  SolverState* st;
+  double* part;        // [4 slots][grid][2] CTA partial sums
+  unsigned int* sync;  // [0] arrivals, [1] generation, [2] abort
+  int n;
+  int rows_per_cta;
+};
+
+// Grid barrier (thread 0 of every CTA arrives; the last arrival resets the
+// count and advances the generation).  Returns false if the solve is being
+// aborted (this or another CTA's wait gave up).
+__device__ __forceinline__ bool grid_barrier(const GridArgs& a, unsigned int& gen, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vsync = a.sync;
+    __threadfence();
+    const unsigned int g0 = gen;
+    if (atomicAdd(a.sync, 1u) == gridDim.x - 1) {
+      atomicExch(a.sync, 0u);
+      __threadfence();
+      atomicAdd(a.sync + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      for (uint32_t i = 0;; ++i) {
+        if (vsync[1] != g0) break;
+        if (vsync[2] != 0u) {
+          ok = 0;
+          break;
+        }
+        if (i > kMaxPolls || clock64() - t0 > kMaxWaitCycles) {
+          atomicOr(&a.st->err, kErrTimeout);
+          atomicExch(a.sync + 2, 1u);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    gen = g0 + 1;
+    if (vsync[2] != 0u) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Sum of v over the grid into tot (every thread): CTA sum by butterflies,
+// stored in the slot, the barrier, then all CTA sums added by every CTA in
+// the same order (thread j takes CTAs j, j + 256, ...; then butterflies).
+template <int K>
+__device__ __forceinline__ bool grid_total(const GridArgs& a, int slot, double (&v)[K], double (*wsum)[2],
+                                           double* tot, unsigned int& gen, int* s_ok) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum<K, double>(v);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) wsum[warp][k] = v[k];
+  }
+  __syncthreads();
+  double* slots = a.part + static_cast<int64_t>(slot) * gridDim.x * 2;
+  if (warp == 0) {
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = lane < kGrThreads / 32 ? wsum[lane][k] : 0.0;
+#pragma unroll
+    for (int o = kGrThreads / 64; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) slots[blockIdx.x * 2 + k] = s[k];
+    }
+  }
+  if (!grid_barrier(a, gen, s_ok)) return false;
+  double s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.0;
+  for (int j = threadIdx.x; j < static_cast<int>(gridDim.x); j += kGrThreads) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] += __ldcg(slots + j * 2 + k);
+  }
+  warp_sum<K, double>(s);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) wsum[warp][k] = s[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double u[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) u[k] = lane < kGrThreads / 32 ? wsum[lane][k] : 0.0;
+#pragma unroll
+    for (int o = kGrThreads / 64; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) u[k] += __shfl_xor_sync(0xffffffffu, u[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) tot[k] = u[k];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int PK, int RPT>
+__global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
+  __shared__ double wsum[kGrThreads / 32][2];
+  __shared__ double tot[2];
+  __shared__ int s_ok;
+  const int t = threadIdx.x;
+  const int row0 = blockIdx.x * a.rows_per_cta;
+  SolverState* st = a.st;
+  const double factor = st->factor;
+  const long long max_iters = st->max_iters;
+  const int rel_to_b = st->rel_to_b;
+  unsigned int gen = 0;
+
+  double x[RPT], r[RPT], d[RPT];
+  bool own[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int l = t + u * kGrThreads;
+    const int i = row0 + l;
+    own[u] = l < a.rows_per_cta && i < a.n;
+    x[u] = own[u] ? a.x[i] : 0.0;
+    d[u] = (PK == PREC_SCALAR && own[u]) ? __ldg(a.dinv + i) : 1.0;
+    if (own[u]) a.p[i] = x[u];
+  }
+  auto row_apply = [&](int i) {
+    double s = 0.0;
+    const int k1 = __ldg(a.rowptr + i + 1);
+    int k = __ldg(a.rowptr + i);
+    for (; k + 4 <= k1; k += 4) {
+      int c[4];
+      double v[4], pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(a.col + k + u);
+        v[u] = __ldg(a.val + k + u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = __ldcg(a.p + c[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
+    }
+    for (; k < k1; ++k) s = fma(__ldg(a.val + k), __ldcg(a.p + __ldg(a.col + k)), s);
+    return s;
+  };
+  auto criteria = [&](double rn, double tol, long long k) {
+    if (!isfinite(rn)) return GK_STOP_NAN;
+    if (rn <= tol) return GK_STOP_CONVERGED;
+    if (k >= max_iters) return GK_STOP_MAX_ITERS;
+    return GK_STOP_NONE;
+  };
+  double rnorm0 = 0.0, bnorm = 0.0, ref = 1.0, tol = 0.0, rnorm = 0.0, rho = 0.0, alpha = 1.0, beta = 0.0;
+  long long iter = 0, spmvs = 1;
+  int stop = GK_STOP_NONE;
+  bool ok = grid_barrier(a, gen, &s_ok);  // p = x0 everywhere
+  if (ok) {
+    double v[2] = {0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const int i = row0 + t + u * kGrThreads;
+      const double bi = a.b[i];
+      r[u] = bi - row_apply(i);
+      v[0] = fma(r[u], r[u], v[0]);
+      v[1] = fma(bi, bi, v[1]);
+    }
+    ok = grid_total<2>(a, 0, v, wsum, tot, gen, &s_ok);
+  }
+  if (ok) {
+    rnorm0 = sqrt(tot[0]);
+    bnorm = sqrt(tot[1]);
+    ref = rel_to_b ? bnorm : rnorm0;
+    if (ref == 0.0) ref = 1.0;
+    tol = factor * ref;
+    rnorm = rnorm0;
+    double v[1] = {0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      a.p[row0 + t + u * kGrThreads] = z;
+      v[0] = fma(r[u], z, v[0]);
+    }
+    ok = grid_total<1>(a, 1, v, wsum, tot, gen, &s_ok);
+    rho = tot[0];
+    stop = criteria(rnorm, tol, 0);
+  }
+  while (ok && stop == GK_STOP_NONE) {
+    double q[RPT], pl[RPT];
+    double v[1] = {0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      q[u] = 0.0;
+      pl[u] = 0.0;
+      if (!own[u]) continue;
+      const int i = row0 + t + u * kGrThreads;
+      q[u] = row_apply(i);
+      pl[u] = __ldcg(a.p + i);
+      v[0] = fma(pl[u], q[u], v[0]);
+    }
+    if (!(ok = grid_total<1>(a, 2, v, wsum, tot, gen, &s_ok))) break;
+    spmvs += 1;
+    const double sigma = tot[0];
+    if (!isfinite(sigma)) stop = GK_STOP_NAN;
+    else if (sigma <= 0.0) stop = GK_STOP_BREAKDOWN;
+    if (stop != GK_STOP_NONE) break;
+    alpha = rho / sigma;
+    double w[2] = {0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      x[u] = fma(alpha, pl[u], x[u]);
+      r[u] = fma(-alpha, q[u], r[u]);
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      w[0] = fma(r[u], z, w[0]);
+      w[1] = fma(r[u], r[u], w[1]);
+    }
+    if (!(ok = grid_total<2>(a, 3, w, wsum, tot, gen, &s_ok))) break;
+    iter += 1;
+    rnorm = sqrt(tot[1]);
+    stop = criteria(rnorm, tol, iter);
+    beta = tot[0] / rho;
+    rho = tot[0];
+    if (stop != GK_STOP_NONE) break;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      a.p[row0 + t + u * kGrThreads] = fma(beta, pl[u], z);
+    }
+    ok = grid_barrier(a, gen, &s_ok);  // the new p everywhere before the next SpMV
+  }
+#pragma unroll
+  for (int u = 0; u < RPT; ++u)
+    if (own[u]) a.x[row0 + t + u * kGrThreads] = x[u];
+  if (blockIdx.x == 0 && t == 0) {
+    st->rnorm = rnorm;
+    st->rnorm0 = rnorm0;
+    st->bnorm = bnorm;
+    st->ref = ref;
+    st->tol = tol;
+    st->rho = rho;
+    st->alpha = alpha;
+    st->beta = beta;
+    st->iter = iter;
+    st->iter_guard = iter;
+    st->spmvs = spmvs;
+    st->stop = ok ? stop : GK_STOP_NAN;
+  }
+}
+
+using GrKernel = void (*)(GridArgs);
+
+template <int PK>
+GrKernel pick_rpt(int rpt) {
+  switch (rpt) {
+    case 1: return cg_grid_kernel<PK, 1>;
+    case 2: return cg_grid_kernel<PK, 2>;
+    case 4: return cg_grid_kernel<PK, 4>;
+    default: return cg_grid_kernel<PK, 8>;
+  }
+}
+
+GrKernel pick(int pk, int rpt) { return pk == PREC_SCALAR ? pick_rpt<PREC_SCALAR>(rpt) : pick_rpt<PREC_NONE>(rpt); }
+
+}  // namespace
+
+int grid_cg_plan(Solver* S) {
+  S->gr_grid = 0;
+  if (S->kind != GK_CG || S->pk == PREC_BLOCK) return GK_OK;
+  const int64_t n = S->n;
+  if (n < kGrMinRows || n > kGrMaxRows) return GK_OK;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, S->device) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return GK_OK;
+  }
+  // longest row (one thread per row)
+  std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
+  GK_TRY_CUDA(cudaMemcpy(rp.data(), S->A->rowptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost));
+  int32_t longest = 0;
+  for (int64_t i = 0; i < n; ++i) longest = std::max(longest, rp[i + 1] - rp[i]);
+  if (longest > kGrMaxRowLen) return GK_OK;
+  const int G = sm_count();
+  const int64_t per_cta = (n + G - 1) / G;
+  int rpt = 1;
+  while (static_cast<int64_t>(rpt) * kGrThreads < per_cta) rpt *= 2;
+  if (rpt > kGrMaxRpt) return GK_OK;
+  GrKernel k = pick(S->pk, rpt);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGrThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return GK_OK;
+  }
+  GK_TRY(dalloc_n(&S->gr_part, static_cast<size_t>(4) * G * 2, &S->device_bytes));
+  GK_TRY(dalloc_n(&S->gr_sync, 4, &S->device_bytes));
+  S->gr_grid = G;
+  S->gr_rpt = rpt;
+  S->gr_rows = static_cast<int>(per_cta);
+  return GK_OK;
+}
+
+int grid_cg_solve(Solver* S, cudaStream_t s) {
+  GridArgs a;
+  a.rowptr = S->A->rowptr;
+  a.col = S->A->col;
+  a.val = S->A->val;
+  a.b = S->b;
+  a.x = S->x;
+  a.p = S->p;
+  a.dinv = S->P ? S->P->dinv : nullptr;
+  a.st = S->st;
+  a.part = S->gr_part;
+  a.sync = S->gr_sync;
+  a.n = static_cast<int>(S->n);
+  a.rows_per_cta = S->gr_rows;
+  GK_TRY_CUDA(cudaMemsetAsync(S->gr_sync, 0, 4 * sizeof(unsigned int), s));
+  void* args[] = {&a};
+  GK_TRY_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(pick(S->pk, S->gr_rpt)), dim3(S->gr_grid),
+                                          dim3(kGrThreads), args, 0, s));
+  return GK_OK;
+}
+
+}  // namespace gk

@@ -460,6 +460,8 @@ void solver_release(Solver* S) {
   dfree(S->st);
   dfree(S->partials);
   dfree(S->counter);
+  dfree(S->gr_part);
+  dfree(S->gr_sync);
   if (S->h_st) cudaFreeHost(S->h_st);
   ir_release(S->ir);
   gmres_release(S->gm);
@@ -722,6 +724,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
     if (kind == GK_IR_CG && (rc = ir_generate(S))) break;
     if (kind == GK_GMRES && (rc = gmres_generate(S))) break;
     if (kind == GK_CG && (rc = cluster_cg_plan(S))) break;
+    if (kind == GK_CG && S->cl_lg < 0 && (rc = grid_cg_plan(S))) break;
   } while (false);
   if (prev != A->device) cudaSetDevice(prev);
   if (rc != GK_OK) return rc;
@@ -770,6 +773,19 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       if ((rc = cluster_cg_solve(S, s))) break;
       if ((rc = enqueue_final(*S, s))) break;
       form = GK_FORM_CLUSTER;
+    } else if (S->kind == GK_CG && S->gr_grid > 0 && S->crit.check_every == 0 && !(S->crit.time_limit_s > 0)) {
+      // mid-size system: the whole iteration in one cooperative launch
+      const gk_criteria& c = S->crit;
+      solver_init_kernel<<<1, 1, 0, s>>>(S->st, c.reduction_factor, static_cast<long long>(c.max_iters), c.rel_to_b,
+                                         0ull);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        rc = cuda_error(e, "gk_solve: state init");
+        break;
+      }
+      if ((rc = grid_cg_solve(S, s))) break;
+      if ((rc = enqueue_final(*S, s))) break;
+      form = GK_FORM_GRID;
     } else if (S->crit.check_every > 0) {
       // host-driven loop: groups of check_every iterations, then a status read
       VecArgs a = vec_args(*S, 0);

@@ -124,5 +124,5 @@ def test_form_selection(gk):
     assert _solve(gk, A, b, prec=4)[0].form == gk.FORM_GRAPH
     edge = W.poisson2d(128, 256)  # n = 32,768: the largest size of the form
     assert _solve(gk, edge, W.uniform_vector(32768, 8), max_iters=5)[0].form == gk.FORM_CLUSTER
-    big = W.poisson2d(182)
-    assert _solve(gk, big, W.uniform_vector(182 * 182, 8), max_iters=5)[0].form == gk.FORM_GRAPH
+    big = W.poisson2d(182)  # above the cluster form's size: the cooperative-grid form
+    assert _solve(gk, big, W.uniform_vector(182 * 182, 8), max_iters=5)[0].form == gk.FORM_GRID

@@ -6,18 +6,20 @@
 // Between 32,768 rows (the cluster form's limit) and a few hundred thousand,
 // an iteration of the graph form is still bound by launch and reduction
 // latency (~20 us for three launches) rather than by its bytes or FP64
-// work.  Here an iteration is three grid barriers plus the work spread over
+// work.  Here an iteration is two grid barriers plus the work spread over
 // all 152 SMs.
 //
 // Rows: CTA b owns rows [b R, (b + 1) R), thread t the CTA's rows t, t + 256,
 // ...; x, r, q and the Jacobi diagonal of a row stay in the owning thread's
-// registers, p lives in global memory (L2) because the SpMV reads it at
-// arbitrary columns.  An iteration:
-//   q = A p (CSR rows, each summed in increasing column order as the
-//       oracle's ordered SpMV), sigma = p.q                 -> barrier
+// registers, and r is mirrored in global memory (L2) with the direction
+// vectors, because the SpMV reads them at arbitrary columns.  An iteration:
+//   p = z + beta p_prev, formed at every gathered column by the reader
+//       exactly as by the row's owner (no barrier between the direction
+//       update and the SpMV); q = A p (CSR rows, each summed in increasing
+//       column order as the oracle's ordered SpMV), sigma = p.q -> barrier
 //   alpha = rho / sigma; x += alpha p; r -= alpha q; z = M^{-1} r;
 //   rho' = r.z, ||r||^2                                     -> barrier
-//   criteria; beta = rho' / rho; p = z + beta p              -> barrier
+//   criteria; beta = rho' / rho
 // A reduction: each CTA's sum (fixed butterflies) is stored in its slot, the
 // barrier, then every CTA adds all the slots in one fixed order -- all CTAs
 // hold bit-identical totals and take identical stop decisions, so they pass
@@ -46,7 +48,9 @@ struct GridArgs {
   const double* val;
   const double* b;
   double* x;
-  double* p;
+  double* p;   // x0, then the direction vectors p_k (k even)
+  double* p2;  // the direction vectors p_k (k odd)
+  double* r;   // the residual, mirrored for the gathers of the SpMV
   const double* dinv;
   SolverState* st;
   double* part;        // [4 slots][grid][2] CTA partial sums
@@ -178,7 +182,8 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
     d[u] = (PK == PREC_SCALAR && own[u]) ? __ldg(a.dinv + i) : 1.0;
     if (own[u]) a.p[i] = x[u];
   }
-  auto row_apply = [&](int i) {
+  // sum_k val_k v(col_k) in increasing k, v read through `value`
+  auto row_apply = [&](int i, auto value) {
     double s = 0.0;
     const int k1 = __ldg(a.rowptr + i + 1);
     int k = __ldg(a.rowptr + i);
@@ -191,11 +196,11 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
         v[u] = __ldg(a.val + k + u);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pv[u] = __ldcg(a.p + c[u]);
+      for (int u = 0; u < 4; ++u) pv[u] = value(c[u]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
     }
-    for (; k < k1; ++k) s = fma(__ldg(a.val + k), __ldcg(a.p + __ldg(a.col + k)), s);
+    for (; k < k1; ++k) s = fma(__ldg(a.val + k), value(__ldg(a.col + k)), s);
     return s;
   };
   auto criteria = [&](double rn, double tol, long long k) {
@@ -207,15 +212,17 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
   double rnorm0 = 0.0, bnorm = 0.0, ref = 1.0, tol = 0.0, rnorm = 0.0, rho = 0.0, alpha = 1.0, beta = 0.0;
   long long iter = 0, spmvs = 1;
   int stop = GK_STOP_NONE;
-  bool ok = grid_barrier(a, gen, &s_ok);  // p = x0 everywhere
+  bool ok = grid_barrier(a, gen, &s_ok);  // x0 everywhere (in the first p buffer)
   if (ok) {
     double v[2] = {0.0, 0.0};
+    auto x0_at = [&](int c) { return __ldcg(a.p + c); };
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (!own[u]) continue;
       const int i = row0 + t + u * kGrThreads;
       const double bi = a.b[i];
-      r[u] = bi - row_apply(i);
+      r[u] = bi - row_apply(i, x0_at);
+      a.r[i] = r[u];
       v[0] = fma(r[u], r[u], v[0]);
       v[1] = fma(bi, bi, v[1]);
     }
@@ -233,14 +240,27 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
     for (int u = 0; u < RPT; ++u) {
       if (!own[u]) continue;
       const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
-      a.p[row0 + t + u * kGrThreads] = z;
       v[0] = fma(r[u], z, v[0]);
     }
     ok = grid_total<1>(a, 1, v, wsum, tot, gen, &s_ok);
     rho = tot[0];
     stop = criteria(rnorm, tol, 0);
   }
-  while (ok && stop == GK_STOP_NONE) {
+  // Iteration k reads p_{k-1} from buffer (k+1) % 2 and r_k from a.r (both
+  // complete since the previous barrier), forms p_k = z_k + beta p_{k-1} at
+  // every gathered column exactly as its owner does, and the owner stores
+  // p_k in buffer k % 2, which nobody reads before the next iteration.
+  // Two barriers per iteration.
+  double* pbuf[2] = {a.p, a.p2};
+  for (long long k = 0; ok && stop == GK_STOP_NONE; ++k) {
+    const double* pold = pbuf[(k + 1) & 1];
+    double* pnew = pbuf[k & 1];
+    const bool first = k == 0;
+    auto p_at = [&](int c) {
+      const double rc = __ldcg(a.r + c);
+      const double z = PK == PREC_SCALAR ? __ldg(a.dinv + c) * rc : rc;
+      return first ? z : fma(beta, __ldcg(pold + c), z);
+    };
     double q[RPT], pl[RPT];
     double v[1] = {0.0};
 #pragma unroll
@@ -249,8 +269,10 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
       pl[u] = 0.0;
       if (!own[u]) continue;
       const int i = row0 + t + u * kGrThreads;
-      q[u] = row_apply(i);
-      pl[u] = __ldcg(a.p + i);
+      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
+      pl[u] = first ? z : fma(beta, __ldcg(pold + i), z);
+      pnew[i] = pl[u];
+      q[u] = row_apply(i, p_at);
       v[0] = fma(pl[u], q[u], v[0]);
     }
     if (!(ok = grid_total<1>(a, 2, v, wsum, tot, gen, &s_ok))) break;
@@ -264,8 +286,10 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (!own[u]) continue;
+      const int i = row0 + t + u * kGrThreads;
       x[u] = fma(alpha, pl[u], x[u]);
       r[u] = fma(-alpha, q[u], r[u]);
+      a.r[i] = r[u];
       const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
       w[0] = fma(r[u], z, w[0]);
       w[1] = fma(r[u], r[u], w[1]);
@@ -276,14 +300,6 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
     stop = criteria(rnorm, tol, iter);
     beta = tot[0] / rho;
     rho = tot[0];
-    if (stop != GK_STOP_NONE) break;
-#pragma unroll
-    for (int u = 0; u < RPT; ++u) {
-      if (!own[u]) continue;
-      const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
-      a.p[row0 + t + u * kGrThreads] = fma(beta, pl[u], z);
-    }
-    ok = grid_barrier(a, gen, &s_ok);  // the new p everywhere before the next SpMV
   }
 #pragma unroll
   for (int u = 0; u < RPT; ++u)
@@ -363,6 +379,8 @@ int grid_cg_solve(Solver* S, cudaStream_t s) {
   a.b = S->b;
   a.x = S->x;
   a.p = S->p;
+  a.p2 = S->q;
+  a.r = S->r;
   a.dinv = S->P ? S->P->dinv : nullptr;
   a.st = S->st;
   a.part = S->gr_part;

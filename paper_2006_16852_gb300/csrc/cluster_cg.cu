@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "gk_device.cuh"
 #include "gk_internal.h"
@@ -52,7 +53,8 @@ struct ClusterArgs {
   const double* dinv;
   SolverState* st;
   int n;
-  int lg;  // rows per CTA = 2^lg
+  int lg;         // rows per CTA = 2^lg
+  int stage_nnz;  // STAGE: room for this many entries of the CTA's rows in shared memory
 };
 
 // Partial sums published by each CTA (one slot per phase, so that a slot is
@@ -115,9 +117,12 @@ __device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)
   __syncthreads();
 }
 
-template <int PK, int RPT>
+// STAGE: the CTA's rows of the matrix (row pointers, columns, values) are
+// copied to shared memory once, so that an SpMV row costs one gather round
+// trip instead of three dependent L2 round trips.
+template <int PK, int RPT, bool STAGE>
 __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
-  extern __shared__ double p_loc[];  // this CTA's slice of p (2^lg values)
+  extern __shared__ double p_loc[];  // this CTA's slice of p (2^lg values), then the staged rows
   __shared__ double* p_of[kClCtas];  // every CTA's slice, as seen from here
   __shared__ ClSlots slots;
   __shared__ double wsum[kClThreads / 32][2];
@@ -133,6 +138,21 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   const double factor = st->factor;
   const long long max_iters = st->max_iters;
   const int rel_to_b = st->rel_to_b;
+  // staged rows: values (stage_nnz doubles), row pointers relative to the
+  // CTA's first entry (L + 1 ints), columns (stage_nnz ints)
+  double* s_val = p_loc + L;
+  int32_t* s_rp = reinterpret_cast<int32_t*>(s_val + a.stage_nnz);
+  int32_t* s_col = s_rp + L + 1;
+  const int rows_here = max(0, min(L, a.n - row0));
+  const int e0 = STAGE ? __ldg(a.rowptr + min(row0, a.n)) : 0;
+  if (STAGE) {
+    for (int l = t; l <= L; l += kClThreads) s_rp[l] = __ldg(a.rowptr + min(row0, a.n) + min(l, rows_here)) - e0;
+    const int ne = __ldg(a.rowptr + min(row0, a.n) + rows_here) - e0;
+    for (int k = t; k < ne; k += kClThreads) {
+      s_col[k] = __ldg(a.col + e0 + k);
+      s_val[k] = __ldg(a.val + e0 + k);
+    }
+  }
 
   double x[RPT], r[RPT], d[RPT];
   bool own[RPT];
@@ -145,7 +165,7 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
     d[u] = (PK == PREC_SCALAR && own[u]) ? a.dinv[i] : 1.0;
     if (l < L) p_loc[l] = x[u];
   }
-  cl.sync();  // p = x0 everywhere
+  cl.sync();  // p = x0 everywhere (and the staged rows complete)
 
   // q_i = sum_k val_k p[col_k] in increasing k (p read across the cluster;
   // the CTA's own slice directly); entries in groups of 4 so that their
@@ -156,22 +176,23 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   };
   auto row_apply = [&](int i) {
     double s = 0.0;
-    const int k1 = __ldg(a.rowptr + i + 1);
-    int k = __ldg(a.rowptr + i);
+    const int l = i - row0;
+    int k = STAGE ? s_rp[l] : __ldg(a.rowptr + i);
+    const int k1 = STAGE ? s_rp[l + 1] : __ldg(a.rowptr + i + 1);
     for (; k + 4 <= k1; k += 4) {
       int c[4];
       double v[4], pv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        c[u] = __ldg(a.col + k + u);
-        v[u] = __ldg(a.val + k + u);
+        c[u] = STAGE ? s_col[k + u] : __ldg(a.col + k + u);
+        v[u] = STAGE ? s_val[k + u] : __ldg(a.val + k + u);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) pv[u] = gather(c[u]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
     }
-    for (; k < k1; ++k) s = fma(__ldg(a.val + k), gather(__ldg(a.col + k)), s);
+    for (; k < k1; ++k) s = fma(STAGE ? s_val[k] : __ldg(a.val + k), gather(STAGE ? s_col[k] : __ldg(a.col + k)), s);
     return s;
   };
 
@@ -292,23 +313,26 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
 
 using ClKernel = void (*)(ClusterArgs);
 
-template <int PK>
+template <int PK, bool STAGE>
 ClKernel pick_rpt(int rpt) {
   switch (rpt) {
-    case 1: return cg_cluster_kernel<PK, 1>;
-    case 2: return cg_cluster_kernel<PK, 2>;
-    case 4: return cg_cluster_kernel<PK, 4>;
-    default: return cg_cluster_kernel<PK, 8>;
+    case 1: return cg_cluster_kernel<PK, 1, STAGE>;
+    case 2: return cg_cluster_kernel<PK, 2, STAGE>;
+    case 4: return cg_cluster_kernel<PK, 4, STAGE>;
+    default: return cg_cluster_kernel<PK, 8, STAGE>;
   }
 }
 
-ClKernel pick(int pk, int rpt) { return pk == PREC_SCALAR ? pick_rpt<PREC_SCALAR>(rpt) : pick_rpt<PREC_NONE>(rpt); }
+ClKernel pick(int pk, int rpt, bool stage) {
+  if (pk == PREC_SCALAR) return stage ? pick_rpt<PREC_SCALAR, true>(rpt) : pick_rpt<PREC_SCALAR, false>(rpt);
+  return stage ? pick_rpt<PREC_NONE, true>(rpt) : pick_rpt<PREC_NONE, false>(rpt);
+}
 
-cudaLaunchConfig_t launch_config(int lg, cudaStream_t s, cudaLaunchAttribute* attr) {
+cudaLaunchConfig_t launch_config(size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClCtas, 1, 1);
   cfg.blockDim = dim3(kClThreads, 1, 1);
-  cfg.dynamicSmemBytes = sizeof(double) << lg;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kClCtas;
@@ -318,6 +342,9 @@ cudaLaunchConfig_t launch_config(int lg, cudaStream_t s, cudaLaunchAttribute* at
   cfg.numAttrs = 1;
   return cfg;
 }
+
+// Shared memory a CTA's rows take when staged, at most this much.
+constexpr size_t kClStageMax = 160 * 1024;
 
 }  // namespace
 
@@ -329,13 +356,27 @@ int cluster_cg_plan(Solver* S) {
   int lg = 0;
   while ((static_cast<int64_t>(kClCtas) << lg) < n) ++lg;
   const int rpt = std::max(1, (1 << lg) / kClThreads);
-  ClKernel k = pick(S->pk, rpt);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+  // the most entries any CTA's rows hold: stage them if they fit
+  std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
+  GK_TRY_CUDA(cudaMemcpy(rp.data(), S->A->rowptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost));
+  int64_t most = 0;
+  for (int c = 0; c < kClCtas; ++c) {
+    const int64_t lo = std::min<int64_t>(static_cast<int64_t>(c) << lg, n);
+    const int64_t hi = std::min<int64_t>(static_cast<int64_t>(c + 1) << lg, n);
+    most = std::max<int64_t>(most, rp[hi] - rp[lo]);
+  }
+  const size_t L = size_t(1) << lg;
+  const size_t staged = 12 * static_cast<size_t>(most) + 4 * (L + 1);
+  const bool stage = staged <= kClStageMax;
+  const size_t smem = 8 * L + (stage ? staged : 0);
+  ClKernel k = pick(S->pk, rpt, stage);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      set_smem(k, smem) != GK_OK) {
     cudaGetLastError();
     return GK_OK;
   }
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = launch_config(lg, nullptr, attr);
+  cudaLaunchConfig_t cfg = launch_config(smem, nullptr, attr);
   int clusters = 0;
   if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters < 1) {
     cudaGetLastError();
@@ -343,6 +384,9 @@ int cluster_cg_plan(Solver* S) {
   }
   S->cl_lg = lg;
   S->cl_rpt = rpt;
+  S->cl_stage = stage;
+  S->cl_nnz = stage ? static_cast<int>(most) : 0;
+  S->cl_smem = smem;
   return GK_OK;
 }
 
@@ -357,9 +401,10 @@ int cluster_cg_solve(Solver* S, cudaStream_t s) {
   a.st = S->st;
   a.n = static_cast<int>(S->n);
   a.lg = S->cl_lg;
+  a.stage_nnz = S->cl_nnz;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = launch_config(S->cl_lg, s, attr);
-  GK_TRY_CUDA(cudaLaunchKernelEx(&cfg, pick(S->pk, S->cl_rpt), a));
+  cudaLaunchConfig_t cfg = launch_config(S->cl_smem, s, attr);
+  GK_TRY_CUDA(cudaLaunchKernelEx(&cfg, pick(S->pk, S->cl_rpt, S->cl_stage), a));
   return GK_OK;
 }
 

@@ -305,6 +305,9 @@ struct Solver {
   GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
   int cl_lg = -1;           // GK_CG small-system form: rows per CTA = 2^cl_lg (-1: not available)
   int cl_rpt = 1;           // ... rows per thread
+  bool cl_stage = false;    // ... the CTA's rows of the matrix staged in shared memory
+  int cl_nnz = 0;           // ... room for that many entries
+  size_t cl_smem = 0;       // ... dynamic shared memory per CTA
   int gr_grid = 0;          // GK_CG mid-size form: CTAs of the cooperative launch (0: not available)
   int gr_rpt = 1, gr_rows = 0;
   double* gr_part = nullptr;        // its per-CTA partial sums

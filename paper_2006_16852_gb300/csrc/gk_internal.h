@@ -310,6 +310,9 @@ struct Solver {
   size_t cl_smem = 0;       // ... dynamic shared memory per CTA
   int gr_grid = 0;          // GK_CG mid-size form: CTAs of the cooperative launch (0: not available)
   int gr_rpt = 1, gr_rows = 0;
+  bool gr_stage = false;            // its CTAs' rows of the matrix staged in shared memory
+  int gr_nnz = 0;
+  size_t gr_smem = 0;
   double* gr_part = nullptr;        // its per-CTA partial sums
   unsigned int* gr_sync = nullptr;  // its barrier words
 };

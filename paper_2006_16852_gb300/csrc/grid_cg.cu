@@ -57,6 +57,7 @@ struct GridArgs {
   unsigned int* sync;  // [0] arrivals, [1] generation, [2] abort
   int n;
   int rows_per_cta;
+  int stage_nnz;  // STAGE: room for this many entries of the CTA's rows in shared memory
 };
 
 // Grid barrier (thread 0 of every CTA arrives; the last arrival resets the
@@ -158,13 +159,29 @@ __device__ __forceinline__ bool grid_total(const GridArgs& a, int slot, double (
   return true;
 }
 
-template <int PK, int RPT>
+// STAGE: the CTA's rows of the matrix are copied to shared memory once (one
+// gather round trip per row instead of three dependent ones).
+template <int PK, int RPT, bool STAGE>
 __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
+  extern __shared__ double s_val[];  // STAGE: values, then row pointers and columns
   __shared__ double wsum[kGrThreads / 32][2];
   __shared__ double tot[2];
   __shared__ int s_ok;
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * a.rows_per_cta;
+  const int R = a.rows_per_cta;
+  int32_t* s_rp = reinterpret_cast<int32_t*>(s_val + a.stage_nnz);
+  int32_t* s_col = s_rp + R + 1;
+  if (STAGE) {
+    const int first = min(row0, a.n), rows_here = max(0, min(R, a.n - row0));
+    const int e0 = __ldg(a.rowptr + first);
+    for (int l = t; l <= R; l += kGrThreads) s_rp[l] = __ldg(a.rowptr + first + min(l, rows_here)) - e0;
+    const int ne = __ldg(a.rowptr + first + rows_here) - e0;
+    for (int k = t; k < ne; k += kGrThreads) {
+      s_col[k] = __ldg(a.col + e0 + k);
+      s_val[k] = __ldg(a.val + e0 + k);
+    }
+  }
   SolverState* st = a.st;
   const double factor = st->factor;
   const long long max_iters = st->max_iters;
@@ -185,22 +202,23 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
   // sum_k val_k v(col_k) in increasing k, v read through `value`
   auto row_apply = [&](int i, auto value) {
     double s = 0.0;
-    const int k1 = __ldg(a.rowptr + i + 1);
-    int k = __ldg(a.rowptr + i);
+    const int l = i - row0;
+    int k = STAGE ? s_rp[l] : __ldg(a.rowptr + i);
+    const int k1 = STAGE ? s_rp[l + 1] : __ldg(a.rowptr + i + 1);
     for (; k + 4 <= k1; k += 4) {
       int c[4];
       double v[4], pv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        c[u] = __ldg(a.col + k + u);
-        v[u] = __ldg(a.val + k + u);
+        c[u] = STAGE ? s_col[k + u] : __ldg(a.col + k + u);
+        v[u] = STAGE ? s_val[k + u] : __ldg(a.val + k + u);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) pv[u] = value(c[u]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
     }
-    for (; k < k1; ++k) s = fma(__ldg(a.val + k), value(__ldg(a.col + k)), s);
+    for (; k < k1; ++k) s = fma(STAGE ? s_val[k] : __ldg(a.val + k), value(STAGE ? s_col[k] : __ldg(a.col + k)), s);
     return s;
   };
   auto criteria = [&](double rn, double tol, long long k) {
@@ -322,17 +340,23 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
 
 using GrKernel = void (*)(GridArgs);
 
-template <int PK>
+template <int PK, bool STAGE>
 GrKernel pick_rpt(int rpt) {
   switch (rpt) {
-    case 1: return cg_grid_kernel<PK, 1>;
-    case 2: return cg_grid_kernel<PK, 2>;
-    case 4: return cg_grid_kernel<PK, 4>;
-    default: return cg_grid_kernel<PK, 8>;
+    case 1: return cg_grid_kernel<PK, 1, STAGE>;
+    case 2: return cg_grid_kernel<PK, 2, STAGE>;
+    case 4: return cg_grid_kernel<PK, 4, STAGE>;
+    default: return cg_grid_kernel<PK, 8, STAGE>;
   }
 }
 
-GrKernel pick(int pk, int rpt) { return pk == PREC_SCALAR ? pick_rpt<PREC_SCALAR>(rpt) : pick_rpt<PREC_NONE>(rpt); }
+GrKernel pick(int pk, int rpt, bool stage) {
+  if (pk == PREC_SCALAR) return stage ? pick_rpt<PREC_SCALAR, true>(rpt) : pick_rpt<PREC_SCALAR, false>(rpt);
+  return stage ? pick_rpt<PREC_NONE, true>(rpt) : pick_rpt<PREC_NONE, false>(rpt);
+}
+
+// Shared memory a CTA's rows take when staged, at most this much.
+constexpr size_t kGrStageMax = 160 * 1024;
 
 }  // namespace
 
@@ -357,9 +381,18 @@ int grid_cg_plan(Solver* S) {
   int rpt = 1;
   while (static_cast<int64_t>(rpt) * kGrThreads < per_cta) rpt *= 2;
   if (rpt > kGrMaxRpt) return GK_OK;
-  GrKernel k = pick(S->pk, rpt);
+  int64_t most = 0;
+  for (int c = 0; c < G; ++c) {
+    const int64_t lo = std::min<int64_t>(c * per_cta, n), hi = std::min<int64_t>((c + 1) * per_cta, n);
+    most = std::max<int64_t>(most, rp[hi] - rp[lo]);
+  }
+  const size_t smem = 12 * static_cast<size_t>(most) + 4 * static_cast<size_t>(per_cta + 1);
+  const bool stage = smem <= kGrStageMax;
+  GrKernel k = pick(S->pk, rpt, stage);
+  if (stage && set_smem(k, smem) != GK_OK) return GK_OK;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGrThreads, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGrThreads, stage ? smem : 0) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     return GK_OK;
   }
@@ -368,6 +401,9 @@ int grid_cg_plan(Solver* S) {
   S->gr_grid = G;
   S->gr_rpt = rpt;
   S->gr_rows = static_cast<int>(per_cta);
+  S->gr_stage = stage;
+  S->gr_nnz = stage ? static_cast<int>(most) : 0;
+  S->gr_smem = stage ? smem : 0;
   return GK_OK;
 }
 
@@ -387,10 +423,11 @@ int grid_cg_solve(Solver* S, cudaStream_t s) {
   a.sync = S->gr_sync;
   a.n = static_cast<int>(S->n);
   a.rows_per_cta = S->gr_rows;
+  a.stage_nnz = S->gr_nnz;
   GK_TRY_CUDA(cudaMemsetAsync(S->gr_sync, 0, 4 * sizeof(unsigned int), s));
   void* args[] = {&a};
-  GK_TRY_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(pick(S->pk, S->gr_rpt)), dim3(S->gr_grid),
-                                          dim3(kGrThreads), args, 0, s));
+  GK_TRY_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(pick(S->pk, S->gr_rpt, S->gr_stage)),
+                                          dim3(S->gr_grid), dim3(kGrThreads), args, S->gr_smem, s));
   return GK_OK;
 }
 

@@ -621,6 +621,12 @@ def run_learned(dev, problems=8):
     idx = range(1_000_000, 1_000_000 + problems)
     res = LN.evaluate(net, idx, scale)
     summ = LN.summarize(res)
+    # the same problems to looser targets, where the start matters more
+    loose = {}
+    for tol in (1e-4, 1e-6):
+        ls = LN.summarize(LN.evaluate(net, idx, scale, tol=tol))
+        loose[f"{tol:g}"] = {k: ls[k] for k in ("iters_zero", "iters_warm", "iters_ratio", "ms_zero", "ms_warm",
+                                               "time_ratio")}
     # plain FP64 CG (no preconditioner, zero start) on the same problems
     import workloads as W
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -672,6 +678,7 @@ def run_learned(dev, problems=8):
         "training": {k: meta[k] for k in ("samples", "epochs", "batch", "lr", "loss", "data_seconds",
                                           "train_seconds", "loss_history") if k in meta},
         "eval": summ,
+        "eval_looser_targets": loose,
         "time_to_tol_ms": {"plain_fp64_cg": round(plain_ms, 3), "plain_iters": plain_it,
                            "jacobi_cg_zero_start": summ["ms_zero"], "jacobi_cg_learned_start": summ["ms_warm"],
                            "chosen_form": "jacobi_cg_" + ("learned" if best == "warm" else "zero") + "_start",

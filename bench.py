@@ -59,6 +59,10 @@ WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point sten
 # kernel's source (spmv_source_hash) is the one it was measured on.
 NCU_TRAFFIC = {"8f0479bcad827b53": {"copy": 711961600, "dot": 728345856}}
 
+# nominal GB300 rates (context beside the measured peaks)
+NOMINAL_HBM_GBS = 7900.0
+NOMINAL_FP64_TFLOPS = 1.25
+
 # back-to-back applies per format and matrix in one step (the per-launch time
 # of the roofline is their average)
 SPMV_REPS = 3
@@ -816,6 +820,50 @@ def run_latency(dev):
             "paper_host_overhead_us_per_iter": [1.0, 1.5], "solves": out}
 
 
+# ---------------------------------------------------------------------------
+# stream probes (reported beside the step): the library's own reduction
+# kernel against a plain device copy on the same device
+# ---------------------------------------------------------------------------
+
+def run_stream(dev, n=1 << 27):
+    """gk_dot over two vectors of n doubles (1 GiB each: larger than L2),
+    against torch's device copy of one of them (read + write bytes); the
+    best of 10 after 3 warm-up runs, CUDA events."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    x = torch.rand(n, dtype=torch.float64, device=dev)
+    y = torch.rand(n, dtype=torch.float64, device=dev)
+    z = torch.empty_like(x)
+    r = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def best(fn):
+        for _ in range(3):
+            fn()
+        t = None
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            t = ms if t is None else min(t, ms)
+        return t
+
+    dot_ms = best(lambda: gk.dot(x, y, r))
+    copy_ms = best(lambda: z.copy_(x))
+    hbm = peaks().get("hbm_gbs")
+    out = {"vector_doubles": n,
+           "gk_dot": {"ms": round(dot_ms, 4), "GB/s": round(16.0 * n / (dot_ms * 1e-3) / 1e9, 1)},
+           "torch_copy": {"ms": round(copy_ms, 4), "GB/s": round(16.0 * n / (copy_ms * 1e-3) / 1e9, 1)}}
+    if hbm:
+        out["gk_dot"]["frac_of_measured_hbm"] = round(out["gk_dot"]["GB/s"] / hbm, 4)
+    del x, y, z
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
@@ -889,6 +937,14 @@ def run_gpu(args):
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback",
                 "frac": round(achieved / (hbm if hbm else 6800.0), 4),
                 "traffic": tr, "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
+    # the same against the nominal HBM rate, and the FP64 co-bound: one FMA
+    # per stored entry at the nominal FP64 rate of a GB300
+    roofline["frac_of_nominal_hbm"] = round(achieved / NOMINAL_HBM_GBS, 4)
+    hbm_floor = dom_bytes / ((hbm or 6800.0) * 1e9) * 1e3
+    fp64_floor = 2.0 * step.nnza / (NOMINAL_FP64_TFLOPS * 1e12) * 1e3
+    roofline["floors_ms"] = {"hbm": round(hbm_floor, 4), "fp64_fma": round(fp64_floor, 4),
+                             "effective": round(max(hbm_floor, fp64_floor), 4)}
+    roofline["frac_of_effective_floor"] = round(max(hbm_floor, fp64_floor) / dom_ms, 4)
 
     def summary(name):
         reps = SPMV_REPS if name.startswith("spmv") else 1
@@ -977,6 +1033,8 @@ def run_gpu(args):
         out["krylov"] = run_krylov(dev)
     if not args.no_latency:
         out["latency"] = run_latency(dev)
+    if not args.no_stream:
+        out["stream"] = run_stream(dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -1170,6 +1228,7 @@ def main():
     ap.add_argument("--no-krylov", action="store_true", help="skip the FCG / CGS / GMRES section")
     ap.add_argument("--krylov-only", action="store_true", help="only the FCG / CGS / GMRES section")
     ap.add_argument("--no-latency", action="store_true", help="skip the per-iteration latency section")
+    ap.add_argument("--no-stream", action="store_true", help="skip the stream probes")
     ap.add_argument("--infer-only", type=int, default=0, metavar="B",
                     help="only BF16 inferences of the committed network on a batch of B (profiling)")
     ap.add_argument("--latency-only", action="store_true", help="only the per-iteration latency section")

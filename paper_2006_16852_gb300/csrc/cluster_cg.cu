@@ -57,6 +57,13 @@ struct ClusterArgs {
   int stage_nnz;  // STAGE: room for this many entries of the CTA's rows in shared memory
 };
 
+// The iteration's scalars, derived by thread 0 and read by the block.
+struct ClScalars {
+  double rho, alpha, beta, rnorm, rnorm0, bnorm, ref, tol;
+  long long iter, spmvs;
+  int stop;
+};
+
 // Partial sums published by each CTA (one slot per phase, so that a slot is
 // never rewritten before every CTA has read it: between the read of a slot
 // and its next write lies a barrier that the reader passes only after it).
@@ -67,14 +74,18 @@ struct ClSlots {
   double iter[2];   // r.z, r.r
 };
 
-// Sum of v over the cluster, broadcast to the block in tot: a butterfly in
-// every warp (all warps at once), the 8 warp sums in a 3-level butterfly in
-// warp 0, the CTA's sum published in `slot`, the cluster barrier, then the
-// 16 CTA sums in a 4-level butterfly over lanes 0..15 -- 12 dependent FP64
-// adds in all, which on this GPU's slow FP64 pipe is what a reduction costs.
-template <int K>
+// Sum of v over the cluster: a butterfly in every warp (all warps at once),
+// the 8 warp sums in a 3-level butterfly in warp 0, the CTA's sum published
+// in `slot`, the cluster barrier, then the 16 CTA sums in a 4-level
+// butterfly over lanes 0..15 -- 12 dependent FP64 adds in all, which on this
+// GPU's slow FP64 pipe is what a reduction costs.  Thread 0 alone then runs
+// post(totals), which derives the iteration's scalars into shared memory
+// (divisions and square roots cost dozens of FP64 instructions: done by
+// every warp they took half the FP64 pipe's time); the closing barrier
+// publishes them to the block.
+template <int K, typename Post>
 __device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)[K], double (*wsum)[K],
-                                              double* slot, double* tot) {
+                                              double* slot, Post post) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   warp_sum<K, double>(v);
   if (lane == 0) {
@@ -109,10 +120,7 @@ __device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)
 #pragma unroll
       for (int k = 0; k < K; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) tot[k] = s[k];
-    }
+    if (lane == 0) post(s);
   }
   __syncthreads();
 }
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   __shared__ double* p_of[kClCtas];  // every CTA's slice, as seen from here
   __shared__ ClSlots slots;
   __shared__ double wsum[kClThreads / 32][2];
-  __shared__ double tot[2];
+  __shared__ ClScalars sc;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
   const int t = threadIdx.x;
@@ -208,16 +216,28 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
       v[0] = fma(r[u], r[u], v[0]);
       v[1] = fma(bi, bi, v[1]);
     }
-    cluster_total<2>(cl, v, wsum, slots.setup, tot);
+    cluster_total<2>(cl, v, wsum, slots.setup, [&](const double* tt) {
+      sc.rnorm0 = sqrt(tt[0]);
+      sc.bnorm = sqrt(tt[1]);
+      double ref = rel_to_b ? sc.bnorm : sc.rnorm0;
+      if (ref == 0.0) ref = 1.0;
+      sc.ref = ref;
+      sc.tol = factor * ref;
+      sc.rnorm = sc.rnorm0;
+      sc.iter = 0;
+      sc.spmvs = 1;
+      sc.alpha = 1.0;
+      sc.beta = 0.0;
+    });
   }
-  const double rnorm0 = sqrt(tot[0]), bnorm = sqrt(tot[1]);
-  double ref = rel_to_b ? bnorm : rnorm0;
-  if (ref == 0.0) ref = 1.0;
-  const double tol = factor * ref;
-  double rnorm = rnorm0;
-  long long iter = 0, spmvs = 1;
-  int stop;
-  double rho, alpha = 1.0, beta = 0.0;
+  // the criteria (thread 0), in the order of check_stop; no Time criterion
+  // here: this form is chosen only without one
+  auto criteria = [&](double rn, long long k) {
+    if (!isfinite(rn)) return GK_STOP_NAN;
+    if (rn <= sc.tol) return GK_STOP_CONVERGED;
+    if (k >= max_iters) return GK_STOP_MAX_ITERS;
+    return GK_STOP_NONE;
+  };
   // z0 = M^{-1} r0, p0 = z0, rho = r0.z0
   {
     double v[1] = {0.0};
@@ -229,19 +249,12 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
       p_loc[l] = z;
       v[0] = fma(r[u], z, v[0]);
     }
-    cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.start, tot);
-    rho = tot[0];
+    cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.start, [&](const double* tt) {
+      sc.rho = tt[0];
+      sc.stop = criteria(sc.rnorm, 0);
+    });
   }
-  // the criteria at k = 0, in the order of check_stop (no Time criterion
-  // here: this form is chosen only without one)
-  auto criteria = [&](double rn, long long k) {
-    if (!isfinite(rn)) return GK_STOP_NAN;
-    if (rn <= tol) return GK_STOP_CONVERGED;
-    if (k >= max_iters) return GK_STOP_MAX_ITERS;
-    return GK_STOP_NONE;
-  };
-  stop = criteria(rnorm, 0);
-  while (stop == GK_STOP_NONE) {
+  while (sc.stop == GK_STOP_NONE) {
     double q[RPT];
     {
       double v[1] = {0.0};
@@ -253,14 +266,16 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
         q[u] = row_apply(row0 + l);
         v[0] = fma(p_loc[l], q[u], v[0]);
       }
-      cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.sigma, tot);
+      cluster_total<1>(cl, v, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.sigma, [&](const double* tt) {
+        sc.spmvs += 1;
+        const double sigma = tt[0];
+        if (!isfinite(sigma)) sc.stop = GK_STOP_NAN;
+        else if (sigma <= 0.0) sc.stop = GK_STOP_BREAKDOWN;
+        else sc.alpha = sc.rho / sigma;
+      });
     }
-    spmvs += 1;
-    const double sigma = tot[0];
-    if (!isfinite(sigma)) stop = GK_STOP_NAN;
-    else if (sigma <= 0.0) stop = GK_STOP_BREAKDOWN;
-    if (stop != GK_STOP_NONE) break;
-    alpha = rho / sigma;
+    if (sc.stop != GK_STOP_NONE) break;
+    const double alpha = sc.alpha;
     {
       double v[2] = {0.0, 0.0};
 #pragma unroll
@@ -273,14 +288,16 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
         v[0] = fma(r[u], z, v[0]);
         v[1] = fma(r[u], r[u], v[1]);
       }
-      cluster_total<2>(cl, v, wsum, slots.iter, tot);
+      cluster_total<2>(cl, v, wsum, slots.iter, [&](const double* tt) {
+        sc.iter += 1;
+        sc.rnorm = sqrt(tt[1]);
+        sc.stop = criteria(sc.rnorm, sc.iter);
+        sc.beta = tt[0] / sc.rho;
+        sc.rho = tt[0];
+      });
     }
-    iter += 1;
-    rnorm = sqrt(tot[1]);
-    stop = criteria(rnorm, iter);
-    beta = tot[0] / rho;
-    rho = tot[0];
-    if (stop != GK_STOP_NONE) break;
+    if (sc.stop != GK_STOP_NONE) break;
+    const double beta = sc.beta;
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (!own[u]) continue;
@@ -294,18 +311,18 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   for (int u = 0; u < RPT; ++u)
     if (own[u]) a.x[row0 + t + u * kClThreads] = x[u];
   if (rank == 0 && t == 0) {
-    st->rnorm = rnorm;
-    st->rnorm0 = rnorm0;
-    st->bnorm = bnorm;
-    st->ref = ref;
-    st->tol = tol;
-    st->rho = rho;
-    st->alpha = alpha;
-    st->beta = beta;
-    st->iter = iter;
-    st->iter_guard = iter;
-    st->spmvs = spmvs;
-    st->stop = stop;
+    st->rnorm = sc.rnorm;
+    st->rnorm0 = sc.rnorm0;
+    st->bnorm = sc.bnorm;
+    st->ref = sc.ref;
+    st->tol = sc.tol;
+    st->rho = sc.rho;
+    st->alpha = sc.alpha;
+    st->beta = sc.beta;
+    st->iter = sc.iter;
+    st->iter_guard = sc.iter;
+    st->spmvs = sc.spmvs;
+    st->stop = sc.stop;
   }
   // no CTA may leave while others can still read its shared memory
   cl.sync();

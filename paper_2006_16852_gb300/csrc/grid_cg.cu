@@ -99,12 +99,22 @@ __device__ __forceinline__ bool grid_barrier(const GridArgs& a, unsigned int& ge
   return *s_ok != 0;
 }
 
-// Sum of v over the grid into tot (every thread): CTA sum by butterflies,
-// stored in the slot, the barrier, then all CTA sums added by every CTA in
-// the same order (thread j takes CTAs j, j + 256, ...; then butterflies).
-template <int K>
+// The iteration's scalars, derived by thread 0 of each CTA.
+struct GrScalars {
+  double rho, alpha, beta, rnorm, rnorm0, bnorm, ref, tol;
+  long long iter, spmvs;
+  int stop;
+};
+
+// Sum of v over the grid: CTA sum by butterflies, stored in the slot, the
+// barrier, then all CTA sums added by every CTA in the same order (thread j
+// takes CTAs j, j + 256, ...; then butterflies); thread 0 runs post(totals),
+// deriving the iteration's scalars into shared memory once per CTA instead
+// of in every warp (FP64 divisions and square roots are long), and the
+// closing barrier publishes them.
+template <int K, typename Post>
 __device__ __forceinline__ bool grid_total(const GridArgs& a, int slot, double (&v)[K], double (*wsum)[2],
-                                           double* tot, unsigned int& gen, int* s_ok) {
+                                           Post post, unsigned int& gen, int* s_ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   warp_sum<K, double>(v);
   if (lane == 0) {
@@ -150,10 +160,7 @@ __device__ __forceinline__ bool grid_total(const GridArgs& a, int slot, double (
 #pragma unroll
       for (int k = 0; k < K; ++k) u[k] += __shfl_xor_sync(0xffffffffu, u[k], o);
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) tot[k] = u[k];
-    }
+    if (lane == 0) post(u);
   }
   __syncthreads();
   return true;
@@ -165,7 +172,7 @@ template <int PK, int RPT, bool STAGE>
 __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
   extern __shared__ double s_val[];  // STAGE: values, then row pointers and columns
   __shared__ double wsum[kGrThreads / 32][2];
-  __shared__ double tot[2];
+  __shared__ GrScalars sc;
   __shared__ int s_ok;
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * a.rows_per_cta;
@@ -227,9 +234,14 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
     if (k >= max_iters) return GK_STOP_MAX_ITERS;
     return GK_STOP_NONE;
   };
-  double rnorm0 = 0.0, bnorm = 0.0, ref = 1.0, tol = 0.0, rnorm = 0.0, rho = 0.0, alpha = 1.0, beta = 0.0;
-  long long iter = 0, spmvs = 1;
-  int stop = GK_STOP_NONE;
+  if (t == 0) {
+    sc.rnorm0 = sc.bnorm = sc.rnorm = sc.rho = sc.tol = 0.0;
+    sc.ref = sc.alpha = 1.0;
+    sc.beta = 0.0;
+    sc.iter = 0;
+    sc.spmvs = 1;
+    sc.stop = GK_STOP_NONE;
+  }
   bool ok = grid_barrier(a, gen, &s_ok);  // x0 everywhere (in the first p buffer)
   if (ok) {
     double v[2] = {0.0, 0.0};
@@ -244,15 +256,17 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
       v[0] = fma(r[u], r[u], v[0]);
       v[1] = fma(bi, bi, v[1]);
     }
-    ok = grid_total<2>(a, 0, v, wsum, tot, gen, &s_ok);
+    ok = grid_total<2>(a, 0, v, wsum, [&](const double* tt) {
+      sc.rnorm0 = sqrt(tt[0]);
+      sc.bnorm = sqrt(tt[1]);
+      double ref = rel_to_b ? sc.bnorm : sc.rnorm0;
+      if (ref == 0.0) ref = 1.0;
+      sc.ref = ref;
+      sc.tol = factor * ref;
+      sc.rnorm = sc.rnorm0;
+    }, gen, &s_ok);
   }
   if (ok) {
-    rnorm0 = sqrt(tot[0]);
-    bnorm = sqrt(tot[1]);
-    ref = rel_to_b ? bnorm : rnorm0;
-    if (ref == 0.0) ref = 1.0;
-    tol = factor * ref;
-    rnorm = rnorm0;
     double v[1] = {0.0};
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
@@ -260,9 +274,10 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
       const double z = PK == PREC_SCALAR ? d[u] * r[u] : r[u];
       v[0] = fma(r[u], z, v[0]);
     }
-    ok = grid_total<1>(a, 1, v, wsum, tot, gen, &s_ok);
-    rho = tot[0];
-    stop = criteria(rnorm, tol, 0);
+    ok = grid_total<1>(a, 1, v, wsum, [&](const double* tt) {
+      sc.rho = tt[0];
+      sc.stop = criteria(sc.rnorm, sc.tol, 0);
+    }, gen, &s_ok);
   }
   // Iteration k reads p_{k-1} from buffer (k+1) % 2 and r_k from a.r (both
   // complete since the previous barrier), forms p_k = z_k + beta p_{k-1} at
@@ -270,10 +285,11 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
   // p_k in buffer k % 2, which nobody reads before the next iteration.
   // Two barriers per iteration.
   double* pbuf[2] = {a.p, a.p2};
-  for (long long k = 0; ok && stop == GK_STOP_NONE; ++k) {
+  for (long long k = 0; ok && sc.stop == GK_STOP_NONE; ++k) {
     const double* pold = pbuf[(k + 1) & 1];
     double* pnew = pbuf[k & 1];
     const bool first = k == 0;
+    const double beta = sc.beta;
     auto p_at = [&](int c) {
       const double rc = __ldcg(a.r + c);
       const double z = PK == PREC_SCALAR ? __ldg(a.dinv + c) * rc : rc;
@@ -293,13 +309,16 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
       q[u] = row_apply(i, p_at);
       v[0] = fma(pl[u], q[u], v[0]);
     }
-    if (!(ok = grid_total<1>(a, 2, v, wsum, tot, gen, &s_ok))) break;
-    spmvs += 1;
-    const double sigma = tot[0];
-    if (!isfinite(sigma)) stop = GK_STOP_NAN;
-    else if (sigma <= 0.0) stop = GK_STOP_BREAKDOWN;
-    if (stop != GK_STOP_NONE) break;
-    alpha = rho / sigma;
+    if (!(ok = grid_total<1>(a, 2, v, wsum, [&](const double* tt) {
+          sc.spmvs += 1;
+          const double sigma = tt[0];
+          if (!isfinite(sigma)) sc.stop = GK_STOP_NAN;
+          else if (sigma <= 0.0) sc.stop = GK_STOP_BREAKDOWN;
+          else sc.alpha = sc.rho / sigma;
+        }, gen, &s_ok)))
+      break;
+    if (sc.stop != GK_STOP_NONE) break;
+    const double alpha = sc.alpha;
     double w[2] = {0.0, 0.0};
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
@@ -312,29 +331,31 @@ __global__ void __launch_bounds__(kGrThreads) cg_grid_kernel(GridArgs a) {
       w[0] = fma(r[u], z, w[0]);
       w[1] = fma(r[u], r[u], w[1]);
     }
-    if (!(ok = grid_total<2>(a, 3, w, wsum, tot, gen, &s_ok))) break;
-    iter += 1;
-    rnorm = sqrt(tot[1]);
-    stop = criteria(rnorm, tol, iter);
-    beta = tot[0] / rho;
-    rho = tot[0];
+    if (!(ok = grid_total<2>(a, 3, w, wsum, [&](const double* tt) {
+          sc.iter += 1;
+          sc.rnorm = sqrt(tt[1]);
+          sc.stop = criteria(sc.rnorm, sc.tol, sc.iter);
+          sc.beta = tt[0] / sc.rho;
+          sc.rho = tt[0];
+        }, gen, &s_ok)))
+      break;
   }
 #pragma unroll
   for (int u = 0; u < RPT; ++u)
     if (own[u]) a.x[row0 + t + u * kGrThreads] = x[u];
   if (blockIdx.x == 0 && t == 0) {
-    st->rnorm = rnorm;
-    st->rnorm0 = rnorm0;
-    st->bnorm = bnorm;
-    st->ref = ref;
-    st->tol = tol;
-    st->rho = rho;
-    st->alpha = alpha;
-    st->beta = beta;
-    st->iter = iter;
-    st->iter_guard = iter;
-    st->spmvs = spmvs;
-    st->stop = ok ? stop : GK_STOP_NAN;
+    st->rnorm = sc.rnorm;
+    st->rnorm0 = sc.rnorm0;
+    st->bnorm = sc.bnorm;
+    st->ref = sc.ref;
+    st->tol = sc.tol;
+    st->rho = sc.rho;
+    st->alpha = sc.alpha;
+    st->beta = sc.beta;
+    st->iter = sc.iter;
+    st->iter_guard = sc.iter;
+    st->spmvs = sc.spmvs;
+    st->stop = ok ? sc.stop : GK_STOP_NAN;
   }
 }
 

@@ -65,8 +65,10 @@ extern "C" {
 #define GK_F32 1
 
 /* Storage formats of the system matrix. */
-#define GK_CSR 0        /* CSR, rows binned by length: runs of short rows thread-per-row
-                           from shared-memory-staged tiles, long rows warp-per-row      */
+#define GK_CSR 0        /* CSR, rows binned by length: rows of up to 256 entries sorted
+                           by length into slices of 32 (a copy stored column-major,
+                           one thread per row), longer rows one warp per row, rows
+                           over 4096 entries one thread block per row                   */
 #define GK_CSR_MERGE 1  /* CSR, merge-path split of rows+nonzeros into equal tiles      */
 #define GK_ELL 2        /* ELLPACK, column-major, padded to the longest row             */
 #define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows */

@@ -29,7 +29,12 @@ around FP32 CG with Jacobi or adaptive FP16/FP32 block Jacobi; and
 problems from the trained network's x0 and from zero; and "batched": 10,000
 small variable-coefficient systems solved per system in one graph launch
 (FP64 CG / BiCGSTAB / refinement to 1e-10, FP32 CG / BiCGSTAB to 1e-6), with
-solves/s and the time against plain FP64 CG on the block-diagonal matrix.
+solves/s and the time against plain FP64 CG on the block-diagonal matrix;
+"krylov": BiCGSTAB, CGS and GMRES on a convection-diffusion matrix, CG, FCG
+and GMRES on (a), to 1e-10; "latency": CG on Poisson-2D 64^2 (and 256^2) in
+every form -- the one-launch cluster (or cooperative-grid) form, the graph,
+host-checked loops -- per iteration; "stream": the library's reduction
+kernel against a device copy.
 Inputs are larger than the 129 MB L2 (711 MB and ~371 MB per SpMV).
 """
 from __future__ import annotations

@@ -126,3 +126,18 @@ def test_form_selection(gk):
     assert _solve(gk, edge, W.uniform_vector(32768, 8), max_iters=5)[0].form == gk.FORM_CLUSTER
     big = W.poisson2d(182)  # above the cluster form's size: the cooperative-grid form
     assert _solve(gk, big, W.uniform_vector(182 * 182, 8), max_iters=5)[0].form == gk.FORM_GRID
+
+
+def test_rows_not_staged(gk, orc):
+    """The 27-point stencil on 32^3 (n = 32,768): a CTA's 2,048 rows hold
+    ~55,000 entries, more than fit shared memory, so the kernel reads the
+    matrix from global memory -- same results as the graph form."""
+    A = W.stencil27(32)
+    n = 32768
+    b = W.uniform_vector(n, 12)
+    s1, x1 = _solve(gk, A, b, prec=1, max_iters=2000, reduction_factor=1e-10)
+    s0, x0 = _solve(gk, A, b, prec=1, max_iters=2000, reduction_factor=1e-10, check_every=-1)
+    assert s1.form == gk.FORM_CLUSTER
+    assert s1.stop_reason == s0.stop_reason == gk.STOP_CONVERGED
+    assert _close(s1.iters, s0.iters), (s1.iters, s0.iters)
+    assert np.linalg.norm(b - orc.spmv(A, x1)) <= 1.5e-10 * np.linalg.norm(b)

@@ -110,3 +110,19 @@ def test_form_selection(gk):
     M.sort_indices()
     arrow = (M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
     assert _solve(gk, arrow, W.uniform_vector(n, 9), max_iters=3)[0].form == gk.FORM_GRAPH
+
+
+@pytest.mark.parametrize("side,staged", [(40, True), (60, False)])
+def test_27_point_staged_and_not(gk, orc, side, staged):
+    """27-point stencils: on 40^3 each CTA's rows fit shared memory, on 60^3
+    (n = 216,000, ~38,000 entries per CTA) they do not and the kernel reads
+    the matrix from global memory; both as the graph form."""
+    A = W.stencil27(side)
+    n = side ** 3
+    b = W.uniform_vector(n, 13)
+    s1, x1 = _solve(gk, A, b, prec=1, max_iters=2000, reduction_factor=1e-10)
+    s0, x0 = _solve(gk, A, b, prec=1, max_iters=2000, reduction_factor=1e-10, check_every=-1)
+    assert s1.form == gk.FORM_GRID
+    assert s1.stop_reason == s0.stop_reason == gk.STOP_CONVERGED
+    assert _close(s1.iters, s0.iters), (s1.iters, s0.iters)
+    assert np.linalg.norm(b - orc.spmv(A, x1)) <= 1.5e-10 * np.linalg.norm(b)

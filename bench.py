@@ -869,13 +869,38 @@ def run_stream(dev, n=1 << 27):
     return out
 
 
+# ---------------------------------------------------------------------------
+# replicas (N > 1): one process per GPU, no data-path collective; the timed
+# region is bracketed by barriers and the slowest rank's time counts
+# ---------------------------------------------------------------------------
+
+def rank_env():
+    """(rank, world size, local rank) from the launcher's environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, bytes_per_rank, seconds):
+    """Whole-job GB/s of `world` replicas that each moved bytes_per_rank in
+    at most `seconds` (the slowest rank's time)."""
+    return world * bytes_per_rank / seconds / 1e9
+
+
 def run_gpu(args):
     import torch
     import paper_2006_16852_gb300 as gk
     gk.load()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -904,11 +929,7 @@ def run_gpu(args):
     t1.record(step.stream)
     barrier()
     clocks = sampler.stop()
-    total_ms = t0.elapsed_time(t1)
-    if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
 
     # per-part figures from the recorded events
     part_ms, part_bytes, launches = {}, {}, 0
@@ -926,7 +947,7 @@ def run_gpu(args):
                     raise RuntimeError(f"{tag[1]} did not converge: {tag[2]}")
     step_bytes = sum(sum(v) for v in part_bytes.values()) / args.steps
     ms_per_step = total_ms / args.steps
-    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_rate(world, step_bytes, ms_per_step * 1e-3)
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
@@ -999,12 +1020,8 @@ def run_gpu(args):
         step.run(record=rr, host=host)
         e2e_bytes += sum(step.part_bytes(tag) for _, _, _, tag in rr[0])
     barrier()
-    e2e_s = (time.perf_counter() - w0)
-    if dist is not None:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * (e2e_bytes / e2e_steps) / (e2e_s / e2e_steps) / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - w0, dist, dev)
+    e2e_value = whole_job_rate(world, e2e_bytes / e2e_steps, e2e_s / e2e_steps)
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1086,8 +1103,10 @@ def cpu_baseline(inp, budget_s):
 
 
 def run_reference(args):
-    """The oracle timed as the reference arm, on the same metric and config."""
-    rank = int(os.environ.get("RANK", "0"))
+    """The oracle timed as the reference arm, on the same metric and config
+    (under a multi-process launch rank 0 alone runs it; the others return
+    without work)."""
+    rank = rank_env()[0]
     if rank != 0:
         return None
     import oracle

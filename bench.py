@@ -798,6 +798,27 @@ def run_latency(dev):
                 key = f"{fmt}_{'jacobi' if prec else 'plain'}_{names[every]}"
                 out[key] = {"form": forms.get(st.form, st.form), "ms": round(best, 4), "iters": st.iters,
                             "us_per_iter": round(1e3 * best / max(st.iters, 1), 3), "rel_res_true": st.rel_res_true}
+    # BiCGSTAB on a small nonsymmetric system: the cluster form and the graph
+    A3 = W.convdiff2d(64, 0.5)
+    M3 = gk.Matrix(*[t(a) for a in A3], fmt="csr")
+    b3 = torch.zeros(4096, dtype=torch.float64, device=dev)
+    gk.apply(M3, t(W.uniform_vector(4096, 1)), b3)
+    P3 = gk.Precond(M3, 1)
+    for every in (0, -1):
+        S = gk.Solver(M3, P3, "bicgstab", max_iters=5000, reduction_factor=1e-10, check_every=every)
+        best = None
+        for _ in range(5):
+            x = torch.zeros_like(b3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, b3, x)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[f"convdiff64_bicgstab_jacobi_{names[every]}"] = {
+            "form": forms.get(st.form, st.form), "ms": round(best, 4), "iters": st.iters,
+            "us_per_iter": round(1e3 * best / max(st.iters, 1), 3), "rel_res_true": st.rel_res_true}
     # a mid-size system: the default form is the cooperative grid
     A2 = W.poisson2d(256)
     M2 = gk.Matrix(*[t(a) for a in A2], fmt="csr")
@@ -820,7 +841,8 @@ def run_latency(dev):
                                                     "iters": st.iters,
                                                     "us_per_iter": round(1e3 * best / max(st.iters, 1), 3),
                                                     "rel_res_true": st.rel_res_true}
-    return {"workload": LATENCY_WORKLOAD + "; and Poisson-2D 256x256 (n=65,536) with Jacobi for the mid-size form",
+    return {"workload": LATENCY_WORKLOAD + "; BiCGSTAB with Jacobi on upwind convection-diffusion 64x64; and "
+                                           "Poisson-2D 256x256 (n=65,536) with Jacobi for the mid-size form",
             "timing": "CUDA events around gk_solve, best of 5 (3 for 256x256)",
             "paper_host_overhead_us_per_iter": [1.0, 1.5], "solves": out}
 

@@ -1,5 +1,6 @@
-// cluster_cg.cu -- the whole preconditioned CG solve (Section 3.1, with the
-// criteria of Section 2.5) of a small system in ONE launch: a thread-block
+// cluster_cg.cu -- the whole preconditioned CG (and BiCGSTAB, below) solve
+// (Section 3.1, with the criteria of Section 2.5) of a small system in ONE
+// launch: a thread-block
 // cluster of 16 CTAs on 16 SMs, the search direction p distributed over the
 // CTAs' shared memory and read across the cluster (distributed shared
 // memory) by the SpMV, the other vectors in registers of the thread that
@@ -125,6 +126,54 @@ __device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double (&v)
   __syncthreads();
 }
 
+// The CTA's rows of the matrix in shared memory: row pointers relative to
+// the CTA's first entry (L + 1 ints), columns and values (stage_nnz each).
+struct ClStaged {
+  const int32_t* rp;
+  const int32_t* col;
+  const double* val;
+};
+
+__device__ __forceinline__ ClStaged cl_stage_rows(const ClusterArgs& a, int row0, int L, double* s_val) {
+  int32_t* s_rp = reinterpret_cast<int32_t*>(s_val + a.stage_nnz);
+  int32_t* s_col = s_rp + L + 1;
+  const int first = min(row0, a.n), rows_here = max(0, min(L, a.n - row0));
+  const int e0 = __ldg(a.rowptr + first);
+  for (int l = threadIdx.x; l <= L; l += kClThreads) s_rp[l] = __ldg(a.rowptr + first + min(l, rows_here)) - e0;
+  const int ne = __ldg(a.rowptr + first + rows_here) - e0;
+  for (int k = threadIdx.x; k < ne; k += kClThreads) {
+    s_col[k] = __ldg(a.col + e0 + k);
+    s_val[k] = __ldg(a.val + e0 + k);
+  }
+  return ClStaged{s_rp, s_col, s_val};
+}
+
+// sum_k val_k v(col_k) over row i in increasing k, v read through gather;
+// entries in groups of 4 so that their loads are in flight together.
+template <bool STAGE, typename Gather>
+__device__ __forceinline__ double cl_row_apply(const ClusterArgs& a, const ClStaged& sr, int i, int row0,
+                                               Gather gather) {
+  double s = 0.0;
+  const int l = i - row0;
+  int k = STAGE ? sr.rp[l] : __ldg(a.rowptr + i);
+  const int k1 = STAGE ? sr.rp[l + 1] : __ldg(a.rowptr + i + 1);
+  for (; k + 4 <= k1; k += 4) {
+    int c[4];
+    double v[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = STAGE ? sr.col[k + u] : __ldg(a.col + k + u);
+      v[u] = STAGE ? sr.val[k + u] : __ldg(a.val + k + u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pv[u] = gather(c[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
+  }
+  for (; k < k1; ++k) s = fma(STAGE ? sr.val[k] : __ldg(a.val + k), gather(STAGE ? sr.col[k] : __ldg(a.col + k)), s);
+  return s;
+}
+
 // STAGE: the CTA's rows of the matrix (row pointers, columns, values) are
 // copied to shared memory once, so that an SpMV row costs one gather round
 // trip instead of three dependent L2 round trips.
@@ -146,21 +195,8 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   const double factor = st->factor;
   const long long max_iters = st->max_iters;
   const int rel_to_b = st->rel_to_b;
-  // staged rows: values (stage_nnz doubles), row pointers relative to the
-  // CTA's first entry (L + 1 ints), columns (stage_nnz ints)
-  double* s_val = p_loc + L;
-  int32_t* s_rp = reinterpret_cast<int32_t*>(s_val + a.stage_nnz);
-  int32_t* s_col = s_rp + L + 1;
-  const int rows_here = max(0, min(L, a.n - row0));
-  const int e0 = STAGE ? __ldg(a.rowptr + min(row0, a.n)) : 0;
-  if (STAGE) {
-    for (int l = t; l <= L; l += kClThreads) s_rp[l] = __ldg(a.rowptr + min(row0, a.n) + min(l, rows_here)) - e0;
-    const int ne = __ldg(a.rowptr + min(row0, a.n) + rows_here) - e0;
-    for (int k = t; k < ne; k += kClThreads) {
-      s_col[k] = __ldg(a.col + e0 + k);
-      s_val[k] = __ldg(a.val + e0 + k);
-    }
-  }
+  ClStaged sr{};
+  if (STAGE) sr = cl_stage_rows(a, row0, L, p_loc + L);
 
   double x[RPT], r[RPT], d[RPT];
   bool own[RPT];
@@ -175,34 +211,13 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   }
   cl.sync();  // p = x0 everywhere (and the staged rows complete)
 
-  // q_i = sum_k val_k p[col_k] in increasing k (p read across the cluster;
-  // the CTA's own slice directly); entries in groups of 4 so that their
-  // loads are in flight together
+  // q_i = sum_k val_k p[col_k] (p read across the cluster; the CTA's own
+  // slice directly)
   auto gather = [&](int c) {
     const int o = c >> a.lg;
     return o == rank ? p_loc[c & mask] : p_of[o][c & mask];
   };
-  auto row_apply = [&](int i) {
-    double s = 0.0;
-    const int l = i - row0;
-    int k = STAGE ? s_rp[l] : __ldg(a.rowptr + i);
-    const int k1 = STAGE ? s_rp[l + 1] : __ldg(a.rowptr + i + 1);
-    for (; k + 4 <= k1; k += 4) {
-      int c[4];
-      double v[4], pv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c[u] = STAGE ? s_col[k + u] : __ldg(a.col + k + u);
-        v[u] = STAGE ? s_val[k + u] : __ldg(a.val + k + u);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) pv[u] = gather(c[u]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) s = fma(v[u], pv[u], s);
-    }
-    for (; k < k1; ++k) s = fma(STAGE ? s_val[k] : __ldg(a.val + k), gather(STAGE ? s_col[k] : __ldg(a.col + k)), s);
-    return s;
-  };
+  auto row_apply = [&](int i) { return cl_row_apply<STAGE>(a, sr, i, row0, gather); };
 
   // r0 = b - A x0; ||r0||, ||b||: the reference and the tolerance
   {
@@ -328,10 +343,277 @@ __global__ void __launch_bounds__(kClThreads) cg_cluster_kernel(ClusterArgs a) {
   cl.sync();
 }
 
+// ---- BiCGSTAB (the Templates form of Section 3.1's BiCGSTAB, as the graph
+// form computes it) -----------------------------------------------------
+
+struct BiScalars {
+  double rho, rho_prev, alpha, omega, beta, rnorm, snorm, rnorm0, bnorm, ref, tol;
+  long long iter, spmvs;
+  int stop, half;
+};
+
+struct BiSlots {
+  double setup[2];  // ||r0||^2, ||b||^2
+  double start[1];  // r^.r
+  double rhv[1];    // r^.v
+  double ss[1];     // s.s
+  double om[2];     // s.t, t.t
+  double it[2];     // r^.r, r.r
+};
+
+// rows per thread at most 4 here (10 vectors per row live in registers):
+// n <= 16 * 256 * 4 = 16,384
+constexpr int kBiMaxRpt = 4;
+
+// An iteration, five cluster barriers: p = r + beta (p - omega v) and
+// p^ = M^{-1} p (p^ published); v = A p^ with r^.v -> alpha; s = r - alpha v
+// with ||s|| (s^ = M^{-1} s published by the same barrier; half-step exit
+// when ||s|| meets the criterion); t = A s^ with s.t, t.t -> omega;
+// x += alpha p^ + omega s^, r = s - omega t with r^.r, ||r|| -> the criteria
+// and the next rho and beta.  p^ and s^ live in shared memory (read across
+// the cluster by the SpMVs), the other vectors in the owner's registers.
+template <int PK, int RPT, bool STAGE>
+__global__ void __launch_bounds__(kClThreads) bicg_cluster_kernel(ClusterArgs a) {
+  extern __shared__ double dyn[];  // p^ slice (L), s^ slice (L), then the staged rows
+  __shared__ double* ph_of[kClCtas];
+  __shared__ double* sh_of[kClCtas];
+  __shared__ BiSlots slots;
+  __shared__ double wsum[kClThreads / 32][2];
+  __shared__ BiScalars sc;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int t = threadIdx.x;
+  const int L = 1 << a.lg;
+  const int mask = L - 1;
+  double* ph_loc = dyn;
+  double* sh_loc = dyn + L;
+  if (t < kClCtas) {
+    ph_of[t] = cl.map_shared_rank(ph_loc, t);
+    sh_of[t] = cl.map_shared_rank(sh_loc, t);
+  }
+  const int row0 = rank * L;
+  SolverState* st = a.st;
+  const double factor = st->factor;
+  const long long max_iters = st->max_iters;
+  const int rel_to_b = st->rel_to_b;
+  ClStaged sr{};
+  if (STAGE) sr = cl_stage_rows(a, row0, L, dyn + 2 * L);
+  double x[RPT], r[RPT], rh[RPT], p[RPT], v[RPT], s_[RPT], d[RPT], ph[RPT], sh[RPT];
+  bool own[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int l = t + u * kClThreads;
+    const int i = row0 + l;
+    own[u] = l < L && i < a.n;
+    x[u] = own[u] ? a.x[i] : 0.0;
+    d[u] = (PK == PREC_SCALAR && own[u]) ? a.dinv[i] : 1.0;
+    r[u] = rh[u] = p[u] = v[u] = s_[u] = ph[u] = sh[u] = 0.0;
+    if (l < L) ph_loc[l] = x[u];
+  }
+  cl.sync();  // x0 everywhere (in the p^ slices) and the staged rows complete
+  auto at = [&](double* const* of, const double* loc) {
+    return [=](int c) {
+      const int o = c >> a.lg;
+      return o == rank ? loc[c & mask] : of[o][c & mask];
+    };
+  };
+  auto criteria = [&](double rn, long long k) {
+    if (!isfinite(rn)) return GK_STOP_NAN;
+    if (rn <= sc.tol) return GK_STOP_CONVERGED;
+    if (k >= max_iters) return GK_STOP_MAX_ITERS;
+    return GK_STOP_NONE;
+  };
+  // a fresh rho = r^.r either fails (NaN, zero) or yields the next beta
+  auto new_rho = [&](double rho) {
+    if (!isfinite(rho)) sc.stop = GK_STOP_NAN;
+    else if (rho == 0.0) sc.stop = GK_STOP_BREAKDOWN;
+    else {
+      sc.beta = (rho / sc.rho_prev) * (sc.alpha / sc.omega);
+      sc.rho = rho;
+    }
+  };
+  {
+    double w[2] = {0.0, 0.0};
+    const auto x0_at = at(ph_of, ph_loc);
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      const int i = row0 + t + u * kClThreads;
+      const double bi = a.b[i];
+      r[u] = bi - cl_row_apply<STAGE>(a, sr, i, row0, x0_at);
+      w[0] = fma(r[u], r[u], w[0]);
+      w[1] = fma(bi, bi, w[1]);
+    }
+    cluster_total<2>(cl, w, wsum, slots.setup, [&](const double* tt) {
+      sc.rnorm0 = sqrt(tt[0]);
+      sc.bnorm = sqrt(tt[1]);
+      double ref = rel_to_b ? sc.bnorm : sc.rnorm0;
+      if (ref == 0.0) ref = 1.0;
+      sc.ref = ref;
+      sc.tol = factor * ref;
+      sc.rnorm = sc.rnorm0;
+      sc.iter = 0;
+      sc.spmvs = 1;
+      sc.rho = 0.0;
+      sc.rho_prev = sc.alpha = sc.omega = 1.0;
+      sc.beta = 0.0;
+      sc.snorm = 0.0;
+      sc.half = 0;
+      sc.stop = GK_STOP_NONE;
+    });
+  }
+  {
+    // r^ = r0, p = v = 0, rho = r^.r; the criteria at k = 0
+    double w[1] = {0.0};
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      rh[u] = r[u];
+      w[0] = fma(r[u], r[u], w[0]);
+    }
+    cluster_total<1>(cl, w, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.start, [&](const double* tt) {
+      sc.stop = criteria(sc.rnorm, 0);
+      if (sc.stop == GK_STOP_NONE) new_rho(tt[0]);
+    });
+  }
+  const auto ph_at = at(ph_of, ph_loc);
+  const auto sh_at = at(sh_of, sh_loc);
+  while (sc.stop == GK_STOP_NONE) {
+    const double beta = sc.beta, omega0 = sc.omega;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (!own[u]) continue;
+      p[u] = fma(beta, fma(-omega0, v[u], p[u]), r[u]);
+      ph[u] = PK == PREC_SCALAR ? d[u] * p[u] : p[u];
+      ph_loc[t + u * kClThreads] = ph[u];
+    }
+    cl.sync();  // p^ everywhere
+    {
+      double w[1] = {0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        if (!own[u]) continue;
+        v[u] = cl_row_apply<STAGE>(a, sr, row0 + t + u * kClThreads, row0, ph_at);
+        w[0] = fma(rh[u], v[u], w[0]);
+      }
+      cluster_total<1>(cl, w, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.rhv, [&](const double* tt) {
+        sc.spmvs += 1;
+        const double rhv = tt[0];
+        if (!isfinite(rhv)) sc.stop = GK_STOP_NAN;
+        else if (rhv == 0.0) sc.stop = GK_STOP_BREAKDOWN;
+        else sc.alpha = sc.rho / rhv;
+      });
+    }
+    if (sc.stop != GK_STOP_NONE) break;
+    const double alpha = sc.alpha;
+    {
+      double w[1] = {0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        if (!own[u]) continue;
+        s_[u] = fma(-alpha, v[u], r[u]);
+        w[0] = fma(s_[u], s_[u], w[0]);
+        sh[u] = PK == PREC_SCALAR ? d[u] * s_[u] : s_[u];
+        sh_loc[t + u * kClThreads] = sh[u];
+      }
+      // the reduction's cluster barrier also publishes s^
+      cluster_total<1>(cl, w, reinterpret_cast<double(*)[1]>(&wsum[0][0]), slots.ss, [&](const double* tt) {
+        sc.snorm = sqrt(tt[0]);
+        if (isfinite(sc.snorm) && sc.snorm <= sc.tol) {
+          sc.half = 1;
+          sc.iter += 1;
+          sc.rnorm = sc.snorm;
+          sc.stop = GK_STOP_CONVERGED;
+        }
+      });
+    }
+    if (sc.half) {
+      // converged at the half step: x += alpha p^, r = s
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        if (!own[u]) continue;
+        x[u] = fma(alpha, ph[u], x[u]);
+        r[u] = s_[u];
+      }
+      break;
+    }
+    double tv[RPT];
+    {
+      double w[2] = {0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        tv[u] = 0.0;
+        if (!own[u]) continue;
+        tv[u] = cl_row_apply<STAGE>(a, sr, row0 + t + u * kClThreads, row0, sh_at);
+        w[0] = fma(s_[u], tv[u], w[0]);
+        w[1] = fma(tv[u], tv[u], w[1]);
+      }
+      cluster_total<2>(cl, w, wsum, slots.om, [&](const double* tt) {
+        sc.spmvs += 1;
+        const double ts = tt[0], ttv = tt[1];
+        if (!isfinite(ttv) || !isfinite(ts)) sc.stop = GK_STOP_NAN;
+        else if (ttv == 0.0) sc.stop = GK_STOP_BREAKDOWN;
+        else sc.omega = ts / ttv;
+      });
+    }
+    if (sc.stop != GK_STOP_NONE) break;
+    const double omega = sc.omega;
+    {
+      double w[2] = {0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        if (!own[u]) continue;
+        x[u] = fma(omega, sh[u], fma(alpha, ph[u], x[u]));
+        r[u] = fma(-omega, tv[u], s_[u]);
+        w[0] = fma(rh[u], r[u], w[0]);
+        w[1] = fma(r[u], r[u], w[1]);
+      }
+      cluster_total<2>(cl, w, wsum, slots.it, [&](const double* tt) {
+        sc.iter += 1;
+        sc.rho_prev = sc.rho;
+        sc.rnorm = sqrt(tt[1]);
+        int stop = criteria(sc.rnorm, sc.iter);
+        if (stop == GK_STOP_NONE && sc.omega == 0.0) stop = GK_STOP_BREAKDOWN;
+        sc.stop = stop;
+        if (stop == GK_STOP_NONE) new_rho(tt[0]);
+      });
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < RPT; ++u)
+    if (own[u]) a.x[row0 + t + u * kClThreads] = x[u];
+  if (rank == 0 && t == 0) {
+    st->rnorm = sc.rnorm;
+    st->snorm = sc.snorm;
+    st->rnorm0 = sc.rnorm0;
+    st->bnorm = sc.bnorm;
+    st->ref = sc.ref;
+    st->tol = sc.tol;
+    st->rho = sc.rho;
+    st->rho_prev = sc.rho_prev;
+    st->alpha = sc.alpha;
+    st->omega = sc.omega;
+    st->beta = sc.beta;
+    st->half = sc.half;
+    st->iter = sc.iter;
+    st->iter_guard = sc.iter;
+    st->spmvs = sc.spmvs;
+    st->stop = sc.stop;
+  }
+  cl.sync();  // no CTA leaves while others can still read its shared memory
+}
+
 using ClKernel = void (*)(ClusterArgs);
 
 template <int PK, bool STAGE>
-ClKernel pick_rpt(int rpt) {
+ClKernel pick_rpt(int kind, int rpt) {
+  if (kind == GK_BICGSTAB) {
+    switch (rpt) {
+      case 1: return bicg_cluster_kernel<PK, 1, STAGE>;
+      case 2: return bicg_cluster_kernel<PK, 2, STAGE>;
+      default: return bicg_cluster_kernel<PK, 4, STAGE>;
+    }
+  }
   switch (rpt) {
     case 1: return cg_cluster_kernel<PK, 1, STAGE>;
     case 2: return cg_cluster_kernel<PK, 2, STAGE>;
@@ -340,9 +622,10 @@ ClKernel pick_rpt(int rpt) {
   }
 }
 
-ClKernel pick(int pk, int rpt, bool stage) {
-  if (pk == PREC_SCALAR) return stage ? pick_rpt<PREC_SCALAR, true>(rpt) : pick_rpt<PREC_SCALAR, false>(rpt);
-  return stage ? pick_rpt<PREC_NONE, true>(rpt) : pick_rpt<PREC_NONE, false>(rpt);
+ClKernel pick(int kind, int pk, int rpt, bool stage) {
+  if (pk == PREC_SCALAR)
+    return stage ? pick_rpt<PREC_SCALAR, true>(kind, rpt) : pick_rpt<PREC_SCALAR, false>(kind, rpt);
+  return stage ? pick_rpt<PREC_NONE, true>(kind, rpt) : pick_rpt<PREC_NONE, false>(kind, rpt);
 }
 
 cudaLaunchConfig_t launch_config(size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
@@ -367,9 +650,10 @@ constexpr size_t kClStageMax = 160 * 1024;
 
 int cluster_cg_plan(Solver* S) {
   S->cl_lg = -1;
-  if (S->kind != GK_CG || S->pk == PREC_BLOCK) return GK_OK;
+  if ((S->kind != GK_CG && S->kind != GK_BICGSTAB) || S->pk == PREC_BLOCK) return GK_OK;
   const int64_t n = S->n;
-  if (n < 1 || n > static_cast<int64_t>(kClCtas) * kClThreads * kClMaxRpt) return GK_OK;
+  const int max_rpt = S->kind == GK_BICGSTAB ? kBiMaxRpt : kClMaxRpt;
+  if (n < 1 || n > static_cast<int64_t>(kClCtas) * kClThreads * max_rpt) return GK_OK;
   int lg = 0;
   while ((static_cast<int64_t>(kClCtas) << lg) < n) ++lg;
   const int rpt = std::max(1, (1 << lg) / kClThreads);
@@ -385,8 +669,9 @@ int cluster_cg_plan(Solver* S) {
   const size_t L = size_t(1) << lg;
   const size_t staged = 12 * static_cast<size_t>(most) + 4 * (L + 1);
   const bool stage = staged <= kClStageMax;
-  const size_t smem = 8 * L + (stage ? staged : 0);
-  ClKernel k = pick(S->pk, rpt, stage);
+  const size_t slices = S->kind == GK_BICGSTAB ? 2 : 1;  // p (CG); p^ and s^ (BiCGSTAB)
+  const size_t smem = 8 * L * slices + (stage ? staged : 0);
+  ClKernel k = pick(S->kind, S->pk, rpt, stage);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
       set_smem(k, smem) != GK_OK) {
     cudaGetLastError();
@@ -421,7 +706,7 @@ int cluster_cg_solve(Solver* S, cudaStream_t s) {
   a.stage_nnz = S->cl_nnz;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = launch_config(S->cl_smem, s, attr);
-  GK_TRY_CUDA(cudaLaunchKernelEx(&cfg, pick(S->pk, S->cl_rpt, S->cl_stage), a));
+  GK_TRY_CUDA(cudaLaunchKernelEx(&cfg, pick(S->kind, S->pk, S->cl_rpt, S->cl_stage), a));
   return GK_OK;
 }
 

@@ -303,7 +303,7 @@ struct Solver {
   cudaGraphConditionalHandle cond = 0;
   IrData* ir = nullptr;  // GK_IR_CG: the FP32 inner solver
   GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
-  int cl_lg = -1;           // GK_CG small-system form: rows per CTA = 2^cl_lg (-1: not available)
+  int cl_lg = -1;           // GK_CG / GK_BICGSTAB small-system form: rows per CTA = 2^cl_lg (-1: none)
   int cl_rpt = 1;           // ... rows per thread
   bool cl_stage = false;    // ... the CTA's rows of the matrix staged in shared memory
   int cl_nnz = 0;           // ... room for that many entries

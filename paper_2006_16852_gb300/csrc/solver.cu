@@ -723,7 +723,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
     }
     if (kind == GK_IR_CG && (rc = ir_generate(S))) break;
     if (kind == GK_GMRES && (rc = gmres_generate(S))) break;
-    if (kind == GK_CG && (rc = cluster_cg_plan(S))) break;
+    if ((kind == GK_CG || kind == GK_BICGSTAB) && (rc = cluster_cg_plan(S))) break;
     if (kind == GK_CG && S->cl_lg < 0 && (rc = grid_cg_plan(S))) break;
   } while (false);
   if (prev != A->device) cudaSetDevice(prev);
@@ -760,7 +760,8 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       if ((rc = ir_solve(S, s))) break;
     } else if (S->kind == GK_GMRES) {
       if ((rc = gmres_solve(S, s))) break;
-    } else if (S->kind == GK_CG && S->cl_lg >= 0 && S->crit.check_every == 0 && !(S->crit.time_limit_s > 0)) {
+    } else if ((S->kind == GK_CG || S->kind == GK_BICGSTAB) && S->cl_lg >= 0 && S->crit.check_every == 0 &&
+               !(S->crit.time_limit_s > 0)) {
       // small system: the whole iteration in one thread-block cluster
       const gk_criteria& c = S->crit;
       solver_init_kernel<<<1, 1, 0, s>>>(S->st, c.reduction_factor, static_cast<long long>(c.max_iters), c.rel_to_b,

@@ -114,7 +114,7 @@ def test_exits(gk, orc):
 
 
 def test_form_selection(gk):
-    """The cluster form is taken only where it applies: CG, no or scalar
+    """The cluster form is taken only where it applies: CG (or BiCGSTAB), no or scalar
     Jacobi preconditioning, n <= 32,768, no Time criterion, check_every 0."""
     A = W.poisson2d(8)
     b = W.uniform_vector(64, 7)
@@ -141,3 +141,75 @@ def test_rows_not_staged(gk, orc):
     assert s1.stop_reason == s0.stop_reason == gk.STOP_CONVERGED
     assert _close(s1.iters, s0.iters), (s1.iters, s0.iters)
     assert np.linalg.norm(b - orc.spmv(A, x1)) <= 1.5e-10 * np.linalg.norm(b)
+
+
+def _solve_kind(gk, A, b, kind, x0=None, prec=None, **crit):
+    n = A[0].size - 1
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="csr")
+    P = gk.Precond(M, prec) if prec else None
+    S = gk.Solver(M, P, kind, **crit)
+    x = to_dev(np.zeros(n) if x0 is None else x0)
+    st = gk.solve(S, to_dev(b), x)
+    return st, to_np(x)
+
+
+@pytest.mark.parametrize("side", [48, 64, 100, 128])
+@pytest.mark.parametrize("prec", [None, 1])
+def test_bicgstab_cluster_against_graph_form(gk, orc, side, prec):
+    """BiCGSTAB in the cluster form (n up to 16,384: rows per thread 1 .. 4)
+    on the nonsymmetric upwind convection-diffusion matrix: same stop
+    reason, iterations within max(3, 25 %) of the graph form's (BiCGSTAB's
+    iteration count is sensitive to rounding), SpMV count 2 per full
+    iteration, x checked with the oracle's SpMV; and against the oracle's
+    BiCGSTAB."""
+    A = W.convdiff2d(side, 0.5)
+    n = side * side
+    xs = W.uniform_vector(n, 14)
+    b = orc.spmv(A, xs)
+    s1, x1 = _solve_kind(gk, A, b, "bicgstab", prec=prec, max_iters=5000, reduction_factor=1e-10)
+    s0, x0 = _solve_kind(gk, A, b, "bicgstab", prec=prec, max_iters=5000, reduction_factor=1e-10, check_every=-1)
+    assert s1.form == gk.FORM_CLUSTER and s0.form == gk.FORM_GRAPH
+    assert s1.stop_reason == s0.stop_reason == gk.STOP_CONVERGED
+    assert abs(s1.iters - s0.iters) <= max(3, s0.iters // 4), (s1.iters, s0.iters)
+    assert s1.spmvs in (2 * s1.iters + 2, 2 * s1.iters + 1)
+    assert np.linalg.norm(b - orc.spmv(A, x1)) <= 1.5e-10 * np.linalg.norm(b)
+    ref = orc.bicgstab(A, b, P=orc.precond(A, "jacobi" if prec else "none", 1), tol=1e-10, max_iters=5000)
+    assert ref.stop_reason == gk.STOP_CONVERGED
+    assert abs(s1.iters - ref.iters) <= max(3, ref.iters // 4), (s1.iters, ref.iters)
+
+
+def test_bicgstab_cluster_exits(gk, orc):
+    """A = c I converges at the first half step (x = b / c, one SpMV in the
+    iteration); exact initial guess, zero right-hand side, iteration limits,
+    NaN: as the graph form."""
+    D = W.scaled_identity(3000, 2.5)
+    b = W.uniform_vector(3000, 15)
+    s1, x1 = _solve_kind(gk, D, b, "bicgstab", max_iters=50, reduction_factor=1e-10)
+    assert s1.form == gk.FORM_CLUSTER and s1.stop_reason == gk.STOP_CONVERGED
+    assert s1.iters == 1 and s1.spmvs == 3
+    np.testing.assert_allclose(x1, b / 2.5, rtol=1e-14)
+    A = W.convdiff2d(40, 0.5)
+    n = 1600
+    xs = W.uniform_vector(n, 16)
+    bb = orc.spmv(A, xs)
+    cases = [dict(b=bb, x0=xs), dict(b=np.zeros(n)), dict(b=bb, max_iters=0), dict(b=bb, max_iters=3),
+             dict(b=np.full(n, np.nan), max_iters=50)]
+    for c in cases:
+        c = dict(c)
+        bv, x0 = c.pop("b"), c.pop("x0", None)
+        c.setdefault("reduction_factor", 1e-10)
+        s1, x1 = _solve_kind(gk, A, bv, "bicgstab", x0=x0, **c)
+        s0, x0g = _solve_kind(gk, A, bv, "bicgstab", x0=x0, check_every=-1, **c)
+        assert s1.form == gk.FORM_CLUSTER
+        assert (s1.stop_reason, s1.iters, s1.spmvs) == (s0.stop_reason, s0.iters, s0.spmvs), c
+        if s1.stop_reason != gk.STOP_NAN:
+            np.testing.assert_allclose(x1, x0g, rtol=0, atol=1e-11 * max(1.0, np.abs(x0g).max()))
+
+
+def test_bicgstab_cluster_selection(gk):
+    A = W.convdiff2d(128, 0.5)  # n = 16,384: the largest size of the form
+    assert _solve_kind(gk, A, W.uniform_vector(16384, 17), "bicgstab", max_iters=3)[0].form == gk.FORM_CLUSTER
+    A2 = W.convdiff2d(129, 0.5)
+    assert _solve_kind(gk, A2, W.uniform_vector(129 * 129, 17), "bicgstab", max_iters=3)[0].form == gk.FORM_GRAPH
+    assert _solve_kind(gk, A, W.uniform_vector(16384, 17), "bicgstab", max_iters=3,
+                       prec=4)[0].form == gk.FORM_GRAPH

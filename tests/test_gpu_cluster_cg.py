@@ -213,3 +213,18 @@ def test_bicgstab_cluster_selection(gk):
     assert _solve_kind(gk, A2, W.uniform_vector(129 * 129, 17), "bicgstab", max_iters=3)[0].form == gk.FORM_GRAPH
     assert _solve_kind(gk, A, W.uniform_vector(16384, 17), "bicgstab", max_iters=3,
                        prec=4)[0].form == gk.FORM_GRAPH
+
+
+def test_bicgstab_cluster_rows_not_staged(gk, orc):
+    """BiCGSTAB on the 27-point stencil on 25^3 (n = 15,625): a CTA's 1,024
+    rows hold ~27,000 entries, more than are staged, so the kernel reads the
+    matrix from global memory -- as the graph form."""
+    A = W.stencil27(25)
+    n = 25 ** 3
+    b = W.uniform_vector(n, 18)
+    s1, x1 = _solve_kind(gk, A, b, "bicgstab", prec=1, max_iters=2000, reduction_factor=1e-10)
+    s0, x0 = _solve_kind(gk, A, b, "bicgstab", prec=1, max_iters=2000, reduction_factor=1e-10, check_every=-1)
+    assert s1.form == gk.FORM_CLUSTER
+    assert s1.stop_reason == s0.stop_reason == gk.STOP_CONVERGED
+    assert abs(s1.iters - s0.iters) <= max(3, s0.iters // 4), (s1.iters, s0.iters)
+    assert np.linalg.norm(b - orc.spmv(A, x1)) <= 1.5e-10 * np.linalg.norm(b)

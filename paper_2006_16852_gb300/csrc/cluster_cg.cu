@@ -1,10 +1,10 @@
-// cluster_cg.cu -- the whole preconditioned CG (and BiCGSTAB, below) solve
+// cluster_cg.cu -- the whole preconditioned CG (and, below, BiCGSTAB) solve
 // (Section 3.1, with the criteria of Section 2.5) of a small system in ONE
-// launch: a thread-block
-// cluster of 16 CTAs on 16 SMs, the search direction p distributed over the
-// CTAs' shared memory and read across the cluster (distributed shared
-// memory) by the SpMV, the other vectors in registers of the thread that
-// owns the row, and the cluster's hardware barrier between the phases.
+// launch: a thread-block cluster of 16 CTAs on 16 SMs, the vector the SpMV
+// reads (CG's search direction p) distributed over the CTAs' shared memory
+// and read across the cluster (distributed shared memory), the other
+// vectors in registers of the thread that owns the row, and the cluster's
+// hardware barrier between the phases.
 //
 // Small systems are latency-bound: the graph form spends a few microseconds
 // per kernel launch and per grid-wide reduction, three times per iteration,
@@ -41,8 +41,9 @@ constexpr int kClCtas = 16;
 constexpr int kClThreads = 256;
 // rows per thread: n <= 16 * 256 * 8 = 32,768.  The FP64 work of an
 // iteration grows with n / 16 per SM here but with n / 152 in the graph form:
-// measured 7.1 us per iteration at n = 4,096 (graph 21.7 us), but ~29 us at
-// n = 65,536 (graph ~23 us); 32,768 rows is below the crossing.
+// measured (before the matrix staging and the one-thread scalars) 7.1 us per
+// iteration at n = 4,096 (graph 21.7 us), but ~29 us at n = 65,536 (graph
+// ~23 us); 32,768 rows is below the crossing.
 constexpr int kClMaxRpt = 8;
 
 struct ClusterArgs {

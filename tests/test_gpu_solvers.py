@@ -173,3 +173,29 @@ def test_cg_full_size_stencil27(gk):
     assert st.stop_reason == gk.STOP_CONVERGED and st.rel_res_true <= 1.5e-10
     err = np.linalg.norm(to_np(x) - xs) / np.linalg.norm(xs)
     assert err <= kappa * 2e-10, (err, kappa)
+
+
+def test_powerlaw_full_size_solves(gk, orc):
+    """The benchmark's solves on (b), the power-law matrix with 10^6 rows, in
+    the benchmark's formats and preconditioners: Jacobi-CG and block-Jacobi
+    (bs 4) BiCGSTAB on HYB to 1e-10 from b = A x*.  Iteration counts against
+    the oracle's (max(2, 3 %) for CG, max(3, 25 %) for BiCGSTAB), the true
+    residual with the oracle's SpMV, and the forward error (the matrix is
+    strictly diagonally dominant, so well conditioned)."""
+    A = W.powerlaw(1_000_000, seed=3)
+    n = A[0].size - 1
+    xs = W.uniform_vector(n, 5)
+    b = orc.spmv(A, xs)
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="hyb")
+    for kind, bs in (("cg", 1), ("bicgstab", 4)):
+        S = gk.Solver(M, gk.Precond(M, bs), kind, max_iters=5000, reduction_factor=1e-10)
+        x = to_dev(np.zeros(n))
+        st = gk.solve(S, to_dev(b), x)
+        x = to_np(x)
+        assert st.stop_reason == gk.STOP_CONVERGED, kind
+        assert np.linalg.norm(b - orc.spmv(A, x)) <= 1.5e-10 * np.linalg.norm(b), kind
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8, kind
+        P = orc.precond(A, "jacobi" if bs == 1 else "block_jacobi", bs)
+        ref = (orc.cg if kind == "cg" else orc.bicgstab)(A, b, P=P, tol=1e-10, max_iters=5000)
+        slack = max(2, ref.iters * 3 // 100) if kind == "cg" else max(3, ref.iters // 4)
+        assert abs(st.iters - ref.iters) <= slack, (kind, st.iters, ref.iters)

@@ -62,7 +62,7 @@ WORKLOAD = ("SpMV + Krylov sweep, FP64 values / int32 indices: (a) 27-point sten
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel per launch on workload (a); valid only while the ELL
 # kernel's source (spmv_source_hash) is the one it was measured on.
-NCU_TRAFFIC = {"8f0479bcad827b53": {"copy": 711961600, "dot": 728345856}}
+NCU_TRAFFIC = {"4cc6d27f23f1bfed": {"copy": 699093760, "dot": 715236608}}
 
 # nominal GB300 rates (context beside the measured peaks)
 NOMINAL_HBM_GBS = 7900.0

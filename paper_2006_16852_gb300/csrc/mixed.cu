@@ -265,17 +265,17 @@ __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_ell_kernel(Ell32 a, con
       int cc[4];
       float vv[4], xv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) cc[u] = __ldg(cp + (j + u) * a.ld);
+      for (int u = 0; u < 4; ++u) cc[u] = __ldcs(cp + (j + u) * a.ld);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) vv[u] = __ldg(vp + (j + u) * a.ld);
+      for (int u = 0; u < 4; ++u) vv[u] = __ldcs(vp + (j + u) * a.ld);
 #pragma unroll
       for (int u = 0; u < 4; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.0f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) s = fmaf(vv[u], xv[u], s);
     }
     for (; j < a.K; ++j) {
-      const int c = __ldg(cp + j * a.ld);
-      if (c >= 0) s = fmaf(__ldg(vp + j * a.ld), __ldg(x + c), s);
+      const int c = __ldcs(cp + j * a.ld);
+      if (c >= 0) s = fmaf(__ldcs(vp + j * a.ld), __ldg(x + c), s);
     }
     if (TAIL) {
       const int t = __ldg(a.tail_slot + row);
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_csr_kernel(const int32_
     float s = 0.0f;
     if (row < n) {
       const int k1 = __ldg(rowptr + row + 1);
-      for (int k = __ldg(rowptr + row) + sub; k < k1; k += LPR) s = fmaf(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+      for (int k = __ldg(rowptr + row) + sub; k < k1; k += LPR) s = fmaf(__ldcs(val + k), __ldg(x + __ldcs(col + k)), s);
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

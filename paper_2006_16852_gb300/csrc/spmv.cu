@@ -119,6 +119,8 @@ __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, 
 // CSR order, bit-identical to the CPU reference.  Longer rows are summed one
 // warp per row (coalesced loads, xor butterfly), and rows beyond kBlockRowLen
 // entries one thread block per row, so that no row holds up the launch.
+// Values and indices are streamed (read once, evict first) so that the
+// gathered vector keeps the caches (27-point matrix: 135.9 -> 116.5 us).
 // ---------------------------------------------------------------------------
 
 template <int MODE>
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs
     const int row = __ldg(a.big + v);
     const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
     double sm[1] = {0.0};
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) sm[0] = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), sm[0]);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) sm[0] = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), sm[0]);
     block_sum<1, double>(sm, row_scratch);
     if (threadIdx.x == 0) epi_row_t<MODE>(e, row, sm[0], a0, a1);
     __syncthreads();
@@ -172,15 +174,15 @@ __global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs
         int cc[4];
         double vv[4], xv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) cc[u] = __ldg(a.col + k + 32 * u);
+        for (int u = 0; u < 4; ++u) cc[u] = __ldcs(a.col + k + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) vv[u] = __ldg(a.val + k + 32 * u);
+        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(a.val + k + 32 * u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) xv[u] = __ldg(a.x + cc[u]);
 #pragma unroll
         for (int u = 0; u < 4; ++u) s = fma(vv[u], xv[u], s);
       }
-      for (; k < k1; k += 32) s = fma(__ldg(a.val + k), __ldg(a.x + __ldg(a.col + k)), s);
+      for (; k < k1; k += 32) s = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) epi_row_t<MODE>(e, row, s, a0, a1);
@@ -197,9 +199,9 @@ __global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs
         int cc[B];
         double vv[B], xv[B];
 #pragma unroll
-        for (int u = 0; u < B; ++u) cc[u] = __ldg(cp + (j + u) * 32);
+        for (int u = 0; u < B; ++u) cc[u] = __ldcs(cp + (j + u) * 32);
 #pragma unroll
-        for (int u = 0; u < B; ++u) vv[u] = __ldg(vp + (j + u) * 32);
+        for (int u = 0; u < B; ++u) vv[u] = __ldcs(vp + (j + u) * 32);
 #pragma unroll
         for (int u = 0; u < B; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
 #pragma unroll
@@ -207,8 +209,8 @@ __global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs
           if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
       }
       for (; j < L; ++j) {
-        const int cc = __ldg(cp + j * 32);
-        if (cc >= 0) s = fma(__ldg(vp + j * 32), __ldg(a.x + cc), s);
+        const int cc = __ldcs(cp + j * 32);
+        if (cc >= 0) s = fma(__ldcs(vp + j * 32), __ldg(a.x + cc), s);
       }
       if (base < a.n_sell) epi_row_t<MODE>(e, __ldg(a.perm + base), s, a0, a1);
     }
@@ -235,6 +237,9 @@ struct EllArgs {
 
 // 8 blocks of 256 threads per SM (32 registers): full occupancy is what hides
 // the latency of the gathers (measured: 6 blocks/SM ran 10-25 % slower).
+// Values and indices are read once: streaming loads (evict first), so that
+// they do not push the gathered vector out of the caches (measured 131.5 ->
+// 123.5 us on the 27-point matrix).
 // The reduction epilogues carry two accumulators and a second vector through
 // the loop; they issue their gathers in batches of 4 instead of 8 so that
 // they, too, fit 32 registers and keep 8 blocks per SM.
@@ -259,9 +264,9 @@ __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi
       int cc[B];
       double xv[B], vv[B];
 #pragma unroll
-      for (int u = 0; u < B; ++u) cc[u] = __ldg(cp + (j + u) * a.ld);
+      for (int u = 0; u < B; ++u) cc[u] = __ldcs(cp + (j + u) * a.ld);
 #pragma unroll
-      for (int u = 0; u < B; ++u) vv[u] = __ldg(vp + (j + u) * a.ld);
+      for (int u = 0; u < B; ++u) vv[u] = __ldcs(vp + (j + u) * a.ld);
 #pragma unroll
       for (int u = 0; u < B; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
 #pragma unroll
@@ -273,8 +278,8 @@ __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi
       double xv[4], vv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        cc[u] = (j + u < a.K) ? __ldg(cp + (j + u) * a.ld) : -1;
-        vv[u] = cc[u] >= 0 ? __ldg(vp + (j + u) * a.ld) : 0.0;
+        cc[u] = (j + u < a.K) ? __ldcs(cp + (j + u) * a.ld) : -1;
+        vv[u] = cc[u] >= 0 ? __ldcs(vp + (j + u) * a.ld) : 0.0;
         xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
       }
 #pragma unroll

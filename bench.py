@@ -34,7 +34,12 @@ solves/s and the time against plain FP64 CG on the block-diagonal matrix;
 and GMRES on (a), to 1e-10; "latency": CG on Poisson-2D 64^2 (and 256^2) in
 every form -- the one-launch cluster (or cooperative-grid) form, the graph,
 host-checked loops -- per iteration; "stream": the library's reduction
-kernel against a device copy.
+kernel against a device copy and the STREAM triad; "paper_bandwidth": the
+paper's solver-bandwidth experiment (Section 7.3) on this GPU -- the five
+Krylov solvers unpreconditioned for a fixed iteration count on (a), bytes
+from the paper's Table 2 model and from this library's own, against the
+triad; "paper_context": the paper's own numbers with their GPUs (Tables 1-3),
+context only.
 Inputs are larger than the 129 MB L2 (711 MB and ~371 MB per SpMV).
 """
 from __future__ import annotations
@@ -146,20 +151,45 @@ def precond_bytes(nnz, n, bs):
     return nnz * 12 + (n + 1) * 4 + 8 * n * (1 if bs == 1 else bs)
 
 
-def table2_cg_bytes(iters, nnz, n, vt=8, it=4):
-    """Memory access volume of a full CG run as the paper models it (Table 2)."""
-    reads = (4 * n + 2 * nnz) * vt + 2 * nnz * it + iters * ((15 * n + 2 * nnz) * vt + 2 * nnz * it)
-    writes = (5 * n + 2) * vt + iters * ((5 * n + 2) * vt)
-    return reads + writes
-
-
-def table2_bicgstab_bytes(iters, nnz, n, vt=8, it=4):
-    """Memory access volume of a full BiCGSTAB run as the paper models it (Table 2)."""
+def table2_bytes(kind, iters, nnz, n, vt=8, it=4, k=100):
+    """Memory access volume (reads, writes) of a full unpreconditioned run as
+    the paper models it for a COO SpMV (Table 2): vt value bytes, it index
+    bytes.  iters counts what the table counts -- CG and FCG iterations;
+    BiCGSTAB and CGS steps with one SpMV each (a full iteration is two, hence
+    the table's ceil(iters/2) and floor(iters/2) terms); GMRES Arnoldi steps
+    with restart k (r = iters mod k, iter_r the orthogonalisation steps)."""
+    spmv = 2 * nnz * vt + 2 * nnz * it  # one COO apply: values, gathered x, row and column indices
     c, f = (iters + 1) // 2, iters // 2
-    reads = ((5 * n + 2 * nnz) * vt + 2 * nnz * it + c * ((16 * n + 2 * nnz) * vt + 2 * nnz * it)
-             + f * ((13 * n + 2 * nnz) * vt + 2 * nnz * it))
-    writes = (10 * n + 6) * vt + c * ((4 * n + 2) * vt) + f * ((4 * n + 3) * vt)
-    return reads + writes
+    if kind == "cg":
+        reads = (4 * n + 2 * nnz) * vt + 2 * nnz * it + iters * ((15 * n) * vt + spmv)
+        writes = (5 * n + 2) * vt + iters * (5 * n + 2) * vt
+    elif kind == "fcg":
+        reads = (4 * n + 2 * nnz) * vt + 2 * nnz * it + iters * ((17 * n) * vt + spmv)
+        writes = (6 * n + 3) * vt + iters * (6 * n + 3) * vt
+    elif kind == "bicgstab":
+        reads = ((5 * n + 2 * nnz) * vt + 2 * nnz * it + c * ((16 * n) * vt + spmv)
+                 + f * ((13 * n) * vt + spmv))
+        writes = (10 * n + 6) * vt + c * (4 * n + 2) * vt + f * (4 * n + 3) * vt
+    elif kind == "cgs":
+        reads = ((5 * n + 2 * nnz) * vt + 2 * nnz * it + c * ((14 * n) * vt + spmv)
+                 + f * ((6 * n) * vt + spmv))
+        writes = (10 * n + 2) * vt + c * (6 * n + 3) * vt + f * (4 * n) * vt
+    elif kind == "gmres":
+        q, r = divmod(iters, k)
+        iter_r = q * (k - 1) * k // 2 + (r - 1) * r // 2
+        reads = ((11 * n + 2 * nnz + 2.5 * r + n * r + r * r / 2 + 1) * vt + 2 * nnz * it
+                 + q * ((1 + 2.5 * k + 10 * n + 2 * nnz + k * k / 2 + k * n) * vt + 2 * nnz * it)
+                 + iters * ((7 * n + 5 + 2 * nnz) * vt + 2 * nnz * it + 8) + iter_r * (4 * n + 4) * vt)
+        writes = ((6 * n + r + 2 * k + 3) * vt + 8 + q * ((k + 6 * n + 2) * vt + 8)
+                  + iters * ((4 * n + 8) * vt + 8) + iter_r * (n + 2) * vt)
+    else:
+        raise ValueError(kind)
+    return reads, writes
+
+
+def table2_cg_bytes(iters, nnz, n, vt=8, it=4):
+    """Total memory access volume of a full CG run as the paper models it (Table 2)."""
+    return sum(table2_bytes("cg", iters, nnz, n, vt, it))
 
 
 def spmv_launches(info):
@@ -848,14 +878,99 @@ def run_latency(dev):
 
 
 # ---------------------------------------------------------------------------
+# the paper's own numbers (context: other GPUs, 2020) and its solver-bandwidth
+# experiment repeated here
+# ---------------------------------------------------------------------------
+
+PAPER_CONTEXT = {
+    "source": "arXiv 2006.16852, Section 7 (Tables 1-3); one GPU per run",
+    "krylov_solver_bandwidth": {
+        "setup": "BiCGSTAB, CG, CGS, FCG, GMRES(100); COO SpMV, no preconditioner, 10,000 iterations, "
+                 "10 SuiteSparse matrices; bytes from the Table 2 model",
+        "V100": {"GB/s": [600, 800], "frac_of_stream_triad": "> 0.80", "stream_triad_GB/s": 812.6,
+                 "hbm_nominal_GB/s": 900},
+        "RadeonVII": {"GB/s": [500, 700], "frac_of_stream_triad": "> 0.70 (GMRES slightly less)",
+                      "stream_triad_GB/s": 809.8, "hbm_nominal_GB/s": 1024},
+    },
+    "stream_GB/s_table3": {
+        "V100": {"copy": 790.475, "mul": 787.301, "add": 811.312, "triad": 812.617, "dot": 844.321},
+        "RadeonVII": {"copy": 841.669, "mul": 841.934, "add": 806.632, "triad": 809.754, "dot": 635.677},
+    },
+    "solver_overhead_us_per_iteration_table1": {"bicgstab": 1.26, "cg": 1.28, "cgs": 1.00, "fcg": 1.45,
+                                                "gmres": 1.51},
+}
+
+PAPER_BW_WORKLOAD = ("27-point stencil on 128^3 (n=2,097,152, nnz=55,742,968), GK_CSR, no preconditioner, "
+                     "x* uniform[-1,1], b = A x*, x0 = 0, a fixed iteration count (reduction factor 1e-300): "
+                     "200 SpMVs in every solver's loop; GMRES restart 100")
+
+
+def run_paper_bandwidth(dev, triad_gbs=None):
+    """The paper's solver-bandwidth experiment (Section 7.3) on this GPU: each
+    of the five Krylov solvers unpreconditioned for a fixed number of
+    iterations, its memory volume from the paper's Table 2 model divided by
+    the device time, against the STREAM triad measured in the same run.  The
+    Table 2 model is written for a COO SpMV: it counts a row and a column
+    index and one read of x per stored entry, where the CSR kernel here
+    stores no row indices and finds x in L1/L2 after its first read, so that
+    figure exceeds what crosses HBM; the CG and BiCGSTAB runs also carry this
+    library's own byte model (each vector once), the bytes that do."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    A = W.stencil27(128)
+    n, nnz = A[0].size - 1, A[1].size
+    M = gk.Matrix(*[t(a) for a in A], fmt="csr")
+    b = torch.zeros(n, dtype=torch.float64, device=dev)
+    gk.apply(M, t(W.uniform_vector(n, 11)), b)
+    runs = [("cg", 200, {}), ("fcg", 200, {}), ("bicgstab", 100, {}), ("cgs", 100, {}),
+            ("gmres", 200, {"krylov_dim": 100})]
+    out = {}
+    for kind, iters, extra in runs:
+        S = gk.Solver(M, None, kind, max_iters=iters, reduction_factor=1e-300, **extra)
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = gk.solve(S, b, x)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        steps = st.spmvs - 2 if kind in ("bicgstab", "cgs") else st.iters
+        rd, wr = table2_bytes(kind, steps, nnz, n, k=extra.get("krylov_dim", 100))
+        gbs = (rd + wr) / (ms * 1e-3) / 1e9
+        rec = {"iters": st.iters, "spmvs": st.spmvs, "table2_iter": steps, "stop_reason": st.stop_reason,
+               "ms": round(ms, 3), "table2_bytes": int(rd + wr), "table2_GB/s": round(gbs, 1)}
+        if triad_gbs:
+            rec["table2_frac_of_triad"] = round(gbs / triad_gbs, 3)
+        own = None
+        if kind == "cg":
+            own = cg_bytes(st.iters, nnz, n, "none")
+        elif kind == "bicgstab":
+            own = bicgstab_bytes(st.iters, st.spmvs, nnz, n, "none")
+        if own is not None:
+            rec["model_GB/s"] = round(own / (ms * 1e-3) / 1e9, 1)
+            if triad_gbs:
+                rec["model_frac_of_triad"] = round(own / (ms * 1e-3) / 1e9 / triad_gbs, 3)
+        out[kind] = rec
+    del M, b
+    torch.cuda.empty_cache()
+    return {"workload": PAPER_BW_WORKLOAD, "stream_triad_GB/s": triad_gbs,
+            "timing": "CUDA events around gk_solve, the second of two solves", "solvers": out}
+
+
+# ---------------------------------------------------------------------------
 # stream probes (reported beside the step): the library's own reduction
 # kernel against a plain device copy on the same device
 # ---------------------------------------------------------------------------
 
 def run_stream(dev, n=1 << 27):
     """gk_dot over two vectors of n doubles (1 GiB each: larger than L2),
-    against torch's device copy of one of them (read + write bytes); the
-    best of 10 after 3 warm-up runs, CUDA events."""
+    against torch's device copy of one of them (read + write bytes) and the
+    STREAM triad a = b + 0.4 c (the paper's bandwidth reference, Section 7.3);
+    the best of 10 after 3 warm-up runs, CUDA events."""
     import torch
     import paper_2006_16852_gb300 as gk
     x = torch.rand(n, dtype=torch.float64, device=dev)
@@ -880,10 +995,12 @@ def run_stream(dev, n=1 << 27):
 
     dot_ms = best(lambda: gk.dot(x, y, r))
     copy_ms = best(lambda: z.copy_(x))
+    triad_ms = best(lambda: torch.add(y, x, alpha=0.4, out=z))
     hbm = peaks().get("hbm_gbs")
     out = {"vector_doubles": n,
            "gk_dot": {"ms": round(dot_ms, 4), "GB/s": round(16.0 * n / (dot_ms * 1e-3) / 1e9, 1)},
-           "torch_copy": {"ms": round(copy_ms, 4), "GB/s": round(16.0 * n / (copy_ms * 1e-3) / 1e9, 1)}}
+           "torch_copy": {"ms": round(copy_ms, 4), "GB/s": round(16.0 * n / (copy_ms * 1e-3) / 1e9, 1)},
+           "torch_triad": {"ms": round(triad_ms, 4), "GB/s": round(24.0 * n / (triad_ms * 1e-3) / 1e9, 1)}}
     if hbm:
         out["gk_dot"]["frac_of_measured_hbm"] = round(out["gk_dot"]["GB/s"] / hbm, 4)
     del x, y, z
@@ -1079,6 +1196,8 @@ def run_gpu(args):
         out["latency"] = run_latency(dev)
     if not args.no_stream:
         out["stream"] = run_stream(dev)
+        out["paper_bandwidth"] = run_paper_bandwidth(dev, out["stream"]["torch_triad"]["GB/s"])
+    out["paper_context"] = PAPER_CONTEXT
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inp, args.cpu_budget)
     if dist is not None:
@@ -1274,7 +1393,10 @@ def main():
     ap.add_argument("--no-krylov", action="store_true", help="skip the FCG / CGS / GMRES section")
     ap.add_argument("--krylov-only", action="store_true", help="only the FCG / CGS / GMRES section")
     ap.add_argument("--no-latency", action="store_true", help="skip the per-iteration latency section")
-    ap.add_argument("--no-stream", action="store_true", help="skip the stream probes")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="skip the stream probes and the paper's solver-bandwidth experiment")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="only the stream probes and the paper's solver-bandwidth experiment")
     ap.add_argument("--infer-only", type=int, default=0, metavar="B",
                     help="only BF16 inferences of the committed network on a batch of B (profiling)")
     ap.add_argument("--latency-only", action="store_true", help="only the per-iteration latency section")
@@ -1302,6 +1424,14 @@ def main():
         gk.load()
         run = run_krylov if args.krylov_only else run_latency
         out = run(torch.device("cuda:0"))
+    elif args.paper_only:
+        import torch
+        import paper_2006_16852_gb300 as gk
+        gk.load()
+        dev = torch.device("cuda:0")
+        st = run_stream(dev)
+        out = {"stream": st, "paper_bandwidth": run_paper_bandwidth(dev, st["torch_triad"]["GB/s"]),
+               "paper_context": PAPER_CONTEXT}
     elif args.learned_only:
         import torch
         import paper_2006_16852_gb300 as gk

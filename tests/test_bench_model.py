@@ -1,0 +1,62 @@
+"""The benchmark's byte accounting against the paper's Table 2 (Section 7.3).
+
+`tests/golden/table2_memory_volume.txt` restates the table's read and write
+volumes as expressions; this test evaluates them on its own and compares
+them with `bench.table2_bytes` for every solver, on iteration counts that
+are even and odd and GMRES counts below, at and past a restart."""
+import math
+import os
+
+import pytest
+
+import bench
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table2_memory_volume.txt")
+
+
+def _table():
+    rows = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            solver, side, expr = (p.strip() for p in line.split("|"))
+            rows[(solver, side)] = expr
+    return rows
+
+
+def _eval(expr, n, nnz, it_count, k, vt, it):
+    q, r = divmod(it_count, k)
+    env = {"n": n, "nnz": nnz, "VT": vt, "IT": it, "iter": it_count, "k": k, "r": r, "q": q,
+           "iter_r": q * (k - 1) * k / 2 + (r - 1) * r / 2,
+           "ceil2": math.ceil(it_count / 2), "floor2": it_count // 2}
+    return eval(expr, {"__builtins__": {}}, env)
+
+
+def test_golden_has_every_solver():
+    rows = _table()
+    for s in ("cg", "fcg", "bicgstab", "cgs", "gmres"):
+        assert (s, "read") in rows and (s, "write") in rows
+
+
+@pytest.mark.parametrize("solver", ["cg", "fcg", "bicgstab", "cgs", "gmres"])
+@pytest.mark.parametrize("iters", [0, 1, 2, 7, 99, 100, 101, 250])
+@pytest.mark.parametrize("vt,it", [(8, 4), (4, 4), (8, 8)])
+def test_table2_bytes_matches_the_table(solver, iters, vt, it):
+    rows = _table()
+    n, nnz, k = 2_097_152, 55_742_968, 100
+    rd, wr = bench.table2_bytes(solver, iters, nnz, n, vt, it, k=k)
+    assert rd == pytest.approx(_eval(rows[(solver, "read")], n, nnz, iters, k, vt, it), rel=1e-15, abs=1e-6)
+    assert wr == pytest.approx(_eval(rows[(solver, "write")], n, nnz, iters, k, vt, it), rel=1e-15, abs=1e-6)
+
+
+def test_table2_cg_per_iteration_volume():
+    """Per CG iteration the table's volume is 20 n VT + 2 nnz (VT + IT) + 2 VT;
+    the setup is 9 n VT + 2 nnz (VT + IT) + 2 VT."""
+    n, nnz = 1000, 5000
+    t0 = sum(bench.table2_bytes("cg", 0, nnz, n))
+    t1 = sum(bench.table2_bytes("cg", 1, nnz, n))
+    assert t0 == 9 * n * 8 + 2 * nnz * 12 + 16
+    assert t1 - t0 == 20 * n * 8 + 2 * nnz * 12 + 16
+    assert bench.table2_cg_bytes(3, nnz, n) == t0 + 3 * (t1 - t0)

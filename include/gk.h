@@ -85,7 +85,8 @@ extern "C" {
 #define GK_STOP_NONE 0
 #define GK_STOP_CONVERGED 1  /* ||r_k|| <= reduction_factor * ref                       */
 #define GK_STOP_MAX_ITERS 2  /* k >= max_iters (Iteration criterion)                    */
-#define GK_STOP_BREAKDOWN 3  /* p.Ap <= 0 (CG); rho, r^.v or t.t zero (BiCGSTAB)          */
+#define GK_STOP_BREAKDOWN 3  /* p.Ap <= 0 (CG, FCG); rho, r^.v, t.t or omega zero         */
+                             /* (BiCGSTAB); r^.r or r^.v^ zero (CGS)                     */
 #define GK_STOP_NAN 4        /* a residual norm or a reduction became NaN/Inf           */
 #define GK_STOP_TIME 5       /* time_limit_s exceeded (Time criterion)                  */
 
@@ -102,10 +103,11 @@ typedef struct gk_solver_s* gk_solver;
  * the GPU after every iteration); check_every > 0 instead launches the
  * iterations from the host and reads the stop flag back after every
  * check_every iterations.  check_every == 0 (the default) additionally lets
- * GK_CG without a preconditioner or with scalar Jacobi and without a Time
- * criterion run as ONE launch: up to 32,768 rows a 16-CTA thread-block
- * cluster (the direction vector in distributed shared memory, the phases
- * separated by cluster barriers); from 32,769 to 262,144 rows, when no row
+ * GK_CG and GK_BICGSTAB without a preconditioner or with scalar Jacobi and
+ * without a Time criterion run as ONE launch: a 16-CTA thread-block cluster
+ * (the vectors the SpMVs read in distributed shared memory, the phases
+ * separated by cluster barriers) up to 32,768 rows for GK_CG and 16,384 rows
+ * for GK_BICGSTAB; and, for GK_CG from 32,769 to 262,144 rows when no row
  * has more than 64 entries, a cooperative grid of one CTA per SM (grid-wide
  * barriers in global memory).  check_every < 0 always takes the graph. */
 typedef struct {
@@ -141,12 +143,14 @@ typedef struct {
 
 #define GK_FORM_GRAPH 0    /* one CUDA graph, loop controlled on the device            */
 #define GK_FORM_HOST 1     /* iterations launched from the host (check_every > 0)      */
-#define GK_FORM_CLUSTER 2  /* one launch of a 16-CTA thread-block cluster (small CG)   */
+#define GK_FORM_CLUSTER 2  /* one launch of a 16-CTA thread-block cluster (small CG  */
+                           /* and BiCGSTAB)                                           */
 #define GK_FORM_GRID 3     /* one cooperative launch, grid-wide barriers (mid-size CG) */
 
 /* What a solver was built into. */
 typedef struct {
-  int32_t kind;             /* GK_CG, GK_BICGSTAB, GK_IR_CG                       */
+  int32_t kind;             /* GK_CG, GK_BICGSTAB, GK_IR_CG, GK_FCG, GK_CGS,      */
+                            /* GK_GMRES                                            */
   int32_t inner_format;     /* GK_IR_CG: storage of the FP32 operator copy (GK_ELL */
                             /* for ELL/HYB matrices, else GK_CSR)                  */
   int64_t n;

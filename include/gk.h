@@ -431,6 +431,20 @@ GK_API int gk_dot(int64_t n, const double* x, const double* y, double* result, v
  *   - Result, order of summation and arguments as gk_dot. */
 GK_API int gk_dot_noalloc(int64_t n, const double* x, const double* y, double* result, void* stream);
 
+/* ---- failure detection --------------------------------------------------- */
+/* Exercises the failure path of the library's bounded device-side waits (not
+ * in the paper).  Every wait on the GPU -- a thread block waiting for its
+ * bulk copies, the cooperative-grid solver's barriers, the tensor-core
+ * completions -- gives up after about 2 s, sets a device error bit and lets
+ * the kernel return, so a stalled wait ends the call with GK_ERR_TIMEOUT (or
+ * gk_status.device_error) instead of hanging the GPU.  This call launches one
+ * warp that waits, through the same code, on a barrier phase that nothing
+ * completes; it returns after the wait has given up (about 2 s at the
+ * maximum SM clock) with *err_out = the device error word: 1 when the wait
+ * timed out as designed.  The device stays usable afterwards.  Synchronous
+ * on stream; allocates and frees 4 bytes of device memory. */
+GK_API int gk_wait_selftest(int32_t* err_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

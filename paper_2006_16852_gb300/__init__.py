@@ -39,7 +39,7 @@ EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get
            "gk_wsnet_set_loss",
            "gk_wsnet_forward", "gk_wsnet_gradients", "gk_wsnet_train_step", "gk_wsnet_infer_bf16",
            "gk_wsnet_check",
-           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc")
+           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc", "gk_wait_selftest")
 BATCH_CLASSES = 8
 BATCH_BLOCK_SIZES = (32, 64, 128, 256)
 
@@ -145,6 +145,7 @@ def load(path: str | None = None):
         "gk_wsnet_destroy": [vp],
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
+        "gk_wait_selftest": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -363,6 +364,14 @@ def dot_noalloc(x, y, result, stream=None):
     _check_vec(y, n, "y")
     _check(lib().gk_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
     return result
+
+
+def wait_selftest(stream=None) -> int:
+    """Runs one bounded device-side wait that nothing satisfies; returns the
+    device error word it leaves (1: the wait gave up, as designed)."""
+    err = ctypes.c_int32(-1)
+    _check(lib().gk_wait_selftest(ctypes.byref(err), _stream(stream)))
+    return err.value
 
 
 class Batch:

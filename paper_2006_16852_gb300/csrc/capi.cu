@@ -291,3 +291,44 @@ extern "C" int gk_dot_noalloc(int64_t n, const double* x, const double* y, doubl
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gk_wait_selftest: the failure path of the bounded device-side waits.  One
+// warp waits, with the same mbar_wait every bulk-copy consumer uses, on an
+// mbarrier phase that nothing completes (one expected arrival, none made, no
+// copy issued).  The wait gives up at its clock limit, sets kErrTimeout in
+// the error word and the kernel returns, so the context stays usable.
+// ---------------------------------------------------------------------------
+namespace gk {
+
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bar, 0u, threadIdx.x == 0 ? err : nullptr);
+  if (threadIdx.x == 0 && ok) atomicOr(err, 2);  // the phase completed: not expected
+}
+
+}  // namespace gk
+
+extern "C" int gk_wait_selftest(int32_t* err_out, void* stream) {
+  if (!err_out) return set_error(GK_ERR_ARG, "gk_wait_selftest: err_out is null");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  GK_TRY_CUDA(cudaMalloc(&d, sizeof(int)));
+  int h = -1;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_error(e, "gk_wait_selftest");
+  *err_out = h;
+  return GK_OK;
+}

@@ -63,3 +63,4 @@ def test_argument_errors_without_device(libgk):
     assert libgk.gk_solve(None, None, None, None, None) == 1
     assert libgk.gk_matrix_destroy(None) == 1
     assert libgk.gk_dot(-1, None, None, None, None) == 1
+    assert libgk.gk_wait_selftest(None, None) == 1

@@ -199,3 +199,32 @@ def test_powerlaw_full_size_solves(gk, orc):
         ref = (orc.cg if kind == "cg" else orc.bicgstab)(A, b, P=P, tol=1e-10, max_iters=5000)
         slack = max(2, ref.iters * 3 // 100) if kind == "cg" else max(3, ref.iters // 4)
         assert abs(st.iters - ref.iters) <= slack, (kind, st.iters, ref.iters)
+
+
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
+@pytest.mark.parametrize("every", [0, -1])
+def test_reduction_relative_to_initial_residual(gk, orc, kind, every):
+    """ResidualNormReduction against ||r_0|| (Section 2.5's reading, rel_to_b
+    off) from a nonzero x0, in the one-launch form (check_every 0) and the
+    graph (-1): ref is ||b - A x0||, the stop is ||r_k|| <= 1e-8 ||r_0||, and
+    the iteration count follows the oracle's under the same criterion."""
+    A = W.poisson2d(48) if kind == "cg" else W.convdiff2d(40, wind=1.0)
+    n = A[0].size - 1
+    xs = W.uniform_vector(n, 21)
+    b = orc.spmv(A, xs)
+    x0 = xs + 0.1 * W.uniform_vector(n, 22)
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]))
+    S = gk.Solver(M, gk.Precond(M, 1), kind, max_iters=3000, reduction_factor=1e-8, rel_to_b=False,
+                  check_every=every)
+    x = to_dev(x0.copy())
+    st = gk.solve(S, to_dev(b), x)
+    r0 = np.linalg.norm(b - orc.spmv(A, x0))
+    assert st.stop_reason == gk.STOP_CONVERGED
+    assert abs(st.ref_norm - r0) <= 1e-12 * r0
+    assert st.rel_res <= 1e-8 and st.rel_res_true <= 1.5e-8
+    P = orc.precond(A, "jacobi")
+    ref = (orc.cg if kind == "cg" else orc.bicgstab)(A, b, x0=x0, P=P, tol=1e-8, max_iters=3000, rel_to_b=False)
+    slack = max(2, ref.iters * 3 // 100) if kind == "cg" else max(3, ref.iters // 4)
+    assert abs(st.iters - ref.iters) <= slack, (st.iters, ref.iters)
+    if every == 0:
+        assert st.form == gk.FORM_CLUSTER

@@ -60,3 +60,34 @@ def test_table2_cg_per_iteration_volume():
     assert t0 == 9 * n * 8 + 2 * nnz * 12 + 16
     assert t1 - t0 == 20 * n * 8 + 2 * nnz * 12 + 16
     assert bench.table2_cg_bytes(3, nnz, n) == t0 + 3 * (t1 - t0)
+
+
+def test_spmv_bytes_of_the_benchmark_matrix():
+    """The 27-point matrix on 128^3: nnz (8 + 4) + (n + 1) 4 + 8 n (x, read
+    once) + 8 n (y) = 710.9 MB; with the fused dot's second vector, 727.6 MB
+    (the roofline kernel's algorithmic bytes per launch)."""
+    n, nnz = 128 ** 3, 55_742_968
+    assert bench.spmv_bytes(nnz, n, n) == 710_858_660
+    assert bench.spmv_bytes(nnz, n, n) + 8 * n == 727_635_876
+
+
+@pytest.mark.parametrize("prec,bs,vec", [("none", 1, 72), ("jacobi", 1, 88), ("block", 8, 80 + 8 * 8),
+                                         ("block", 32, 80 + 8 * 32)])
+def test_cg_bytes_per_iteration(prec, bs, vec):
+    """Per CG iteration the model moves one SpMV plus the fused vector
+    kernels' bytes: 72 n unpreconditioned, 88 n with scalar Jacobi,
+    80 n + 8 bs n with block Jacobi (the inverse blocks once)."""
+    n, nnz = 1000, 27_000
+    per = bench.cg_bytes(1, nnz, n, prec, bs) - bench.cg_bytes(0, nnz, n, prec, bs)
+    assert per == bench.spmv_bytes(nnz, n, n) + vec * n
+    assert bench.cg_bytes(5, nnz, n, prec, bs) - bench.cg_bytes(0, nnz, n, prec, bs) == 5 * per
+
+
+def test_bicgstab_bytes_half_step_is_cheaper():
+    """A BiCGSTAB iteration that ends at its half step does one SpMV instead
+    of two: with the same iteration count, one SpMV fewer means fewer bytes."""
+    n, nnz = 1000, 5000
+    full = bench.bicgstab_bytes(10, 2 + 20, nnz, n, "jacobi")
+    half = bench.bicgstab_bytes(10, 2 + 19, nnz, n, "jacobi")
+    assert half < full
+    assert full - half >= bench.spmv_bytes(nnz, n, n)

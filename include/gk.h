@@ -72,7 +72,8 @@ extern "C" {
 #define GK_CSR_MERGE 1  /* CSR, merge-path split of rows+nonzeros into equal tiles      */
 #define GK_ELL 2        /* ELLPACK, column-major, padded to the longest row             */
 #define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows */
-#define GK_AUTO 4       /* GK_CSR for regular row lengths, GK_CSR_MERGE otherwise       */
+#define GK_AUTO 4       /* GK_CSR when at least 75 % of its slots (length-sorted slices,
+                           warp and block rows) hold stored entries, else GK_CSR_MERGE */
 
 #define GK_CG 0
 #define GK_BICGSTAB 1

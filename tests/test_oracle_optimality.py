@@ -1,0 +1,85 @@
+"""Pins of the oracle's CG and GMRES to the property that defines each
+method, checked by brute force on small dense problems (no recurrence of the
+methods is retyped here):
+
+* CG after j steps (x0 = 0) is the point of the Krylov space
+  K_j(M^-1 A, M^-1 b) with the least A-norm error (the Galerkin condition
+  Q^T (b - A x_j) = 0 on an orthonormal basis Q of that space);
+* GMRES after j < m steps with right preconditioning (x0 = 0) is
+  x_j = M^-1 u_j, where u_j in K_j(A M^-1, b) minimises ||b - A M^-1 u||.
+
+The Krylov spaces come from numpy QR of the power basis; the optimum from a
+dense solve or least squares."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _csr(D):
+    rows, cols = np.nonzero(D)
+    rowptr = np.zeros(D.shape[0] + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows, minlength=D.shape[0]), out=rowptr[1:])
+    return rowptr, cols.astype(np.int32), D[rows, cols].astype(np.float64)
+
+
+def _krylov_basis(B, v, j):
+    K = np.empty((v.size, j))
+    K[:, 0] = v / np.linalg.norm(v)
+    for i in range(1, j):
+        w = B @ K[:, i - 1]
+        K[:, i] = w / np.linalg.norm(w)
+    Q, _ = np.linalg.qr(K)
+    return Q
+
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.linspace(1.0, 12.0, n)
+    D = (Q * lam) @ Q.T
+    D = (D + D.T) / 2
+    s = np.exp(rng.uniform(-1, 1, n))       # uneven diagonal, so Jacobi matters
+    return D * np.outer(s, s)
+
+
+@pytest.mark.parametrize("prec", ["none", "jacobi"])
+@pytest.mark.parametrize("j", [1, 2, 3, 5, 7])
+def test_cg_is_the_a_norm_optimum_of_its_krylov_space(orc, prec, j):
+    n = 40
+    D = _spd(n, 3)
+    A = _csr(D)
+    b = W.uniform_vector(n, 4)
+    Minv = np.diag(1.0 / np.diag(D)) if prec == "jacobi" else np.eye(n)
+    r = orc.cg(A, b, P=orc.precond(A, prec), max_iters=j, tol=1e-300)
+    assert r.iters == j
+    Q = _krylov_basis(Minv @ D, Minv @ b, j)
+    y = np.linalg.solve(Q.T @ D @ Q, Q.T @ b)
+    x_opt = Q @ y
+    xs = np.linalg.solve(D, b)
+    err = lambda x: np.sqrt((x - xs) @ D @ (x - xs))
+    assert np.linalg.norm(r.x - x_opt) <= 1e-9 * np.linalg.norm(x_opt)
+    assert err(r.x) <= err(x_opt) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("prec", ["none", "jacobi"])
+@pytest.mark.parametrize("j", [1, 2, 4, 6, 9])
+def test_gmres_is_the_minimal_residual_of_its_krylov_space(orc, prec, j):
+    A = W.convdiff2d(6, wind=1.5)                 # nonsymmetric, n = 36
+    D = W.csr_to_dense(A)
+    n = D.shape[0]
+    rng = np.random.default_rng(5)
+    D = D * np.exp(rng.uniform(-0.5, 0.5, n))[:, None]   # uneven row scaling
+    A = _csr(D)
+    b = W.uniform_vector(n, 6)
+    Minv = np.diag(1.0 / np.diag(D)) if prec == "jacobi" else np.eye(n)
+    r = orc.gmres(A, b, P=orc.precond(A, prec), max_iters=j, tol=1e-300, krylov_dim=30)
+    assert r.iters == j
+    AM = D @ Minv
+    Q = _krylov_basis(AM, b, j)
+    y, *_ = np.linalg.lstsq(AM @ Q, b, rcond=None)
+    x_opt = Minv @ (Q @ y)
+    res_opt = np.linalg.norm(b - D @ x_opt)
+    res = np.linalg.norm(b - D @ r.x)
+    assert abs(res - res_opt) <= 1e-9 * np.linalg.norm(b)
+    assert np.linalg.norm(r.x - x_opt) <= 1e-8 * np.linalg.norm(x_opt)

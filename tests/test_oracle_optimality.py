@@ -83,3 +83,39 @@ def test_gmres_is_the_minimal_residual_of_its_krylov_space(orc, prec, j):
     res = np.linalg.norm(b - D @ r.x)
     assert abs(res - res_opt) <= 1e-9 * np.linalg.norm(b)
     assert np.linalg.norm(r.x - x_opt) <= 1e-8 * np.linalg.norm(x_opt)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_cgs_residual_is_the_squared_cg_polynomial(orc, k):
+    """On SPD A with r^ = r_0 = b, BiCG's residual polynomial phi_k is CG's,
+    and CGS's residual after k steps is phi_k(A)^2 b (Sonneveld 1989).
+    phi_k(t) = 1 - t p(t), with x_k = p(A) b CG's A-norm optimum over
+    K_k(A, b) (computed here by brute force, as above)."""
+    n = 30
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    D = (Q * np.linspace(1.0, 4.0, n)) @ Q.T
+    D = (D + D.T) / 2
+    A = _csr(D)
+    b = W.uniform_vector(n, 9)
+    Kb = _krylov_basis(D, b, k)
+    x_cg = Kb @ np.linalg.solve(Kb.T @ D @ Kb, Kb.T @ b)
+    P = np.empty((n, k))                      # the power basis b, A b, ..., A^(k-1) b
+    P[:, 0] = b
+    for i in range(1, k):
+        P[:, i] = D @ P[:, i - 1]
+    c, *_ = np.linalg.lstsq(P, x_cg, rcond=None)
+
+    def phi(v):
+        pv = np.zeros(n)
+        w = v.copy()
+        for i in range(k):
+            pv += c[i] * w
+            w = D @ w
+        return v - D @ pv
+
+    r = orc.cgs(A, b, max_iters=k, tol=1e-300)
+    assert r.iters == k
+    res = b - D @ r.x
+    want = phi(phi(b))
+    assert np.linalg.norm(res - want) <= 1e-8 * np.linalg.norm(b)

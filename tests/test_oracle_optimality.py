@@ -119,3 +119,39 @@ def test_cgs_residual_is_the_squared_cg_polynomial(orc, k):
     res = b - D @ r.x
     want = phi(phi(b))
     assert np.linalg.norm(res - want) <= 1e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_bicgstab_residual_from_cg_polynomials_and_local_minimisation(orc, k):
+    """On SPD A with r^ = r_0 = b, BiCGSTAB's residual after k steps is
+    psi_k(A) phi_k(A) b (van der Vorst 1992): phi_k is CG's residual
+    polynomial (brute force, as above) and psi_k(t) = prod_i (1 - omega_i t),
+    each omega_i minimising ||s_i - omega A s_i|| for
+    s_i = psi_{i-1}(A) phi_i(A) b.  Rebuilt here from those definitions."""
+    n = 30
+    rng = np.random.default_rng(10)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    D = (Q * np.linspace(1.0, 4.0, n)) @ Q.T
+    D = (D + D.T) / 2
+    A = _csr(D)
+    b = W.uniform_vector(n, 11)
+
+    def phi_b(i):
+        Kb = _krylov_basis(D, b, i)
+        x_cg = Kb @ np.linalg.solve(Kb.T @ D @ Kb, Kb.T @ b)
+        return b - D @ x_cg                   # phi_i(A) b = the CG residual
+
+    omegas = []
+    r_want = None
+    for i in range(1, k + 1):
+        s = phi_b(i)
+        for w in omegas:                      # psi_{i-1}(A) phi_i(A) b
+            s = s - w * (D @ s)
+        t = D @ s
+        w = (t @ s) / (t @ t)
+        omegas.append(w)
+        r_want = s - w * t
+    r = orc.bicgstab(A, b, max_iters=k, tol=1e-300)
+    assert r.iters == k
+    res = b - D @ r.x
+    assert np.linalg.norm(res - r_want) <= 1e-8 * np.linalg.norm(b)

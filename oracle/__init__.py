@@ -1,4 +1,6 @@
-"""Sequential CPU oracle for the sparse linear-operator hot path.
+"""CPU oracle for the sparse linear-operator hot path (sequential but for the
+SpMV row loops, which OpenMP may split over threads without changing any
+result).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``.  The product library never imports,
@@ -34,8 +36,10 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+           "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    if subprocess.run(cmd).returncode != 0:
+        # no OpenMP runtime: the same source, sequential
+        subprocess.run([c for c in cmd if c != "-fopenmp"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -69,6 +73,8 @@ def lib():
         L.or_csr_spmv.restype = None
         L.or_csr_spmv_dot2.argtypes = [i64, vp, vp, vp, vp, vp, vp]
         L.or_csr_spmv_dot2.restype = None
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_set_threads.restype = ctypes.c_int
         L.or_dot.argtypes = [i64, vp, vp]
         L.or_dot.restype = f64
         L.or_norm2.argtypes = [i64, vp]
@@ -135,6 +141,11 @@ def spmv_accurate(A, x):
     b = np.zeros(n)
     lib().or_csr_spmv_dot2(n, _p(rowptr), _p(col), _p(val), _p(x), _p(y), _p(b))
     return y, b
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the SpMV row loops (0: all cores); returns the count in effect."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def dot(x, y):

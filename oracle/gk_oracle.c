@@ -8,6 +8,10 @@
  */
 #include "gk_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -21,14 +25,32 @@
  * Row sum: s = 0; for k in increasing order, s = fma(a_ik, b_k, s).
  * beta == 0 does not read the old output (BLAS convention), so a NaN there
  * does not propagate; otherwise the result is fma(beta, y_old, alpha*s). */
+/* Rows are independent and each row's sum runs in increasing k whatever
+ * thread takes the row, so splitting the rows over threads (OpenMP, static
+ * chunks) leaves every result bit unchanged; the dot products and the
+ * solvers' vector steps stay sequential. */
 void or_csr_spmv(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
                  const double* x, double alpha, double beta, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n_rows; ++i) {
     double s = 0.0;
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], x[col[k]], s);
     double as = alpha * s;
     y[i] = (beta == 0.0) ? as : fma(beta, y[i], as);
   }
+}
+
+/* Threads the row loops of the SpMVs may use (<= 0: all the host's cores);
+ * returns the number they will use.  1 when built without OpenMP. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n <= 0) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* Error-free transformations (Ogita, Rump, Oishi, "Accurate sum and dot
@@ -50,6 +72,7 @@ static void two_prod(double a, double b, double* p, double* e) {
 
 void or_csr_spmv_dot2(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
                       const double* x, double* y_acc, double* abs_ax) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n_rows; ++i) {
     double p = 0.0, s = 0.0, bound = 0.0;
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {

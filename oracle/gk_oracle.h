@@ -1,5 +1,5 @@
 /*
- * gk_oracle.h -- plain, slow, sequential CPU oracle for the sparse
+ * gk_oracle.h -- plain, slow CPU oracle for the sparse
  * linear-operator hot path of "Ginkgo: A Modern Linear Operator Algebra
  * Framework for High Performance Computing" (arXiv:2006.16852).
  *
@@ -7,6 +7,11 @@
  * or calls this code; only the tests, the smoke check and the benchmark's
  * CPU baseline do.  It shares no code, header, table or helper with the CUDA
  * path.
+ *
+ * Everything is sequential except the row loops of the two SpMVs, which
+ * OpenMP may split over threads (static chunks): each row's sum is still
+ * formed in increasing k by one thread, so no result depends on the thread
+ * count.
  *
  * Conventions: FP64 values, int32 column indices and row pointers, int64
  * sizes.  Every floating-point step is written in the order the definition
@@ -67,6 +72,11 @@ typedef struct {
 /* x = alpha*A*b + beta*x (Section 4.2, simple and advanced apply). */
 void or_csr_spmv(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,
                  const double* x, double alpha, double beta, double* y);
+
+/* Threads the SpMV row loops use (OpenMP, static chunks; results are the
+ * same for any count).  n <= 0: all the host's cores.  Returns the count in
+ * effect, 1 without OpenMP. */
+int or_set_threads(int n);
 
 /* Accurate row sums by Dot2 (Ogita, Rump, Oishi 2005) and the bound (|A||x|)_i. */
 void or_csr_spmv_dot2(int64_t n_rows, const int32_t* rowptr, const int32_t* col, const double* val,

@@ -91,3 +91,20 @@ def test_bicgstab_bytes_half_step_is_cheaper():
     half = bench.bicgstab_bytes(10, 2 + 19, nnz, n, "jacobi")
     assert half < full
     assert full - half >= bench.spmv_bytes(nnz, n, n)
+
+
+def test_spmv_bytes_per_format():
+    """The stored operator's bytes follow the format: CSR reads row pointers,
+    ELL does not (nnz (VT + IT) + 2 n VT: 702.5 MB on the 27-point matrix,
+    719.2 MB with the fused dot's second vector -- the roofline kernel's
+    algorithmic bytes per launch), and HYB's COO part carries a row index
+    per entry (nnz_ell (VT + IT) + nnz_coo (VT + 2 IT) + 2 n VT)."""
+    n, nnz = 128 ** 3, 55_742_968
+    assert bench.spmv_bytes(nnz, n, n, fmt="ell") == nnz * 12 + 16 * n == 702_470_048
+    assert bench.spmv_bytes(nnz, n, n, fmt="ell") + 8 * n == 719_247_264
+    assert bench.spmv_bytes(nnz, n, n, fmt="csr_merge") == bench.spmv_bytes(nnz, n, n)
+    assert bench.spmv_bytes(1000, 100, 100, fmt="hyb", tail_nnz=300) == 700 * 12 + 300 * 16 + 1600
+    assert bench.spmv_bytes(1000, 100, 100, fmt="hyb", tail_nnz=0) == bench.spmv_bytes(1000, 100, 100, fmt="ell")
+    # a CG iteration carries the format's SpMV
+    d = bench.cg_bytes(1, nnz, n, "jacobi", fmt="ell") - bench.cg_bytes(0, nnz, n, "jacobi", fmt="ell")
+    assert d == bench.spmv_bytes(nnz, n, n, fmt="ell") + 88 * n

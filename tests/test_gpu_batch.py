@@ -250,19 +250,34 @@ def test_batch_every_block_size_matches_oracle(gk, orc, kind, threads):
         B.set_threads([48] * gk.BATCH_CLASSES)
 
 
+@pytest.mark.parametrize("kind", ["cg", "bicgstab"])
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-6)])
-def test_batch_full_size_sampled(gk, orc, dtype, tol):
-    """10,000 systems, side U{6..32}: every system converges; a sample is
-    checked against the oracle one by one."""
+def test_batch_full_size_sampled(gk, orc, dtype, tol, kind):
+    """The benchmark's batched workload at full size (10,000 systems, side
+    U{6..32}, b seed 28) in every benchmark form of CG and BiCGSTAB: every
+    system converges (the oracle converges on all of them), and a sample --
+    12 random systems plus the largest and the smallest -- is checked
+    against the oracle one by one at the batched parity bar."""
     sys_ptr, A = W.batch_varcoef2d(10000, seed=5)
     b = W.uniform_vector(int(sys_ptr[-1]), 28)
-    st, x = _run(gk, sys_ptr, A, b, "cg", True, dtype, tol)
-    assert np.all(st["stop_reason"] == gk.STOP_CONVERGED)
+    st, x = _run(gk, sys_ptr, A, b, kind, True, dtype, tol, max_iters=20000)
+    bad = np.flatnonzero(st["stop_reason"] != gk.STOP_CONVERGED)
+    assert bad.size == 0, [(int(s), int(st["stop_reason"][s]), int(st["iters"][s])) for s in bad[:5]]
     assert st["rel_res"].max() <= tol
-    sample = list(np.random.default_rng(0).choice(10000, 12, replace=False))
-    xo, res = orc.batch_solve(sys_ptr, A, b, kind="cg", jacobi=True, dtype=dtype, tol=tol, systems=sample)
+    sizes = np.diff(sys_ptr)
+    sample = sorted(set(int(s) for s in np.random.default_rng(0).choice(10000, 12, replace=False))
+                    | {int(np.argmax(sizes)), int(np.argmin(sizes))})
+    xo, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, dtype=dtype, tol=tol, systems=sample,
+                              max_iters=20000)
     for s, r in zip(sample, res):
         r0, r1 = sys_ptr[s], sys_ptr[s + 1]
-        assert abs(int(st["iters"][s]) - r.iters) <= (1 if dtype == "f64" else 2 + r.iters // 20)
+        assert r.stop_reason == gk.STOP_CONVERGED
+        if kind == "cg":
+            slack = 1 if dtype == "f64" else 2 + r.iters // 20
+        else:
+            slack = max(3, r.iters // 4) if dtype == "f64" else max(5, r.iters // 4)
+        assert abs(int(st["iters"][s]) - r.iters) <= slack, (s, int(st["iters"][s]), r.iters)
         err = np.linalg.norm(x[r0:r1] - xo[r0:r1]) / np.linalg.norm(xo[r0:r1])
-        assert err <= (1e-6 if dtype == "f64" else 2e-3)
+        assert err <= (1e-6 if dtype == "f64" else 2e-3), (s, err)
+    if dtype == "f64":
+        assert _true_rel(orc, sys_ptr, A, b, x).max() <= 3e-10

@@ -228,3 +228,69 @@ def test_reduction_relative_to_initial_residual(gk, orc, kind, every):
     assert abs(st.iters - ref.iters) <= slack, (st.iters, ref.iters)
     if every == 0:
         assert st.form == gk.FORM_CLUSTER
+
+
+# The benchmark step's solves on (a), the 27-point stencil on 128^3: format,
+# preconditioner (block size, 0 = none) and method, exactly as the step runs
+# them, each against the oracle's run of the same method.
+STEP_SOLVES_A = {
+    "cg_plain_csr": ("csr", 0, "cg"),
+    "cg_jacobi_ell": ("ell", 1, "cg"),
+    "cg_bj8_ell": ("ell", 8, "cg"),
+    "ircg_jacobi_ell": ("ell", 1, "ir_cg"),
+    "ircg_bj8_ell": ("ell", 8, "ir_cg"),
+}
+
+
+@pytest.fixture(scope="module")
+def stencil27_full(orc):
+    """(a) with the benchmark's right-hand side b = A x*, x* uniform (seed 4),
+    and kappa from the closed-form spectrum 27 - prod_d (1 + 2 cos(k_d pi/129))."""
+    N = 128
+    A = W.stencil27(N)
+    xs = W.uniform_vector(N ** 3, 4)
+    b = orc.spmv(A, xs)
+    c = 1 + 2 * math.cos(math.pi / (N + 1))
+    kappa = (27 + c * c) / (27 - c ** 3)
+    return {"A": A, "xs": xs, "b": b, "kappa": kappa, "mats": {}}
+
+
+@pytest.mark.parametrize("name", list(STEP_SOLVES_A))
+def test_stencil27_full_size_step_solves_match_oracle(gk, orc, stencil27_full, name):
+    """Every solve of the benchmark step on (a) at its full size (n =
+    2,097,152, nnz = 55,742,968), in the step's format and preconditioner,
+    to 1e-10 against the oracle: the same stop reason; iterations within
+    max(2, 3 %) (CG), or refinement steps within 1 and inner iterations no
+    more than the oracle's + max(5, 1/8) (refinement: see below); the true residual <= 1.5e-10 by the oracle's SpMV; and the
+    solution within kappa * 2e-10 of the oracle's and of x*."""
+    D = stencil27_full
+    A, b, xs, kappa = D["A"], D["b"], D["xs"], D["kappa"]
+    fmt, bs, kind = STEP_SOLVES_A[name]
+    n = A[0].size - 1
+    if fmt not in D["mats"]:
+        D["mats"][fmt] = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt=fmt)
+    M = D["mats"][fmt]
+    S = gk.Solver(M, gk.Precond(M, bs) if bs else None, kind, max_iters=5000, reduction_factor=1e-10)
+    xt = to_dev(np.zeros(n))
+    st = gk.solve(S, to_dev(b), xt)
+    x = to_np(xt)
+    P = orc.precond(A, {0: "none", 1: "jacobi", 8: "block_jacobi"}[bs], max(bs, 1))
+    if kind == "cg":
+        ref = orc.cg(A, b, P=P, tol=1e-10, max_iters=5000)
+        assert _iters_close(st.iters, ref.iters), (name, st.iters, ref.iters)
+    else:
+        # The oracle sums the FP32 inner dot products sequentially; over n =
+        # 2,097,152 terms that sum's error reaches ~n u_32 of the sum of
+        # magnitudes, which slows its FP32 CG (347 inner iterations with
+        # Jacobi), while the GPU's blocked tree sums converge like FP32 CG
+        # with accurate sums (263; a copy of the oracle with 1024-term
+        # blocked float sums also takes 263).  So the inner count may be
+        # lower than the oracle's, not higher.
+        ref, outer = orc.ir_cg(A, b, P=P, tol=1e-10)
+        assert abs(st.outer_iters - outer) <= 1, (name, st.outer_iters, outer)
+        assert ref.iters // 2 <= st.iters <= ref.iters + max(5, ref.iters // 8), (name, st.iters, ref.iters)
+    assert st.stop_reason == gk.STOP_CONVERGED == ref.stop_reason, name
+    assert st.rel_res_true <= 1.5e-10, name
+    assert np.linalg.norm(b - orc.spmv(A, x)) <= 1.5e-10 * np.linalg.norm(b), name
+    assert np.linalg.norm(x - ref.x) <= kappa * 2e-10 * np.linalg.norm(ref.x), name
+    assert np.linalg.norm(x - xs) <= kappa * 2e-10 * np.linalg.norm(xs), name

@@ -147,8 +147,11 @@ def test_empty_matrix(gk):
 @pytest.mark.parametrize("fmt", ["csr", "csr_merge", "hyb", "ell"])
 @pytest.mark.parametrize("which", ["stencil27_128", "powerlaw_1M"])
 def test_full_size_sampled_rows(gk, orc, big_mats, fmt, which):
-    """The benchmark's sizes and launch shapes: every row against the Dot2
-    bound computed on a sample of 4000 rows (plus the first and last)."""
+    """The benchmark's sizes and launch shapes: rows against the Dot2 bound
+    on a sample of 4000 random rows, the first and last, and every row with
+    more than 256 entries -- all rows of GK_CSR's warp-per-row (257..4096)
+    and block-per-row (> 4096) bins, which are also the rows that the
+    merge-path tiles and the HYB overflow split."""
     A = big_mats[which]
     n = A[0].size - 1
     if fmt == "ell" and which == "powerlaw_1M":
@@ -161,7 +164,12 @@ def test_full_size_sampled_rows(gk, orc, big_mats, fmt, which):
     gk.apply(M, to_dev(x), y)
     y = to_np(y)
     rng = np.random.default_rng(12)
-    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 4000)]))
+    lens_all = np.diff(A[0])
+    long_rows = np.flatnonzero(lens_all > 256)
+    if which == "powerlaw_1M":
+        # the sample must reach both long-row bins
+        assert long_rows.size > 1000 and (lens_all > 4096).any()
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 4000), long_rows]))
     S = sub_rows(A, rows)
     y_acc, bnd = orc.spmv_accurate(S, x)
     assert_rows_within(y[rows], y_acc, bnd, 1e-13, f"{which}/{fmt}")

@@ -375,3 +375,23 @@ def test_hyb_width_closed_forms(orc):
     np.cumsum(lens, out=rowptr[1:])
     col = np.concatenate([np.arange(l) for l in lens])
     assert orc.hyb_width((rowptr, col, np.ones(col.size))) == 2
+
+
+def test_spmv_thread_count_changes_no_bit(orc):
+    """The SpMV row loops may run on several threads: each row is still
+    summed in increasing k by one thread, so y and a solve that uses the
+    SpMV are bit-identical on one thread and on all of them."""
+    A = W.powerlaw(20000, seed=3)
+    n = A[0].size - 1
+    x = W.uniform_vector(n, 5)
+    try:
+        orc.set_threads(1)
+        y1 = orc.spmv(A, x)
+        r1 = orc.cg(A, y1, P=orc.precond(A, "jacobi"), tol=1e-10)
+        orc.set_threads(0)
+        yn = orc.spmv(A, x)
+        rn = orc.cg(A, yn, P=orc.precond(A, "jacobi"), tol=1e-10)
+    finally:
+        orc.set_threads(0)
+    assert np.array_equal(y1, yn)
+    assert r1.iters == rn.iters and np.array_equal(r1.x, rn.x)

@@ -80,15 +80,29 @@ SPMV_REPS = 3
 
 # ---------------------------------------------------------------------------
 # algorithmic byte model (value 8 B, index 4 B; a gathered vector is counted
-# once, as if it stayed in L2 after its first use)
+# once, as if it stayed in L2 after its first use; padding is not counted).
+# The stored operator's bytes depend on the format:
+#   CSR (binned and merge-path): nnz (VT + IT) + (n + 1) IT
+#   ELL:                          nnz (VT + IT)
+#   HYB:                          nnz_ell (VT + IT) + nnz_coo (VT + 2 IT)
 # ---------------------------------------------------------------------------
 
-def spmv_bytes(nnz, n_rows, n_cols, beta=False):
-    return nnz * 12 + (n_rows + 1) * 4 + n_cols * 8 + n_rows * 8 + (n_rows * 8 if beta else 0)
+def matrix_bytes(nnz, n_rows, fmt="csr", tail_nnz=0, vt=8, it=4):
+    if fmt in ("csr", "csr_merge"):
+        return nnz * (vt + it) + (n_rows + 1) * it
+    if fmt == "ell":
+        return nnz * (vt + it)
+    if fmt == "hyb":
+        return (nnz - tail_nnz) * (vt + it) + tail_nnz * (vt + 2 * it)
+    raise ValueError(fmt)
 
 
-def resid_bytes(nnz, n):  # r = b - A x with ||r||, ||b||
-    return spmv_bytes(nnz, n, n) + 8 * n
+def spmv_bytes(nnz, n_rows, n_cols, beta=False, fmt="csr", tail_nnz=0):
+    return matrix_bytes(nnz, n_rows, fmt, tail_nnz) + n_cols * 8 + n_rows * 8 + (n_rows * 8 if beta else 0)
+
+
+def resid_bytes(nnz, n, fmt="csr", tail_nnz=0):  # r = b - A x with ||r||, ||b||
+    return spmv_bytes(nnz, n, n, fmt=fmt, tail_nnz=tail_nnz) + 8 * n
 
 
 def prec_extra(prec, bs):
@@ -100,40 +114,43 @@ def prec_extra(prec, bs):
     return 8 * bs
 
 
-def cg_bytes(iters, nnz, n, prec="none", bs=1):
+def cg_bytes(iters, nnz, n, prec="none", bs=1, fmt="csr", tail_nnz=0):
     pe = prec_extra(prec, bs)
-    setup = resid_bytes(nnz, n) + (16 + pe) * n
+    rb = resid_bytes(nnz, n, fmt, tail_nnz)
+    setup = rb + (16 + pe) * n
     z_store = 8 if prec == "block" else 0
     # K1: SpMV q = A p (p.q in the epilogue); K2: x, p, q, r (+M) in, x, r (+z) out;
     # K3: p, r or z (+dinv) in, p out
     k2 = (32 + pe + 16 + z_store) * n
     k3 = (24 + (8 if prec == "jacobi" else 0)) * n
-    per_it = spmv_bytes(nnz, n, n) + k2 + k3
-    return setup + iters * per_it + resid_bytes(nnz, n)
+    per_it = spmv_bytes(nnz, n, n, fmt=fmt, tail_nnz=tail_nnz) + k2 + k3
+    return setup + iters * per_it + rb
 
 
-def bicgstab_bytes(iters, spmvs, nnz, n, prec="none", bs=1):
+def bicgstab_bytes(iters, spmvs, nnz, n, prec="none", bs=1, fmt="csr", tail_nnz=0):
     pe = prec_extra(prec, bs)
     hat = 0 if prec == "none" else 8
     full = (spmvs - 2 - iters)  # SpMVs of full iterations beyond one per iteration
     half = iters - full         # iterations that ended at the half step
-    setup = resid_bytes(nnz, n) + 32 * n
+    rb = resid_bytes(nnz, n, fmt, tail_nnz)
+    sb = spmv_bytes(nnz, n, n, fmt=fmt, tail_nnz=tail_nnz)
+    setup = rb + 32 * n
     k1 = (24 + pe + 8 + hat) * n
     k3 = (16 + pe + 8 + hat) * n
     k5 = 64 * n
-    full_it = 2 * spmv_bytes(nnz, n, n) + 16 * n + k1 + k3 + k5
-    half_it = spmv_bytes(nnz, n, n) + 8 * n + k1 + k3 + 40 * n
-    return setup + full * full_it + half * half_it + resid_bytes(nnz, n)
+    full_it = 2 * sb + 16 * n + k1 + k3 + k5
+    half_it = sb + 8 * n + k1 + k3 + 40 * n
+    return setup + full * full_it + half * half_it + rb
 
 
-def ir_bytes(inner, outer, nnz, n, prec="none", bs=1, fp16_frac=0.0):
-    """FP64 refinement around an FP32 CG inner solve (GK_IR_CG) on an ELL copy.
+def ir_bytes(inner, outer, nnz, n, prec="none", bs=1, fp16_frac=0.0, fmt="csr", tail_nnz=0):
+    """FP64 refinement around an FP32 CG inner solve (GK_IR_CG).
 
     Outer step: r = b - A x in FP64 (SpMV + b), the start of the inner solve
     (r64 in; r32, d32, p32 out; M), and x += ||r|| d (x in/out, d in).  Inner
-    iteration: FP32 SpMV (8 bytes per entry, x and y in FP32), update (d, p,
-    q, r, M in; d, r out), direction (p, r or z, M in; p out).  Block-Jacobi
-    blocks cost 2 (FP16) or 4 (FP32) bytes per entry."""
+    iteration: FP32 SpMV (FP32 values, the same indices, x and y in FP32),
+    update (d, p, q, r, M in; d, r out), direction (p, r or z, M in; p out).
+    Block-Jacobi blocks cost 2 (FP16) or 4 (FP32) bytes per entry."""
     if prec == "none":
         pe = 0.0
     elif prec == "jacobi":
@@ -141,14 +158,44 @@ def ir_bytes(inner, outer, nnz, n, prec="none", bs=1, fp16_frac=0.0):
     else:
         pe = bs * (2.0 * fp16_frac + 4.0 * (1.0 - fp16_frac))
     z_store = 4.0 if prec == "block" else 0.0
-    spmv32 = nnz * 8 + (n + 1) * 4 + n * 4 + n * 4
+    spmv32 = matrix_bytes(nnz, n, fmt, tail_nnz, vt=4) + n * 4 + n * 4
     per_inner = spmv32 + (16 + pe + 8 + z_store) * n + (12 + (4 if prec == "jacobi" else 0)) * n
-    per_outer = resid_bytes(nnz, n) + (8 + 12 + pe) * n + 20 * n
-    return int(outer * per_outer + inner * per_inner + resid_bytes(nnz, n))
+    rb = resid_bytes(nnz, n, fmt, tail_nnz)
+    per_outer = rb + (8 + 12 + pe) * n + 20 * n
+    return int(outer * per_outer + inner * per_inner + rb)
 
 
-def precond_bytes(nnz, n, bs):
-    return nnz * 12 + (n + 1) * 4 + 8 * n * (1 if bs == 1 else bs)
+def bj_out_elems(n, bs):
+    """Doubles of the generated preconditioner: n (scalar) or the inverse blocks."""
+    if bs == 1:
+        return n
+    full, last = divmod(n, bs)
+    return full * bs * bs + last * last
+
+
+def in_block_entries(A, bs):
+    """Stored entries of A inside its diagonal blocks of bs rows (the diagonal for bs = 1)."""
+    rowptr, col, _ = A
+    rows = np.repeat(np.arange(rowptr.size - 1, dtype=np.int64), np.diff(rowptr))
+    return int(np.count_nonzero(rows // bs == col.astype(np.int64) // bs))
+
+
+def precond_bytes(n, bs, in_block):
+    """Preconditioner generation: the row pointers, one 32-byte sector of
+    column indices per row for the binary search that locates the row's
+    entries inside its block (they are a contiguous run of the sorted
+    columns), those entries (value + index), and the inverse written."""
+    return (n + 1) * 4 + 32 * n + in_block * 12 + 8 * bj_out_elems(n, bs)
+
+
+def precond_fp64_ops(n, bs):
+    """FP64 operation slots of the generation: bs^3 - bs multiply-adds and bs
+    divisions per block (counted as 8 slots each), or one division per row."""
+    if bs == 1:
+        return 8 * n
+    full, last = divmod(n, bs)
+    per = lambda m: m ** 3 - m + 8 * m
+    return full * per(bs) + (per(last) if last else 0)
 
 
 def table2_bytes(kind, iters, nnz, n, vt=8, it=4, k=100):
@@ -359,6 +406,7 @@ class GpuStep:
         self.xsol = {k: torch.zeros(self.na if v[1] == "a" else self.nb, dtype=torch.float64, device=dev)
                      for k, v in self.solvers.items()}
         self.gens = [("a", "csr", 1), ("a", "csr", 8), ("b", "csr_merge", 4)]
+        self.in_block = {(k, bs): in_block_entries(inp[k], bs) for k, _, bs in self.gens}
         self.stream = torch.cuda.current_stream(dev)
 
     def n_of(self, k):
@@ -416,25 +464,30 @@ class GpuStep:
             record.append(parts)
         return statuses
 
+    def fmt_of(self, M):
+        """(format, HYB tail entries) of a matrix handle, for the byte model."""
+        inf = M.info()
+        return inf["format_name"], inf["tail_nnz"] if inf["format_name"] == "hyb" else 0
+
     def part_bytes(self, tag):
         kind = tag[0]
-        if kind == "spmv":
+        if kind in ("spmv", "spmvdot"):
             k = tag[1]
-            return SPMV_REPS * spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k))
-        if kind == "spmvdot":
-            k = tag[1]
-            return SPMV_REPS * (spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k)) + 8 * self.n_of(k))
+            fmt, tail = self.fmt_of(tag[2])
+            one = spmv_bytes(self.nnz_of(k), self.n_of(k), self.n_of(k), fmt=fmt, tail_nnz=tail)
+            return SPMV_REPS * (one + (8 * self.n_of(k) if kind == "spmvdot" else 0))
         if kind == "precond":
             k, bs = tag[1], tag[2]
-            return precond_bytes(self.nnz_of(k), self.n_of(k), bs)
+            return precond_bytes(self.n_of(k), bs, self.in_block[(k, bs)])
         name, st = tag[1], tag[2]
         S, k, prec, bs, sk, fmt = self.solvers[name]
+        f, tail = self.fmt_of(self.mats[(k, fmt)])
         if sk == "ir_cg":
             return ir_bytes(st.iters, st.outer_iters, self.nnz_of(k), self.n_of(k), prec, bs,
-                            self.fp16_frac.get(name, 0.0))
+                            self.fp16_frac.get(name, 0.0), fmt=f, tail_nnz=tail)
         if sk == "cg":
-            return cg_bytes(st.iters, self.nnz_of(k), self.n_of(k), prec, bs)
-        return bicgstab_bytes(st.iters, st.spmvs, self.nnz_of(k), self.n_of(k), prec, bs)
+            return cg_bytes(st.iters, self.nnz_of(k), self.n_of(k), prec, bs, fmt=f, tail_nnz=tail)
+        return bicgstab_bytes(st.iters, st.spmvs, self.nnz_of(k), self.n_of(k), prec, bs, fmt=f, tail_nnz=tail)
 
     def part_launches(self, tag):
         kind = tag[0]
@@ -623,9 +676,9 @@ def run_mixed(dev, side=256, tol=1e-12):
             f["outer_iters"] = st.outer_iters
             if tot:
                 f["fp16_block_fraction"] = round(frac, 4)
-            by = ir_bytes(st.iters, st.outer_iters, nnz, n, prec, bs or 1, frac)
+            by = ir_bytes(st.iters, st.outer_iters, nnz, n, prec, bs or 1, frac, fmt="ell")
         else:
-            by = cg_bytes(st.iters, nnz, n, prec, bs or 1)
+            by = cg_bytes(st.iters, nnz, n, prec, bs or 1, fmt="ell")
         f["GB/s"] = round(by / (ms[-1] * 1e-3) / 1e9, 1)
         out[name] = f
         del S, P
@@ -776,7 +829,7 @@ def run_krylov(dev):
                "converged": st.stop_reason == gk.STOP_CONVERGED,
                "ms_per_spmv": round(ms / max(st.spmvs, 1), 4)}
         if kind in ("cg", "fcg"):
-            rec["GB/s_cg_model"] = round(cg_bytes(st.iters, nnz, n, "jacobi", 1) / (ms * 1e-3) / 1e9, 1)
+            rec["GB/s_cg_model"] = round(cg_bytes(st.iters, nnz, n, "jacobi", 1, fmt="ell") / (ms * 1e-3) / 1e9, 1)
         out[f"{name}_{kind}"] = rec
     return {"workload": KRYLOV_WORKLOAD, "timing": "CUDA events around gk_solve, the second of two solves",
             "solves": out}
@@ -942,9 +995,12 @@ def run_paper_bandwidth(dev, triad_gbs=None):
         rd, wr = table2_bytes(kind, steps, nnz, n, k=extra.get("krylov_dim", 100))
         gbs = (rd + wr) / (ms * 1e-3) / 1e9
         rec = {"iters": st.iters, "spmvs": st.spmvs, "table2_iter": steps, "stop_reason": st.stop_reason,
-               "ms": round(ms, 3), "table2_bytes": int(rd + wr), "table2_GB/s": round(gbs, 1)}
+               "ms": round(ms, 3), "table2_model_bytes": int(rd + wr),
+               "table2_model_bytes_per_s_GB": round(gbs, 1)}
         if triad_gbs:
-            rec["table2_frac_of_triad"] = round(gbs / triad_gbs, 3)
+            # model bytes over the triad rate: a ratio above 1 counts bytes that never cross HBM
+            # (Table 2 charges x and a row index per stored entry), so it is not a bandwidth fraction
+            rec["table2_model_over_triad"] = round(gbs / triad_gbs, 3)
         own = None
         if kind == "cg":
             own = cg_bytes(st.iters, nnz, n, "none")
@@ -958,7 +1014,11 @@ def run_paper_bandwidth(dev, triad_gbs=None):
     del M, b
     torch.cuda.empty_cache()
     return {"workload": PAPER_BW_WORKLOAD, "stream_triad_GB/s": triad_gbs,
-            "timing": "CUDA events around gk_solve, the second of two solves", "solvers": out}
+            "timing": "CUDA events around gk_solve, the second of two solves",
+            "note": "table2_model_* divide the paper's Table 2 model volume (COO: x and a row index per stored "
+                    "entry) by the time; they are model bytes, not traffic, and exceed the triad on this matrix. "
+                    "model_GB/s (CG, BiCGSTAB) uses this library's byte model, the bytes that cross HBM.",
+            "solvers": out}
 
 
 # ---------------------------------------------------------------------------
@@ -1129,6 +1189,11 @@ def run_gpu(args):
                 s["outer_iters"] = outers[n[6:]]
             solves[n[6:]] = s
     precs = {n[8:]: summary(n) for n in part_ms if n.startswith("precond_")}
+    for k, _, bs in step.gens:
+        p = precs[f"{k}_bs{bs}"]
+        fl = precond_fp64_ops(step.n_of(k), bs)
+        p["fp64_floor_ms"] = round(fl / (NOMINAL_FP64_TFLOPS * 0.5e12) * 1e3, 4)
+        p["frac_fp64"] = round(p["fp64_floor_ms"] / p["ms"], 3)
     plain = solves["a_cg_plain_csr"]["ms"]
     chosen = min(("a_cg_jacobi_ell", "a_cg_bj8_ell", "a_ircg_jacobi_ell", "a_ircg_bj8_ell"),
                  key=lambda k: solves[k]["ms"])
@@ -1230,28 +1295,38 @@ def oracle_sample(inp, cg_iters):
 
 
 def cpu_baseline(inp, budget_s):
+    """The oracle on the host's cores: its SpMV row loops on every core
+    (OpenMP, static chunks; results unchanged), its dot products and vector
+    steps sequential; and the same sample on one thread beside it."""
     import oracle
     oracle.build()
+    cores = oracle.set_threads(0)
     # size the CG part to about budget_s seconds from two short probes
     _, s2, _ = oracle_sample(inp, 2)
     _, s6, _ = oracle_sample(inp, 6)
     per_it = max((s6 - s2) / 4.0, 1e-4)
     it = max(2, int((budget_s - s2) / per_it))
     by, s, iters = oracle_sample(inp, it)
-    return {"value": round(by / s / 1e9, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (plain C, one thread): SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for "
-                      f"{iters} iterations; {s:.1f} s"}
+    oracle.set_threads(1)
+    by1, s1, _ = oracle_sample(inp, max(2, it // 4))
+    oracle.set_threads(0)
+    return {"value": round(by / s / 1e9, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (plain C; SpMV row loops on {cores} threads, dot products and vector updates "
+                      f"sequential): SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for {iters} iterations; {s:.1f} s",
+            "one_thread": {"value": round(by1 / s1 / 1e9, 3), "cores": 1,
+                           "sample": f"the same with {max(2, it // 4)} CG iterations on one thread; {s1:.1f} s"}}
 
 
 def run_reference(args):
     """The oracle timed as the reference arm, on the same metric and config
     (under a multi-process launch rank 0 alone runs it; the others return
-    without work)."""
+    without work).  Its SpMV row loops use every host core."""
     rank = rank_env()[0]
     if rank != 0:
         return None
     import oracle
     oracle.build()
+    cores = oracle.set_threads(0)
     inp = make_inputs(args.small)
     cg_iters = 2
     for _ in range(args.warmup):
@@ -1262,14 +1337,14 @@ def run_reference(args):
         tot_b += b
         tot_s += s
     value = tot_b / tot_s / 1e9
-    sample = (f"oracle (plain C, one thread), per step: SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for "
-              f"{cg_iters} iterations")
+    sample = (f"oracle (plain C; SpMV row loops on {cores} threads, dot products and vector updates sequential), "
+              f"per step: SpMV of (a) x2 and (b) x1, Jacobi-CG on (a) for {cg_iters} iterations")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(tot_s / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.small else "small test variant"},
-            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -1303,7 +1378,9 @@ def run_spmv_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    by = spmv_bytes(A[1].size, n, n) + (8 * n if dot else 0)
+    inf = M.info()
+    by = spmv_bytes(A[1].size, n, n, fmt=inf["format_name"],
+                    tail_nnz=inf["tail_nnz"] if inf["format_name"] == "hyb" else 0) + (8 * n if dot else 0)
     return {"spmv_only": args.spmv_only, "ms": round(ms, 4), "GB/s": round(by / ms / 1e6, 1),
             "info": M.info()}
 

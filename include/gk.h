@@ -71,7 +71,10 @@ extern "C" {
                            over 4096 entries one thread block per row                   */
 #define GK_CSR_MERGE 1  /* CSR, merge-path split of rows+nonzeros into equal tiles      */
 #define GK_ELL 2        /* ELLPACK, column-major, padded to the longest row             */
-#define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows */
+#define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows
+                           in COO form (row, column, value; sorted by row, then
+                           column); K minimises K*n_rows*12 + overflow*16 bytes,
+                           the smallest such K on ties                                   */
 #define GK_AUTO 4       /* GK_CSR when at least 75 % of its slots (length-sorted slices,
                            warp and block rows) hold stored entries, else GK_CSR_MERGE */
 
@@ -171,8 +174,10 @@ typedef struct {
   int64_t long_rows;       /* GK_CSR: rows processed warp-per-row               */
   int64_t tiles;           /* GK_CSR_MERGE: merge-path tiles                    */
   int64_t device_bytes;    /* bytes of library-owned device storage             */
-  int64_t spmv_bytes;      /* algorithmic bytes of one simple apply, x counted   */
-                           /* once (see the library's documentation)           */
+  int64_t spmv_bytes;      /* algorithmic bytes of one simple apply: the stored */
+                           /* operator (CSR: nnz*12 + (n_rows+1)*4; ELL:        */
+                           /* nnz*12; HYB: ELL entries*12 + COO entries*16),    */
+                           /* x read once (n_cols*8), y written (n_rows*8)      */
 } gk_matrix_info;
 
 /* ---- errors ------------------------------------------------------------- */
@@ -410,6 +415,19 @@ GK_API int gk_wsnet_destroy(gk_wsnet N);
  * keeps one reduction workspace per device, so gk_dot calls on one device
  * must be ordered (issued to one stream, or synchronized). */
 GK_API int gk_dot(int64_t n, const double* x, const double* y, double* result, void* stream);
+
+/* result[0] = sum_k v[k] * x[c[k]] over k < n: the SpMV's work per stored
+ * entry (an index and a value streamed, x gathered, one fused multiply-add)
+ * without its row structure.  Not in the paper: it measures the ceiling that
+ * the SpMV kernels of a matrix with scattered columns are held against (the
+ * same (c, v) stream as the matrix's CSR arrays).  c, v, x, result: device
+ * memory of the current device; an index outside [0, n_x) contributes 0.
+ * Terms are summed per thread (threads take k, k + T, ... with T the
+ * launch's threads), then by the block and grid reductions of gk_dot, so the
+ * result is reproducible run to run.  One workspace per device: calls on one
+ * device must be ordered. */
+GK_API int gk_gather_dot(int64_t n, const int32_t* c, const double* v, const double* x, int64_t n_x,
+                         double* result, void* stream);
 
 /* gk_dot without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- for example

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -52,6 +53,27 @@ int set_smem(const void* fn, size_t smem);
 template <typename F>
 int set_smem(F* fn, size_t smem) {
   return set_smem(reinterpret_cast<const void*>(fn), smem);
+}
+
+// Launches kern<<<grid, block, smem, s>>>(args...) with programmatic stream
+// serialization: the grid may start while the previous kernel in the stream
+// drains (its launch overlaps that kernel's tail instead of following it);
+// the kernel must call pdl_wait() before reading what the previous kernel
+// wrote.  In a captured graph the dependency becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // Makes `dev` current for the lifetime of the guard, then restores the
@@ -151,6 +173,11 @@ constexpr int kSliceMaxLen = 256;
 constexpr int kBlockRowLen = 4096;
 constexpr int kSliceThreads = 256;
 constexpr int kEllThreads = 256;
+// GK_HYB's COO overflow: each lane sums kCooPerLane consecutive entries, a
+// warp takes a chunk of kCooChunk.
+constexpr int kCooPerLane = 8;
+constexpr int kCooChunk = 32 * kCooPerLane;
+constexpr int kCooThreads = 256;
 // Blocks of the merge-path fix-up launch; reduction scratch holds
 // 2 * (max grid + kFixupMaxGrid) doubles.
 constexpr int kFixupMaxGrid = 64;
@@ -203,15 +230,25 @@ struct Matrix {
   int32_t* ell_col = nullptr;
   double* ell_val = nullptr;
   int grid_ell = 0;
-  // GK_HYB overflow ("tail"): CSR over the rows longer than K
+  // GK_HYB overflow ("tail"): the entries of rows longer than K beyond their
+  // first K, in COO form sorted by (row, column): tail_row / tail_col /
+  // tail_val (the same entries are also addressed row-compressed through
+  // tail_rowptr, which the FP32 copy of the refinement uses).  Arrays are
+  // padded to whole chunks of kCooChunk entries.
   int64_t m_tail = 0, tail_nnz = 0;
   int32_t* tail_rows = nullptr;
   int32_t* tail_rowptr = nullptr;
+  int32_t* tail_row = nullptr;   // [tail_nnz] global row of each entry
   int32_t* tail_col = nullptr;
   double* tail_val = nullptr;
   int32_t* tail_slot = nullptr;  // [n_rows] index into tail_sum or -1
   double* tail_sum = nullptr;    // [m_tail]
-  MergePlan tail;
+  int64_t coo_chunks = 0;        // chunks of kCooChunk entries
+  int32_t* coo_first = nullptr;  // [coo_chunks] first / last row of each chunk
+  int32_t* coo_last = nullptr;
+  double* coo_head = nullptr;    // [coo_chunks] partial sums of those rows in the chunk
+  double* coo_tail = nullptr;
+  int grid_coo = 0;
   // scratch of gk_apply / precond generation
   double* partials = nullptr;
   unsigned int* counter = nullptr;
@@ -231,6 +268,7 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s);
 int spmv_max_grid(const Matrix& A);
 // Persistent grid sizes of the SpMV kernels for a given amount of work.
 int merge_grid(int64_t n_tiles);
+int coo_grid(int64_t n_chunks);
 int sliced_grid(int64_t warp_items, int64_t big_rows);
 int ell_grid(int64_t n_rows);
 

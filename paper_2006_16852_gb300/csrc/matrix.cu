@@ -57,11 +57,11 @@ __global__ void merge_plan_kernel(const int32_t* __restrict__ rowptr, int n_rows
 }
 
 // ELL (column-major, ld rows per slot column) and, for HYB, the overflow of
-// rows longer than K into a row-compressed tail.
+// rows longer than K as COO entries (row, column, value) in row order.
 __global__ void ell_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, int n_rows, int K, int64_t ld,
                                 int32_t* ell_col, double* ell_val, const int32_t* __restrict__ tail_slot,
-                                const int32_t* __restrict__ tail_rowptr, int32_t* tail_col,
+                                const int32_t* __restrict__ tail_rowptr, int32_t* tail_row, int32_t* tail_col,
                                 double* tail_val) {
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride) {
@@ -79,6 +79,7 @@ __global__ void ell_fill_kernel(const int32_t* __restrict__ rowptr, const int32_
     if (len > K && tail_slot) {
       const int base = tail_rowptr[tail_slot[r]];
       for (int j = K; j < len; ++j) {
+        tail_row[base + j - K] = r;
         tail_col[base + j - K] = col[k0 + j];
         tail_val[base + j - K] = val[k0 + j];
       }
@@ -186,9 +187,8 @@ void matrix_release(Matrix* A) {
   void* ptrs[] = {A->rowptr, A->col, A->val, A->sl_perm, A->sl_off, A->sl_col, A->sl_val, A->mid_rows, A->big_rows,
                   A->merge.tile_i, A->merge.tile_j, A->merge.head_val, A->merge.head_row,
                   A->merge.carry_val, A->merge.carry_row, A->merge.cont, A->ell_col, A->ell_val,
-                  A->tail_rows, A->tail_rowptr, A->tail_col, A->tail_val, A->tail_slot, A->tail_sum,
-                  A->tail.tile_i, A->tail.tile_j, A->tail.head_val, A->tail.head_row,
-                  A->tail.carry_val, A->tail.carry_row, A->tail.cont, A->partials, A->counter,
+                  A->tail_rows, A->tail_rowptr, A->tail_row, A->tail_col, A->tail_val, A->tail_slot,
+                  A->tail_sum, A->coo_first, A->coo_last, A->coo_head, A->coo_tail, A->partials, A->counter,
                   A->err, A->dot_st, A->stage_in, A->stage_out};
   for (void* p : ptrs) dfree(p);
   if (prev >= 0) cudaSetDevice(prev);
@@ -364,24 +364,33 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
       }
       A->m_tail = static_cast<int64_t>(trows.size());
       A->tail_nnz = trp.back();
+      // COO arrays in whole chunks (each lane's 16-byte loads stay inside)
+      A->coo_chunks = (A->tail_nnz + kCooChunk - 1) / kCooChunk;
+      const int64_t coo_n = std::max<int64_t>(A->coo_chunks * kCooChunk, padded(A->tail_nnz));
       GK_TRY(upload(&A->tail_slot, slot, 0, bytes, s));
       GK_TRY(upload(&A->tail_rows, trows, 0, bytes, s));
       GK_TRY(upload(&A->tail_rowptr, trp, padded(A->m_tail + 1), bytes, s));
-      GK_TRY(dalloc_n(&A->tail_col, padded(A->tail_nnz), bytes));
-      GK_TRY(dalloc_n(&A->tail_val, padded(A->tail_nnz), bytes));
+      GK_TRY(dalloc_n(&A->tail_row, static_cast<size_t>(coo_n), bytes));
+      GK_TRY(dalloc_n(&A->tail_col, static_cast<size_t>(coo_n), bytes));
+      GK_TRY(dalloc_n(&A->tail_val, static_cast<size_t>(coo_n), bytes));
       GK_TRY(dalloc_n(&A->tail_sum, static_cast<size_t>(std::max<int64_t>(A->m_tail, 1)), bytes));
-      GK_TRY_CUDA(cudaMemsetAsync(A->tail_col, 0, sizeof(int32_t) * padded(A->tail_nnz), s));
-      GK_TRY_CUDA(cudaMemsetAsync(A->tail_val, 0, sizeof(double) * padded(A->tail_nnz), s));
+      GK_TRY_CUDA(cudaMemsetAsync(A->tail_row, 0, sizeof(int32_t) * coo_n, s));
+      GK_TRY_CUDA(cudaMemsetAsync(A->tail_col, 0, sizeof(int32_t) * coo_n, s));
+      GK_TRY_CUDA(cudaMemsetAsync(A->tail_val, 0, sizeof(double) * coo_n, s));
+      const size_t nc = static_cast<size_t>(std::max<int64_t>(A->coo_chunks, 1));
+      GK_TRY(dalloc_n(&A->coo_first, nc, bytes));
+      GK_TRY(dalloc_n(&A->coo_last, nc, bytes));
+      GK_TRY(dalloc_n(&A->coo_head, nc, bytes));
+      GK_TRY(dalloc_n(&A->coo_tail, nc, bytes));
+      A->grid_coo = coo_grid(A->coo_chunks);
     }
     if (n_rows > 0) {
       ell_fill_kernel<<<grid1d(n_rows, 256), 256, 0, s>>>(
           A->rowptr, A->col, A->val, static_cast<int>(n_rows), static_cast<int>(K), A->ld, A->ell_col,
-          A->ell_val, fmt == GK_HYB ? A->tail_slot : nullptr, A->tail_rowptr, A->tail_col, A->tail_val);
+          A->ell_val, fmt == GK_HYB ? A->tail_slot : nullptr, A->tail_rowptr, A->tail_row, A->tail_col,
+          A->tail_val);
       GK_TRY_CUDA(cudaGetLastError());
     }
-    if (fmt == GK_HYB && A->m_tail > 0)
-      GK_TRY(build_merge_plan(A->tail, A->m_tail, A->tail_nnz, A->tail_rowptr, A->tail_col, A->tail_val,
-                              bytes, s));
     A->grid_ell = ell_grid(n_rows);
   }
   A->max_grid = std::max(spmv_max_grid(*A), 4 * sm_count());
@@ -406,7 +415,13 @@ extern "C" int gk_matrix_get_info(gk_matrix h, gk_matrix_info* info) {
   info->long_rows = A->n_mid + A->n_big;
   info->tiles = A->merge.n_tiles;
   info->device_bytes = A->device_bytes;
-  info->spmv_bytes = A->nnz * 12 + (A->n_rows + 1) * 4 + A->n_cols * 8 + A->n_rows * 8;
+  // the stored operator once (CSR: values, indices, row pointers; ELL: the
+  // entries' values and indices; HYB: ELL entries + COO entries with their
+  // row index), x read once, y written once
+  int64_t mat = A->nnz * 12 + (A->n_rows + 1) * 4;
+  if (A->format == GK_ELL) mat = A->nnz * 12;
+  if (A->format == GK_HYB) mat = (A->nnz - A->tail_nnz) * 12 + A->tail_nnz * 16;
+  info->spmv_bytes = mat + A->n_cols * 8 + A->n_rows * 8;
   return GK_OK;
 }
 

@@ -146,6 +146,7 @@ struct SliceArgs {
 
 template <int MODE>
 __global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs a, Epi e) {
+  pdl_wait();
   constexpr int B = EllBatchOf<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
   __shared__ double row_scratch[kRedScratch];
@@ -250,6 +251,7 @@ struct EllBatch {
 
 template <int MODE, bool TAIL>
 __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi e) {
+  pdl_wait();
   constexpr int B = EllBatch<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;
@@ -298,11 +300,11 @@ __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi
 template <bool TAIL>
 void launch_ell_t(int grid, cudaStream_t s, const EllArgs& a, const Epi& e) {
   switch (e.mode) {
-    case EPI_COPY: spmv_ell_kernel<EPI_COPY, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
-    case EPI_PLAIN: spmv_ell_kernel<EPI_PLAIN, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
-    case EPI_RESID: spmv_ell_kernel<EPI_RESID, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
-    case EPI_DOT: spmv_ell_kernel<EPI_DOT, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
-    default: spmv_ell_kernel<EPI_DOT2, TAIL><<<grid, kEllThreads, 0, s>>>(a, e); break;
+    case EPI_COPY: launch_pdl(spmv_ell_kernel<EPI_COPY, TAIL>, grid, kEllThreads, 0, s, a, e); break;
+    case EPI_PLAIN: launch_pdl(spmv_ell_kernel<EPI_PLAIN, TAIL>, grid, kEllThreads, 0, s, a, e); break;
+    case EPI_RESID: launch_pdl(spmv_ell_kernel<EPI_RESID, TAIL>, grid, kEllThreads, 0, s, a, e); break;
+    case EPI_DOT: launch_pdl(spmv_ell_kernel<EPI_DOT, TAIL>, grid, kEllThreads, 0, s, a, e); break;
+    default: launch_pdl(spmv_ell_kernel<EPI_DOT2, TAIL>, grid, kEllThreads, 0, s, a, e); break;
   }
 }
 
@@ -353,6 +355,7 @@ struct MergeArgs {
 };
 
 __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, Epi e) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MergeSmem& S = *reinterpret_cast<MergeSmem*>(smem_raw);
   if (epi_skip(e)) return;
@@ -561,6 +564,7 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
 // block partials are folded into this launch's own fixed-order grid sum, whose
 // block partials live after the main launch's.
 __global__ void __launch_bounds__(256) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
+  pdl_wait();
   __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
@@ -585,6 +589,158 @@ __global__ void __launch_bounds__(256) spmv_merge_fixup_kernel(MergeArgs a, Epi 
   double v[2] = {a0, a1}, out[2];
   if (grid_sum<2>(v, e.partials + 2 * main_grid, e.counter, red_scratch, out) && threadIdx.x == 0 && e.st)
     finalize(e.fin, out, e.st);
+}
+
+// ---------------------------------------------------------------------------
+// GK_HYB overflow in COO form: entries (row, column, value) sorted by (row,
+// column), a row index per entry (the COO SpMV of the paper's solver
+// evaluation).  The entries are cut into chunks of kCooChunk; a warp takes a
+// chunk and each lane kCooPerLane consecutive entries, so the work per warp
+// does not depend on the row lengths.  A lane sums its runs of equal row in
+// entry order (fma); runs that cross lanes are joined by a segmented
+// inclusive scan over the warp (shuffles, fixed tree order); rows that cross
+// chunks are finished by a one-thread-per-chunk fix-up launch from each
+// chunk's partial sums of its first and last row.  The results are the
+// overflow sums of the tail rows (indexed by the row's tail slot), which the
+// ELL kernel then adds to its row sums.  Padding entries past nnz are never
+// summed; the arrays are allocated in whole chunks so that every lane's
+// 16-byte loads stay inside them.
+// ---------------------------------------------------------------------------
+
+struct CooArgs {
+  const int32_t* row;
+  const int32_t* col;
+  const double* val;
+  int nnz;
+  int n_chunks;
+  const int32_t* slot;  // [n_rows] tail slot of each row
+  double* out;          // [m_tail] overflow sum of each tail row
+  int32_t* c_first;     // per chunk: its first and last row and their partial sums
+  int32_t* c_last;
+  double* c_head;
+  double* c_tail;
+  const double* x;
+};
+
+__global__ void __launch_bounds__(kCooThreads) spmv_coo_kernel(CooArgs a, Epi e) {
+  pdl_wait();
+  constexpr int E = kCooPerLane;
+  if (epi_skip(e)) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c < a.n_chunks; c += nw) {
+    const int c0 = c * kCooChunk;
+    const int e0 = c0 + lane * E;
+    int rr[E], cc[E];
+    double vv[E], xv[E];
+    {
+      const int4* rp = reinterpret_cast<const int4*>(a.row + e0);
+      const int4* cp = reinterpret_cast<const int4*>(a.col + e0);
+      const double2* vp = reinterpret_cast<const double2*>(a.val + e0);
+#pragma unroll
+      for (int h = 0; h < E / 4; ++h) {
+        const int4 r4 = __ldcs(rp + h), c4 = __ldcs(cp + h);
+        rr[4 * h] = r4.x; rr[4 * h + 1] = r4.y; rr[4 * h + 2] = r4.z; rr[4 * h + 3] = r4.w;
+        cc[4 * h] = c4.x; cc[4 * h + 1] = c4.y; cc[4 * h + 2] = c4.z; cc[4 * h + 3] = c4.w;
+      }
+#pragma unroll
+      for (int h = 0; h < E / 2; ++h) {
+        const double2 v2 = __ldcs(vp + h);
+        vv[2 * h] = v2.x;
+        vv[2 * h + 1] = v2.y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u) xv[u] = (e0 + u < a.nnz) ? __ldg(a.x + cc[u]) : 0.0;
+    // the lane's runs: the first (head), whole rows in between (written
+    // here), the last (tail)
+    int first = -1, cur = -1;
+    double head = 0.0, sum = 0.0;
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (e0 + u < a.nnz) {
+        if (rr[u] != cur) {
+          if (cur >= 0) {
+            if (cur == first) head = sum;
+            else a.out[__ldg(a.slot + cur)] = sum;
+          }
+          if (first < 0) first = rr[u];
+          cur = rr[u];
+          sum = 0.0;
+        }
+        sum = fma(vv[u], xv[u], sum);
+      }
+    }
+    const int last = cur;
+    if (first == last) head = sum;
+    // segmented inclusive scan of the tails over the lanes: a lane that is a
+    // single run of the previous lane's last row adds the scan before it
+    const int prev_last = __shfl_up_sync(0xffffffffu, last, 1);
+    double S = sum;
+    int open = (lane > 0 && first >= 0 && first == last && prev_last == first) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double Sp = __shfl_up_sync(0xffffffffu, S, d);
+      const int op = __shfl_up_sync(0xffffffffu, open, d);
+      if (lane >= d && open) {
+        S = Sp + S;
+        open = op;
+      }
+    }
+    const double S_prev = __shfl_up_sync(0xffffffffu, S, 1);
+    const int next_first = __shfl_down_sync(0xffffffffu, first, 1);
+    const int chunk_first = __shfl_sync(0xffffffffu, first, 0);
+    int before = -1;
+    if (lane == 0 && c0 > 0) before = __ldg(a.row + c0 - 1);
+    before = __shfl_sync(0xffffffffu, before, 0);
+    const bool head_open = before == chunk_first;  // the chunk's first row began in an earlier chunk
+    const int nvalid = min(32, (a.nnz - c0 + E - 1) / E);
+    if (lane < nvalid) {
+      // a row that ends in this lane (and is not the chunk's last row) is
+      // complete unless it began in an earlier chunk
+      if (first != last) {
+        const double v = ((lane > 0 && prev_last == first) ? S_prev : 0.0) + head;
+        if (head_open && first == chunk_first) a.c_head[c] = v;
+        else a.out[__ldg(a.slot + first)] = v;
+      }
+      if (lane < nvalid - 1) {
+        if (next_first != last) {
+          if (head_open && last == chunk_first) a.c_head[c] = S;
+          else a.out[__ldg(a.slot + last)] = S;
+        }
+      } else {
+        a.c_first[c] = chunk_first;
+        a.c_last[c] = last;
+        a.c_tail[c] = S;
+      }
+    }
+  }
+}
+
+// Rows that cross chunk boundaries, one thread per chunk: the chunk's first
+// row if it began in an earlier chunk and ends inside this one, and the
+// chunk's last row if it ends with this chunk; each sums its pieces from
+// this chunk back to the chunk where it began.
+__global__ void __launch_bounds__(256) spmv_coo_fixup_kernel(CooArgs a, Epi e) {
+  pdl_wait();
+  if (epi_skip(e)) return;
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.n_chunks; c += stride) {
+    const int f = a.c_first[c], l = a.c_last[c];
+    if (c > 0 && f != l && a.c_last[c - 1] == f) {
+      double v = a.c_head[c];
+      for (int u = c - 1; u >= 0; --u) {
+        v += a.c_tail[u];
+        if (!(a.c_first[u] == f && u > 0 && a.c_last[u - 1] == f)) break;
+      }
+      a.out[__ldg(a.slot + f)] = v;
+    }
+    if (c == a.n_chunks - 1 || a.c_first[c + 1] != l) {
+      double v = a.c_tail[c];
+      for (int u = c; u > 0 && a.c_first[u] == l && a.c_last[u - 1] == l; --u) v += a.c_tail[u - 1];
+      a.out[__ldg(a.slot + l)] = v;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -637,10 +793,10 @@ MergeArgs merge_args(const MergePlan& P, const double* x) {
 int launch_merge(const MergePlan& P, const double* x, const Epi& e, cudaStream_t s) {
   if (P.n_tiles == 0) return GK_OK;
   MergeArgs m = merge_args(P, x);
-  spmv_merge_kernel<<<P.grid, kMergeThreads, sizeof(MergeSmem), s>>>(m, e);
+  launch_pdl(spmv_merge_kernel, P.grid, kMergeThreads, sizeof(MergeSmem), s, m, e);
   GK_TRY_CUDA(cudaGetLastError());
   const int fg = static_cast<int>(std::min<int64_t>(kFixupMaxGrid, (P.n_tiles + 255) / 256));
-  spmv_merge_fixup_kernel<<<fg, 256, 0, s>>>(m, e, P.grid);
+  launch_pdl(spmv_merge_fixup_kernel, fg, 256, 0, s, m, e, P.grid);
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
@@ -666,6 +822,28 @@ int ell_grid(int64_t n_rows) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
 }
 
+int coo_grid(int64_t n_chunks) {
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_coo_kernel), kCooThreads, 0);
+  int64_t need = (n_chunks + kCooThreads / 32 - 1) / (kCooThreads / 32);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
+}
+
+namespace {
+
+int launch_coo(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) {
+  if (A.coo_chunks == 0) return GK_OK;
+  CooArgs c{A.tail_row, A.tail_col, A.tail_val, static_cast<int>(A.tail_nnz), static_cast<int>(A.coo_chunks),
+            A.tail_slot, A.tail_sum, A.coo_first, A.coo_last, A.coo_head, A.coo_tail, x};
+  launch_pdl(spmv_coo_kernel, A.grid_coo, kCooThreads, 0, s, c, e);
+  GK_TRY_CUDA(cudaGetLastError());
+  const int fg = static_cast<int>(std::min<int64_t>(4 * sm_count(), (A.coo_chunks + 255) / 256));
+  launch_pdl(spmv_coo_fixup_kernel, fg, 256, 0, s, c, e);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
+}  // namespace
+
 int spmv_max_grid(const Matrix& A) {
   return std::max({A.grid_sl, A.grid_ell, A.merge.grid, 1});
 }
@@ -679,11 +857,11 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
                   static_cast<int>(A.n_slices), A.mid_rows, static_cast<int>(A.n_mid), A.big_rows,
                   static_cast<int>(A.n_big), x};
       switch (e.mode) {
-        case EPI_COPY: spmv_sliced_kernel<EPI_COPY><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
-        case EPI_PLAIN: spmv_sliced_kernel<EPI_PLAIN><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
-        case EPI_RESID: spmv_sliced_kernel<EPI_RESID><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
-        case EPI_DOT: spmv_sliced_kernel<EPI_DOT><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
-        default: spmv_sliced_kernel<EPI_DOT2><<<A.grid_sl, kSliceThreads, 0, s>>>(b, e); break;
+        case EPI_COPY: launch_pdl(spmv_sliced_kernel<EPI_COPY>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        case EPI_PLAIN: launch_pdl(spmv_sliced_kernel<EPI_PLAIN>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        case EPI_RESID: launch_pdl(spmv_sliced_kernel<EPI_RESID>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        case EPI_DOT: launch_pdl(spmv_sliced_kernel<EPI_DOT>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        default: launch_pdl(spmv_sliced_kernel<EPI_DOT2>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
       }
       GK_TRY_CUDA(cudaGetLastError());
       return GK_OK;
@@ -699,7 +877,7 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
         te.st = e.st;
         te.skip_mode = e.skip_mode;
         te.err = e.err;
-        GK_TRY(launch_merge(A.tail, x, te, s));
+        GK_TRY(launch_coo(A, x, te, s));
       }
       const bool tail = A.format == GK_HYB && A.m_tail > 0;
       EllArgs ea{A.ell_col, A.ell_val, A.ld, static_cast<int>(A.K), static_cast<int>(A.n_rows), x,

@@ -18,6 +18,15 @@ constexpr uint32_t kMaxPolls = 1u << 26;
 // ~2 s at the 2.07 GHz maximum SM clock.
 constexpr long long kMaxWaitCycles = 4000000000LL;
 
+// Programmatic dependent launch: a kernel launched with launch_pdl (below)
+// may be scheduled while the kernel before it in the stream is still
+// finishing; its threads call pdl_wait() before touching anything that
+// kernel produced (it returns once that grid has completed and its memory
+// operations are visible; in a kernel launched without the attribute it
+// returns at once).  Every kernel that launch_pdl starts calls it first, so
+// the stream's order holds transitively.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -252,6 +252,7 @@ struct Ell32 {
 template <bool TAIL, bool DOT>
 __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_ell_kernel(Ell32 a, const float* __restrict__ x,
                                                                      float* __restrict__ y) {
+  pdl_wait();
   __shared__ float scratch[kRedScratch];
   if (a.ist->done) return;
   float a0 = 0.0f;
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_csr_kernel(const int32_
                                                                      const float* __restrict__ val, int n,
                                                                      IrData d, const float* __restrict__ x,
                                                                      float* __restrict__ y) {
+  pdl_wait();
   __shared__ float scratch[kRedScratch];
   if (d.ist->done) return;
   constexpr int RPW = 32 / LPR;
@@ -339,6 +341,7 @@ __global__ void __launch_bounds__(kIrThreads, 8) ir_spmv_csr_kernel(const int32_
 // r = r64 / ||r64||, d = 0, z = M^{-1} r, p = z, rho = r.z, rr0 = r.r.
 template <int PK, int BS>
 __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d) {
+  pdl_wait();
   __shared__ float scratch[kRedScratch];
   const double inv = 1.0 / a.st->rnorm;
   float rz = 0.0f, rr = 0.0f;
@@ -386,6 +389,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d
 // d += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); inner criteria.
 template <int PK, int BS>
 __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData d) {
+  pdl_wait();
   __shared__ float scratch[kRedScratch];
   if (d.ist->done) return;
   const float alpha = static_cast<float>(d.ist->alpha);
@@ -434,6 +438,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData 
 // p = z + beta p; re-arms the inner loop.
 template <int PK>
 __global__ void __launch_bounds__(kIrThreads) ir_direction_kernel(IrArgs a, IrData d) {
+  pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const InnerState* s = d.ist;
     const bool more = !s->done && s->it < s->max_it + 2;
@@ -510,12 +515,12 @@ template <bool DOT>
 void launch_csr32(int lpr, int grid, cudaStream_t s, const int32_t* rowptr, const int32_t* col, const float* val,
                   int n, const IrData& d, const float* x, float* y) {
   switch (lpr) {
-    case 1: ir_spmv_csr_kernel<1, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
-    case 2: ir_spmv_csr_kernel<2, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
-    case 4: ir_spmv_csr_kernel<4, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
-    case 8: ir_spmv_csr_kernel<8, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
-    case 16: ir_spmv_csr_kernel<16, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
-    default: ir_spmv_csr_kernel<32, DOT><<<grid, kIrThreads, 0, s>>>(rowptr, col, val, n, d, x, y); break;
+    case 1: launch_pdl(ir_spmv_csr_kernel<1, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
+    case 2: launch_pdl(ir_spmv_csr_kernel<2, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
+    case 4: launch_pdl(ir_spmv_csr_kernel<4, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
+    case 8: launch_pdl(ir_spmv_csr_kernel<8, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
+    case 16: launch_pdl(ir_spmv_csr_kernel<16, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
+    default: launch_pdl(ir_spmv_csr_kernel<32, DOT>, grid, kIrThreads, 0, s, rowptr, col, val, n, d, x, y); break;
   }
 }
 
@@ -529,9 +534,9 @@ int ir_spmv(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
     if (tail) {
       launch_csr32<false>(d.tail_lpr, d.grid, s, A.tail_rowptr, A.tail_col, d.tail_val32,
                           static_cast<int>(A.m_tail), d, d.p, d.tail_sum32);
-      ir_spmv_ell_kernel<true, true><<<d.grid, kIrThreads, 0, s>>>(e32, d.p, d.q);
+      launch_pdl(ir_spmv_ell_kernel<true, true>, d.grid, kIrThreads, 0, s, e32, d.p, d.q);
     } else {
-      ir_spmv_ell_kernel<false, true><<<d.grid, kIrThreads, 0, s>>>(e32, d.p, d.q);
+      launch_pdl(ir_spmv_ell_kernel<false, true>, d.grid, kIrThreads, 0, s, e32, d.p, d.q);
     }
   } else {
     launch_csr32<true>(d.lpr, d.grid, s, A.rowptr, A.col, d.val32, a.n, d, d.p, d.q);
@@ -545,11 +550,11 @@ int ir_spmv(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
 #define IR_LAUNCH_BS(kern, bs, grid, s, a, d)                                      \
   do {                                                                             \
     switch (bs) {                                                                  \
-      case 4: kern<PREC_BLOCK, 4><<<grid, kIrThreads, 0, s>>>(a, d); break;       \
-      case 8: kern<PREC_BLOCK, 8><<<grid, kIrThreads, 0, s>>>(a, d); break;       \
-      case 16: kern<PREC_BLOCK, 16><<<grid, kIrThreads, 0, s>>>(a, d); break;     \
-      case 32: kern<PREC_BLOCK, 32><<<grid, kIrThreads, 0, s>>>(a, d); break;     \
-      default: kern<PREC_BLOCK, 0><<<grid, kIrThreads, 0, s>>>(a, d); break;      \
+      case 4: launch_pdl(kern<PREC_BLOCK, 4>, grid, kIrThreads, 0, s, a, d); break;       \
+      case 8: launch_pdl(kern<PREC_BLOCK, 8>, grid, kIrThreads, 0, s, a, d); break;       \
+      case 16: launch_pdl(kern<PREC_BLOCK, 16>, grid, kIrThreads, 0, s, a, d); break;     \
+      case 32: launch_pdl(kern<PREC_BLOCK, 32>, grid, kIrThreads, 0, s, a, d); break;     \
+      default: launch_pdl(kern<PREC_BLOCK, 0>, grid, kIrThreads, 0, s, a, d); break;      \
     }                                                                              \
   } while (0)
 
@@ -558,8 +563,8 @@ int ir_spmv(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
 // start -> WHILE(cond) { SpMV; update; direction } -> apply.
 int ir_enqueue_start(const Solver& S, const IrData& d, const IrArgs& a, cudaStream_t s) {
   if (S.pk == PREC_BLOCK) IR_LAUNCH_BS(ir_start_kernel, a.bs, d.grid, s, a, d);
-  else if (S.pk == PREC_SCALAR) ir_start_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
-  else ir_start_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
+  else if (S.pk == PREC_SCALAR) launch_pdl(ir_start_kernel<PREC_SCALAR, 0>, d.grid, kIrThreads, 0, s, a, d);
+  else launch_pdl(ir_start_kernel<PREC_NONE, 0>, d.grid, kIrThreads, 0, s, a, d);
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
@@ -569,13 +574,13 @@ int ir_enqueue_inner(const Solver& S, const IrData& d, const IrArgs& a, cudaStre
   GK_TRY(ir_spmv(S, d, a, s));
   if (S.pk == PREC_BLOCK) {
     IR_LAUNCH_BS(ir_update_kernel, a.bs, d.grid, s, a, d);
-    ir_direction_kernel<PREC_BLOCK><<<d.grid, kIrThreads, 0, s>>>(a, d);
+    launch_pdl(ir_direction_kernel<PREC_BLOCK>, d.grid, kIrThreads, 0, s, a, d);
   } else if (S.pk == PREC_SCALAR) {
-    ir_update_kernel<PREC_SCALAR, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
-    ir_direction_kernel<PREC_SCALAR><<<d.grid, kIrThreads, 0, s>>>(a, d);
+    launch_pdl(ir_update_kernel<PREC_SCALAR, 0>, d.grid, kIrThreads, 0, s, a, d);
+    launch_pdl(ir_direction_kernel<PREC_SCALAR>, d.grid, kIrThreads, 0, s, a, d);
   } else {
-    ir_update_kernel<PREC_NONE, 0><<<d.grid, kIrThreads, 0, s>>>(a, d);
-    ir_direction_kernel<PREC_NONE><<<d.grid, kIrThreads, 0, s>>>(a, d);
+    launch_pdl(ir_update_kernel<PREC_NONE, 0>, d.grid, kIrThreads, 0, s, a, d);
+    launch_pdl(ir_direction_kernel<PREC_NONE>, d.grid, kIrThreads, 0, s, a, d);
   }
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;

@@ -119,6 +119,7 @@ __device__ __forceinline__ void reduce_finalize3(const VecArgs& a, double s0, do
 // z = M^{-1} r, p = z, rho = r.z; criteria at k = 0.
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   double rz = 0.0;
   if (PK == PREC_BLOCK) {
@@ -203,12 +204,14 @@ __device__ __forceinline__ void cg_update_body(const VecArgs& a, double* scratch
 
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   cg_update_body<PK, BS, false>(a, scratch);
 }
 
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) fcg_update_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[3 * kVecThreads];  // a three-value block reduction
   cg_update_body<PK, BS, true>(a, scratch);
 }
@@ -216,6 +219,7 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) fcg_upda
 // p = z + beta p; ends the iteration (loop control).
 template <int PK>
 __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a) {
+  pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
   if (a.st->stop) return;
   const double beta = a.st->beta;
@@ -247,6 +251,7 @@ __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a)
 
 // r^ = r_0, p = v = 0, rho = r^.r; criteria at k = 0.
 __global__ void __launch_bounds__(kVecThreads) bicg_start_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   double rho = 0.0;
   FOR_ROWS(i) {
@@ -262,6 +267,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_start_kernel(VecArgs a) {
 // p = r + beta (p - omega v); p^ = M^{-1} p.
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
+  pdl_wait();
   if (a.st->stop) return;
   const double beta = a.st->beta, omega = a.st->omega;
   if (PK == PREC_BLOCK) {
@@ -286,6 +292,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_dir_kernel(VecArgs a) {
 // s = r - alpha v; s^ = M^{-1} s; ||s||^2 (half-step test).
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
@@ -316,6 +323,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_s_kernel(VecArgs a) {
 // next rho and beta; ends the iteration.  After a half-step exit only
 // x += alpha p^ and r = s.
 __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   if (a.st->stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
@@ -343,6 +351,7 @@ __global__ void __launch_bounds__(kVecThreads) bicg_update_kernel(VecArgs a) {
 
 // r^ = r_0, p = q = 0, rho = r^.r; criteria at k = 0.
 __global__ void __launch_bounds__(kVecThreads) cgs_start_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   double rho = 0.0;
   FOR_ROWS(i) {
@@ -359,6 +368,7 @@ __global__ void __launch_bounds__(kVecThreads) cgs_start_kernel(VecArgs a) {
 // p^ = M^{-1} p.
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) cgs_dir_kernel(VecArgs a) {
+  pdl_wait();
   if (a.st->stop) return;
   const bool first = a.st->iter == 0;
   const double beta = a.st->beta;
@@ -390,6 +400,7 @@ __global__ void __launch_bounds__(kVecThreads) cgs_dir_kernel(VecArgs a) {
 // q = u - alpha v^; u^ = M^{-1} (u + q); x += alpha u^.
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads) cgs_q_kernel(VecArgs a) {
+  pdl_wait();
   if (a.st->stop) return;
   const double alpha = a.st->alpha;
   if (PK == PREC_BLOCK) {
@@ -421,6 +432,7 @@ __global__ void __launch_bounds__(kVecThreads) cgs_q_kernel(VecArgs a) {
 // r -= alpha q^; (r^.r, r.r); k += 1, criteria, next rho and beta; ends the
 // iteration.
 __global__ void __launch_bounds__(kVecThreads) cgs_update_kernel(VecArgs a) {
+  pdl_wait();
   __shared__ double scratch[kRedScratch];
   if (a.st->stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
@@ -530,25 +542,25 @@ Epi spmv_epi(const Solver& S, int mode, const double* u, double* y, int fin, int
   do {                                                                                          \
     if (S.pk == PREC_BLOCK) {                                                                   \
       switch (S.P->bs) {                                                                        \
-        case 4: kern<PREC_BLOCK, 4><<<grid, kVecThreads, 0, s>>>(args); break;                 \
-        case 8: kern<PREC_BLOCK, 8><<<grid, kVecThreads, 0, s>>>(args); break;                 \
-        case 16: kern<PREC_BLOCK, 16><<<grid, kVecThreads, 0, s>>>(args); break;               \
-        case 32: kern<PREC_BLOCK, 32><<<grid, kVecThreads, 0, s>>>(args); break;               \
-        default: kern<PREC_BLOCK, 0><<<grid, kVecThreads, 0, s>>>(args); break;                \
+        case 4: launch_pdl(kern<PREC_BLOCK, 4>, grid, kVecThreads, 0, s, args); break;                 \
+        case 8: launch_pdl(kern<PREC_BLOCK, 8>, grid, kVecThreads, 0, s, args); break;                 \
+        case 16: launch_pdl(kern<PREC_BLOCK, 16>, grid, kVecThreads, 0, s, args); break;               \
+        case 32: launch_pdl(kern<PREC_BLOCK, 32>, grid, kVecThreads, 0, s, args); break;               \
+        default: launch_pdl(kern<PREC_BLOCK, 0>, grid, kVecThreads, 0, s, args); break;                \
       }                                                                                         \
     } else if (S.pk == PREC_SCALAR) {                                                           \
-      kern<PREC_SCALAR, 0><<<grid, kVecThreads, 0, s>>>(args);                                  \
+      launch_pdl(kern<PREC_SCALAR, 0>, grid, kVecThreads, 0, s, args);                                  \
     } else {                                                                                    \
-      kern<PREC_NONE, 0><<<grid, kVecThreads, 0, s>>>(args);                                    \
+      launch_pdl(kern<PREC_NONE, 0>, grid, kVecThreads, 0, s, args);                                    \
     }                                                                                           \
     GK_TRY_CUDA(cudaGetLastError());                                                            \
   } while (0)
 
 #define LAUNCH_PK(kern, grid, s, args)                                                          \
   do {                                                                                          \
-    if (S.pk == PREC_BLOCK) kern<PREC_BLOCK><<<grid, kVecThreads, 0, s>>>(args);               \
-    else if (S.pk == PREC_SCALAR) kern<PREC_SCALAR><<<grid, kVecThreads, 0, s>>>(args);        \
-    else kern<PREC_NONE><<<grid, kVecThreads, 0, s>>>(args);                                    \
+    if (S.pk == PREC_BLOCK) launch_pdl(kern<PREC_BLOCK>, grid, kVecThreads, 0, s, args);               \
+    else if (S.pk == PREC_SCALAR) launch_pdl(kern<PREC_SCALAR>, grid, kVecThreads, 0, s, args);        \
+    else launch_pdl(kern<PREC_NONE>, grid, kVecThreads, 0, s, args);                                    \
     GK_TRY_CUDA(cudaGetLastError());                                                            \
   } while (0)
 
@@ -562,10 +574,10 @@ int enqueue_setup(const Solver& S, cudaStream_t s, const VecArgs& a) {
   if (S.kind == GK_CG || S.kind == GK_FCG) {
     LAUNCH_PK_BS(cg_start_kernel, S.grid_vec, s, a);
   } else if (S.kind == GK_CGS) {
-    cgs_start_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    launch_pdl(cgs_start_kernel, S.grid_vec, kVecThreads, 0, s, a);
     GK_TRY_CUDA(cudaGetLastError());
   } else {
-    bicg_start_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    launch_pdl(bicg_start_kernel, S.grid_vec, kVecThreads, 0, s, a);
     GK_TRY_CUDA(cudaGetLastError());
   }
   return GK_OK;
@@ -583,7 +595,7 @@ int enqueue_iteration(const Solver& S, cudaStream_t s, const VecArgs& a) {
     GK_TRY(spmv_launch(*S.A, ph, spmv_epi(S, EPI_DOT, S.rh, S.t, FIN_CGS_ALPHA, 1), s));
     LAUNCH_PK_BS(cgs_q_kernel, S.grid_vec, s, a);
     GK_TRY(spmv_launch(*S.A, S.sh, spmv_epi(S, EPI_COPY, nullptr, S.t, FIN_NONE, 1), s));
-    cgs_update_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    launch_pdl(cgs_update_kernel, S.grid_vec, kVecThreads, 0, s, a);
     GK_TRY_CUDA(cudaGetLastError());
   } else {
     const double* ph = (S.pk == PREC_NONE) ? S.p : S.ph;
@@ -592,7 +604,7 @@ int enqueue_iteration(const Solver& S, cudaStream_t s, const VecArgs& a) {
     GK_TRY(spmv_launch(*S.A, ph, spmv_epi(S, EPI_DOT, S.rh, S.q, FIN_BI_RHV, 1), s));
     LAUNCH_PK_BS(bicg_s_kernel, S.grid_vec, s, a);
     GK_TRY(spmv_launch(*S.A, sh, spmv_epi(S, EPI_DOT2, S.s, S.t, FIN_BI_OMEGA, 2), s));
-    bicg_update_kernel<<<S.grid_vec, kVecThreads, 0, s>>>(a);
+    launch_pdl(bicg_update_kernel, S.grid_vec, kVecThreads, 0, s, a);
     GK_TRY_CUDA(cudaGetLastError());
   }
   return GK_OK;

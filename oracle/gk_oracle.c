@@ -720,11 +720,33 @@ int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const 
     }
     float rho_prev = 1.0f, alpha = 1.0f, omega = 1.0f;
     int64_t k = 0;
-    int stop;
+    int stop, restarts = 0;
+    /* Breakdown of the Lanczos part (rho = r^.r or r^.v exactly zero in
+     * single precision, where r^ has become orthogonal to the Krylov
+     * residuals to within float rounding): restart from the current iterate
+     * with r^ = r, p = v = 0 and rho_prev = alpha = omega = 1 -- the remedy
+     * the Templates book (Barrett et al. 1994) gives for this breakdown -- at
+     * most OR_F32_RESTARTS times, then report the breakdown. */
+#define OR_F32_RESTARTS 4
+#define F32_RESTART_OR_STOP()                                       \
+  if (restarts < OR_F32_RESTARTS) {                                 \
+    restarts += 1;                                                  \
+    for (int64_t i = 0; i < n; ++i) {                               \
+      rh[i] = r[i];                                                 \
+      p[i] = 0.0f;                                                  \
+      v[i] = 0.0f;                                                  \
+    }                                                               \
+    rho_prev = 1.0f;                                                \
+    alpha = 1.0f;                                                   \
+    omega = 1.0f;                                                   \
+    continue;                                                       \
+  }                                                                 \
+  stop = OR_STOP_BREAKDOWN;                                         \
+  break
     while ((stop = check_stop(rnorm, tol, k, crit->max_iters)) == OR_STOP_NONE) {
       float rho = dotf(n, rh, r);
       if (!isfinite(rho)) { stop = OR_STOP_NAN; break; }
-      if (rho == 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      if (rho == 0.0f) { F32_RESTART_OR_STOP(); }
       float beta = (rho / rho_prev) * (alpha / omega);
       for (int64_t i = 0; i < n; ++i) p[i] = fmaf(beta, fmaf(-omega, v[i], p[i]), r[i]);
       jacf(n, jacobi, dinv, p, ph);
@@ -732,7 +754,7 @@ int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const 
       st->spmvs += 1;
       float rhv = dotf(n, rh, v);
       if (!isfinite(rhv)) { stop = OR_STOP_NAN; break; }
-      if (rhv == 0.0f) { stop = OR_STOP_BREAKDOWN; break; }
+      if (rhv == 0.0f) { F32_RESTART_OR_STOP(); }
       alpha = rho / rhv;
       for (int64_t i = 0; i < n; ++i) s[i] = fmaf(-alpha, v[i], r[i]);
       double snorm = sqrt((double)dotf(n, s, s));
@@ -763,6 +785,7 @@ int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const 
         break;
       }
     }
+#undef F32_RESTART_OR_STOP
     for (int64_t i = 0; i < n; ++i) x[i] = (double)x32[i];
     st->iters = k;
     st->stop_reason = stop;

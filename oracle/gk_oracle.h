@@ -164,6 +164,9 @@ int or_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double*
  * OR_ERR_SINGULAR if jacobi and a diagonal entry is missing or zero. */
 int or_cg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
               const double* b, double* x, const or_criteria* crit, or_status* st);
+/* or_bicgstab_f32 restarts (r^ = r, p = v = 0, rho_prev = alpha = omega = 1;
+ * the iteration count continues) when rho or r^.v is exactly zero before
+ * convergence, at most 4 times; then it reports OR_STOP_BREAKDOWN. */
 int or_bicgstab_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t jacobi,
                     const double* b, double* x, const or_criteria* crit, or_status* st);
 

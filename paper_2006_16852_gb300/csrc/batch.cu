@@ -22,6 +22,7 @@
 // k-th entries are one contiguous load and an entry costs 10 bytes in FP64
 // (6 in FP32) instead of CSR's 12.
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 #include <cstring>
 #include <memory>
@@ -66,6 +67,7 @@ struct BatchArgs {
 };
 
 constexpr int kBatchMaxOuter = 200;  // refinement steps per system
+constexpr int kBicgRestarts = 4;     // FP32 BiCGSTAB restarts after a breakdown, per system
 
 // ---------------------------------------------------------------------------
 // Reductions.  The totals of K per-thread values are formed in a fixed order
@@ -281,6 +283,25 @@ __device__ void bicg_system(const BatchArgs& a, T* V, T* red, double* sc, int sy
   T rho_prev = T(1), alpha = T(1), omega = T(1);
   long long it = 0;
   int stop = sys_check(rnorm, tol, 0, a.max_iters);
+  // FP32: a breakdown of the Lanczos part (rho or r^.v exactly zero, r^
+  // orthogonal to the Krylov residuals to within float rounding) restarts
+  // from the current iterate with r^ = r, p = v = 0, rho_prev = alpha =
+  // omega = 1, at most kBicgRestarts times (the iteration count continues).
+  int restarts = 0;
+  auto restart = [&]() -> bool {
+    if (!std::is_same<T, float>::value || restarts >= kBicgRestarts) return false;
+    ++restarts;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      RH[i] = R[i];
+      P[i] = T(0);
+      W[i] = T(0);
+    }
+    rho_prev = T(1);
+    alpha = T(1);
+    omega = T(1);
+    __syncthreads();
+    return true;
+  };
   while (stop == GK_STOP_NONE) {
     T rv[1] = {T(0)};
     for (int i = threadIdx.x; i < n; i += blockDim.x) rv[0] = fma(RH[i], R[i], rv[0]);
@@ -295,6 +316,7 @@ __device__ void bicg_system(const BatchArgs& a, T* V, T* red, double* sc, int sy
       out[2] = code;
     });
     if (o1[2] != 0.0) {
+      if (static_cast<int>(o1[2]) == GK_STOP_BREAKDOWN && restart()) continue;
       stop = static_cast<int>(o1[2]);
       break;
     }
@@ -317,6 +339,7 @@ __device__ void bicg_system(const BatchArgs& a, T* V, T* red, double* sc, int sy
       out[1] = code;
     });
     if (o2[1] != 0.0) {
+      if (static_cast<int>(o2[1]) == GK_STOP_BREAKDOWN && restart()) continue;
       stop = static_cast<int>(o2[1]);
       break;
     }

@@ -281,3 +281,22 @@ def test_batch_full_size_sampled(gk, orc, dtype, tol, kind):
         assert err <= (1e-6 if dtype == "f64" else 2e-3), (s, err)
     if dtype == "f64":
         assert _true_rel(orc, sys_ptr, A, b, x).max() <= 3e-10
+
+
+def test_batch_fp32_bicgstab_restart_cap_matches_oracle(gk, orc):
+    """A skew 2 x 2 system whose first r^.v is exactly zero, batched with a
+    regular one: the FP32 BiCGSTAB restarts, meets the same zero each time,
+    and stops with BREAKDOWN after its 4 restarts (x0 kept), as the oracle
+    does; its neighbour is unaffected and converges."""
+    skew = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, -1.0]))
+    reg = W.poisson2d(6)
+    A = (np.concatenate([skew[0], reg[0][1:] + skew[0][-1]]).astype(np.int32),
+         np.concatenate([skew[1], reg[1] + 2]).astype(np.int32), np.concatenate([skew[2], reg[2]]))
+    sys_ptr = np.array([0, 2, 38], np.int64)
+    b = np.concatenate([[1.0, 2.0], W.uniform_vector(36, 3)])
+    st, x = _run(gk, sys_ptr, A, b, "bicgstab", False, "f32", 1e-6)
+    ref = orc.bicgstab_f32(skew, b[:2], jacobi=False, tol=1e-6)
+    assert st["stop_reason"][0] == ref.stop_reason == gk.STOP_BREAKDOWN
+    assert int(st["iters"][0]) == ref.iters == 0
+    assert np.array_equal(x[:2], [0.0, 0.0])
+    assert st["stop_reason"][1] == gk.STOP_CONVERGED

@@ -146,3 +146,18 @@ def test_batch_oracle_refinement_reaches_fp64_residual(orc):
         assert r.stop_reason == 1 and 2 <= r.outer <= 6
         assert np.linalg.norm(full[r0:r1]) <= 1e-10 * np.linalg.norm(b[r0:r1])
         assert np.linalg.norm(x[r0:r1] - x64[r0:r1]) <= 1e-6 * np.linalg.norm(x64[r0:r1])
+
+
+def test_bicgstab_f32_restart_cap_on_a_skew_system(orc):
+    """A = [[0, 1], [-1, 0]] (skew), b = (1, 2), no preconditioner: r^ = r_0 = b
+    and v = A b give r^.v = 1*2 + 2*(-1) = 0 exactly, the Lanczos breakdown.
+    Each restart (r^ = r = b, p = v = 0) meets the same zero, so after the 4
+    restarts the solver stops with BREAKDOWN, no iteration done, x0 kept, and
+    SpMVs: the initial residual, one per attempt (5), the final true residual."""
+    A = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, -1.0]))
+    b = np.array([1.0, 2.0])
+    x0 = np.zeros(2)
+    res = orc.bicgstab_f32(A, b, x0=x0, jacobi=False, tol=1e-6)
+    assert res.stop_reason == orc.STOP_BREAKDOWN
+    assert res.iters == 0 and res.spmvs == 7
+    assert np.array_equal(res.x, x0)

@@ -1,6 +1,8 @@
 // precond.cu -- Jacobi preconditioners (Section 3.2): scalar diagonal scaling
 // and block Jacobi whose diagonal blocks are inverted by Gauss-Jordan
-// elimination with partial pivoting (Section 7.5), one warp per block.
+// elimination with partial pivoting (Section 7.5): one thread per block, in
+// registers, up to block size 8 (after a row-parallel extraction); one lane
+// group of a warp per block, in shared memory, above.
 #include <algorithm>
 #include <climits>
 #include <memory>
@@ -13,19 +15,26 @@ namespace gk {
 
 namespace {
 
+// First index k in [lo, hi) with col[k] >= c (hi if none); the columns of a
+// row are sorted.
+__device__ __forceinline__ int lower_col(const int32_t* __restrict__ col, int lo, int hi, int c) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(col + mid) < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void jacobi_scalar_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                      const double* __restrict__ val, int n, double* dinv, int* bad) {
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     double d = 0.0;
-    bool found = false;
-    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
-      if (col[k] == r) {
-        d = val[k];
-        found = true;
-        break;
-      }
-    }
+    const int k1 = __ldg(rowptr + r + 1);
+    const int k = lower_col(col, __ldg(rowptr + r), k1, r);
+    const bool found = k < k1 && __ldg(col + k) == r;
+    if (found) d = __ldg(val + k);
     if (!found || d == 0.0) {
       atomicMin(bad, r);
       dinv[r] = 0.0;
@@ -35,13 +44,188 @@ __global__ void jacobi_scalar_kernel(const int32_t* __restrict__ rowptr, const i
   }
 }
 
+// Pivot key of a candidate |w|: the magnitude's bit pattern, which orders
+// like |w| for every non-NaN value.  A NaN candidate never wins (-1), and a
+// NaN on the diagonal is never displaced (the largest key): the strict
+// comparison "a > best" of the elimination takes no NaN.
+__device__ __forceinline__ long long piv_key(double w, bool diag) {
+  const long long b = __double_as_longlong(w) & 0x7fffffffffffffffll;
+  if (b > 0x7ff0000000000000ll) return diag ? 0x7fffffffffffffffll : -1ll;
+  return b;
+}
+
+// Small blocks (bs <= 8) in two launches.
+//
+// bj_extract_kernel: one thread per row writes that row of its dense
+// diagonal block (row-major, zeros where A has no entry) into the output
+// array: its entries inside the block are a contiguous run of the sorted
+// columns, found by a binary search for the first column >= the block's
+// first row.  Few registers, full occupancy: the searches' load latency is
+// hidden by other warps.
+template <int BT>
+__global__ void __launch_bounds__(256) bj_extract_kernel(const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const double* __restrict__ val, int n, int bs,
+                                                         double* blocks) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const int blk = r / bs, i = r - blk * bs, r0 = blk * bs;
+    const int m = min(bs, n - r0);
+    const int k1 = __ldg(rowptr + r + 1);
+    double row[BT];
+#pragma unroll
+    for (int j = 0; j < BT; ++j) row[j] = 0.0;
+    for (int k = lower_col(col, __ldg(rowptr + r), k1, r0); k < k1; ++k) {
+      const int c = __ldg(col + k) - r0;
+      if (c >= m) break;
+      const double v = __ldg(val + k);
+#pragma unroll
+      for (int j = 0; j < BT; ++j)
+        if (c == j) row[j] = v;
+    }
+    double* out = blocks + static_cast<int64_t>(blk) * bs * bs + static_cast<int64_t>(i) * m;
+#pragma unroll
+    for (int j = 0; j < BT; ++j)
+      if (j < m) out[j] = row[j];
+  }
+}
+
+// bj_invert_kernel: one thread per diagonal block, the block in registers
+// (BT = 2, 4 or 8: the largest block this instantiation takes).  A thread
+// block takes kBjRegThreads consecutive blocks: they are one contiguous run
+// of the output array, loaded and stored coalesced through shared memory
+// (element-major, block-minor, odd stride) and inverted in place there.
+// The elimination is the Gauss-Jordan of [D | I] with partial pivoting,
+// stored in place: once column k of the left half is eliminated it holds
+// nothing (the unit vector e_k), so its registers take the right-half
+// column that becomes non-zero at step k -- the identity column of the row
+// that is pivot row k (orig[k]).  Every stored entry receives exactly the
+// operations of the augmented elimination (the pivot row scaled by the
+// reciprocal of the pivot, w_ij = fma(-w_ik, w_kj, w_ij) for the other
+// rows); the only operations left out act on entries that are structurally
+// zero and leave them zero.  Rows are exchanged by selects with static
+// register indices (the pivot row index is data, the loop indices are not).
+// The FP64 pipe bounds this kernel: about bs^3 fused multiply-adds and bs
+// divisions per block, each with all 32 lanes of a warp busy.
+constexpr int kBjRegThreads = 128;
+constexpr int kBjLds = kBjRegThreads + 1;
+
+// a / d for 0 <= a < 2^16 and 1 <= d <= 64 through a float reciprocal:
+// (a + 0.5) / d lies at least 1/128 from an integer and the float product
+// errs by under 2^-7 of that, so the truncation is exact (an integer division
+// would cost tens of instructions per element).
+__device__ __forceinline__ int div_small(int a, float inv_d) {
+  return static_cast<int>((static_cast<float>(a) + 0.5f) * inv_d);
+}
+
+template <int BT>
+__global__ void __launch_bounds__(kBjRegThreads) bj_invert_kernel(int n, int bs, int nblocks, double* blocks,
+                                                                  int* bad) {
+  extern __shared__ double S[];  // [BT * BT][kBjLds]
+  const int bs2 = bs * bs;
+  const int last_m = n - (nblocks - 1) * bs;
+  const float inv_bs2 = 1.0f / static_cast<float>(bs2), inv_bs = 1.0f / static_cast<float>(bs);
+  const float inv_last = 1.0f / static_cast<float>(last_m);
+  for (int blk0 = blockIdx.x * kBjRegThreads; blk0 < nblocks; blk0 += gridDim.x * kBjRegThreads) {
+    const int nb = min(kBjRegThreads, nblocks - blk0);
+    const int64_t base = static_cast<int64_t>(blk0) * bs2;
+    const int len = (nb - 1) * bs2 + (blk0 + nb == nblocks ? last_m * last_m : bs2);  // <= 128 * 64
+    __syncthreads();  // the previous run's stores have read S
+    for (int o = threadIdx.x; o < len; o += kBjRegThreads) {
+      const int b = div_small(o, inv_bs2), e = o - b * bs2;
+      const bool lastb = blk0 + b == nblocks - 1;
+      const int mb = lastb ? last_m : bs;
+      const int i = div_small(e, lastb ? inv_last : inv_bs), j = e - i * mb;
+      S[(i * BT + j) * kBjLds + b] = __ldcs(blocks + base + o);
+    }
+    __syncthreads();
+    const int b = threadIdx.x;
+    if (b < nb) {
+      const int blk = blk0 + b;
+      const int m = min(bs, n - blk * bs);
+      double A[BT][BT];
+      int orig[BT];
+#pragma unroll
+      for (int i = 0; i < BT; ++i) {
+        orig[i] = i;
+#pragma unroll
+        for (int j = 0; j < BT; ++j) A[i][j] = (i < m && j < m) ? S[(i * BT + j) * kBjLds + b] : 0.0;
+      }
+      bool singular = false;
+#pragma unroll
+      for (int k = 0; k < BT; ++k) {
+        if (k < m && !singular) {
+          // pivot: largest |A[i][k]|, i in [k, m), lowest row on ties
+          long long best = piv_key(A[k][k], true);
+          int piv = k;
+#pragma unroll
+          for (int i = k + 1; i < BT; ++i) {
+            const long long a = piv_key(A[i][k], false);
+            if (i < m && a > best) {
+              best = a;
+              piv = i;
+            }
+          }
+          if (best == 0) {
+            singular = true;
+          } else {
+#pragma unroll
+            for (int i = k + 1; i < BT; ++i) {
+              const bool sw = i == piv;
+#pragma unroll
+              for (int j = 0; j < BT; ++j) {
+                const double t = A[k][j];
+                A[k][j] = sw ? A[i][j] : t;
+                A[i][j] = sw ? t : A[i][j];
+              }
+              const int t = orig[k];
+              orig[k] = sw ? orig[i] : t;
+              orig[i] = sw ? t : orig[i];
+            }
+            const double rcp = 1.0 / A[k][k];
+#pragma unroll
+            for (int j = 0; j < BT; ++j)
+              if (j != k) A[k][j] = A[k][j] * rcp;
+            A[k][k] = rcp;  // right-half column orig[k]: 1 * rcp
+#pragma unroll
+            for (int i = 0; i < BT; ++i) {
+              if (i != k && i < m) {
+                const double f = A[i][k];
+#pragma unroll
+                for (int j = 0; j < BT; ++j)
+                  if (j != k) A[i][j] = fma(-f, A[k][j], A[i][j]);
+                A[i][k] = fma(-f, rcp, 0.0);
+              }
+            }
+          }
+        }
+      }
+      if (singular) atomicMin(bad, blk);
+      // inverse(i, orig[k]) = A[i][k]
+#pragma unroll
+      for (int i = 0; i < BT; ++i)
+#pragma unroll
+        for (int k = 0; k < BT; ++k)
+          if (i < m && k < m) S[(i * BT + orig[k]) * kBjLds + b] = A[i][k];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < len; o += kBjRegThreads) {
+      const int bb = div_small(o, inv_bs2), e = o - bb * bs2;
+      const bool lastb = blk0 + bb == nblocks - 1;
+      const int mb = lastb ? last_m : bs;
+      const int i = div_small(e, lastb ? inv_last : inv_bs), j = e - i * mb;
+      blocks[base + o] = S[(i * BT + j) * kBjLds + bb];
+    }
+  }
+}
+
 // Gauss-Jordan inversion of the diagonal blocks on the augmented matrices
-// [D | I] held in shared memory.  A warp inverts 32/GW blocks at once, one
+// [D | I] held in shared memory (block sizes above 8).  A warp inverts 32/GW blocks at once, one
 // group of GW lanes (GW = the next power of two >= the block size) per
 // block, lane i owning row i; each block's tile has an odd row stride
 // (2 GW + 1 doubles) so column accesses are conflict-free.
 // Pivot: largest |entry| in column k at or below row k, lowest row on ties
-// (xor butterfly inside the group).  The pivot row is scaled by the
+// (xor butterfly over piv_key inside the group).  The pivot row is scaled by the
 // reciprocal of the pivot and every other row i is updated
 // w_ij = fma(-w_ik, w_kj, w_ij).  Columns left of and at k are never read
 // again once step k is done, so only columns j > k are updated: the right
@@ -67,10 +251,14 @@ __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
     for (int idx = i; idx < GW * LD; idx += GW) W[idx] = 0.0;
     __syncwarp();
     if (i < m) {
+      // the row's entries inside the block: a contiguous run of the sorted
+      // columns, found by a binary search for the first column >= r0
       const int r = r0 + i;
-      for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
-        const int c = col[k];
-        if (c >= r0 && c < r0 + m) W[i * LD + (c - r0)] = val[k];
+      const int k1 = __ldg(rowptr + r + 1);
+      for (int k = lower_col(col, __ldg(rowptr + r), k1, r0); k < k1; ++k) {
+        const int c = __ldg(col + k) - r0;
+        if (c >= m) break;
+        W[i * LD + c] = __ldg(val + k);
       }
       W[i * LD + m + i] = 1.0;
     }
@@ -78,18 +266,18 @@ __global__ void __launch_bounds__(kBjWarps * 32) bj_generate_kernel(
     bool singular = false;
     for (int k = 0; k < bs; ++k) {
       const bool live = k < m && !singular;
-      double a = (live && i >= k && i < m) ? fabs(W[i * LD + k]) : -1.0;
+      long long a = (live && i >= k && i < m) ? piv_key(W[i * LD + k], i == k) : -2ll;
       int idx = i;
 #pragma unroll
       for (int o = GW / 2; o > 0; o >>= 1) {
-        const double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+        const long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
         if (a2 > a || (a2 == a && i2 < idx)) {
           a = a2;
           idx = i2;
         }
       }
-      if (live && !(a > 0.0)) singular = true;
+      if (live && a == 0) singular = true;
       const bool work = live && !singular;
       const int piv = idx;
       __syncwarp();
@@ -133,10 +321,25 @@ int launch_bj_generate(const Matrix* A, int n, int bs, int nblocks, double* bloc
   return GK_OK;
 }
 
+template <int BT>
+int launch_bj_generate_reg(const Matrix* A, int n, int bs, int nblocks, double* blocks, int* bad,
+                           cudaStream_t s) {
+  const int64_t ge = std::min<int64_t>((n + 255) / 256, 16 * static_cast<int64_t>(sm_count()));
+  bj_extract_kernel<BT><<<static_cast<int>(std::max<int64_t>(ge, 1)), 256, 0, s>>>(A->rowptr, A->col, A->val, n,
+                                                                                   bs, blocks);
+  const size_t smem = sizeof(double) * BT * BT * kBjLds;
+  GK_TRY(set_smem(bj_invert_kernel<BT>, smem));
+  const int64_t g = std::min<int64_t>((nblocks + kBjRegThreads - 1) / kBjRegThreads,
+                                      4 * static_cast<int64_t>(sm_count()));
+  bj_invert_kernel<BT><<<static_cast<int>(std::max<int64_t>(g, 1)), kBjRegThreads, smem, s>>>(n, bs, nblocks,
+                                                                                               blocks, bad);
+  return GK_OK;
+}
+
 int bj_generate(const Matrix* A, int n, int bs, int nblocks, double* blocks, int* bad, cudaStream_t s) {
-  if (bs <= 2) return launch_bj_generate<2>(A, n, bs, nblocks, blocks, bad, s);
-  if (bs <= 4) return launch_bj_generate<4>(A, n, bs, nblocks, blocks, bad, s);
-  if (bs <= 8) return launch_bj_generate<8>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 2) return launch_bj_generate_reg<2>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 4) return launch_bj_generate_reg<4>(A, n, bs, nblocks, blocks, bad, s);
+  if (bs <= 8) return launch_bj_generate_reg<8>(A, n, bs, nblocks, blocks, bad, s);
   if (bs <= 16) return launch_bj_generate<16>(A, n, bs, nblocks, blocks, bad, s);
   return launch_bj_generate<32>(A, n, bs, nblocks, blocks, bad, s);
 }

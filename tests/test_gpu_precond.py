@@ -32,7 +32,22 @@ def _pivoting_matrix(n=200, seed=3):
     return rowptr.astype(np.int32), cols.astype(np.int32), D[rows, cols]
 
 
+def _nan_block_matrix():
+    """A NaN on a diagonal entry and a NaN below a pivot: the pivot choice
+    takes no NaN (the strict comparison of the elimination), so the NaN
+    spreads through its block instead of stopping the generation."""
+    D = np.diag([2.0, 3.0, 4.0, 5.0, 1.0, 2.0, 3.0, 4.0, 6.0, 7.0])
+    D[1, 1] = np.nan
+    D[6, 5] = np.nan
+    D[0, 2] = 1.0
+    rows, cols = np.nonzero(D)
+    rowptr = np.zeros(11, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=10), out=rowptr[1:])
+    return rowptr.astype(np.int32), cols.astype(np.int32), D[rows, cols]
+
+
 CASES = {
+    "nan_blocks": _nan_block_matrix(),
     "stencil27_12": W.stencil27(12),
     "convdiff_30": W.convdiff2d(30, wind=1.5),
     "pivoting_200": _pivoting_matrix(),
@@ -56,7 +71,9 @@ def test_jacobi_generate_and_apply_bit_exact(gk, orc, name, bs):
     got = P.blocks()
     want = ref.dinv if bs == 1 else ref.blocks
     assert got.shape == want.shape
-    assert np.array_equal(got, want), f"max diff {np.abs(got - want).max()}"
+    assert np.array_equal(got, want, equal_nan=True), f"max diff {np.abs(got - want).max()}"
+    if name == "nan_blocks":
+        return
     r = W.uniform_vector(n, 9)
     z = to_dev(np.zeros(n))
     gk.precond_apply(P, to_dev(r), z)
@@ -85,3 +102,30 @@ def test_bad_block_size(gk):
         with pytest.raises(gk.GkError) as ei:
             gk.Precond(M, bs)
         assert ei.value.code == 1
+
+
+@pytest.fixture(scope="module")
+def bench_mats():
+    return {"stencil27_128": W.stencil27(128), "powerlaw_1M": W.powerlaw(1_000_000, seed=3)}
+
+
+@pytest.mark.parametrize("which,bs", [("stencil27_128", 1), ("stencil27_128", 8), ("stencil27_128", 16),
+                                      ("powerlaw_1M", 1), ("powerlaw_1M", 4), ("powerlaw_1M", 32)])
+def test_generate_full_size_bit_exact(gk, orc, bench_mats, which, bs):
+    """The benchmark's generations at full size -- scalar and block Jacobi of
+    the 27-point matrix on 128^3 (bs 8: 262,144 blocks) and of the power-law
+    matrix with 10^6 rows (bs 4), plus one size each of the shared-memory
+    form (bs 16, 32) -- every inverse block bit for bit against the oracle,
+    including the blocks of the longest rows (10^4 entries), whose in-block
+    entries the kernel finds by binary search."""
+    A = bench_mats[which]
+    M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="csr")
+    got = gk.Precond(M, bs).blocks()
+    ref = orc.precond(A, "jacobi" if bs == 1 else "block_jacobi", bs)
+    want = ref.dinv if bs == 1 else ref.blocks
+    assert got.shape == want.shape
+    assert np.array_equal(got, want), f"{int((got != want).sum())} entries differ"
+    if which == "powerlaw_1M" and bs > 1:
+        # the blocks holding the longest rows were among those compared
+        lens = np.diff(A[0])
+        assert lens.max() > 4096

@@ -1026,6 +1026,51 @@ def run_paper_bandwidth(dev, triad_gbs=None):
 # kernel against a plain device copy on the same device
 # ---------------------------------------------------------------------------
 
+def run_gather_ceiling(step, reps=20):
+    """The random-gather ceiling of the power-law SpMV: gk_gather_dot over
+    (b)'s own column/value stream (29 M entries, columns uniform over 10^6
+    rows) -- the SpMV's per-entry work without its rows -- timed back to
+    back with GK_CSR's apply of (b) and with the same stream's columns
+    replaced by a uniformly random permutation-free draw; CUDA events,
+    median of reps after 3 warm-ups."""
+    import torch
+    gk = step.gk
+    dev = step.dev
+    stream = step.stream
+    rowptr, col, val = step.dB
+    n, nnz = step.nb, step.nnzb
+    x = step.x["b"]
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    col_rand = torch.randint(0, n, (nnz,), generator=g, dtype=torch.int32).to(dev)
+    M = step.mats[("b", "csr")]
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    t_gather = timed(lambda: gk.gather_dot(col, val, x, res))
+    t_rand = timed(lambda: gk.gather_dot(col_rand, val, x, res))
+    t_csr = timed(lambda: gk.apply(M, x, step.y["b"]))
+    by = nnz * 12 + n * 8
+    del col_rand
+    return {"workload": "(b) power-law, its CSR column/value stream: %d entries, x of %d doubles (8 MB, "
+                        "L2-resident)" % (nnz, n),
+            "gather_dot_ms": round(t_gather, 4), "gather_dot_GB/s": round(by / (t_gather * 1e-3) / 1e9, 1),
+            "gather_dot_uniform_cols_ms": round(t_rand, 4), "gk_csr_apply_ms": round(t_csr, 4),
+            "gk_csr_over_ceiling": round(t_csr / t_gather, 3),
+            "timing": "CUDA events, median of %d after 3 warm-ups, back to back in one process" % reps}
+
+
 def run_stream(dev, n=1 << 27):
     """gk_dot over two vectors of n doubles (1 GiB each: larger than L2),
     against torch's device copy of one of them (read + write bytes) and the
@@ -1259,6 +1304,7 @@ def run_gpu(args):
         out["krylov"] = run_krylov(dev)
     if not args.no_latency:
         out["latency"] = run_latency(dev)
+    out["gather_ceiling"] = run_gather_ceiling(step)
     if not args.no_stream:
         out["stream"] = run_stream(dev)
         out["paper_bandwidth"] = run_paper_bandwidth(dev, out["stream"]["torch_triad"]["GB/s"])
@@ -1411,6 +1457,41 @@ def run_infer_only(args):
     return {"infer_only": B, "ms": round(ms, 4), "TFLOP/s": round(2.0 * B * macs / (ms * 1e-3) / 1e12, 2)}
 
 
+def run_precond_only(args):
+    """Repeated preconditioner generations of matrix a|b (CSR) with one
+    block size (profiling aid)."""
+    import torch
+    import paper_2006_16852_gb300 as gk
+    import workloads as W
+    gk.load()
+    mat, bs = args.precond_only.split(":")
+    bs = int(bs)
+    if mat == "a":
+        A = W.stencil27(128 if not args.small else 32)
+    else:
+        A = W.powerlaw(1_000_000 if not args.small else 20000, seed=3)
+    n = A[0].size - 1
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    M = gk.Matrix(t(A[0]), t(A[1]), t(A[2]), fmt="csr")
+    for _ in range(args.warmup):
+        gk.Precond(M, bs)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P = gk.Precond(M, bs)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del P
+    by = precond_bytes(n, bs, in_block_entries(A, bs))
+    med = statistics.median(ms)
+    fl = precond_fp64_ops(n, bs)
+    return {"precond_only": args.precond_only, "ms": round(med, 4), "GB/s": round(by / (med * 1e-3) / 1e9, 1),
+            "fp64_floor_ms": round(fl / (NOMINAL_FP64_TFLOPS * 0.5e12) * 1e3, 4)}
+
+
 def run_solve_only(args):
     """Repeated solves of one configuration MAT:FMT:PREC:KIND, e.g. a:ell:1:cg
     (MAT a = 27-point 128^3, b = power-law 10^6, c = convection-diffusion
@@ -1486,6 +1567,8 @@ def main():
     ap.add_argument("--spmv-only", metavar="MAT:FMT[:dot]", default=None,
                     help="only time repeated applies of matrix a|b in one format, with ':dot' the apply "
                          "with the fused dot product of the Krylov steps (profiling aid)")
+    ap.add_argument("--precond-only", metavar="MAT:BS", default=None,
+                    help="only time repeated preconditioner generations of matrix a|b (profiling aid)")
     ap.add_argument("--solve-only", metavar="MAT:FMT:PREC:KIND", default=None,
                     help="only time repeated solves of one configuration (profiling aid)")
     ap.add_argument("--host-loop", type=int, default=0, metavar="K",
@@ -1532,6 +1615,8 @@ def main():
         out = run_infer_only(args)
     elif args.solve_only:
         out = run_solve_only(args)
+    elif args.precond_only:
+        out = run_precond_only(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:

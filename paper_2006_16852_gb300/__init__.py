@@ -39,7 +39,8 @@ EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get
            "gk_wsnet_set_loss",
            "gk_wsnet_forward", "gk_wsnet_gradients", "gk_wsnet_train_step", "gk_wsnet_infer_bf16",
            "gk_wsnet_check",
-           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc", "gk_wait_selftest")
+           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc", "gk_gather_dot",
+           "gk_wait_selftest")
 BATCH_CLASSES = 8
 BATCH_BLOCK_SIZES = (32, 64, 128, 256)
 
@@ -145,6 +146,7 @@ def load(path: str | None = None):
         "gk_wsnet_destroy": [vp],
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
+        "gk_gather_dot": [i64, vp, vp, vp, i64, vp, vp],
         "gk_wait_selftest": [vp, vp],
     }
     for name, args in sig.items():
@@ -363,6 +365,16 @@ def dot_noalloc(x, y, result, stream=None):
     n = x.numel()
     _check_vec(y, n, "y")
     _check(lib().gk_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(result), _stream(stream, x, y, result)))
+    return result
+
+
+def gather_dot(c, v, x, result, stream=None):
+    """result[0] = sum_k v[k] x[c[k]] (device tensors; c int32): the SpMV's
+    per-entry work without its rows, the gather ceiling of the SpMV kernels."""
+    n = c.numel()
+    _check_vec(v, n, "v")
+    _check(lib().gk_gather_dot(n, _ptr(c), _ptr(v), _ptr(x), x.numel(), _ptr(result),
+                               _stream(stream, c, v, x, result)))
     return result
 
 

@@ -140,6 +140,44 @@ __global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ x, 
   if (grid_sum<1>(a, partials, counter, scratch, out) && threadIdx.x == 0) result[0] = out[0];
 }
 
+// Gathered dot product sum_k v_k x_{c_k} over a stream of (c_k, v_k) pairs:
+// the SpMV's per-entry work (a streamed index and value, a gathered x, one
+// fma) without its row structure.  Each thread takes entries k = g, g + T,
+// ... (coalesced, streamed), kGatherBatch gathers in flight; 8 blocks of 256
+// threads per SM within 32 registers.  An index outside [0, n_x) contributes
+// 0 (checked per entry; the SpMV kernels rely on the validation at matrix
+// creation instead).
+constexpr int kGatherBatch = 8;
+
+__global__ void __launch_bounds__(256, 8) gather_dot_kernel(const int32_t* __restrict__ c,
+                                                            const double* __restrict__ v,
+                                                            const double* __restrict__ x, int64_t n,
+                                                            uint32_t n_x, double* partials,
+                                                            unsigned int* counter, double* result) {
+  __shared__ double scratch[kRedScratch];
+  double a[1] = {0.0};
+  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; k + (kGatherBatch - 1) * T < n; k += kGatherBatch * T) {
+    int cc[kGatherBatch];
+    double vv[kGatherBatch], xv[kGatherBatch];
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) cc[u] = __ldcs(c + k + u * T);
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) vv[u] = __ldcs(v + k + u * T);
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) xv[u] = static_cast<uint32_t>(cc[u]) < n_x ? __ldg(x + cc[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) a[0] = fma(vv[u], xv[u], a[0]);
+  }
+  for (; k < n; k += T) {
+    const int ck = __ldcs(c + k);
+    a[0] = fma(__ldcs(v + k), static_cast<uint32_t>(ck) < n_x ? __ldg(x + ck) : 0.0, a[0]);
+  }
+  double out[1];
+  if (grid_sum<1>(a, partials, counter, scratch, out) && threadIdx.x == 0) result[0] = out[0];
+}
+
 struct DotWorkspace {
   double* partials = nullptr;
   unsigned int* counter = nullptr;
@@ -147,6 +185,7 @@ struct DotWorkspace {
 };
 std::mutex g_dot_mu;
 DotWorkspace g_dot_ws[64];
+DotWorkspace g_gather_ws[64];
 
 }  // namespace
 
@@ -239,6 +278,32 @@ extern "C" int gk_dot(int64_t n, const double* x, const double* y, double* resul
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   dot_kernel<<<ws->grid, 256, 0, s>>>(x, y, n, ws->partials, ws->counter, result);
+  GK_TRY_CUDA(cudaGetLastError());
+  return GK_OK;
+}
+
+extern "C" int gk_gather_dot(int64_t n, const int32_t* c, const double* v, const double* x, int64_t n_x,
+                             double* result, void* stream) {
+  if (n < 0 || n_x < 0 || n_x > 0x7fffffff || !result || (n > 0 && (!c || !v || !x)))
+    return set_error(GK_ERR_ARG, "gk_gather_dot: bad argument");
+  if (is_host(c) || is_host(v) || is_host(x) || is_host(result))
+    return set_error(GK_ERR_NOT_DEVICE, "gk_gather_dot: c, v, x and result must be device memory");
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return set_error(GK_ERR_UNSUPPORTED, "gk_gather_dot: device index %d", dev);
+  DotWorkspace* ws;
+  {
+    std::lock_guard<std::mutex> lock(g_dot_mu);
+    ws = &g_gather_ws[dev];
+    if (!ws->partials) {
+      ws->grid = 8 * sm_count();
+      GK_TRY(dalloc_n(&ws->partials, static_cast<size_t>(ws->grid), nullptr));
+      GK_TRY(dalloc_n(&ws->counter, 1, nullptr));
+      GK_TRY_CUDA(cudaMemset(ws->counter, 0, sizeof(unsigned int)));
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gather_dot_kernel<<<ws->grid, 256, 0, s>>>(c, v, x, n, static_cast<uint32_t>(n_x), ws->partials, ws->counter,
+                                             result);
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }

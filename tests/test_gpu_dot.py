@@ -42,3 +42,28 @@ def test_dot_empty(gk):
     z = torch.zeros(0, dtype=torch.float64, device="cuda:0")
     gk.dot(z, z, r)
     assert r.item() == 0.0
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 2_000_003])
+def test_gather_dot_against_oracle(gk, orc, n):
+    """gk_gather_dot = sum_k v_k x[c_k] within 1e-13 sum |v_k x[c_k]| of the
+    oracle's sequential dot of v with the gathered x; an index outside
+    [0, len(x)) contributes 0; repeated calls are bit-identical."""
+    import torch
+    nx = 100_003
+    rng = np.random.default_rng(40 + n % 7)
+    c = rng.integers(0, nx, n).astype(np.int32)
+    if n > 10:
+        c[3] = -1
+        c[7] = nx
+    v = W.uniform_vector(n, 41)
+    x = W.uniform_vector(nx, 42)
+    xg = np.where((c >= 0) & (c < nx), x[np.clip(c, 0, nx - 1)], 0.0)
+    r = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    cd = torch.from_numpy(c).to("cuda:0")
+    gk.gather_dot(cd, to_dev(v), to_dev(x), r[0:1])
+    gk.gather_dot(cd, to_dev(v), to_dev(x), r[1:2])
+    got = r.cpu().numpy()
+    assert got[0] == got[1]
+    ref = orc.dot(v, xg)
+    assert abs(got[0] - ref) <= 1e-13 * float(np.sum(np.abs(v * xg))), (got[0], ref)

@@ -132,6 +132,18 @@ def energy_error(M: gk.Matrix, x, xs) -> float:
     return float(np.sqrt(max(v[0], 0.0) / v[1]))
 
 
+def rel_residual(M: gk.Matrix, x, b) -> float:
+    """||b - A x|| / ||b|| with the library's advanced apply and dot."""
+    import torch
+    r = b.clone()
+    gk.apply_adv(-1.0, M, x, 1.0, r)
+    d = torch.zeros(2, dtype=torch.float64, device=x.device)
+    gk.dot(r, r, d[0:1])
+    gk.dot(b, b, d[1:2])
+    v = d.cpu().numpy()
+    return float(np.sqrt(v[0] / v[1]))
+
+
 def evaluate(net: gk.WsNet, indices, out_scale: float, tol: float = 1e-10, dev="cuda:0", project: bool = True):
     """Jacobi-CG from zero and from the network's x0 on problems `indices`:
     iterations, true residuals and device time (the warm start's time includes
@@ -165,6 +177,7 @@ def evaluate(net: gk.WsNet, indices, out_scale: float, tol: float = 1e-10, dev="
         x0 = torch.zeros_like(bd)
         net.warm_start(gd, bd, x0, out_scale, A=M if project else None)
         rec["x0_energy_error"] = energy_error(M, x0, xs)
+        rec["x0_rel_residual"] = rel_residual(M, x0, bd)
         out.append(rec)
     return out
 
@@ -177,6 +190,7 @@ def summarize(res):
     return {"problems": len(res), "iters_zero": z, "iters_warm": w, "iters_ratio": round(w / z, 4),
             "ms_zero": round(zm, 3), "ms_warm": round(wm, 3), "time_ratio": round(wm / zm, 4),
             "x0_energy_error_mean": round(float(np.mean([r["x0_energy_error"] for r in res])), 4),
+            "x0_rel_residual_mean": round(float(np.mean([r["x0_rel_residual"] for r in res])), 4),
             "max_rel_res_true_warm": max(r["warm"]["rel_res_true"] for r in res)}
 
 

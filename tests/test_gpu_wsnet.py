@@ -170,11 +170,13 @@ def test_features_and_targets(gk):
 def test_warm_start_against_zero_start(gk, orc):
     """Train on 2,048 problems of the family at 64 x 64 (solutions from the
     library's CG, energy-norm loss), then solve 12 held-out problems from the
-    network's x0 and from zero.  The gain: the predicted x0 is much closer to
+    network's x0 and from zero.  What the network gains: x0 is much closer to
     the solution than x0 = 0 in the A-norm CG minimises (relative energy error
-    < 0.5, against 1 for zero).  Judged by CG: every warm-started solve meets
-    ||b - A x|| <= 1e-10 ||b|| (the oracle's SpMV) and needs no more than 3 %
-    more iterations than the zero start."""
+    < 0.5, against 1 for zero).  What it does not: its residual b - A x0 is
+    larger than b itself (its error is broadband and A amplifies the high
+    frequencies), so CG to ||r|| <= 1e-10 ||b|| needs as many iterations as
+    from zero -- asserted as measured: within 2 % of the zero start, every
+    warm-started solve meeting the criterion (the oracle's SpMV)."""
     from paper_2006_16852_gb300 import learned as LN
     net = gk.WsNet(64, 64, 16, LN.dilations_for(64))
     net.set_params(LN.init_params(0))
@@ -186,7 +188,8 @@ def test_warm_start_against_zero_start(gk, orc):
     s = LN.summarize(res)
     print(s)
     assert s["x0_energy_error_mean"] < 0.5
-    assert s["iters_warm"] <= 1.03 * s["iters_zero"]
+    assert s["x0_rel_residual_mean"] > 1.0
+    assert s["iters_warm"] <= 1.02 * s["iters_zero"]
     for i, r in zip(range(100000, 100012), res):
         assert r["zero"]["stop_reason"] == r["warm"]["stop_reason"] == gk.STOP_CONVERGED
         assert r["warm"]["rel_res_true"] <= 1.05e-10
@@ -203,8 +206,10 @@ def test_warm_start_against_zero_start(gk, orc):
 
 def test_committed_network_on_held_out_problems(gk, orc):
     """The trained 256 x 256 network shipped with the package: on held-out
-    problems its x0 is closer to the solution than zero in the A-norm, and
-    CG from it meets the criterion (checked with the oracle's SpMV)."""
+    problems its x0 is closer to the solution than zero in the A-norm while
+    its residual exceeds ||b|| (7.5-10.8 ||b|| measured on held-out
+    problems), and CG from it meets the criterion (checked with the
+    oracle's SpMV)."""
     import os
     from paper_2006_16852_gb300 import learned as LN
     path = os.path.join(LN.DATA_DIR, "wsnet_256.npz")
@@ -213,6 +218,7 @@ def test_committed_network_on_held_out_problems(gk, orc):
     res = LN.evaluate(net, [1_000_100, 1_000_101], scale)
     for i, r in zip((1_000_100, 1_000_101), res):
         assert r["x0_energy_error"] < 0.6
+        assert r["x0_rel_residual"] > 1.0
         assert r["warm"]["stop_reason"] == gk.STOP_CONVERGED
     g, A, b = W.grf_problem(256, 1_000_100)
     M = gk.Matrix(to_dev(A[0]), to_dev(A[1]), to_dev(A[2]), fmt="ell")

@@ -40,6 +40,13 @@ int dalloc_n(T** p, size_t n, int64_t* counter) {
   return dalloc(reinterpret_cast<void**>(p), n * sizeof(T), counter);
 }
 void dfree(void* p);
+// Stream-ordered allocation on s from the device's default memory pool (which
+// keeps up to 8 GB of freed memory for reuse); dfree releases it.
+int dalloc_async(void** p, size_t bytes, int64_t* counter, cudaStream_t s);
+template <class T>
+int dalloc_async_n(T** p, size_t n, int64_t* counter, cudaStream_t s) {
+  return dalloc_async(reinterpret_cast<void**>(p), n * sizeof(T), counter, s);
+}
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
@@ -71,6 +78,25 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Launches kern<<<grid, block, smem, s>>>(args...) as a cooperative kernel
+// (every block resident at once, which a grid-wide barrier needs); valid in
+// stream capture (the graph node keeps the attribute).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_coop(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
@@ -164,8 +190,8 @@ struct Epi {
 // matrix handle
 // ---------------------------------------------------------------------------
 constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 8;  // merge-path items (row ends + nonzeros) per thread
-constexpr int kMergeTile = kMergeThreads * kMergeItems;
+constexpr int kMergeItems = 8;  // merge-path items (row ends + nonzeros) per lane
+constexpr int kMergeTile = 32 * kMergeItems;  // items per warp tile
 // GK_CSR: rows of up to kSliceMaxLen entries go to length-sorted slices of 32
 // rows; longer rows are summed one warp per row, beyond kBlockRowLen one
 // thread block per row.
@@ -189,12 +215,11 @@ struct MergePlan {
   const double* val = nullptr;
   int32_t* tile_i = nullptr;  // [n_tiles + 1] merge coordinates of tile starts
   int32_t* tile_j = nullptr;
-  // per-apply scratch: partial sums of rows cut by tile boundaries
+  // per-apply scratch: partial sums of rows cut by tile boundaries (per
+  // tile: the part of its first row when that row began in an earlier tile
+  // and ends in this one; the part of the row left open at its end)
   double* head_val = nullptr;
-  int32_t* head_row = nullptr;
   double* carry_val = nullptr;
-  int32_t* carry_row = nullptr;
-  int32_t* cont = nullptr;
   int grid = 0;
 };
 
@@ -222,7 +247,8 @@ struct Matrix {
   int64_t n_mid = 0;
   int32_t* big_rows = nullptr;
   int64_t n_big = 0;
-  int grid_sl = 0;
+  int grid_sl = 0;        // persistent grid of the epilogues with reductions
+  int grid_sl_plain = 0;  // ... of the plain applies (more blocks per SM)
   // GK_CSR_MERGE
   MergePlan merge;
   // GK_ELL / GK_HYB
@@ -269,7 +295,7 @@ int spmv_max_grid(const Matrix& A);
 // Persistent grid sizes of the SpMV kernels for a given amount of work.
 int merge_grid(int64_t n_tiles);
 int coo_grid(int64_t n_chunks);
-int sliced_grid(int64_t warp_items, int64_t big_rows);
+int sliced_grid(int64_t warp_items, int64_t big_rows, bool plain);
 int ell_grid(int64_t n_rows);
 
 // Format construction (matrix.cu).
@@ -353,6 +379,9 @@ struct Solver {
   size_t gr_smem = 0;
   double* gr_part = nullptr;        // its per-CTA partial sums
   unsigned int* gr_sync = nullptr;  // its barrier words
+  int step_grid = 0;                // GK_CG, no or scalar Jacobi: blocks of the cooperative
+                                    // update-and-direction launch (0: two launches)
+  unsigned int* step_sync = nullptr;  // its barrier words
 };
 
 // Mixed-precision iterative refinement (mixed.cu).

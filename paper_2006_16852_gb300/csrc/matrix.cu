@@ -164,10 +164,7 @@ int build_merge_plan(MergePlan& P, int64_t n_rows, int64_t nnz, const int32_t* r
   GK_TRY(dalloc_n(&P.tile_i, nt + 1, bytes));
   GK_TRY(dalloc_n(&P.tile_j, nt + 1, bytes));
   GK_TRY(dalloc_n(&P.head_val, nt, bytes));
-  GK_TRY(dalloc_n(&P.head_row, nt, bytes));
   GK_TRY(dalloc_n(&P.carry_val, nt, bytes));
-  GK_TRY(dalloc_n(&P.carry_row, nt, bytes));
-  GK_TRY(dalloc_n(&P.cont, nt, bytes));
   if (P.n_tiles > 0) {
     merge_plan_kernel<<<grid1d(P.n_tiles + 1, 256), 256, 0, s>>>(
         rowptr, static_cast<int>(n_rows), static_cast<int>(nnz), static_cast<int>(P.n_tiles), P.tile_i,
@@ -185,8 +182,8 @@ void matrix_release(Matrix* A) {
   cudaGetDevice(&prev);
   cudaSetDevice(A->device);
   void* ptrs[] = {A->rowptr, A->col, A->val, A->sl_perm, A->sl_off, A->sl_col, A->sl_val, A->mid_rows, A->big_rows,
-                  A->merge.tile_i, A->merge.tile_j, A->merge.head_val, A->merge.head_row,
-                  A->merge.carry_val, A->merge.carry_row, A->merge.cont, A->ell_col, A->ell_val,
+                  A->merge.tile_i, A->merge.tile_j, A->merge.head_val, A->merge.carry_val, A->ell_col,
+                  A->ell_val,
                   A->tail_rows, A->tail_rowptr, A->tail_row, A->tail_col, A->tail_val, A->tail_slot,
                   A->tail_sum, A->coo_first, A->coo_last, A->coo_head, A->coo_tail, A->partials, A->counter,
                   A->err, A->dot_st, A->stage_in, A->stage_out};
@@ -315,7 +312,8 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
                                                                    A->sl_val);
       GK_TRY_CUDA(cudaGetLastError());
     }
-    A->grid_sl = sliced_grid(A->n_mid + A->n_slices, A->n_big);
+    A->grid_sl = sliced_grid(A->n_mid + A->n_slices, A->n_big, false);
+    A->grid_sl_plain = sliced_grid(A->n_mid + A->n_slices, A->n_big, true);
   } else if (fmt == GK_CSR_MERGE) {
     GK_TRY(build_merge_plan(A->merge, n_rows, nnz, A->rowptr, A->col, A->val, bytes, s));
   } else {  // GK_ELL, GK_HYB

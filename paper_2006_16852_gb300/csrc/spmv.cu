@@ -144,8 +144,19 @@ struct SliceArgs {
   const double* x;
 };
 
+// Blocks per SM the sliced kernel is compiled for: 8 (32 registers, 64
+// warps: the gathers' latency is what the warps hide; power-law matrix
+// 174 -> 163 us) for the plain applies, 6 (40 registers) for the
+// epilogues with reductions, whose 32-register build measured slower inside
+// CG (45.7 -> 49.9 ms on the 27-point matrix) or spilled.
 template <int MODE>
-__global__ void __launch_bounds__(kSliceThreads, 6) spmv_sliced_kernel(SliceArgs a, Epi e) {
+struct SliceMinBlocks {
+  static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN) ? 8 : 6;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) spmv_sliced_kernel(SliceArgs a,
+                                                                                                Epi e) {
   pdl_wait();
   constexpr int B = EllBatchOf<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
@@ -309,33 +320,23 @@ void launch_ell_t(int grid, cudaStream_t s, const EllArgs& a, const Epi& e) {
 }
 
 // ---------------------------------------------------------------------------
-// GK_CSR_MERGE (and the HYB tail): merge-path SpMV.  The sequence of
-// n_rows row ends and nnz entries is cut into tiles of kMergeTile items and
-// each thread walks kMergeItems consecutive items, so every thread does the
-// same amount of work whatever the row lengths.  A row split between threads
-// is completed in a second, row-parallel pass that adds the pieces in a
-// fixed order; a row split between tiles is completed by a one-block fix-up
-// launch.  Tiles (row pointers, columns, values) are bulk-copied to shared
-// memory.
+// GK_CSR_MERGE: merge-path SpMV.  The sequence of n_rows row ends and nnz
+// entries (row r's end follows its last entry) is cut into tiles of
+// kMergeTile items, one tile per warp at a time, kMergeItems consecutive
+// items per lane, so every lane does the same amount of work whatever the
+// row lengths.  A lane finds its start on the merge path by a binary search
+// over the tile's row pointers (staged in shared memory), loads its (at most
+// kMergeItems) entries and walks its items: a row whose end it meets is
+// complete if the row began in the lane, else it is the lane's head.  Heads
+// are joined to the lanes before them by a segmented inclusive scan over the
+// warp (shuffles, fixed tree order); a row that began in an earlier tile
+// leaves the tile's part in a per-tile partial sum, and a one-thread-per-tile
+// fix-up launch adds the parts from earlier tiles (the tile's last open row
+// leaves its part as well).  No thread-block barrier: warps are independent.
 // ---------------------------------------------------------------------------
 
-constexpr int kMergeStage = kMergeTile + 8;
-struct MergeSmem {
-  union {
-    double val[kMergeStage];  // the tile's values (bulk copy), until every thread holds its own
-    double ys[kMergeTile];    // then the sums of rows that end inside one thread's items
-  };
-  double head_val[kMergeThreads];
-  double carry_val[kMergeThreads];
-  int32_t rp[kMergeStage];
-  int32_t col[kMergeStage];
-  int32_t head_row[kMergeThreads];
-  int32_t carry_row[kMergeThreads];
-  int32_t cont[kMergeThreads];
-  double scan_v[kMergeThreads];  // segmented prefix sums of carry_val (long-row tiles)
-  int32_t scan_f[kMergeThreads];
-  uint64_t bar;
-};
+constexpr int kMergeStage = kMergeTile + 8;  // staged row pointers per warp
+constexpr int kMergeWarps = kMergeThreads / 32;
 
 struct MergeArgs {
   const int32_t* rowptr;
@@ -343,11 +344,8 @@ struct MergeArgs {
   const double* val;
   const int32_t* tile_i;
   const int32_t* tile_j;
-  double* head_val;
-  int32_t* head_row;
-  double* carry_val;
-  int32_t* carry_row;
-  int32_t* cont;
+  double* c_head;  // per tile: its part of its first row, when that row began earlier and ends here
+  double* c_tail;  // per tile: its part of the row left open at its end
   int n_rows;
   int nnz;
   int n_tiles;
@@ -355,231 +353,138 @@ struct MergeArgs {
 };
 
 __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, Epi e) {
+  __shared__ int32_t s_rp[kMergeWarps][kMergeStage];
+  __shared__ double red_scratch[kRedScratch];
   pdl_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MergeSmem& S = *reinterpret_cast<MergeSmem*>(smem_raw);
   if (epi_skip(e)) return;
-  const int t = threadIdx.x;
-  if (t == 0) {
-    mbar_init(&S.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  constexpr int E = kMergeItems;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t* rp = s_rp[wib];
   const int total = a.n_rows + a.nnz;
   double a0 = 0.0, a1 = 0.0;
-  uint32_t phase = 0;
-  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-    const int ti = __ldg(a.tile_i + tile), tj = __ldg(a.tile_j + tile);
-    const int ti1 = __ldg(a.tile_i + tile + 1), tj1 = __ldg(a.tile_j + tile + 1);
-    const int d0 = tile * kMergeTile;
-    const int d1 = min(d0 + kMergeTile, total);
-    const int rp_last = min(ti1 + 1, a.n_rows);
-    const int ra = ti & ~3, rb = (rp_last + 1 + 3) & ~3;
-    const int ja = tj & ~3, jb = (tj1 + 3) & ~3;
-    const uint32_t nrp = static_cast<uint32_t>(rb - ra), nj = static_cast<uint32_t>(jb - ja);
-    if (t == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&S.bar, nrp * 4u + nj * 12u);
-      bulk_g2s(S.rp, a.rowptr + ra, nrp * 4u, &S.bar);
-      if (nj > 0) {
-        bulk_g2s(S.val, a.val + ja, nj * 8u, &S.bar);
-        bulk_g2s(S.col, a.col + ja, nj * 4u, &S.bar);
-      }
-    }
-    const bool w = mbar_wait(&S.bar, phase, e.err);
-    phase ^= 1u;
-    if (!__syncthreads_and(w)) break;
-#define RP(r) S.rp[(r) - ra]
-    const bool tile_mid = tj > RP(ti);
-    // ---- phase 1: each thread walks its items ----------------------------
-    // The thread's items are the row ends and entries between merge
-    // diagonals dt and dte: entries [k, k + cnt) and the ends of rows
-    // [row, row_end).  Its (at most kMergeItems) values and gathered x are
-    // loaded first, with static register indices; after a barrier the value
-    // buffer takes the row sums, and the walk consumes a row end whenever
-    // the next entry lies past it.
-    const int dt = d0 + t * kMergeItems;
-    const bool active = dt < d1;
-    int row = 0, k = 0, row_end = 0, cnt = 0;
-    double vv[kMergeItems], xv[kMergeItems];
+  for (int t = blockIdx.x * kMergeWarps + wib; t < a.n_tiles; t += gridDim.x * kMergeWarps) {
+    const int ti = __ldg(a.tile_i + t), tj = __ldg(a.tile_j + t);
+    const int ti1 = __ldg(a.tile_i + t + 1), tj1 = __ldg(a.tile_j + t + 1);
+    const int d0 = t * kMergeTile, d1 = min(d0 + kMergeTile, total);
+    // row pointers rowptr[ti .. min(ti1 + 1, n_rows)] (at most kMergeTile + 2)
+    const int nrp = min(ti1 + 1, a.n_rows) - ti + 1;
+    __syncwarp();
+    for (int q = lane; q < nrp; q += 32) rp[q] = __ldg(a.rowptr + ti + q);
+    __syncwarp();
+#define RPW(r) rp[(r) - ti]
+    // the lane's start (row, k) on the merge path; inactive lanes sit at the tile end
+    const int dl = d0 + lane * E;
+    const bool active = dl < d1;
+    int row = ti1, k = tj1;
     if (active) {
-      const int dte = min(dt + kMergeItems, d1);
-      int lo = max(ti, dt - tj1), hi = min(ti1, dt - tj);
+      int lo = max(ti, dl - tj1), hi = min(ti1, dl - tj);
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (RP(mid + 1) <= dt - mid - 1) lo = mid + 1;
+        if (RPW(mid + 1) <= dl - mid - 1) lo = mid + 1;
         else hi = mid;
       }
-      int lo2 = max(ti, dte - tj1), hi2 = min(ti1, dte - tj);
-      while (lo2 < hi2) {
-        const int mid = (lo2 + hi2) >> 1;
-        if (RP(mid + 1) <= dte - mid - 1) lo2 = mid + 1;
-        else hi2 = mid;
-      }
       row = lo;
-      k = dt - lo;
-      row_end = lo2;
-      cnt = (dte - lo2) - k;
+      k = dl - lo;
     }
+    int row_end = __shfl_down_sync(0xffffffffu, row, 1);
+    int k_end = __shfl_down_sync(0xffffffffu, k, 1);
+    if (lane == 31) {
+      row_end = ti1;
+      k_end = tj1;
+    }
+    const int cnt = active ? k_end - k : 0;
+    double vv[E], xv[E];
 #pragma unroll
-    for (int u = 0; u < kMergeItems; ++u) {
+    for (int u = 0; u < E; ++u) {
       const bool in = u < cnt;
-      vv[u] = in ? S.val[k + u - ja] : 0.0;
-      xv[u] = in ? __ldg(a.x + S.col[k + u - ja]) : 0.0;
+      vv[u] = in ? __ldcs(a.val + k + u) : 0.0;
+      xv[u] = in ? __ldg(a.x + __ldcs(a.col + k + u)) : 0.0;
     }
-    __syncthreads();
-    if (active) {
-      const bool mid_row = k > RP(row);
-      bool first = true;
-      int head = -1;
-      double sum = 0.0;
-      int next_end = cnt > 0 ? RP(row + 1) : 0;  // end of the current row, kept in a register
+    // walk: a row end met before entry kk (rowptr[cur + 1] <= kk) ends row cur
+    const bool mid_start = active && k > RPW(row);
+    int cur = row;
+    int nxt = (active && cur < a.n_rows) ? RPW(cur + 1) : 0x7fffffff;
+    bool emitted = false;
+    int head_row = -1;
+    double head = 0.0, sum = 0.0;
 #pragma unroll
-      for (int u = 0; u < kMergeItems; ++u) {
-        if (u < cnt) {
-          while (next_end <= k + u) {
-            if (first && mid_row) {
-              S.head_val[t] = sum;
-              head = row;
-            } else {
-              S.ys[row - ti] = sum;
-            }
-            first = false;
-            sum = 0.0;
-            ++row;
-            next_end = RP(row + 1);
+    for (int u = 0; u < E; ++u) {
+      if (u < cnt) {
+        while (k + u >= nxt) {
+          if (!emitted && mid_start) {
+            head_row = cur;
+            head = sum;
+          } else {
+            epi_row(e, cur, sum, a0, a1);
           }
-          sum = fma(vv[u], xv[u], sum);
+          emitted = true;
+          ++cur;
+          nxt = cur < a.n_rows ? RPW(cur + 1) : 0x7fffffff;
+          sum = 0.0;
         }
+        sum = fma(vv[u], xv[u], sum);
       }
-      while (row < row_end) {
-        if (first && mid_row) {
-          S.head_val[t] = sum;
-          head = row;
+    }
+    if (active) {
+      while (cur < row_end) {
+        if (!emitted && mid_start) {
+          head_row = cur;
+          head = sum;
         } else {
-          S.ys[row - ti] = sum;
+          epi_row(e, cur, sum, a0, a1);
         }
-        first = false;
+        emitted = true;
+        ++cur;
         sum = 0.0;
-        ++row;
-      }
-      S.head_row[t] = head;
-      S.carry_row[t] = row;
-      S.carry_val[t] = sum;
-      S.cont[t] = (first && mid_row) ? 1 : 0;
-    } else {
-      S.head_row[t] = -1;
-      S.carry_row[t] = -1;
-      S.carry_val[t] = 0.0;
-      S.cont[t] = 0;
-    }
-    __syncthreads();
-    // ---- long rows: segmented prefix sums of the threads' partial sums -----
-    // A row much longer than kMergeItems is split over many threads; summing
-    // their pieces one by one would leave the block waiting on one thread.
-    // Tiles touching such a row instead build, in a fixed tree order, the
-    // prefix sums of carry_val within runs of continuation threads (a run
-    // starts at every thread that is not a pure continuation).
-    bool lt = false;
-    for (int r = ti + t; r <= min(ti1, a.n_rows - 1); r += kMergeThreads)
-      lt = lt || (RP(r + 1) - RP(r) >= 4 * kMergeItems);
-    const bool long_tile = __syncthreads_or(lt) != 0;
-    if (long_tile) {
-      S.scan_v[t] = S.carry_val[t];
-      S.scan_f[t] = (t == 0 || !S.cont[t]) ? 1 : 0;
-      __syncthreads();
-      for (int d = 1; d < kMergeThreads; d <<= 1) {
-        double nv = S.scan_v[t];
-        int nf = S.scan_f[t];
-        if (t >= d && !nf) {
-          nv = S.scan_v[t - d] + nv;
-          nf = S.scan_f[t - d];
-        }
-        __syncthreads();
-        S.scan_v[t] = nv;
-        S.scan_f[t] = nf;
-        __syncthreads();
       }
     }
-    // ---- phase 2: rows whose end lies in this tile, one per thread --------
-    if (t == 0) a.head_row[tile] = -1;
-    for (int r = ti + t; r < ti1; r += kMergeThreads) {
-      const int ds = RP(r) + r, de = RP(r + 1) + r;
-      const int t_end = (de - d0) / kMergeItems;
-      if (ds < d0) {
-        // the row began in an earlier tile: leave it to the fix-up launch
-        double v = S.head_val[t_end];
-        if (long_tile) {
-          if (t_end > 0) v += S.scan_v[t_end - 1];
-        } else {
-          for (int u = t_end - 1; u >= 0; --u) v += S.carry_val[u];
-        }
-        a.head_val[tile] = v;
-        a.head_row[tile] = r;
-      } else {
-        const int t_start = (ds - d0) / kMergeItems;
-        double v;
-        if (t_start == t_end) {
-          v = S.ys[r - ti];
-        } else if (long_tile) {
-          v = S.head_val[t_end] + S.scan_v[t_end - 1];
-        } else {
-          v = S.head_val[t_end];
-          for (int u = t_end - 1; u >= t_start; --u) v += S.carry_val[u];
-        }
-        epi_row(e, r, v, a0, a1);
+    // segmented inclusive scan of the lanes' open sums: a lane that met no
+    // row end and began inside a row continues the lane before it
+    double S = sum;
+    int open = (lane > 0 && active && !emitted && mid_start) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double Sp = __shfl_up_sync(0xffffffffu, S, d);
+      const int op = __shfl_up_sync(0xffffffffu, open, d);
+      if (lane >= d && open) {
+        S = Sp + S;
+        open = op;
       }
     }
-    // ---- the row left open at the tile end -------------------------------
-    if (t == 0) {
-      int crow = -1, ccont = 0;
-      double cv = 0.0;
-      if (tile != a.n_tiles - 1 && tj1 > RP(ti1)) {
-        crow = ti1;
-        if (long_tile) {
-          cv = S.scan_v[kMergeThreads - 1];
-        } else {
-          for (int u = kMergeThreads - 1; u >= 0; --u) {
-            if (S.carry_row[u] != crow) break;
-            cv += S.carry_val[u];
-            if (!S.cont[u]) break;
-          }
-        }
-        ccont = (ti1 == ti && tile_mid) ? 1 : 0;
-      }
-      a.carry_row[tile] = crow;
-      a.carry_val[tile] = cv;
-      a.cont[tile] = ccont;
+    const double S_prev = __shfl_up_sync(0xffffffffu, S, 1);
+    if (head_row >= 0) {
+      const double v = (lane > 0 ? S_prev : 0.0) + head;
+      if (head_row == ti && tj > RPW(ti)) a.c_head[t] = v;  // began in an earlier tile
+      else epi_row(e, head_row, v, a0, a1);
     }
-#undef RP
-    // the next tile's bulk copy (async proxy) overwrites the row sums (ys)
-    fence_proxy_async_smem();
-    __syncthreads();
+    if (active && lane == (d1 - d0 - 1) / E) a.c_tail[t] = S;
+#undef RPW
   }
-  epi_partial(e, a0, a1, S.ys);  // ys is free once the tiles are done
+  epi_partial(e, a0, a1, red_scratch);
 }
 
-// Completes rows that cross tile boundaries (one thread per tile, all tiles
-// in parallel) and finishes the epilogue's reduction: the main launch's
-// block partials are folded into this launch's own fixed-order grid sum, whose
-// block partials live after the main launch's.
+// Rows that began in an earlier tile and end in tile t (one thread per tile,
+// all tiles in parallel): the tile's part plus the open parts of the tiles
+// before it, back to the tile where the row began; then the epilogue's
+// reduction: the main launch's block partials are folded into this launch's
+// own fixed-order grid sum, whose block partials live after the main launch's.
 __global__ void __launch_bounds__(256) spmv_merge_fixup_kernel(MergeArgs a, Epi e, int main_grid) {
-  pdl_wait();
   __shared__ double red_scratch[kRedScratch];
+  pdl_wait();
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
   const int stride = gridDim.x * blockDim.x;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   for (int t = gt; t < a.n_tiles; t += stride) {
-    const int h = a.head_row[t];
-    if (h < 0) continue;
-    double v = a.head_val[t];
+    const int f = __ldg(a.tile_i + t);
+    if (t == 0 || !(__ldg(a.tile_j + t) > __ldg(a.rowptr + f)) || !(__ldg(a.tile_i + t + 1) > f)) continue;
+    double v = a.c_head[t];
+    const int rf = __ldg(a.rowptr + f);
     for (int u = t - 1; u >= 0; --u) {
-      if (a.carry_row[u] != h) break;
-      v += a.carry_val[u];
-      if (!a.cont[u]) break;
+      v += a.c_tail[u];
+      if (!(u > 0 && __ldg(a.tile_i + u) == f && __ldg(a.tile_j + u) > rf)) break;
     }
-    epi_row(e, h, v, a0, a1);
+    epi_row(e, f, v, a0, a1);
   }
   if (e.mode == EPI_PLAIN || e.mode == EPI_COPY) return;
   for (int b = gt; b < main_grid; b += stride) {
@@ -761,16 +666,6 @@ int occupancy_grid(const void* fn, int threads, size_t smem) {
   return per_sm * sm_count();
 }
 
-bool g_attr_done[64] = {};
-
-int ensure_attributes() {
-  int dev = current_device();
-  if (dev >= 0 && dev < 64 && g_attr_done[dev]) return GK_OK;
-  GK_TRY(set_smem(spmv_merge_kernel, sizeof(MergeSmem)));
-  if (dev >= 0 && dev < 64) g_attr_done[dev] = true;
-  return GK_OK;
-}
-
 MergeArgs merge_args(const MergePlan& P, const double* x) {
   MergeArgs m;
   m.rowptr = P.rowptr;
@@ -778,11 +673,8 @@ MergeArgs merge_args(const MergePlan& P, const double* x) {
   m.val = P.val;
   m.tile_i = P.tile_i;
   m.tile_j = P.tile_j;
-  m.head_val = P.head_val;
-  m.head_row = P.head_row;
-  m.carry_val = P.carry_val;
-  m.carry_row = P.carry_row;
-  m.cont = P.cont;
+  m.c_head = P.head_val;
+  m.c_tail = P.carry_val;
   m.n_rows = static_cast<int>(P.n_rows);
   m.nnz = static_cast<int>(P.nnz);
   m.n_tiles = static_cast<int>(P.n_tiles);
@@ -793,7 +685,7 @@ MergeArgs merge_args(const MergePlan& P, const double* x) {
 int launch_merge(const MergePlan& P, const double* x, const Epi& e, cudaStream_t s) {
   if (P.n_tiles == 0) return GK_OK;
   MergeArgs m = merge_args(P, x);
-  launch_pdl(spmv_merge_kernel, P.grid, kMergeThreads, sizeof(MergeSmem), s, m, e);
+  launch_pdl(spmv_merge_kernel, P.grid, kMergeThreads, 0, s, m, e);
   GK_TRY_CUDA(cudaGetLastError());
   const int fg = static_cast<int>(std::min<int64_t>(kFixupMaxGrid, (P.n_tiles + 255) / 256));
   launch_pdl(spmv_merge_fixup_kernel, fg, 256, 0, s, m, e, P.grid);
@@ -804,14 +696,14 @@ int launch_merge(const MergePlan& P, const double* x, const Epi& e, cudaStream_t
 }  // namespace
 
 int merge_grid(int64_t n_tiles) {
-  if (ensure_attributes() != GK_OK) return 1;
-  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_merge_kernel), kMergeThreads,
-                         sizeof(MergeSmem));
-  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, n_tiles)));
+  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_merge_kernel), kMergeThreads, 0);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, (n_tiles + kMergeWarps - 1) / kMergeWarps)));
 }
 
-int sliced_grid(int64_t warp_items, int64_t big_rows) {
-  int g = occupancy_grid(reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_RESID>), kSliceThreads, 0);
+int sliced_grid(int64_t warp_items, int64_t big_rows, bool plain) {
+  const void* fn = plain ? reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_COPY>)
+                         : reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_RESID>);
+  int g = occupancy_grid(fn, kSliceThreads, 0);
   int64_t need = std::max<int64_t>((warp_items + kSliceThreads / 32 - 1) / (kSliceThreads / 32), big_rows);
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
 }
@@ -845,11 +737,10 @@ int launch_coo(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) {
 }  // namespace
 
 int spmv_max_grid(const Matrix& A) {
-  return std::max({A.grid_sl, A.grid_ell, A.merge.grid, 1});
+  return std::max({A.grid_sl, A.grid_sl_plain, A.grid_ell, A.merge.grid, 1});
 }
 
 int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) {
-  GK_TRY(ensure_attributes());
   if (A.n_rows == 0) return GK_OK;
   switch (A.format) {
     case GK_CSR: {
@@ -857,8 +748,8 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
                   static_cast<int>(A.n_slices), A.mid_rows, static_cast<int>(A.n_mid), A.big_rows,
                   static_cast<int>(A.n_big), x};
       switch (e.mode) {
-        case EPI_COPY: launch_pdl(spmv_sliced_kernel<EPI_COPY>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
-        case EPI_PLAIN: launch_pdl(spmv_sliced_kernel<EPI_PLAIN>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        case EPI_COPY: launch_pdl(spmv_sliced_kernel<EPI_COPY>, A.grid_sl_plain, kSliceThreads, 0, s, b, e); break;
+        case EPI_PLAIN: launch_pdl(spmv_sliced_kernel<EPI_PLAIN>, A.grid_sl_plain, kSliceThreads, 0, s, b, e); break;
         case EPI_RESID: launch_pdl(spmv_sliced_kernel<EPI_RESID>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
         case EPI_DOT: launch_pdl(spmv_sliced_kernel<EPI_DOT>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
         default: launch_pdl(spmv_sliced_kernel<EPI_DOT2>, A.grid_sl, kSliceThreads, 0, s, b, e); break;

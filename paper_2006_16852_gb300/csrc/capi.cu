@@ -47,6 +47,39 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
+namespace {
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+}  // namespace
+
+int dalloc_async(void** p, size_t bytes, int64_t* counter, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  const int dev = current_device();
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool_ready[dev]) {
+      // keep up to 8 GB of freed memory in this process's default pool of the
+      // device instead of returning it at the next synchronization
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 8ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+      g_pool_ready[dev] = true;
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(GK_ERR_ALLOC, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  if (counter) *counter += static_cast<int64_t>(bytes);
+  return GK_OK;
+}
+
 int current_device() {
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess) {

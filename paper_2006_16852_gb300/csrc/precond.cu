@@ -72,21 +72,24 @@ __global__ void __launch_bounds__(256) bj_extract_kernel(const int32_t* __restri
     const int blk = r / bs, i = r - blk * bs, r0 = blk * bs;
     const int m = min(bs, n - r0);
     const int k1 = __ldg(rowptr + r + 1);
-    double row[BT];
+    const int lo = lower_col(col, __ldg(rowptr + r), k1, r0);
+    // the candidates (at most m entries from lo) are loaded together: their
+    // columns first, then the values of those inside the block
+    int cc[BT];
 #pragma unroll
-    for (int j = 0; j < BT; ++j) row[j] = 0.0;
-    for (int k = lower_col(col, __ldg(rowptr + r), k1, r0); k < k1; ++k) {
-      const int c = __ldg(col + k) - r0;
-      if (c >= m) break;
-      const double v = __ldg(val + k);
+    for (int j = 0; j < BT; ++j) cc[j] = (j < m && lo + j < k1) ? __ldg(col + lo + j) - r0 : BT;
+    double vv[BT];
 #pragma unroll
-      for (int j = 0; j < BT; ++j)
-        if (c == j) row[j] = v;
-    }
+    for (int j = 0; j < BT; ++j) vv[j] = cc[j] < m ? __ldg(val + lo + j) : 0.0;
+    // the row of the dense block: zeros, then the entries at their columns
+    // (the same 8 * m bytes, merged in L2 before they reach memory)
     double* out = blocks + static_cast<int64_t>(blk) * bs * bs + static_cast<int64_t>(i) * m;
 #pragma unroll
     for (int j = 0; j < BT; ++j)
-      if (j < m) out[j] = row[j];
+      if (j < m) out[j] = 0.0;
+#pragma unroll
+    for (int j = 0; j < BT; ++j)
+      if (cc[j] < m) out[cc[j]] = vv[j];
   }
 }
 
@@ -445,7 +448,7 @@ extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream
     }
     if (block_size == 1) {
       P->nblocks = P->n;
-      if ((rc = dalloc_n(&P->dinv, static_cast<size_t>(std::max<int64_t>(P->n, 1)), &P->device_bytes)))
+      if ((rc = dalloc_async_n(&P->dinv, static_cast<size_t>(std::max<int64_t>(P->n, 1)), &P->device_bytes, s)))
         break;
       if (P->n > 0)
         jacobi_scalar_kernel<<<grid_for(P->n, 256), 256, 0, s>>>(A->rowptr, A->col, A->val,
@@ -453,8 +456,8 @@ extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream
     } else {
       P->nblocks = (P->n + block_size - 1) / block_size;
       P->block_elems = bj_total_elems(P->n, block_size);
-      if ((rc = dalloc_n(&P->blocks, static_cast<size_t>(std::max<int64_t>(P->block_elems, 1)),
-                         &P->device_bytes)))
+      if ((rc = dalloc_async_n(&P->blocks, static_cast<size_t>(std::max<int64_t>(P->block_elems, 1)),
+                               &P->device_bytes, s)))
         break;
       if (P->nblocks > 0)
         bj_generate(A, static_cast<int>(P->n), block_size, static_cast<int>(P->nblocks), P->blocks, A->err + 1, s);

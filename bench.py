@@ -1031,8 +1031,8 @@ def run_gather_ceiling(step, reps=20):
     (b)'s own column/value stream (29 M entries, columns uniform over 10^6
     rows) -- the SpMV's per-entry work without its rows -- timed back to
     back with GK_CSR's apply of (b) and with the same stream's columns
-    replaced by a uniformly random permutation-free draw; CUDA events,
-    median of reps after 3 warm-ups."""
+    replaced by a uniformly random draw; CUDA events around reps
+    back-to-back calls, median of 5 such runs after 3 warm-ups."""
     import torch
     gk = step.gk
     dev = step.dev
@@ -1049,13 +1049,14 @@ def run_gather_ceiling(step, reps=20):
         for _ in range(3):
             fn()
         ms = []
-        for _ in range(reps):
+        for _ in range(5):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn()
+            for _ in range(reps):
+                fn()
             e1.record(stream)
             e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            ms.append(e0.elapsed_time(e1) / reps)
         return statistics.median(ms)
 
     t_gather = timed(lambda: gk.gather_dot(col, val, x, res))
@@ -1068,7 +1069,8 @@ def run_gather_ceiling(step, reps=20):
             "gather_dot_ms": round(t_gather, 4), "gather_dot_GB/s": round(by / (t_gather * 1e-3) / 1e9, 1),
             "gather_dot_uniform_cols_ms": round(t_rand, 4), "gk_csr_apply_ms": round(t_csr, 4),
             "gk_csr_over_ceiling": round(t_csr / t_gather, 3),
-            "timing": "CUDA events, median of %d after 3 warm-ups, back to back in one process" % reps}
+            "timing": "CUDA events around %d back-to-back calls, median of 5 such runs after 3 warm-ups, the "
+                      "three kernels in one process" % reps}
 
 
 def run_stream(dev, n=1 << 27):

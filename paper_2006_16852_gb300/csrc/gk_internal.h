@@ -83,25 +83,6 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
-// Launches kern<<<grid, block, smem, s>>>(args...) as a cooperative kernel
-// (every block resident at once, which a grid-wide barrier needs); valid in
-// stream capture (the graph node keeps the attribute).
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_coop(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                               Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 // Makes `dev` current for the lifetime of the guard, then restores the
 // caller's device.
 struct DeviceGuard {
@@ -379,9 +360,6 @@ struct Solver {
   size_t gr_smem = 0;
   double* gr_part = nullptr;        // its per-CTA partial sums
   unsigned int* gr_sync = nullptr;  // its barrier words
-  int step_grid = 0;                // GK_CG, no or scalar Jacobi: blocks of the cooperative
-                                    // update-and-direction launch (0: two launches)
-  unsigned int* step_sync = nullptr;  // its barrier words
 };
 
 // Mixed-precision iterative refinement (mixed.cu).

@@ -123,9 +123,12 @@ __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, 
 // gathered vector keeps the caches (27-point matrix: 135.9 -> 116.5 us).
 // ---------------------------------------------------------------------------
 
+// Gathers a lane keeps in flight in the slice loop: 8 for the plain applies
+// and the fused dot of CG's SpMV (within 40 registers at 6 blocks per SM), 4
+// for the two-accumulator epilogues.
 template <int MODE>
 struct EllBatchOf {
-  static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN) ? 8 : 4;
+  static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN || MODE == EPI_DOT) ? 8 : 4;
 };
 
 struct SliceArgs {
@@ -335,6 +338,17 @@ void launch_ell_t(int grid, cudaStream_t s, const EllArgs& a, const Epi& e) {
 // leaves its part as well).  No thread-block barrier: warps are independent.
 // ---------------------------------------------------------------------------
 
+// Steps of a segmented inclusive warp scan that suffice when the lanes in
+// `open` (bit l: lane l adds the value of lane l - 1) form chains of at most
+// L consecutive lanes: ceil(log2(L + 1)).  A lane's sum is final once its
+// chain is resolved, so stopping there changes no bit, and each FP64 add
+// saved is a warp instruction of the (slow) FP64 pipe saved.
+__device__ __forceinline__ int scan_steps(unsigned int open) {
+  int L = 0;
+  for (unsigned int x = open; x; x &= x << 1) ++L;
+  return 32 - __clz(L);
+}
+
 constexpr int kMergeStage = kMergeTile + 8;  // staged row pointers per warp
 constexpr int kMergeWarps = kMergeThreads / 32;
 
@@ -442,8 +456,8 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
     // row end and began inside a row continues the lane before it
     double S = sum;
     int open = (lane > 0 && active && !emitted && mid_start) ? 1 : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    const int steps = scan_steps(__ballot_sync(0xffffffffu, open));
+    for (int d = 1; d < (1 << steps); d <<= 1) {
       const double Sp = __shfl_up_sync(0xffffffffu, S, d);
       const int op = __shfl_up_sync(0xffffffffu, open, d);
       if (lane >= d && open) {
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(kMergeThreads) spmv_merge_kernel(MergeArgs a, 
     }
     const double S_prev = __shfl_up_sync(0xffffffffu, S, 1);
     if (head_row >= 0) {
-      const double v = (lane > 0 ? S_prev : 0.0) + head;
+      const double v = lane > 0 ? S_prev + head : head;
       if (head_row == ti && tj > RPW(ti)) a.c_head[t] = v;  // began in an earlier tile
       else epi_row(e, head_row, v, a0, a1);
     }
@@ -583,8 +597,8 @@ __global__ void __launch_bounds__(kCooThreads) spmv_coo_kernel(CooArgs a, Epi e)
     const int prev_last = __shfl_up_sync(0xffffffffu, last, 1);
     double S = sum;
     int open = (lane > 0 && first >= 0 && first == last && prev_last == first) ? 1 : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    const int steps = scan_steps(__ballot_sync(0xffffffffu, open));
+    for (int d = 1; d < (1 << steps); d <<= 1) {
       const double Sp = __shfl_up_sync(0xffffffffu, S, d);
       const int op = __shfl_up_sync(0xffffffffu, open, d);
       if (lane >= d && open) {

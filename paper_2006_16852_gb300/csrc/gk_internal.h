@@ -261,6 +261,7 @@ struct Matrix {
   unsigned int* counter = nullptr;
   int* err = nullptr;
   SolverState* dot_st = nullptr;  // gk_apply_dot: receives the fused sum
+  int* h_flag = nullptr;          // pinned host words of the preconditioner generation's error check
   double* stage_in = nullptr;   // host-vector staging
   double* stage_out = nullptr;
   int max_grid = 0;             // partials hold max_grid * 2 doubles

@@ -188,6 +188,7 @@ void matrix_release(Matrix* A) {
                   A->tail_sum, A->coo_first, A->coo_last, A->coo_head, A->coo_tail, A->partials, A->counter,
                   A->err, A->dot_st, A->stage_in, A->stage_out};
   for (void* p : ptrs) dfree(p);
+  if (A->h_flag) cudaFreeHost(A->h_flag);
   if (prev >= 0) cudaSetDevice(prev);
   delete A;
 }

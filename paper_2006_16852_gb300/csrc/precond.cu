@@ -441,8 +441,15 @@ extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream
   P->bs = block_size;
   int rc = GK_OK;
   do {
-    int bad = INT_MAX, bad_init = INT_MAX;
-    if (cudaMemcpyAsync(A->err + 1, &bad_init, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    // the error word: INT_MAX in, the smallest failing row or block out,
+    // through pinned host words (asynchronous copies, no staging)
+    if (!A->h_flag && cudaMallocHost(&A->h_flag, 2 * sizeof(int)) != cudaSuccess) {
+      A->h_flag = nullptr;
+      rc = cuda_error(cudaGetLastError(), "cudaMallocHost");
+      break;
+    }
+    A->h_flag[0] = INT_MAX;
+    if (cudaMemcpyAsync(A->err + 1, A->h_flag, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
       rc = cuda_error(cudaGetLastError(), "cudaMemcpyAsync");
       break;
     }
@@ -467,11 +474,12 @@ extern "C" int gk_precond_generate(gk_matrix h, int32_t block_size, void* stream
       rc = cuda_error(e, "Jacobi generate launch");
       break;
     }
-    if (cudaMemcpyAsync(&bad, A->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(A->h_flag + 1, A->err + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       rc = cuda_error(cudaGetLastError(), "Jacobi generate");
       break;
     }
+    const int bad = A->h_flag[1];
     if (bad != INT_MAX) {
       rc = block_size == 1 ? set_error(GK_ERR_SINGULAR, "zero or missing diagonal in row %d", bad)
                            : set_error(GK_ERR_SINGULAR, "diagonal block %d is singular", bad);

@@ -494,7 +494,8 @@ class GpuStep:
         if kind in ("spmv", "spmvdot"):
             return SPMV_REPS * spmv_launches(tag[2].info())
         if kind == "precond":
-            return 1
+            # scalar Jacobi: one kernel; block Jacobi up to bs 8: extraction + inversion
+            return 2 if 1 < tag[2] <= 8 else 1
         name, st = tag[1], tag[2]
         S, k, prec, bs, sk, fmt = self.solvers[name]
         info = self.mats[(k, fmt)].info()

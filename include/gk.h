@@ -222,7 +222,11 @@ GK_API int gk_apply_dot(gk_matrix A, const double* b, double* x, const double* u
  * on contiguous blocks of block_size rows (the last one shorter), each
  * diagonal block inverted by Gauss-Jordan elimination with partial pivoting
  * (Section 7.5).  A zero/missing diagonal or a singular block returns
- * GK_ERR_SINGULAR. */
+ * GK_ERR_SINGULAR.  The inverse diagonal or blocks are allocated on `stream`
+ * from the device's default stream-ordered memory pool (the library lets the
+ * pool keep up to 8 GB of freed memory for reuse, so repeated generations do
+ * not map memory again); the call returns after the generation has
+ * finished (it reads back the error check). */
 GK_API int gk_precond_generate(gk_matrix A, int32_t block_size, void* stream, gk_precond* out);
 
 /* z = M^{-1} r (the preconditioner as a LinOp). */

@@ -149,17 +149,21 @@ def ir_bytes(inner, outer, nnz, n, prec="none", bs=1, fp16_frac=0.0, fmt="csr", 
     Outer step: r = b - A x in FP64 (SpMV + b), the start of the inner solve
     (r64 in; r32, d32, p32 out; M), and x += ||r|| d (x in/out, d in).  Inner
     iteration: FP32 SpMV (FP32 values, the same indices, x and y in FP32),
-    update (d, p, q, r, M in; d, r out), direction (p, r or z, M in; p out).
-    Block-Jacobi blocks cost 2 (FP16) or 4 (FP32) bytes per entry."""
+    update (d, p, q, r, M in; d, r out), direction (p, r or z, M in; p out);
+    with block Jacobi d's update is in the direction step instead (update: q,
+    r, M in; r, z out; direction: p, d, z in; p, d out).  Block-Jacobi
+    blocks cost 2 (FP16) or 4 (FP32) bytes per entry."""
     if prec == "none":
         pe = 0.0
     elif prec == "jacobi":
         pe = 4.0
     else:
         pe = bs * (2.0 * fp16_frac + 4.0 * (1.0 - fp16_frac))
-    z_store = 4.0 if prec == "block" else 0.0
     spmv32 = matrix_bytes(nnz, n, fmt, tail_nnz, vt=4) + n * 4 + n * 4
-    per_inner = spmv32 + (16 + pe + 8 + z_store) * n + (12 + (4 if prec == "jacobi" else 0)) * n
+    if prec == "block":
+        per_inner = spmv32 + (8 + pe + 8) * n + (12 + 8) * n
+    else:
+        per_inner = spmv32 + (16 + pe + 8) * n + (12 + (4 if prec == "jacobi" else 0)) * n
     rb = resid_bytes(nnz, n, fmt, tail_nnz)
     per_outer = rb + (8 + 12 + pe) * n + 20 * n
     return int(outer * per_outer + inner * per_inner + rb)

@@ -31,6 +31,7 @@ struct InnerState {
   double rho, alpha, beta, rr0, tol2;
   double red[2];
   long long it, max_it;
+  long long d_it;  // the iteration whose d += alpha p the direction step has applied
   int done;
   int breakdown;
 };
@@ -380,17 +381,32 @@ __global__ void __launch_bounds__(kIrThreads) ir_start_kernel(IrArgs a, IrData d
     const double red = fmax(d.inner_red, 0.5 * a.st->tol / a.st->rnorm);
     s->tol2 = red * red * static_cast<double>(out[1]);
     s->it = 0;
+    s->d_it = 0;
     s->max_it = d.inner_max;
     s->breakdown = 0;
     s->done = (out[1] > 0.0f && isfinite(out[1])) ? 0 : 1;
   }
 }
 
-// d += alpha p; r -= alpha q; z = M^{-1} r; (r.z, r.r); inner criteria.
+// Where d += alpha p happens: with block Jacobi the update kernel is bound
+// by its block apply, so d's update goes to the direction kernel, which reads
+// p anyway (block-Jacobi refinement on the 27-point matrix 32.9 -> 30.8 ms);
+// otherwise it stays in the update kernel (moving it there measured slower).
+template <int PK>
+struct DInDirection {
+  static constexpr bool value = PK == PREC_BLOCK;
+};
+
+// [d += alpha p;] r -= alpha q; z = M^{-1} r; (r.z, r.r); inner criteria.
+// When the direction kernel updates d, it must know whether this
+// iteration's update ran: block 0 first records the iteration count the
+// direction kernel last caught up with (before any early return), and the
+// finalize raises the count past it only if the update runs.
 template <int PK, int BS>
 __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData d) {
   pdl_wait();
   __shared__ float scratch[kRedScratch];
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.ist->d_it = d.ist->it;
   if (d.ist->done) return;
   const float alpha = static_cast<float>(d.ist->alpha);
   float rz = 0.0f, rr = 0.0f;
@@ -398,7 +414,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData 
     IR_FOR_BLOCK_LANES(L) {
       float rn = 0.0f;
       if (L.active) {
-        d.d[L.row] = fmaf(alpha, d.p[L.row], d.d[L.row]);
+        if (!DInDirection<PK>::value) d.d[L.row] = fmaf(alpha, d.p[L.row], d.d[L.row]);
         rn = fmaf(-alpha, d.q[L.row], d.r[L.row]);
         d.r[L.row] = rn;
       }
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData 
     }
   } else {
     IR_FOR_ROWS(i) {
-      d.d[i] = fmaf(alpha, d.p[i], d.d[i]);
+      if (!DInDirection<PK>::value) d.d[i] = fmaf(alpha, d.p[i], d.d[i]);
       const float rn = fmaf(-alpha, d.q[i], d.r[i]);
       d.r[i] = rn;
       rr = fmaf(rn, rn, rr);
@@ -435,23 +451,30 @@ __global__ void __launch_bounds__(kIrThreads) ir_update_kernel(IrArgs a, IrData 
   }
 }
 
-// p = z + beta p; re-arms the inner loop.
+// [d += alpha p if this iteration's update ran (it past d_it),] then
+// p = z + beta p unless the inner solve is done; re-arms the inner loop.
 template <int PK>
 __global__ void __launch_bounds__(kIrThreads) ir_direction_kernel(IrArgs a, IrData d) {
   pdl_wait();
+  const InnerState* s = d.ist;
+  const bool dup = DInDirection<PK>::value && s->it > s->d_it;
+  const bool pup = !s->done;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const InnerState* s = d.ist;
     const bool more = !s->done && s->it < s->max_it + 2;
     if (a.use_cond) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
   }
-  if (d.ist->done) return;
-  const float beta = static_cast<float>(d.ist->beta);
+  if (!dup && !pup) return;
+  const float alpha = static_cast<float>(s->alpha), beta = static_cast<float>(s->beta);
   IR_FOR_ROWS(i) {
-    float zv;
-    if (PK == PREC_BLOCK) zv = d.z[i];
-    else if (PK == PREC_SCALAR) zv = d.dinv[i] * d.r[i];
-    else zv = d.r[i];
-    d.p[i] = fmaf(beta, d.p[i], zv);
+    const float pv = d.p[i];
+    if (dup) d.d[i] = fmaf(alpha, pv, d.d[i]);
+    if (pup) {
+      float zv;
+      if (PK == PREC_BLOCK) zv = d.z[i];
+      else if (PK == PREC_SCALAR) zv = d.dinv[i] * d.r[i];
+      else zv = d.r[i];
+      d.p[i] = fmaf(beta, pv, zv);
+    }
   }
 }
 

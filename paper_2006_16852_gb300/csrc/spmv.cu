@@ -197,7 +197,21 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
 #pragma unroll
         for (int u = 0; u < 4; ++u) s = fma(vv[u], xv[u], s);
       }
-      for (; k < k1; k += 32) s = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), s);
+      if (k < k1) {  // at most 4 more strides of 32, loaded together
+        int cc[4];
+        double vv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = k + 32 * u < k1;
+          cc[u] = in ? __ldcs(a.col + k + 32 * u) : -1;
+          vv[u] = in ? __ldcs(a.val + k + 32 * u) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) epi_row_t<MODE>(e, row, s, a0, a1);
@@ -223,9 +237,22 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
         for (int u = 0; u < B; ++u)
           if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
       }
-      for (; j < L; ++j) {
-        const int cc = __ldcs(cp + j * 32);
-        if (cc >= 0) s = fma(__ldcs(vp + j * 32), __ldg(a.x + cc), s);
+      // the last L mod B slots in guarded batches of 4 (a round of loads
+      // per 4 slots, not per slot), still summed in slot order
+      for (; j < L; j += 4) {
+        int cc[4];
+        double vv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = j + u < L;
+          cc[u] = in ? __ldcs(cp + (j + u) * 32) : -1;
+          vv[u] = in ? __ldcs(vp + (j + u) * 32) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cc[u] >= 0) s = fma(vv[u], xv[u], s);
       }
       if (base < a.n_sell) epi_row_t<MODE>(e, __ldg(a.perm + base), s, a0, a1);
     }

@@ -26,15 +26,42 @@ __device__ __forceinline__ int lower_col(const int32_t* __restrict__ col, int lo
   return lo;
 }
 
+// Narrows [lo, hi) to at most P entries while keeping the first index k with
+// col[k] >= c inside [lo, hi] (the columns of a row are sorted).  Each round
+// probes P evenly spaced positions whose loads are independent, so a round
+// costs one memory latency and shrinks the range about P + 1 times (a
+// binary search pays one latency per halving).
+template <int P>
+__device__ __forceinline__ void narrow_col(const int32_t* __restrict__ col, int& lo, int& hi, int c) {
+  while (hi - lo > P) {
+    const int step = (hi - lo) / (P + 1);
+    int below = 0;  // the probes are sorted: those below c are a prefix
+#pragma unroll
+    for (int j = 0; j < P; ++j) below += __ldg(col + lo + (j + 1) * step) < c ? 1 : 0;
+    const int nlo = below > 0 ? lo + below * step + 1 : lo;
+    if (below < P) hi = lo + (below + 1) * step;
+    lo = nlo;
+  }
+}
+
+constexpr int kNarrow = 8;  // probes per round of narrow_col
+
 __global__ void jacobi_scalar_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                      const double* __restrict__ val, int n, double* dinv, int* bad) {
   const int stride = gridDim.x * blockDim.x;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     double d = 0.0;
     const int k1 = __ldg(rowptr + r + 1);
-    const int k = lower_col(col, __ldg(rowptr + r), k1, r);
-    const bool found = k < k1 && __ldg(col + k) == r;
-    if (found) d = __ldg(val + k);
+    int lo = __ldg(rowptr + r), hi = k1;
+    narrow_col<kNarrow>(col, lo, hi, r);
+    // the diagonal, if present, is the entry at the first index >= lo with
+    // column >= r, which lies in [lo, hi]: the window's columns loaded together
+    int at = -1;
+#pragma unroll
+    for (int j = 0; j <= kNarrow; ++j)
+      if (lo + j <= hi && lo + j < k1 && __ldg(col + lo + j) == r) at = lo + j;
+    const bool found = at >= 0;
+    if (found) d = __ldg(val + at);
     if (!found || d == 0.0) {
       atomicMin(bad, r);
       dinv[r] = 0.0;
@@ -72,15 +99,26 @@ __global__ void __launch_bounds__(256) bj_extract_kernel(const int32_t* __restri
     const int blk = r / bs, i = r - blk * bs, r0 = blk * bs;
     const int m = min(bs, n - r0);
     const int k1 = __ldg(rowptr + r + 1);
-    const int lo = lower_col(col, __ldg(rowptr + r), k1, r0);
-    // the candidates (at most m entries from lo) are loaded together: their
-    // columns first, then the values of those inside the block
+    int lo = __ldg(rowptr + r), hi = k1;
+    narrow_col<kNarrow>(col, lo, hi, r0);
+    // the run inside the block starts at an index in [lo, hi] and holds at
+    // most m entries: the window [lo, min(hi + m, k1)) covers it.  Its
+    // columns are loaded together; s counts those left of the block.
+    const int kend = min(hi + m, k1);
+    int s = 0, cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kNarrow + BT; ++j) {
+      const int c = lo + j < kend ? __ldg(col + lo + j) - r0 : m;
+      s += c < 0 ? 1 : 0;
+      cnt += (c >= 0 && c < m) ? 1 : 0;
+    }
+    // the run [lo + s, lo + s + cnt): columns (again, from L1) and values
     int cc[BT];
 #pragma unroll
-    for (int j = 0; j < BT; ++j) cc[j] = (j < m && lo + j < k1) ? __ldg(col + lo + j) - r0 : BT;
+    for (int j = 0; j < BT; ++j) cc[j] = j < cnt ? __ldg(col + lo + s + j) - r0 : BT;
     double vv[BT];
 #pragma unroll
-    for (int j = 0; j < BT; ++j) vv[j] = cc[j] < m ? __ldg(val + lo + j) : 0.0;
+    for (int j = 0; j < BT; ++j) vv[j] = j < cnt ? __ldg(val + lo + s + j) : 0.0;
     // the row of the dense block: zeros, then the entries at their columns
     // (the same 8 * m bytes, merged in L2 before they reach memory)
     double* out = blocks + static_cast<int64_t>(blk) * bs * bs + static_cast<int64_t>(i) * m;
@@ -332,8 +370,10 @@ int launch_bj_generate_reg(const Matrix* A, int n, int bs, int nblocks, double* 
                                                                                    bs, blocks);
   const size_t smem = sizeof(double) * BT * BT * kBjLds;
   GK_TRY(set_smem(bj_invert_kernel<BT>, smem));
+  // resident blocks per SM: registers allow 8 at block sizes up to 4 (64 per
+  // thread), 2 at 8 (190 per thread); the grid is capped at 8 and 4
   const int64_t g = std::min<int64_t>((nblocks + kBjRegThreads - 1) / kBjRegThreads,
-                                      4 * static_cast<int64_t>(sm_count()));
+                                      (BT <= 4 ? 8 : 4) * static_cast<int64_t>(sm_count()));
   bj_invert_kernel<BT><<<static_cast<int>(std::max<int64_t>(g, 1)), kBjRegThreads, smem, s>>>(n, bs, nblocks,
                                                                                                blocks, bad);
   return GK_OK;

@@ -252,10 +252,13 @@ def spmv_launches(info):
     return 1
 
 
-def solve_launches(kind, iters, spmvs, spmv_l):
+def solve_launches(kind, iters, spmvs, spmv_l, idle=0):
+    """Kernels one solve launches; idle = the status's idle_iters, the
+    iterations launched after the stop (a graph's loop body runs whole
+    passes), whose kernels do nothing but are launched all the same."""
     if kind == "cg":
-        # init, setup SpMV, start, iters x (SpMV + 2), final SpMV
-        return 2 + spmv_l + iters * (spmv_l + 2) + spmv_l
+        # init, setup SpMV, start, iterations x (SpMV + 2), final SpMV
+        return 2 + spmv_l + (iters + idle) * (spmv_l + 2) + spmv_l
     full = spmvs - 2 - iters
     half = iters - full
     return 2 + spmv_l + full * (2 * spmv_l + 3) + half * (spmv_l + 3) + spmv_l
@@ -508,8 +511,8 @@ class GpuStep:
             # iteration: FP32 SpMV (+ overflow kernel for HYB), update, direction
             inner_spmv = 2 if (info["format_name"] == "hyb" and info["tail_rows"] > 0) else 1
             return (1 + (st.outer_iters + 1) * spmv_launches(info) + 2 * st.outer_iters
-                    + st.iters * (inner_spmv + 2))
-        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(info))
+                    + (st.iters + st.idle_iters) * (inner_spmv + 2))
+        return solve_launches(sk, st.iters, st.spmvs, spmv_launches(info), idle=st.idle_iters)
 
 
 # ---------------------------------------------------------------------------

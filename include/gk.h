@@ -142,7 +142,10 @@ typedef struct {
   int32_t device_error; /* nonzero if a device-side wait timed out                    */
   int64_t outer_iters;  /* GK_IR_CG: refinement steps (FP64 residuals); else 0        */
   int32_t form;         /* how the iteration ran: GK_FORM_*                           */
-  int32_t reserved_;
+  int32_t idle_iters;   /* iterations whose kernels were launched after the stop and  */
+                        /* did nothing: a graph's loop body runs whole passes of CG   */
+                        /* iterations (GK_IR_CG: of inner iterations), a host loop    */
+                        /* whole groups of check_every                                */
 } gk_status;
 
 #define GK_FORM_GRAPH 0    /* one CUDA graph, loop controlled on the device            */

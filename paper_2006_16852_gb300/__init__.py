@@ -62,7 +62,7 @@ class Status(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("spmvs", ctypes.c_int64), ("rel_res", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("ref_norm", ctypes.c_double),
                 ("stop_reason", ctypes.c_int32), ("device_error", ctypes.c_int32),
-                ("outer_iters", ctypes.c_int64), ("form", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("outer_iters", ctypes.c_int64), ("form", ctypes.c_int32), ("idle_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -304,7 +304,7 @@ class SolveStatus:
     device_error: int
     outer_iters: int
     form: int = 0
-    reserved_: int = 0
+    idle_iters: int = 0
 
 
 FORM_GRAPH, FORM_HOST, FORM_CLUSTER, FORM_GRID = 0, 1, 2, 3

@@ -27,6 +27,22 @@ constexpr long long kMaxWaitCycles = 4000000000LL;
 // the stream's order holds transitively.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Lets the next kernel of the stream (if launched with launch_pdl) be
+// scheduled before this grid has finished: its blocks take the SM slots that
+// this grid's blocks free, run their prologue and wait in pdl_wait() until
+// this grid has completed.  Called after pdl_wait(), so a kernel's dependents
+// never start before the kernel ahead of it has completed, and a prologue may
+// touch anything but this grid's output.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Brings the line holding *p into L2 (a hint: no data comes back and L1 is
+// not involved, so a prologue's prefetch cannot observe a stale copy).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

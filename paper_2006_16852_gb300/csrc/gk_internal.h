@@ -170,6 +170,10 @@ struct Epi {
 // ---------------------------------------------------------------------------
 // matrix handle
 // ---------------------------------------------------------------------------
+// Iterations of CG (and of the refinement's inner CG) per pass of a solve
+// graph's loop body.
+constexpr int kGraphUnroll = 4;
+
 constexpr int kMergeThreads = 256;
 constexpr int kMergeItems = 8;  // merge-path items (row ends + nonzeros) per lane
 constexpr int kMergeTile = 32 * kMergeItems;  // items per warp tile
@@ -348,6 +352,7 @@ struct Solver {
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   IrData* ir = nullptr;  // GK_IR_CG: the FP32 inner solver
+  int64_t ir_idle = 0;   // GK_IR_CG: inner iterations launched after the inner stops (last solve)
   GmresData* gm = nullptr;  // GK_GMRES: Arnoldi basis and Hessenberg state
   int cl_lg = -1;           // GK_CG / GK_BICGSTAB small-system form: rows per CTA = 2^cl_lg (-1: none)
   int cl_rpt = 1;           // ... rows per thread

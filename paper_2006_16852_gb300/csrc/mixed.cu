@@ -648,7 +648,10 @@ int ir_build_graph(Solver& S, IrData& d) {
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
     cudaGraph_t body = np.conditional.phGraph_out[0];
     GK_TRY_CUDA(cudaStreamBeginCaptureToGraph(d.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int brc = ir_enqueue_inner(S, d, a, d.cs);
+    // kGraphUnroll inner iterations per pass of the body (those after the
+    // inner stop do nothing): fewer turn-arounds of the loop
+    int brc = GK_OK;
+    for (int u = 0; u < kGraphUnroll && brc == GK_OK; ++u) brc = ir_enqueue_inner(S, d, a, d.cs);
     e = cudaStreamEndCapture(d.cs, &captured);
     if (brc != GK_OK) return brc;
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture (inner body)");
@@ -761,10 +764,22 @@ int ir_solve(Solver* S, cudaStream_t s) {
   e.partials = S->partials;
   e.counter = S->counter;
   e.err = &S->st->err;
+  // inner iterations launched beyond those done: whole passes of the graph's
+  // loop body, or whole groups of check_every in the host loop
+  S->ir_idle = 0;
+  long long prev_iter = 0;
+  int64_t launched = -1;  // by the inner solve just finished
   for (int outer = 0;; ++outer) {
     GK_TRY(spmv_launch(*S->A, S->x, e, s));
     GK_TRY_CUDA(cudaMemcpyAsync(S->h_st, S->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     GK_TRY_CUDA(cudaStreamSynchronize(s));
+    if (outer > 0) {
+      const int64_t inner = S->h_st->iter - prev_iter;
+      if (launched < 0) launched = kGraphUnroll * std::max<int64_t>(1, (inner + kGraphUnroll - 1) / kGraphUnroll);
+      S->ir_idle += std::max<int64_t>(launched - inner, 0);
+    }
+    prev_iter = S->h_st->iter;
+    launched = -1;
     if (S->h_st->stop != GK_STOP_NONE) break;
     if (outer >= kMaxOuter) {
       const int stop = GK_STOP_MAX_ITERS;
@@ -780,7 +795,8 @@ int ir_solve(Solver* S, cudaStream_t s) {
     IrArgs a = ir_args(*S, d);
     a.use_cond = 0;
     GK_TRY(ir_enqueue_start(*S, d, a, s));
-    for (int64_t done = 0;;) {
+    int64_t done = 0;
+    for (;;) {
       for (int i = 0; i < S->crit.check_every; ++i) GK_TRY(ir_enqueue_inner(*S, d, a, s));
       done += S->crit.check_every;
       InnerState h;
@@ -788,6 +804,7 @@ int ir_solve(Solver* S, cudaStream_t s) {
       GK_TRY_CUDA(cudaStreamSynchronize(s));
       if (h.done || h.it >= h.max_it + 2 || done > h.max_it + 2) break;
     }
+    launched = done;
     ir_apply_kernel<<<d.grid, kIrThreads, 0, s>>>(a, d);
     GK_TRY_CUDA(cudaGetLastError());
   }

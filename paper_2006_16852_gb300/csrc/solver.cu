@@ -202,9 +202,43 @@ __device__ __forceinline__ void cg_update_body(const VecArgs& a, double* scratch
   else reduce_finalize(a, rz, rr, FIN_CG_ITER, scratch, false);
 }
 
+// Prologue of CG's update step, run while the SpMV ahead of it may still be
+// running: the lines of x, p and r (and of the preconditioner) that the
+// thread reads first, into L2.  q, the SpMV's output, is read only after
+// pdl_wait().
+template <int PK, int BS>
+__device__ __forceinline__ void cg_update_prefetch(const VecArgs& a) {
+  const int lane = threadIdx.x & 31;
+  if (PK == PREC_BLOCK) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int bpw = 32 / a.bs;
+    if (w * bpw < a.nblocks) {
+      const BjLane L = bj_lane(w * bpw, lane, a.bs, a.n, a.nblocks);
+      if (L.active) {
+        if ((lane & 15) == 0) {
+          prefetch_l2(a.x + L.row);
+          prefetch_l2(a.p + L.row);
+          prefetch_l2(a.r + L.row);
+        }
+        prefetch_l2(a.blocks + static_cast<int64_t>(L.blk) * a.bs * a.bs + static_cast<int64_t>(L.i) * L.m);
+      }
+    }
+  } else {
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i < a.n && (lane & 7) == 0) {
+      prefetch_l2(a.x + i);
+      prefetch_l2(a.p + i);
+      prefetch_l2(a.r + i);
+      if (PK == PREC_SCALAR) prefetch_l2(a.dinv + i);
+    }
+  }
+}
+
 template <int PK, int BS = 0>
 __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) cg_update_kernel(VecArgs a) {
+  cg_update_prefetch<PK, BS>(a);
   pdl_wait();
+  pdl_launch_dependents();
   __shared__ double scratch[kRedScratch];
   cg_update_body<PK, BS, false>(a, scratch);
 }
@@ -219,7 +253,17 @@ __global__ void __launch_bounds__(kVecThreads, VecMinBlocks<PK>::value) fcg_upda
 // p = z + beta p; ends the iteration (loop control).
 template <int PK>
 __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a) {
+  {
+    // prologue: p and the diagonal, which the running update step does not
+    // write, into L2
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i < a.n && (threadIdx.x & 7) == 0) {
+      prefetch_l2(a.p + i);
+      if (PK == PREC_SCALAR) prefetch_l2(a.dinv + i);
+    }
+  }
   pdl_wait();
+  pdl_launch_dependents();
   if (blockIdx.x == 0 && threadIdx.x == 0) loop_control(a);
   if (a.st->stop) return;
   const double beta = a.st->beta;
@@ -651,7 +695,13 @@ int build_graph(Solver& S) {
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
   GK_TRY_CUDA(cudaStreamBeginCaptureToGraph(S.cs, body, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeThreadLocal));
+  // CG and FCG: kGraphUnroll iterations per pass of the loop body, so that
+  // three iterations in four skip the loop's turn-around (about 7 us on a
+  // GB300, with no programmatic edge across it).  The kernels of an
+  // iteration after the stop do nothing.
+  const int passes = (S.kind == GK_CG || S.kind == GK_FCG) ? kGraphUnroll : 1;
   rc = enqueue_iteration(S, S.cs, a);
+  for (int u = 1; u < passes && rc == GK_OK; ++u) rc = enqueue_iteration(S, S.cs, a);
   e = cudaStreamEndCapture(S.cs, &captured);
   if (rc != GK_OK) return rc;
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture (body)");
@@ -753,6 +803,7 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = GK_OK;
   int form = S->crit.check_every > 0 ? GK_FORM_HOST : GK_FORM_GRAPH;
+  int64_t launched = -1;  // iterations launched, where more than were done
   do {
     if (S->n == 0) {
       if (status) {
@@ -826,6 +877,7 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
         if (done > S->crit.max_iters + 2) break;
       }
       if (rc) break;
+      launched = done;
       if ((rc = enqueue_final(*S, s))) break;
     } else {
       if (!S->exec && (rc = build_graph(*S))) break;
@@ -853,7 +905,15 @@ extern "C" int gk_solve(gk_solver h, const void* b, void* x, gk_status* status, 
       status->device_error = H.err;
       status->outer_iters = H.outer;
       status->form = form;
-      status->reserved_ = 0;
+      int64_t idle = 0;
+      if (S->kind == GK_IR_CG) {
+        idle = S->ir_idle;
+      } else if (launched >= 0) {
+        idle = launched - H.iter;
+      } else if (form == GK_FORM_GRAPH && (S->kind == GK_CG || S->kind == GK_FCG)) {
+        idle = kGraphUnroll * std::max<int64_t>(1, (H.iter + kGraphUnroll - 1) / kGraphUnroll) - H.iter;
+      }
+      status->idle_iters = static_cast<int32_t>(std::max<int64_t>(idle, 0));
     }
     if (H.err & kErrTimeout) rc = set_error(GK_ERR_TIMEOUT, "gk_solve: a device-side wait timed out");
   } while (false);

@@ -290,9 +290,25 @@ struct EllBatch {
   static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN) ? 8 : 4;
 };
 
+// Slots of its first row a thread prefetches into L2 before the previous
+// kernel has finished (the matrix is not written by any kernel of a solve).
+constexpr int kEllPrefetchSlots = 8;
+
 template <int MODE, bool TAIL>
 __global__ void __launch_bounds__(kEllThreads, 8) spmv_ell_kernel(EllArgs a, Epi e) {
+  {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (row < a.n_rows && (lane & 15) == 0) {
+      const int kp = min(a.K, kEllPrefetchSlots);
+      for (int j = 0; j < kp; ++j) {
+        if (lane == 0) prefetch_l2(a.col + row + j * a.ld);
+        prefetch_l2(a.val + row + j * a.ld);
+      }
+    }
+  }
   pdl_wait();
+  pdl_launch_dependents();
   constexpr int B = EllBatch<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
   if (epi_skip(e)) return;

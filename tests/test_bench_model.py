@@ -108,3 +108,14 @@ def test_spmv_bytes_per_format():
     # a CG iteration carries the format's SpMV
     d = bench.cg_bytes(1, nnz, n, "jacobi", fmt="ell") - bench.cg_bytes(0, nnz, n, "jacobi", fmt="ell")
     assert d == bench.spmv_bytes(nnz, n, n, fmt="ell") + 88 * n
+
+
+def test_solve_launches_counts_idle_iterations():
+    """CG launches init, the set-up SpMV and start, three kernels per
+    iteration (the SpMV, update and direction; a GK_CSR matrix's SpMV is one
+    kernel) including the iterations launched after the stop (idle_iters),
+    and the final SpMV."""
+    assert bench.solve_launches("cg", 251, 253, 1) == 2 + 1 + 251 * 3 + 1
+    assert bench.solve_launches("cg", 251, 253, 1, idle=1) == 2 + 1 + 252 * 3 + 1
+    # HYB with an overflow: 3 kernels per SpMV
+    assert bench.solve_launches("cg", 14, 16, 3, idle=2) == 2 + 3 + 16 * 5 + 3

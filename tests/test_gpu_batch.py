@@ -7,10 +7,14 @@ sequentially in the oracle, so iterates differ by rounding.  Compared per
 system: the stop reason, the iteration count (within 1 for FP64 CG; within
 max(3, 25%) for BiCGSTAB, whose non-monotone residual makes the step at
 which it crosses the target sensitive to rounding -- the oracle's own count
-on these systems moves by up to 21% when b is perturbed by 1e-16 relative
-noise; within 2 + 5% for CG in FP32
+on these systems moves by about 10% when b is perturbed by 1e-16 relative
+noise, and over 2000 systems of the benchmark workload the GPU's FP64
+counts differ from the oracle's by 2% on average, 11% at the 99th
+percentile and 17% at most; within 2 + 5% for CG in FP32
 and max(5, 25%) for BiCGSTAB in FP32, where 1e-6 lies near the attainable
-accuracy), the
+accuracy: there the same 2000 systems differ by 4% on average, 16% at the
+99th percentile and 31% at most, so the fixed samples below stay inside
+the bar while a few of the 10,000 systems would not), the
 recurred and true residuals, and the solution against the
 oracle's to kappa * tol.  What must hold bit for bit on the GPU (a system's
 result not depending on its neighbours, on the schedule or on the run) is
@@ -257,7 +261,11 @@ def test_batch_full_size_sampled(gk, orc, dtype, tol, kind):
     U{6..32}, b seed 28) in every benchmark form of CG and BiCGSTAB: every
     system converges (the oracle converges on all of them), and a sample --
     12 random systems plus the largest and the smallest -- is checked
-    against the oracle one by one at the batched parity bar."""
+    against the oracle one by one at the batched parity bar.  Over all
+    10,000 systems the iteration counts' relative differences from the
+    oracle's are bounded in distribution: CG's by the per-system bar,
+    BiCGSTAB's on average (5 %), at the 99th percentile (20 %) and at most
+    (50 %)."""
     sys_ptr, A = W.batch_varcoef2d(10000, seed=5)
     b = W.uniform_vector(int(sys_ptr[-1]), 28)
     st, x = _run(gk, sys_ptr, A, b, kind, True, dtype, tol, max_iters=20000)
@@ -267,8 +275,13 @@ def test_batch_full_size_sampled(gk, orc, dtype, tol, kind):
     sizes = np.diff(sys_ptr)
     sample = sorted(set(int(s) for s in np.random.default_rng(0).choice(10000, 12, replace=False))
                     | {int(np.argmax(sizes)), int(np.argmin(sizes))})
-    xo, res = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, dtype=dtype, tol=tol, systems=sample,
-                              max_iters=20000)
+    xo, res_all = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, dtype=dtype, tol=tol, max_iters=20000)
+    oi = np.array([r.iters for r in res_all])
+    rel = np.abs(st["iters"].astype(np.int64) - oi) / oi
+    if kind == "bicgstab":
+        assert rel.mean() <= 0.05 and np.quantile(rel, 0.99) <= 0.20 and rel.max() <= 0.50, (
+            rel.mean(), np.quantile(rel, 0.99), rel.max())
+    res = [res_all[s] for s in sample]
     for s, r in zip(sample, res):
         r0, r1 = sys_ptr[s], sys_ptr[s + 1]
         assert r.stop_reason == gk.STOP_CONVERGED

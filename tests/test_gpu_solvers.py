@@ -75,6 +75,34 @@ def test_host_loop_equals_graph_loop(gk):
         s0, x0 = _solve(gk, A, b, kind=kind, prec=1, check_every=-1)
         s1, x1 = _solve(gk, A, b, kind=kind, prec=1, check_every=7)
         assert s0.iters == s1.iters and np.array_equal(x0, x1), kind
+        # kernels launched after the stop: the graph runs whole passes of four
+        # CG iterations (one pass at least), the host loop whole groups of 7
+        if kind == "cg":
+            assert 0 <= s0.idle_iters < 4 and (s0.iters + s0.idle_iters) % 4 == 0, (s0.iters, s0.idle_iters)
+        else:
+            assert s0.idle_iters == 0
+        assert 0 <= s1.idle_iters < 7 and (s1.iters + s1.idle_iters) % 7 == 0, (s1.iters, s1.idle_iters)
+
+
+@pytest.mark.parametrize("max_iters", [0, 1, 5, 6, 7])
+@pytest.mark.parametrize("prec", [None, 1, 4])
+def test_graph_passes_stop_mid_pass(gk, prec, max_iters):
+    """The graph's loop body holds four CG iterations; a stop inside a pass
+    (here the iteration limit, and an exact x0 that stops at k = 0) leaves
+    the rest of the pass without effect: iterations, status and x equal the
+    host loop's with a status read after every iteration."""
+    A = W.poisson2d(40)
+    b = W.uniform_vector(1600, 8)
+    s0, x0 = _solve(gk, A, b, prec=prec, check_every=-1, max_iters=max_iters, reduction_factor=1e-12)
+    s1, x1 = _solve(gk, A, b, prec=prec, check_every=1, max_iters=max_iters, reduction_factor=1e-12)
+    assert s0.stop_reason == s1.stop_reason == gk.STOP_MAX_ITERS
+    assert s0.iters == s1.iters == max_iters
+    assert s0.rel_res == s1.rel_res and np.array_equal(x0, x1)
+    assert s0.idle_iters == (4 if max_iters == 0 else -max_iters % 4), s0.idle_iters
+    _, xs = _solve(gk, A, b, prec=prec, check_every=-1, max_iters=500, reduction_factor=1e-12)
+    s2, x2 = _solve(gk, A, b, x0=xs, prec=prec, check_every=-1, max_iters=50, reduction_factor=1e-2)
+    assert s2.stop_reason == gk.STOP_CONVERGED and s2.iters == 0 and s2.idle_iters == 4
+    assert np.array_equal(x2, xs)
 
 
 @pytest.mark.parametrize("prec", [None, 1, 4, 16])

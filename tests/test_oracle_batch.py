@@ -161,3 +161,26 @@ def test_bicgstab_f32_restart_cap_on_a_skew_system(orc):
     assert res.stop_reason == orc.STOP_BREAKDOWN
     assert res.iters == 0 and res.spmvs == 7
     assert np.array_equal(res.x, x0)
+
+
+def test_bicgstab_iteration_count_is_rounding_sensitive(orc):
+    """Why the GPU parity bar for BiCGSTAB iteration counts is wider than
+    CG's: on the batched workload, a perturbation of b at the level of one
+    rounding (1e-16 relative) moves the oracle's own BiCGSTAB count by 5 %
+    or more on some system, while every CG count moves by at most one.
+    BiCGSTAB's residual is not monotone, so the step at which it first
+    crosses the target depends on the rounding of every dot product; the
+    GPU's reductions sum in another fixed order."""
+    sys_ptr, A = W.batch_varcoef2d(48, seed=5)
+    b = W.uniform_vector(int(sys_ptr[-1]), 21)
+    bp = b * (1.0 + 1e-16 * np.random.default_rng(7).standard_normal(b.size))
+    moved = {}
+    for kind in ("cg", "bicgstab"):
+        _, r0 = orc.batch_solve(sys_ptr, A, b, kind=kind, jacobi=True, tol=1e-10)
+        _, r1 = orc.batch_solve(sys_ptr, A, bp, kind=kind, jacobi=True, tol=1e-10)
+        assert all(r.stop_reason == 1 for r in r0 + r1)
+        moved[kind] = [abs(p.iters - q.iters) / p.iters for p, q in zip(r0, r1)]
+        if kind == "cg":
+            assert max(abs(p.iters - q.iters) for p, q in zip(r0, r1)) <= 1
+    assert max(moved["bicgstab"]) >= 0.05, max(moved["bicgstab"])
+    assert max(moved["bicgstab"]) <= 0.25, max(moved["bicgstab"])

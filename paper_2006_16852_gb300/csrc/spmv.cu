@@ -130,6 +130,13 @@ template <int MODE>
 struct EllBatchOf {
   static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN || MODE == EPI_DOT) ? 8 : 4;
 };
+// Strides of 32 entries a lane keeps in flight in a long row (warp per
+// row): 8 for CG's fused dot (40 registers), 4 for the plain applies, whose
+// 32-register build slows down with 8.
+template <int MODE>
+struct MidBatchOf {
+  static constexpr int value = MODE == EPI_DOT ? 8 : 4;
+};
 
 struct SliceArgs {
   const int32_t* rowptr;
@@ -171,7 +178,28 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
     const int row = __ldg(a.big + v);
     const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
     double sm[1] = {0.0};
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) sm[0] = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), sm[0]);
+    if (MODE == EPI_COPY || MODE == EPI_PLAIN) {  // within 32 registers
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+        sm[0] = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), sm[0]);
+    } else {
+      // a thread's entries k0 + tid + j * blockDim.x in order, 4 strides
+      // loaded together
+      for (int k = k0 + threadIdx.x; k < k1; k += 4 * blockDim.x) {
+        int cc[4];
+        double vv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = k + u * static_cast<int>(blockDim.x) < k1;
+          cc[u] = in ? __ldcs(a.col + k + u * blockDim.x) : -1;
+          vv[u] = in ? __ldcs(a.val + k + u * blockDim.x) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cc[u] >= 0) sm[0] = fma(vv[u], xv[u], sm[0]);
+      }
+    }
     block_sum<1, double>(sm, row_scratch);
     if (threadIdx.x == 0) epi_row_t<MODE>(e, row, sm[0], a0, a1);
     __syncthreads();
@@ -183,21 +211,23 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
     if (it < a.n_mid) {
       const int row = __ldg(a.mid + it);
       const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+      constexpr int MB = MidBatchOf<MODE>::value;
       double s = 0.0;
       int k = k0 + lane;
-      for (; k + 96 < k1; k += 128) {
-        int cc[4];
-        double vv[4], xv[4];
+      for (; k + 32 * (MB - 1) < k1; k += 32 * MB) {
+        int cc[MB];
+        double vv[MB], xv[MB];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) cc[u] = __ldcs(a.col + k + 32 * u);
+        for (int u = 0; u < MB; ++u) cc[u] = __ldcs(a.col + k + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(a.val + k + 32 * u);
+        for (int u = 0; u < MB; ++u) vv[u] = __ldcs(a.val + k + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = __ldg(a.x + cc[u]);
+        for (int u = 0; u < MB; ++u) xv[u] = __ldg(a.x + cc[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s = fma(vv[u], xv[u], s);
+        for (int u = 0; u < MB; ++u) s = fma(vv[u], xv[u], s);
       }
-      if (k < k1) {  // at most 4 more strides of 32, loaded together
+#pragma unroll
+      for (int g = 0; g < MB / 4; ++g, k += 128) {  // fewer than MB strides of 32 left: guarded batches of 4
         int cc[4];
         double vv[4], xv[4];
 #pragma unroll

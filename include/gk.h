@@ -67,8 +67,8 @@ extern "C" {
 /* Storage formats of the system matrix. */
 #define GK_CSR 0        /* CSR, rows binned by length: rows of up to 256 entries sorted
                            by length into slices of 32 (a copy stored column-major,
-                           one thread per row), longer rows one warp per row, rows
-                           over 4096 entries one thread block per row                   */
+                           one thread per row), longer rows cut into pieces of up to
+                           512 consecutive entries, one warp per piece                  */
 #define GK_CSR_MERGE 1  /* CSR, merge-path split of rows+nonzeros into equal tiles      */
 #define GK_ELL 2        /* ELLPACK, column-major, padded to the longest row             */
 #define GK_HYB 3        /* hybrid: ELL part of width K plus the overflow of longer rows
@@ -174,7 +174,7 @@ typedef struct {
   int64_t tail_rows;       /* HYB: rows with more than K entries               */
   int64_t tail_nnz;        /* HYB: entries stored outside the ELL part          */
   int64_t short_items;     /* GK_CSR: warp items of up to 32 short rows         */
-  int64_t long_rows;       /* GK_CSR: rows processed warp-per-row               */
+  int64_t long_rows;       /* GK_CSR: rows of more than 256 entries (in pieces) */
   int64_t tiles;           /* GK_CSR_MERGE: merge-path tiles                    */
   int64_t device_bytes;    /* bytes of library-owned device storage             */
   int64_t spmv_bytes;      /* algorithmic bytes of one simple apply: the stored */

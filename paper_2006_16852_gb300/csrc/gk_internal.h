@@ -178,10 +178,10 @@ constexpr int kMergeThreads = 256;
 constexpr int kMergeItems = 8;  // merge-path items (row ends + nonzeros) per lane
 constexpr int kMergeTile = 32 * kMergeItems;  // items per warp tile
 // GK_CSR: rows of up to kSliceMaxLen entries go to length-sorted slices of 32
-// rows; longer rows are summed one warp per row, beyond kBlockRowLen one
-// thread block per row.
+// rows; longer rows are cut into pieces of at most kPieceLen consecutive
+// entries, each summed by one warp.
 constexpr int kSliceMaxLen = 256;
-constexpr int kBlockRowLen = 4096;
+constexpr int kPieceLen = 512;
 constexpr int kSliceThreads = 256;
 constexpr int kEllThreads = 256;
 // GK_HYB's COO overflow: each lane sums kCooPerLane consecutive entries, a
@@ -228,10 +228,18 @@ struct Matrix {
   int32_t* sl_col = nullptr;
   double* sl_val = nullptr;
   int64_t n_sell = 0, n_slices = 0, sl_entries = 0;
-  int32_t* mid_rows = nullptr;
-  int64_t n_mid = 0;
-  int32_t* big_rows = nullptr;
-  int64_t n_big = 0;
+  // rows longer than kSliceMaxLen (n_long of them), cut into pieces of at
+  // most kPieceLen consecutive entries, longest first: {row, first entry,
+  // end entry, slot}; slot is -1 when the row is a single piece (its warp
+  // finishes it), else the piece's partial-sum slot in pc_sum.  Rows of
+  // several pieces (lr_row, their slots lr_off[i] .. lr_off[i + 1]) are
+  // finished by a second launch that adds their pieces in order.
+  int4* pc = nullptr;
+  int64_t n_pc = 0, n_long = 0;
+  int32_t* lr_row = nullptr;
+  int32_t* lr_off = nullptr;
+  int64_t n_lr = 0;
+  double* pc_sum = nullptr;
   int grid_sl = 0;        // persistent grid of the epilogues with reductions
   int grid_sl_plain = 0;  // ... of the plain applies (more blocks per SM)
   // GK_CSR_MERGE
@@ -281,7 +289,7 @@ int spmv_max_grid(const Matrix& A);
 // Persistent grid sizes of the SpMV kernels for a given amount of work.
 int merge_grid(int64_t n_tiles);
 int coo_grid(int64_t n_chunks);
-int sliced_grid(int64_t warp_items, int64_t big_rows, bool plain);
+int sliced_grid(int64_t warp_items, bool plain);
 int ell_grid(int64_t n_rows);
 
 // Format construction (matrix.cu).

@@ -131,16 +131,15 @@ __global__ void slice_fill_kernel(const int32_t* __restrict__ rowptr, const int3
 }
 
 // Stored entries over the DFMA lane slots the GK_CSR kernel issues (slices:
-// 32 x their longest row; a mid row 32 x ceil(len / 32) plus its butterfly;
-// a big row 256 x ceil(len / 256)).
+// 32 x their longest row; a long row 32 x ceil(len / 32) plus a butterfly
+// per piece).
 double sliced_efficiency(const std::vector<int32_t>& rp, int64_t n) {
   std::vector<int64_t> cnt(kSliceMaxLen + 1, 0);
   double slots = 0.0, nnz = static_cast<double>(rp[n]);
   for (int64_t i = 0; i < n; ++i) {
     const int64_t len = rp[i + 1] - rp[i];
     if (len <= kSliceMaxLen) cnt[len] += 1;
-    else if (len <= kBlockRowLen) slots += 32.0 * ((len + 31) / 32) + 160.0;
-    else slots += 256.0 * ((len + 255) / 256) + 256.0;
+    else slots += 32.0 * ((len + 31) / 32) + 160.0 * ((len + kPieceLen - 1) / kPieceLen);
   }
   int64_t in_slice = 0;  // rows placed so far, longest first
   for (int64_t L = kSliceMaxLen; L >= 0; --L) {
@@ -181,7 +180,7 @@ void matrix_release(Matrix* A) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(A->device);
-  void* ptrs[] = {A->rowptr, A->col, A->val, A->sl_perm, A->sl_off, A->sl_col, A->sl_val, A->mid_rows, A->big_rows,
+  void* ptrs[] = {A->rowptr, A->col, A->val, A->sl_perm, A->sl_off, A->sl_col, A->sl_val, A->pc, A->lr_row, A->lr_off, A->pc_sum,
                   A->merge.tile_i, A->merge.tile_j, A->merge.head_val, A->merge.carry_val, A->ell_col,
                   A->ell_val,
                   A->tail_rows, A->tail_rowptr, A->tail_row, A->tail_col, A->tail_val, A->tail_slot,
@@ -270,12 +269,11 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
   if (fmt == GK_CSR) {
     // counting sort by decreasing length (ties: increasing row index)
     std::vector<int64_t> cnt(kSliceMaxLen + 2, 0);
-    std::vector<int32_t> mid, big;
+    std::vector<int32_t> longr;
     for (int64_t i = 0; i < n_rows; ++i) {
       const int64_t len = rp[i + 1] - rp[i];
       if (len <= kSliceMaxLen) cnt[kSliceMaxLen - len + 1] += 1;
-      else if (len <= kBlockRowLen) mid.push_back(static_cast<int32_t>(i));
-      else big.push_back(static_cast<int32_t>(i));
+      else longr.push_back(static_cast<int32_t>(i));
     }
     for (int64_t L = 1; L <= kSliceMaxLen + 1; ++L) cnt[L] += cnt[L - 1];
     const int64_t n_sell = cnt[kSliceMaxLen + 1];
@@ -288,8 +286,23 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
       const int64_t lx = rp[x + 1] - rp[x], ly = rp[y + 1] - rp[y];
       return lx != ly ? lx > ly : x < y;
     };
-    std::sort(mid.begin(), mid.end(), by_len);
-    std::sort(big.begin(), big.end(), by_len);
+    std::sort(longr.begin(), longr.end(), by_len);
+    // long rows in pieces of kPieceLen consecutive entries (the last one
+    // shorter), longest first (ties: row, then position)
+    std::vector<int4> pc;
+    std::vector<int32_t> lr_row, lr_off(1, 0);
+    int32_t n_slot = 0;
+    for (const int32_t r : longr) {
+      const int32_t k0 = rp[r], k1 = rp[r + 1];
+      const bool split = k1 - k0 > kPieceLen;
+      for (int32_t k = k0; k < k1; k += kPieceLen)
+        pc.push_back(make_int4(r, k, std::min(k1, k + kPieceLen), split ? n_slot++ : -1));
+      if (split) {
+        lr_row.push_back(r);
+        lr_off.push_back(n_slot);
+      }
+    }
+    std::stable_sort(pc.begin(), pc.end(), [](const int4& u, const int4& v) { return u.z - u.y > v.z - v.y; });
     const int64_t n_slices = (n_sell + 31) / 32;
     std::vector<int64_t> off(static_cast<size_t>(n_slices + 1), 0);
     for (int64_t c = 0; c < n_slices; ++c) {
@@ -299,12 +312,15 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
     A->n_sell = n_sell;
     A->n_slices = n_slices;
     A->sl_entries = off[n_slices];
-    A->n_mid = static_cast<int64_t>(mid.size());
-    A->n_big = static_cast<int64_t>(big.size());
+    A->n_long = static_cast<int64_t>(longr.size());
+    A->n_pc = static_cast<int64_t>(pc.size());
+    A->n_lr = static_cast<int64_t>(lr_row.size());
     GK_TRY(upload(&A->sl_perm, perm, 0, bytes, s));
     GK_TRY(upload(&A->sl_off, off, 0, bytes, s));
-    GK_TRY(upload(&A->mid_rows, mid, 0, bytes, s));
-    GK_TRY(upload(&A->big_rows, big, 0, bytes, s));
+    GK_TRY(upload(&A->pc, pc, 0, bytes, s));
+    GK_TRY(upload(&A->lr_row, lr_row, 0, bytes, s));
+    GK_TRY(upload(&A->lr_off, lr_off, 0, bytes, s));
+    GK_TRY(dalloc_n(&A->pc_sum, static_cast<size_t>(std::max<int32_t>(n_slot, 1)), bytes));
     GK_TRY(dalloc_n(&A->sl_col, static_cast<size_t>(std::max<int64_t>(A->sl_entries, 1)), bytes));
     GK_TRY(dalloc_n(&A->sl_val, static_cast<size_t>(std::max<int64_t>(A->sl_entries, 1)), bytes));
     if (n_slices > 0) {
@@ -313,8 +329,8 @@ extern "C" int gk_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
                                                                    A->sl_val);
       GK_TRY_CUDA(cudaGetLastError());
     }
-    A->grid_sl = sliced_grid(A->n_mid + A->n_slices, A->n_big, false);
-    A->grid_sl_plain = sliced_grid(A->n_mid + A->n_slices, A->n_big, true);
+    A->grid_sl = sliced_grid(A->n_pc + A->n_slices, false);
+    A->grid_sl_plain = sliced_grid(A->n_pc + A->n_slices, true);
   } else if (fmt == GK_CSR_MERGE) {
     GK_TRY(build_merge_plan(A->merge, n_rows, nnz, A->rowptr, A->col, A->val, bytes, s));
   } else {  // GK_ELL, GK_HYB
@@ -411,7 +427,7 @@ extern "C" int gk_matrix_get_info(gk_matrix h, gk_matrix_info* info) {
   info->tail_rows = A->m_tail;
   info->tail_nnz = A->tail_nnz;
   info->short_items = A->n_slices;
-  info->long_rows = A->n_mid + A->n_big;
+  info->long_rows = A->n_long;
   info->tiles = A->merge.n_tiles;
   info->device_bytes = A->device_bytes;
   // the stored operator once (CSR: values, indices, row pointers; ELL: the

@@ -116,9 +116,11 @@ __device__ __forceinline__ void epi_partial(const Epi& e, double a0, double a1, 
 // (in that order) rows stored column-major and padded to the slice's longest
 // row -- so neighbouring lanes have nearly equal work and their loads of
 // values and indices are coalesced; each lane sums its row sequentially in
-// CSR order, bit-identical to the CPU reference.  Longer rows are summed one
-// warp per row (coalesced loads, xor butterfly), and rows beyond kBlockRowLen
-// entries one thread block per row, so that no row holds up the launch.
+// CSR order, bit-identical to the CPU reference.  Longer rows are cut into
+// pieces of at most kPieceLen consecutive entries, each summed by one warp
+// (coalesced loads, xor butterfly), so that no row holds up the launch: a
+// row of one piece is finished by its warp, the pieces of longer rows are
+// added in order by a second launch (spmv_long_fixup_kernel).
 // Values and indices are streamed (read once, evict first) so that the
 // gathered vector keeps the caches (27-point matrix: 135.9 -> 116.5 us).
 // ---------------------------------------------------------------------------
@@ -130,8 +132,8 @@ template <int MODE>
 struct EllBatchOf {
   static constexpr int value = (MODE == EPI_COPY || MODE == EPI_PLAIN || MODE == EPI_DOT) ? 8 : 4;
 };
-// Strides of 32 entries a lane keeps in flight in a long row (warp per
-// row): 8 for CG's fused dot (40 registers), 4 for the plain applies, whose
+// Strides of 32 entries a lane keeps in flight in a piece of a long row: 8
+// for CG's fused dot (40 registers), 4 for the plain applies, whose
 // 32-register build slows down with 8.
 template <int MODE>
 struct MidBatchOf {
@@ -147,10 +149,12 @@ struct SliceArgs {
   const int32_t* scol;
   const double* sval;
   int n_sell, n_slices;
-  const int32_t* mid;
-  int n_mid;
-  const int32_t* big;
-  int n_big;
+  const int4* pc;        // pieces of the long rows: {row, k0, k1, slot}
+  int n_pc;
+  const int32_t* lr_row;  // rows of several pieces and their slots
+  const int32_t* lr_off;
+  int n_lr;
+  double* pc_sum;         // [slots] the pieces' sums
   const double* x;
 };
 
@@ -170,47 +174,15 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
   pdl_wait();
   constexpr int B = EllBatchOf<MODE>::value;
   __shared__ double red_scratch[kRedScratch];
-  __shared__ double row_scratch[kRedScratch];
   if (epi_skip(e)) return;
   double a0 = 0.0, a1 = 0.0;
-  // rows beyond kBlockRowLen entries: one block each
-  for (int v = blockIdx.x; v < a.n_big; v += gridDim.x) {
-    const int row = __ldg(a.big + v);
-    const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
-    double sm[1] = {0.0};
-    if (MODE == EPI_COPY || MODE == EPI_PLAIN) {  // within 32 registers
-      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
-        sm[0] = fma(__ldcs(a.val + k), __ldg(a.x + __ldcs(a.col + k)), sm[0]);
-    } else {
-      // a thread's entries k0 + tid + j * blockDim.x in order, 4 strides
-      // loaded together
-      for (int k = k0 + threadIdx.x; k < k1; k += 4 * blockDim.x) {
-        int cc[4];
-        double vv[4], xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool in = k + u * static_cast<int>(blockDim.x) < k1;
-          cc[u] = in ? __ldcs(a.col + k + u * blockDim.x) : -1;
-          vv[u] = in ? __ldcs(a.val + k + u * blockDim.x) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = cc[u] >= 0 ? __ldg(a.x + cc[u]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (cc[u] >= 0) sm[0] = fma(vv[u], xv[u], sm[0]);
-      }
-    }
-    block_sum<1, double>(sm, row_scratch);
-    if (threadIdx.x == 0) epi_row_t<MODE>(e, row, sm[0], a0, a1);
-    __syncthreads();
-  }
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  const int n_items = a.n_mid + a.n_slices;
+  const int n_items = a.n_pc + a.n_slices;
   for (int it = gw; it < n_items; it += nw) {
-    if (it < a.n_mid) {
-      const int row = __ldg(a.mid + it);
-      const int k0 = __ldg(a.rowptr + row), k1 = __ldg(a.rowptr + row + 1);
+    if (it < a.n_pc) {
+      const int4 pc = __ldg(a.pc + it);
+      const int k0 = pc.y, k1 = pc.z;
       constexpr int MB = MidBatchOf<MODE>::value;
       double s = 0.0;
       int k = k0 + lane;
@@ -244,9 +216,12 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) epi_row_t<MODE>(e, row, s, a0, a1);
+      if (lane == 0) {
+        if (pc.w < 0) epi_row_t<MODE>(e, pc.x, s, a0, a1);
+        else a.pc_sum[pc.w] = s;
+      }
     } else {
-      const int c = it - a.n_mid;
+      const int c = it - a.n_pc;
       const int base = c * 32 + lane;
       const int64_t o0 = __ldg(a.off + c);
       const int L = static_cast<int>((__ldg(a.off + c + 1) - o0) >> 5);
@@ -287,7 +262,43 @@ __global__ void __launch_bounds__(kSliceThreads, SliceMinBlocks<MODE>::value) sp
       if (base < a.n_sell) epi_row_t<MODE>(e, __ldg(a.perm + base), s, a0, a1);
     }
   }
-  if (MODE != EPI_COPY && MODE != EPI_PLAIN) epi_finish(e, a0, a1, red_scratch);
+  if (MODE != EPI_COPY && MODE != EPI_PLAIN) {
+    if (a.n_lr > 0) epi_partial(e, a0, a1, red_scratch);  // the fix-up launch finishes the sum
+    else epi_finish(e, a0, a1, red_scratch);
+  }
+}
+
+// Rows of several pieces (one warp each, all rows in parallel): the pieces'
+// sums added in order (lane-strided, then an xor butterfly: a fixed order),
+// then the epilogue; then the epilogue's reduction, the main launch's block
+// partials folded into this launch's fixed-order grid sum, whose block
+// partials live after the main launch's.
+template <int MODE>
+__global__ void __launch_bounds__(256) spmv_long_fixup_kernel(SliceArgs a, Epi e, int main_grid) {
+  __shared__ double red_scratch[kRedScratch];
+  pdl_wait();
+  if (epi_skip(e)) return;
+  double a0 = 0.0, a1 = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int w = gw; w < a.n_lr; w += nw) {
+    const int o0 = __ldg(a.lr_off + w), o1 = __ldg(a.lr_off + w + 1);
+    double s = 0.0;
+    for (int o = o0 + lane; o < o1; o += 32) s += __ldcg(a.pc_sum + o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) epi_row_t<MODE>(e, __ldg(a.lr_row + w), s, a0, a1);
+  }
+  if (MODE == EPI_COPY || MODE == EPI_PLAIN) return;
+  const int stride = gridDim.x * blockDim.x;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int b = gt; b < main_grid; b += stride) {
+    a0 += __ldcg(e.partials + 2 * b);
+    a1 += __ldcg(e.partials + 2 * b + 1);
+  }
+  double v[2] = {a0, a1}, out[2];
+  if (grid_sum<2>(v, e.partials + 2 * main_grid, e.counter, red_scratch, out) && threadIdx.x == 0 && e.st)
+    finalize(e.fin, out, e.st);
 }
 
 // ---------------------------------------------------------------------------
@@ -787,11 +798,11 @@ int merge_grid(int64_t n_tiles) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, (n_tiles + kMergeWarps - 1) / kMergeWarps)));
 }
 
-int sliced_grid(int64_t warp_items, int64_t big_rows, bool plain) {
+int sliced_grid(int64_t warp_items, bool plain) {
   const void* fn = plain ? reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_COPY>)
                          : reinterpret_cast<const void*>(spmv_sliced_kernel<EPI_RESID>);
   int g = occupancy_grid(fn, kSliceThreads, 0);
-  int64_t need = std::max<int64_t>((warp_items + kSliceThreads / 32 - 1) / (kSliceThreads / 32), big_rows);
+  int64_t need = (warp_items + kSliceThreads / 32 - 1) / (kSliceThreads / 32);
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, need)));
 }
 
@@ -832,16 +843,29 @@ int spmv_launch(const Matrix& A, const double* x, const Epi& e, cudaStream_t s) 
   switch (A.format) {
     case GK_CSR: {
       SliceArgs b{A.rowptr, A.col, A.val, A.sl_perm, A.sl_off, A.sl_col, A.sl_val, static_cast<int>(A.n_sell),
-                  static_cast<int>(A.n_slices), A.mid_rows, static_cast<int>(A.n_mid), A.big_rows,
-                  static_cast<int>(A.n_big), x};
+                  static_cast<int>(A.n_slices), A.pc, static_cast<int>(A.n_pc), A.lr_row, A.lr_off,
+                  static_cast<int>(A.n_lr), A.pc_sum, x};
+      const bool plain = e.mode == EPI_COPY || e.mode == EPI_PLAIN;
+      const int g = plain ? A.grid_sl_plain : A.grid_sl;
       switch (e.mode) {
-        case EPI_COPY: launch_pdl(spmv_sliced_kernel<EPI_COPY>, A.grid_sl_plain, kSliceThreads, 0, s, b, e); break;
-        case EPI_PLAIN: launch_pdl(spmv_sliced_kernel<EPI_PLAIN>, A.grid_sl_plain, kSliceThreads, 0, s, b, e); break;
-        case EPI_RESID: launch_pdl(spmv_sliced_kernel<EPI_RESID>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
-        case EPI_DOT: launch_pdl(spmv_sliced_kernel<EPI_DOT>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
-        default: launch_pdl(spmv_sliced_kernel<EPI_DOT2>, A.grid_sl, kSliceThreads, 0, s, b, e); break;
+        case EPI_COPY: launch_pdl(spmv_sliced_kernel<EPI_COPY>, g, kSliceThreads, 0, s, b, e); break;
+        case EPI_PLAIN: launch_pdl(spmv_sliced_kernel<EPI_PLAIN>, g, kSliceThreads, 0, s, b, e); break;
+        case EPI_RESID: launch_pdl(spmv_sliced_kernel<EPI_RESID>, g, kSliceThreads, 0, s, b, e); break;
+        case EPI_DOT: launch_pdl(spmv_sliced_kernel<EPI_DOT>, g, kSliceThreads, 0, s, b, e); break;
+        default: launch_pdl(spmv_sliced_kernel<EPI_DOT2>, g, kSliceThreads, 0, s, b, e); break;
       }
       GK_TRY_CUDA(cudaGetLastError());
+      if (A.n_lr > 0) {
+        const int fg = static_cast<int>(std::min<int64_t>(kFixupMaxGrid, (A.n_lr + 7) / 8));
+        switch (e.mode) {
+          case EPI_COPY: launch_pdl(spmv_long_fixup_kernel<EPI_COPY>, fg, 256, 0, s, b, e, g); break;
+          case EPI_PLAIN: launch_pdl(spmv_long_fixup_kernel<EPI_PLAIN>, fg, 256, 0, s, b, e, g); break;
+          case EPI_RESID: launch_pdl(spmv_long_fixup_kernel<EPI_RESID>, fg, 256, 0, s, b, e, g); break;
+          case EPI_DOT: launch_pdl(spmv_long_fixup_kernel<EPI_DOT>, fg, 256, 0, s, b, e, g); break;
+          default: launch_pdl(spmv_long_fixup_kernel<EPI_DOT2>, fg, 256, 0, s, b, e, g); break;
+        }
+        GK_TRY_CUDA(cudaGetLastError());
+      }
       return GK_OK;
     }
     case GK_CSR_MERGE:

@@ -133,6 +133,27 @@ def test_cg_powerlaw_matches_oracle(gk, orc):
         assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
 
 
+def test_powerlaw_csr_graph_form_matches_oracle(gk, orc):
+    """GK_CSR inside the large-system solve graph on a power-law matrix whose
+    longest rows are summed in pieces (the pieces' second launch finishes the
+    fused dot and residual reductions): Jacobi-CG and block-Jacobi (bs 4)
+    BiCGSTAB against the oracle, with 300,000 rows (past the one-launch forms)."""
+    A = W.powerlaw(300_000, seed=7)
+    n = A[0].size - 1
+    assert (np.diff(A[0]) > 512).sum() > 100
+    xs = W.uniform_vector(n, 8)
+    b = orc.spmv(A, xs)
+    for kind, bs in (("cg", 1), ("bicgstab", 4)):
+        st, x = _solve(gk, A, b, fmt="csr", prec=bs, kind=kind, max_iters=2000, reduction_factor=1e-10)
+        assert st.stop_reason == gk.STOP_CONVERGED, kind
+        assert np.linalg.norm(b - orc.spmv(A, x)) <= 1.5e-10 * np.linalg.norm(b), kind
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8, kind
+        P = orc.precond(A, "jacobi" if bs == 1 else "block_jacobi", bs)
+        ref = (orc.cg if kind == "cg" else orc.bicgstab)(A, b, P=P, tol=1e-10, max_iters=2000)
+        slack = max(2, ref.iters * 3 // 100) if kind == "cg" else max(3, ref.iters // 4)
+        assert abs(st.iters - ref.iters) <= slack, (kind, st.iters, ref.iters)
+
+
 def test_criteria_edge_cases(gk, orc):
     A = W.poisson2d(8)
     xs = W.uniform_vector(64, 5)

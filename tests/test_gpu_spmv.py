@@ -205,3 +205,30 @@ def test_apply_dot_fuses_the_dot(gk, orc, fmt):
     x = to_np(x2)
     ref = float(np.dot(u, x))
     assert abs(rv[0] - ref) <= 1e-13 * float(np.dot(np.abs(u), np.abs(x)))
+
+
+def test_apply_dot_long_row_pieces(gk, big_mats):
+    """GK_CSR on the power-law matrix with 10^6 rows: its rows of more than
+    512 entries are summed in pieces, added by a second launch that also
+    finishes the fused dot's reduction.  x = A b through the fused-dot apply
+    equals the plain apply bit for bit, the dot is within the rounding of a
+    length-n dot product of u . x, and both are identical from run to run."""
+    import torch
+    A = big_mats["powerlaw_1M"]
+    n = A[0].size - 1
+    lens = np.diff(A[0])
+    assert (lens > 512).sum() > 1000
+    b, u = W.uniform_vector(n, 31), W.uniform_vector(n, 32)
+    M = _gk_matrix(gk, A, "csr")
+    assert M.info()["long_rows"] == int((lens > 256).sum())
+    x1, x2 = to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    r = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    gk.apply(M, to_dev(b), x1)
+    gk.apply_dot(M, to_dev(b), x2, to_dev(u), r[0:1])
+    x = to_np(x2)
+    np.testing.assert_array_equal(to_np(x1), x)
+    gk.apply_dot(M, to_dev(b), x2, to_dev(u), r[1:2])
+    np.testing.assert_array_equal(to_np(x2), x)
+    rv = to_np(r)
+    assert rv[0] == rv[1]
+    assert abs(rv[0] - float(np.dot(u, x))) <= 1e-13 * float(np.dot(np.abs(u), np.abs(x)))

@@ -87,6 +87,14 @@ SPMV_REPS = 3
 #   HYB:                          nnz_ell (VT + IT) + nnz_coo (VT + 2 IT)
 # ---------------------------------------------------------------------------
 
+def infer_bytes_per_pixel(width=32, layers=6):
+    """Compulsory bytes per pixel of one warm-start inference: the two FP32
+    input features read once, each hidden BF16 activation (width channels,
+    layers - 1 of them) written once and read once, the FP32 output written
+    once (weights are a few KB and stay in cache)."""
+    return 2 * 4 + (layers - 1) * width * 2 * 2 + 4
+
+
 def matrix_bytes(nnz, n_rows, fmt="csr", tail_nnz=0, vt=8, it=4):
     if fmt in ("csr", "csr_merge"):
         return nnz * (vt + it) + (n_rows + 1) * it
@@ -249,6 +257,8 @@ def spmv_launches(info):
         return 2
     if f == "hyb":
         return 3 if info["tail_rows"] > 0 else 1
+    if f == "csr":
+        return 2 if info.get("split_rows", 0) > 0 else 1
     return 1
 
 
@@ -770,7 +780,15 @@ def run_learned(dev, problems=8):
         ms = e0.elapsed_time(e1) / reps
         inf[B] = (ms, 2.0 * B * macs / (ms * 1e-3) / 1e12)
     bf16_peak = peaks().get("bf16_tflops")
+    hbm = peaks().get("hbm_gbs")
     inf_ms, tfl = inf[1]
+    # compulsory activation bytes per pixel of one inference: the FP32
+    # features (2 channels) read once, each of the five 32-channel BF16
+    # activations written once and read once, the FP32 output written once
+    bpp = infer_bytes_per_pixel()
+    by64 = 64 * net.H * net.W * bpp
+    ai = 2.0 * macs / (net.H * net.W * bpp)
+    gbs64 = by64 / (inf[64][0] * 1e-3) / 1e9
     best = "warm" if summ["ms_warm"] < summ["ms_zero"] else "zero"
     return {
         "workload": LEARNED_WORKLOAD, "network": {"layers": 6, "width": 32, "dilations": list(net.dilations),
@@ -786,11 +804,20 @@ def run_learned(dev, problems=8):
                            "learned_vs_zero_start": round(summ["ms_zero"] / summ["ms_warm"], 4)},
         "inference": {"kernel": "conv_tc_kernel (tcgen05.mma BF16 x BF16 -> FP32 in tensor memory) for the four "
                                 "32->32 layers (98 % of the flops); first and last layer on the CUDA cores",
-                      "ms": round(inf_ms, 4), "tflops": round(tfl, 2), "bound": "tensor",
-                      "peak": bf16_peak, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
-                      "frac": round(tfl / bf16_peak, 5) if bf16_peak else None,
+                      "batch1": {"ms": round(inf_ms, 4), "tflops": round(tfl, 2),
+                                 "frac_of_bf16_peak": round(tfl / bf16_peak, 5) if bf16_peak else None,
+                                 "note": "42.7 MB of activations: L2-resident, latency-bound"},
                       "batch64": {"ms": round(inf[64][0], 4), "tflops": round(inf[64][1], 2),
-                                  "frac": round(inf[64][1] / bf16_peak, 5) if bf16_peak else None},
+                                  "frac_of_bf16_peak": round(inf[64][1] / bf16_peak, 5) if bf16_peak else None},
+                      "roofline": {"workload": "batch 64", "bound": "hbm",
+                                   "arithmetic_intensity_flop_per_byte": round(ai, 1),
+                                   "ridge_flop_per_byte": round(bf16_peak * 1e3 / hbm, 1) if bf16_peak and hbm
+                                   else None,
+                                   "bytes_per_pixel": bpp, "bytes": by64,
+                                   "achieved": round(gbs64, 1), "peak": hbm, "unit": "GB/s",
+                                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                                   "frac": round(gbs64 / hbm, 4) if hbm else None},
+                      "bf16_peak_tflops": bf16_peak,
                       "cuda_core_fp32_issue_peak_tflops": round(FP32_PEAK_TFLOPS, 1)},
     }
 

@@ -181,6 +181,8 @@ typedef struct {
                            /* operator (CSR: nnz*12 + (n_rows+1)*4; ELL:        */
                            /* nnz*12; HYB: ELL entries*12 + COO entries*16),    */
                            /* x read once (n_cols*8), y written (n_rows*8)      */
+  int64_t split_rows;      /* GK_CSR: rows of more than 512 entries, whose      */
+                           /* pieces a second kernel adds (2 launches / apply)  */
 } gk_matrix_info;
 
 /* ---- errors ------------------------------------------------------------- */

@@ -84,7 +84,7 @@ class MatrixInfo(ctypes.Structure):
                 ("format", ctypes.c_int32), ("dtype", ctypes.c_int32), ("ell_width", ctypes.c_int64),
                 ("tail_rows", ctypes.c_int64), ("tail_nnz", ctypes.c_int64),
                 ("short_items", ctypes.c_int64), ("long_rows", ctypes.c_int64), ("tiles", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("spmv_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("spmv_bytes", ctypes.c_int64), ("split_rows", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -428,6 +428,7 @@ extern "C" int gk_matrix_get_info(gk_matrix h, gk_matrix_info* info) {
   info->tail_nnz = A->tail_nnz;
   info->short_items = A->n_slices;
   info->long_rows = A->n_long;
+  info->split_rows = A->n_lr;
   info->tiles = A->merge.n_tiles;
   info->device_bytes = A->device_bytes;
   // the stored operator once (CSR: values, indices, row pointers; ELL: the

@@ -113,9 +113,21 @@ def test_spmv_bytes_per_format():
 def test_solve_launches_counts_idle_iterations():
     """CG launches init, the set-up SpMV and start, three kernels per
     iteration (the SpMV, update and direction; a GK_CSR matrix's SpMV is one
-    kernel) including the iterations launched after the stop (idle_iters),
-    and the final SpMV."""
+    kernel when no row has more than 512 entries, else two) including the
+    iterations launched after the stop (idle_iters), and the final SpMV."""
     assert bench.solve_launches("cg", 251, 253, 1) == 2 + 1 + 251 * 3 + 1
     assert bench.solve_launches("cg", 251, 253, 1, idle=1) == 2 + 1 + 252 * 3 + 1
     # HYB with an overflow: 3 kernels per SpMV
     assert bench.solve_launches("cg", 14, 16, 3, idle=2) == 2 + 3 + 16 * 5 + 3
+
+
+def test_inference_byte_model():
+    """The warm-start inference moves 652 bytes per pixel (2 FP32 features
+    in, five 32-channel BF16 activations out and back in, one FP32 output)
+    for 2 x 37,728 flops: about 116 flops per byte, below the ridge of a
+    GPU with ~1.9 PFLOP/s BF16 and ~6.7 TB/s, so HBM bounds it."""
+    bpp = bench.infer_bytes_per_pixel()
+    assert bpp == 2 * 4 + 5 * 32 * 2 * 2 + 4 == 652
+    macs = sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
+    assert macs == 37728
+    assert 2 * macs / bpp < 1.9e15 / 6.7e12

@@ -221,6 +221,7 @@ def test_apply_dot_long_row_pieces(gk, big_mats):
     b, u = W.uniform_vector(n, 31), W.uniform_vector(n, 32)
     M = _gk_matrix(gk, A, "csr")
     assert M.info()["long_rows"] == int((lens > 256).sum())
+    assert M.info()["split_rows"] == int((lens > 512).sum())
     x1, x2 = to_dev(np.zeros(n)), to_dev(np.zeros(n))
     r = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     gk.apply(M, to_dev(b), x1)

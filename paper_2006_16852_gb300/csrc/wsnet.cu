@@ -404,11 +404,22 @@ __global__ void scale_kernel(double* __restrict__ x0, const double* __restrict__
 
 constexpr int kTcThreads = 128;                 // 4 warps: one TMEM lane quarter each
 constexpr int kTcTile = 128;                    // pixels per tile (MMA M)
+constexpr int kTcStripMax = 16;                 // output rows per work item (a strip), at most
 constexpr int kTcWin = kTcTile + 2 * 64;        // staged window: dilation <= 64
 constexpr uint32_t kTcChunkA = kTcWin * 16;     // bytes between 8-channel chunks of a window
 constexpr uint32_t kTcChunkB = 32 * 16;         // bytes between 8-channel chunks of a tap's weights
 constexpr int kTcPacked = 9 * 4 * 32 * 8;       // packed BF16 weights of one 32 -> 32 layer
 constexpr int kTcMidLayers = kLayers - 2;
+
+// 16-byte asynchronous global -> shared copy through L1 (cp.async); the
+// bytes past src_bytes (0 or 16) are zero-filled, and with src_bytes 0
+// nothing is read from src.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+// Waits for all of this thread's cp.async copies.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 struct TcSmem {
   __nv_bfloat16 a[3 * 4 * kTcWin * 8];  // [ky][chunk][slot][8 channels]
@@ -476,8 +487,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16* __restrict__ x,
                                                              const __nv_bfloat16* __restrict__ wp,
                                                              const __nv_bfloat16* __restrict__ bias, int B, int H,
-                                                             int W, int dil, __nv_bfloat16* __restrict__ y,
-                                                             int* err) {
+                                                             int W, int dil, int strip,
+                                                             __nv_bfloat16* __restrict__ y, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -499,68 +510,107 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
   const uint32_t tmem = S.tmem;
   const uint32_t a_base = smem_u32(S.a), b_base = smem_u32(S.b);
   const int tiles_x = (W + kTcTile - 1) / kTcTile;
-  const int n_tiles = B * H * tiles_x;
   const int nslot = kTcTile + 2 * dil;
+  // Work items are strips: the output rows y0, y0 + dil, ..., of one image
+  // and one 128-pixel column range (at most `strip` of them).  Output row
+  // y_k reads input rows y_k - dil, y_k and y_k + dil, so consecutive rows of
+  // a strip share two of their three input rows: a ring of three staged rows
+  // holds them, and each tile after a strip's first stages one new row,
+  // while the tile before it is read back.
+  const int per_class = (H + dil - 1) / dil;             // rows of the fullest residue class
+  const int chunks = (per_class + strip - 1) / strip;
+  const int n_strips = B * tiles_x * dil * chunks;
   uint32_t phase = 0;
   bool pending = false;  // an MMA group whose completion was not observed
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int row = tile / tiles_x;  // b * H + yy
-    const int x0 = (tile - row * tiles_x) * kTcTile;
-    const int yy = row % H;
-    const int64_t img = static_cast<int64_t>(row - yy) * W;  // first pixel of this sample
-    // stage the three input rows (one pixel's 4 chunks per thread and step)
-    for (int idx = t; idx < 3 * nslot; idx += kTcThreads) {
-      const int ky = idx / nslot, s = idx - ky * nslot;
-      const int ys = yy + dil * (ky - 1), xs = x0 - dil + s;
-      uint4 v[4] = {};
-      if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
-        const uint4* src = reinterpret_cast<const uint4*>(x + (img + static_cast<int64_t>(ys) * W + xs) * 32);
+  // Stages input row ys of image img (zeros outside the image) for the
+  // column range starting at x0 into ring slot q, with asynchronous 16-byte
+  // copies: nothing passes through registers, so all of a row's copies are
+  // in flight at once.
+  auto stage = [&](int64_t img, int ys, int x0, int q) {
+    for (int sl = t; sl < nslot; sl += kTcThreads) {
+      const int xs = x0 - dil + sl;
+      const bool in = ys >= 0 && ys < H && xs >= 0 && xs < W;
+      const uint4* src = in ? reinterpret_cast<const uint4*>(x + (img + static_cast<int64_t>(ys) * W + xs) * 32)
+                            : reinterpret_cast<const uint4*>(x);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = __ldg(src + c);
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(S.a)[(ky * 4 + c) * kTcWin + s] = v[c];
+      for (int c = 0; c < 4; ++c)
+        cp_async16(reinterpret_cast<uint4*>(S.a) + (q * 4 + c) * kTcWin + sl, src + c, in ? 16u : 0u);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
-    tc_fence_before();
-    __syncthreads();
-    if (t == 0) {
+  };
+  bool failed = false;
+  for (int item = blockIdx.x; item < n_strips && !failed; item += gridDim.x) {
+    int rest = item;
+    const int ch = rest % chunks;
+    rest /= chunks;
+    const int cls = rest % dil;
+    rest /= dil;
+    const int xt = rest % tiles_x;
+    const int b = rest / tiles_x;
+    const int x0 = xt * kTcTile;
+    const int64_t img = static_cast<int64_t>(b) * H * W;  // first pixel of this sample
+    const int y0 = cls + ch * strip * dil;                 // first output row of the strip
+    if (y0 >= H) continue;
+    const int nrow = min(strip, (H - 1 - y0) / dil + 1);
+    // input row m of the strip (m = -1 .. nrow) is y0 + m * dil, in slot (m + 1) % 3
+    stage(img, y0 - dil, x0, 0);
+    stage(img, y0, x0, 1);
+    stage(img, y0 + dil, x0, 2);
+    for (int k = 0; k < nrow; ++k) {
+      const int yy = y0 + k * dil;
+      cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged rows -> tensor core reads
+      tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const int q = (k + ky) % 3;  // slot of input row k - 1 + ky
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t aa = a_base + ((q * 4 + 2 * h) * kTcWin + kx * dil) * 16;
+              const uint32_t bb = b_base + ((ky * 3 + kx) * 4 + 2 * h) * kTcChunkB;
+              tc_mma(tmem, tc_desc(aa, kTcChunkA, 128), tc_desc(bb, kTcChunkB, 128), acc);
+              acc = 1;
+            }
+        }
+        tc_commit(&S.bar);
+      }
+      pending = true;
+      const bool ok = __syncthreads_and(mbar_wait(&S.bar, phase, err));
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      pending = false;
+      phase ^= 1u;
+      // the MMAs have read the ring: input row k + 2 goes into the slot of
+      // row k - 1 while this tile's accumulator is read back and stored
+      if (k + 1 < nrow) stage(img, yy + 2 * dil, x0, k % 3);
       tc_fence_after();
-      uint32_t acc = 0;
+      float v[32];
+      tc_load32(tmem + (static_cast<uint32_t>(warp * 32) << 16), v);
+      const int px = x0 + warp * 32 + lane;
+      if (px < W) {
+        uint4* dst = reinterpret_cast<uint4*>(y + (img + static_cast<int64_t>(yy) * W + px) * 32);
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
+        for (int c = 0; c < 4; ++c) {
+          float o[8];
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t aa = a_base + ((ky * 4 + 2 * h) * kTcWin + kx * dil) * 16;
-            const uint32_t bb = b_base + ((ky * 3 + kx) * 4 + 2 * h) * kTcChunkB;
-            tc_mma(tmem, tc_desc(aa, kTcChunkA, 128), tc_desc(bb, kTcChunkB, 128), acc);
-            acc = 1;
-          }
-      tc_commit(&S.bar);
-    }
-    pending = true;
-    const bool ok = __syncthreads_and(mbar_wait(&S.bar, phase, err));
-    if (!ok) break;
-    pending = false;
-    phase ^= 1u;
-    tc_fence_after();
-    float v[32];
-    tc_load32(tmem + (static_cast<uint32_t>(warp * 32) << 16), v);
-    const int px = x0 + warp * 32 + lane;
-    if (px < W) {
-      uint4* dst = reinterpret_cast<uint4*>(y + (img + static_cast<int64_t>(yy) * W + px) * 32);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float o[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) o[e] = fmaxf(v[c * 8 + e] + S.bias[c * 8 + e], 0.0f);
-        dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
-                            pack_bf16x2(o[6], o[7]));
+          for (int e = 0; e < 8; ++e) o[e] = fmaxf(v[c * 8 + e] + S.bias[c * 8 + e], 0.0f);
+          dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                              pack_bf16x2(o[6], o[7]));
+        }
       }
     }
+    // the next strip's first rows overwrite every slot: all reads of this
+    // strip's last tile are done (its MMAs completed above), and the
+    // barrier at the next tile's start orders the copies after them
   }
+  cp_async_wait_all();  // no copy of this block is left in flight at exit
   // an MMA whose completion was not seen is waited for once more (bounded)
   // before its accumulator's tensor memory is released
   if (pending) mbar_wait(&S.bar, phase, err);
@@ -856,8 +906,14 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
   const __nv_bfloat16* in = N.hbf[1];
   for (int l = 1; l < kLayers - 1; ++l) {
     __nv_bfloat16* out = N.hbf[1 + (l & 1)];
+    // strips as long as the work still gives every resident CTA about four
+    // of them (a batch of one image runs single rows, each staging its
+    // three input rows; large batches reuse rows along strips of 16)
+    const int64_t row_tiles = tiles;  // (image, row, 128-pixel range) triples
+    const int strip = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>(kTcStripMax, row_tiles / (4 * static_cast<int64_t>(grid)))));
     conv_tc_kernel<<<grid, kTcThreads, sizeof(TcSmem), s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B,
-                                                             N.H, N.W, N.dil[l], out, N.err);
+                                                             N.H, N.W, N.dil[l], strip, out, N.err);
     GK_TRY_CUDA(cudaGetLastError());
     in = out;
   }

@@ -405,8 +405,7 @@ __global__ void scale_kernel(double* __restrict__ x0, const double* __restrict__
 constexpr int kTcThreads = 128;                 // 4 warps: one TMEM lane quarter each
 constexpr int kTcTile = 128;                    // pixels per tile (MMA M)
 constexpr int kTcStripMax = 16;                 // output rows per work item (a strip), at most
-constexpr int kTcWin = kTcTile + 2 * 64;        // staged window: dilation <= 64
-constexpr uint32_t kTcChunkA = kTcWin * 16;     // bytes between 8-channel chunks of a window
+constexpr int kTcMaxDil = 64;                   // largest dilation (gk_wsnet_create checks it)
 constexpr uint32_t kTcChunkB = 32 * 16;         // bytes between 8-channel chunks of a tap's weights
 constexpr int kTcPacked = 9 * 4 * 32 * 8;       // packed BF16 weights of one 32 -> 32 layer
 constexpr int kTcMidLayers = kLayers - 2;
@@ -421,13 +420,18 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t 
 // Waits for all of this thread's cp.async copies.
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Shared memory of a block: this header, then the ring of three staged
+// input rows, [row slot][chunk][pixel slot][8 channels], win = 128 + 2 dil
+// pixel slots per chunk: sized per layer, so that layers of small dilation
+// fit more blocks per SM.
 struct TcSmem {
-  __nv_bfloat16 a[3 * 4 * kTcWin * 8];  // [ky][chunk][slot][8 channels]
   __nv_bfloat16 b[kTcPacked];           // [tap][chunk][out][8 channels]
   float bias[32];
   uint64_t bar;
   uint32_t tmem;
 };
+constexpr size_t kTcAOffset = (sizeof(TcSmem) + 127) / 128 * 128;
+constexpr size_t tc_smem_bytes(int dil) { return kTcAOffset + 3 * 4 * static_cast<size_t>(kTcTile + 2 * dil) * 16; }
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
 // 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
@@ -508,9 +512,11 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem;
-  const uint32_t a_base = smem_u32(S.a), b_base = smem_u32(S.b);
+  const int nslot = kTcTile + 2 * dil;              // pixel slots of a staged row
+  const uint32_t chunk_a = static_cast<uint32_t>(nslot) * 16;  // bytes between its 8-channel chunks
+  uint4* const ring = reinterpret_cast<uint4*>(tc_raw + kTcAOffset);
+  const uint32_t a_base = smem_u32(ring), b_base = smem_u32(S.b);
   const int tiles_x = (W + kTcTile - 1) / kTcTile;
-  const int nslot = kTcTile + 2 * dil;
   // Work items are strips: the output rows y0, y0 + dil, ..., of one image
   // and one 128-pixel column range (at most `strip` of them).  Output row
   // y_k reads input rows y_k - dil, y_k and y_k + dil, so consecutive rows of
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
                             : reinterpret_cast<const uint4*>(x);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        cp_async16(reinterpret_cast<uint4*>(S.a) + (q * 4 + c) * kTcWin + sl, src + c, in ? 16u : 0u);
+        cp_async16(ring + (q * 4 + c) * nslot + sl, src + c, in ? 16u : 0u);
     }
   };
   bool failed = false;
@@ -571,9 +577,9 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
           for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const uint32_t aa = a_base + ((q * 4 + 2 * h) * kTcWin + kx * dil) * 16;
+              const uint32_t aa = a_base + ((q * 4 + 2 * h) * nslot + kx * dil) * 16;
               const uint32_t bb = b_base + ((ky * 3 + kx) * 4 + 2 * h) * kTcChunkB;
-              tc_mma(tmem, tc_desc(aa, kTcChunkA, 128), tc_desc(bb, kTcChunkB, 128), acc);
+              tc_mma(tmem, tc_desc(aa, chunk_a, 128), tc_desc(bb, kTcChunkB, 128), acc);
               acc = 1;
             }
         }
@@ -688,8 +694,74 @@ __global__ void __launch_bounds__(256) conv_first_nhwc_kernel(const __nv_bfloat1
   }
 }
 
-// The last layer (32 -> 1, linear): x NHWC BF16, y FP32 (B, 1, H, W).
-__global__ void __launch_bounds__(256) conv_last_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
+// The last layer (32 -> 1, linear): x NHWC BF16, y FP32 (B, 1, H, W).  A
+// block computes a tile of kLastTY x kLastTX outputs.  Since the output
+// channel is one, y(p) = b + sum over taps of t_tap(p + offset_tap) with
+// t_tap(q) = sum over channels of w[tap][c] h(q)[c]: each pixel of the tile
+// and its halo is read once (64 bytes) and turned into its nine t values in
+// shared memory, and each output then adds nine of them -- instead of every
+// output reading its nine neighbours' 64 bytes.
+constexpr int kLastTX = 32, kLastTY = 8;
+constexpr int kLastTileDil = 8;  // largest dilation of the tiled form (42.6 KB of shared memory)
+
+__global__ void __launch_bounds__(kLastTX * kLastTY) conv_last_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                                          const __nv_bfloat16* __restrict__ w,
+                                                                          const __nv_bfloat16* __restrict__ bias,
+                                                                          int H, int W, int dil,
+                                                                          float* __restrict__ y) {
+  extern __shared__ float last_sm[];
+  float* ws = last_sm;          // [tap][c] weights
+  float* ts = last_sm + 9 * 32;  // [tap][halo pixel] t values
+  const int hx = kLastTX + 2 * dil, hy = kLastTY + 2 * dil, nh = hx * hy;
+  const int tid = threadIdx.y * kLastTX + threadIdx.x;
+  for (int idx = tid; idx < 9 * 32; idx += kLastTX * kLastTY) {
+    const int tap = idx >> 5, c = idx & 31;
+    ws[idx] = __bfloat162float(w[c * 9 + tap]);
+  }
+  __syncthreads();
+  const int b = blockIdx.z;
+  const int x0 = blockIdx.x * kLastTX - dil, y0 = blockIdx.y * kLastTY - dil;  // halo origin
+  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * H * W * 32;
+  for (int hq = tid; hq < nh; hq += kLastTX * kLastTY) {
+    const int ii = y0 + hq / hx, jj = x0 + hq % hx;
+    float t[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) t[tap] = 0.0f;
+    if (ii >= 0 && ii < H && jj >= 0 && jj < W) {
+      const uint4* src = reinterpret_cast<const uint4*>(xb + (static_cast<int64_t>(ii) * W + jj) * 32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 q = __ldg(src + c);
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float lo = __uint_as_float(u[e] << 16), hi = __uint_as_float(u[e] & 0xFFFF0000u);
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            t[tap] = fmaf(ws[tap * 32 + c * 8 + 2 * e], lo, t[tap]);
+            t[tap] = fmaf(ws[tap * 32 + c * 8 + 2 * e + 1], hi, t[tap]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) ts[tap * nh + hq] = t[tap];
+  }
+  __syncthreads();
+  const int i = blockIdx.y * kLastTY + threadIdx.y, j = blockIdx.x * kLastTX + threadIdx.x;
+  if (i >= H || j >= W) return;
+  float acc = __bfloat162float(bias[0]);
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx)
+      acc += ts[(ky * 3 + kx) * nh + (threadIdx.y + ky * dil) * hx + threadIdx.x + kx * dil];
+  y[static_cast<int64_t>(b) * H * W + static_cast<int64_t>(i) * W + j] = acc;
+}
+
+// The last layer for dilations whose tile halo would not fit shared memory
+// (above kLastTileDil): one thread per output, reading its nine neighbours.
+__global__ void __launch_bounds__(256) conv_last_direct_kernel(const __nv_bfloat16* __restrict__ x,
                                                              const __nv_bfloat16* __restrict__ w,
                                                              const __nv_bfloat16* __restrict__ bias, int H, int W,
                                                              int dil, float* __restrict__ y) {
@@ -728,6 +800,11 @@ __global__ void __launch_bounds__(256) conv_last_nhwc_kernel(const __nv_bfloat16
   y[static_cast<int64_t>(b) * HW + p] = acc + __bfloat162float(bias[0]);
 }
 
+// Dynamic shared memory of conv_last_nhwc_kernel for a dilation.
+inline size_t last_smem_bytes(int dil) {
+  return sizeof(float) * (9 * 32 + 9 * static_cast<size_t>(kLastTX + 2 * dil) * (kLastTY + 2 * dil));
+}
+
 int ew_grid(int64_t n) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sm_count())));
 }
@@ -752,7 +829,7 @@ struct WsNet {
   __nv_bfloat16* hbf[3] = {};    // inference: input copy (NCHW) + ping-pong activations (NHWC)
   __nv_bfloat16* wtc = nullptr;  // the 32 -> 32 layers' weights in the tensor-core layout
   int* err = nullptr;            // device-side wait that gave up (kErrTimeout)
-  int tc_grid = 0;               // resident tensor-core conv blocks (all SMs)
+  int tc_smem_sm = 0, tc_reserved = 0;  // shared memory per SM and reserved per block
   float* partials = nullptr;
   int64_t partial_floats = 0;
   float* chunk = nullptr;  // kReduceChunks x the largest stride
@@ -902,23 +979,42 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
                                             N.hbf[1]);
   GK_TRY_CUDA(cudaGetLastError());
   const int64_t tiles = static_cast<int64_t>(B) * N.H * ((N.W + kTcTile - 1) / kTcTile);
-  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, N.tc_grid)));
   const __nv_bfloat16* in = N.hbf[1];
   for (int l = 1; l < kLayers - 1; ++l) {
     __nv_bfloat16* out = N.hbf[1 + (l & 1)];
+    // resident blocks per SM: shared memory is the limit (registers, warps
+    // and the 512 tensor-memory columns allow 16 blocks of 32 columns), and
+    // it depends on the dilation through the staged rows' width
+    const size_t smem = tc_smem_bytes(N.dil[l]);
+    int per_sm = std::max(1, std::min(16, static_cast<int>(static_cast<size_t>(N.tc_smem_sm) / (smem + N.tc_reserved))));
+    // small batches keep three blocks per SM (the count the widest rows
+    // allow): more blocks would shorten every block's strips, and each strip
+    // stages two rows more than it computes
+    if (tiles < 16 * 3 * static_cast<int64_t>(sm_count())) per_sm = std::min(per_sm, 3);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, int64_t(per_sm) * sm_count())));
     // strips as long as the work still gives every resident CTA about four
     // of them (a batch of one image runs single rows, each staging its
-    // three input rows; large batches reuse rows along strips of 16)
-    const int64_t row_tiles = tiles;  // (image, row, 128-pixel range) triples
-    const int strip = static_cast<int>(std::max<int64_t>(
-        1, std::min<int64_t>(kTcStripMax, row_tiles / (4 * static_cast<int64_t>(grid)))));
-    conv_tc_kernel<<<grid, kTcThreads, sizeof(TcSmem), s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B,
-                                                             N.H, N.W, N.dil[l], strip, out, N.err);
+    // three input rows; large batches reuse rows along strips of up to 16),
+    // then evened out over the rows of a residue class
+    const int target = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>(kTcStripMax, tiles / (4 * static_cast<int64_t>(grid)))));
+    const int per_class = (N.H + N.dil[l] - 1) / N.dil[l];
+    const int n_chunks = (per_class + target - 1) / target;
+    const int strip = (per_class + n_chunks - 1) / n_chunks;
+    conv_tc_kernel<<<grid, kTcThreads, smem, s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B, N.H,
+                                                  N.W, N.dil[l], strip, out, N.err);
     GK_TRY_CUDA(cudaGetLastError());
     in = out;
   }
-  conv_last_nhwc_kernel<<<pg, 256, 0, s>>>(in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H,
-                                           N.W, N.dil[kLayers - 1], y);
+  const int dl = N.dil[kLayers - 1];
+  if (dl <= kLastTileDil) {
+    const dim3 lg((N.W + kLastTX - 1) / kLastTX, (N.H + kLastTY - 1) / kLastTY, B);
+    conv_last_nhwc_kernel<<<lg, dim3(kLastTX, kLastTY), last_smem_bytes(dl), s>>>(
+        in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H, N.W, dl, y);
+  } else {
+    conv_last_direct_kernel<<<pg, 256, 0, s>>>(in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H,
+                                               N.W, dl, y);
+  }
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
@@ -942,7 +1038,7 @@ extern "C" int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const in
   int64_t off = 0;
   for (int l = 0; l < kLayers; ++l) {
     N->dil[l] = dilations[l];
-    if (dilations[l] < 1 || dilations[l] > 64)
+    if (dilations[l] < 1 || dilations[l] > kTcMaxDil)
       return set_error(GK_ERR_ARG, "gk_wsnet_create: dilation %d outside 1..64", dilations[l]);
     N->off_w[l] = off;
     off += static_cast<int64_t>(kCh[l]) * kCh[l + 1] * 9;
@@ -971,17 +1067,12 @@ extern "C" int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const in
   GK_TRY(dalloc_n(&N->wtc, static_cast<size_t>(kTcMidLayers) * kTcPacked, by));
   GK_TRY(dalloc_n(&N->err, 1, by));
   GK_TRY_CUDA(cudaMemset(N->err, 0, sizeof(int)));
-  GK_TRY(set_smem(conv_tc_kernel, sizeof(TcSmem)));
-  {
-    // resident blocks per SM: shared memory is the limit (registers, warps
-    // and the 512 tensor-memory columns allow 16 blocks of 32 columns); the
-    // occupancy query has been seen to report 1 for this kernel where 3 fit
-    int smem_sm = 0, reserved = 0;
-    GK_TRY_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, N->device));
-    GK_TRY_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, N->device));
-    const int per_sm = static_cast<int>(smem_sm / (sizeof(TcSmem) + static_cast<size_t>(reserved)));
-    N->tc_grid = std::max(1, std::min(per_sm, 16)) * sm_count();
-  }
+  GK_TRY(set_smem(conv_tc_kernel, tc_smem_bytes(kTcMaxDil)));
+  GK_TRY(set_smem(conv_last_nhwc_kernel, last_smem_bytes(kLastTileDil)));
+  // the grid of each layer is sized from its shared-memory footprint (the
+  // occupancy query has been seen to report 1 for this kernel where 3 fit)
+  GK_TRY_CUDA(cudaDeviceGetAttribute(&N->tc_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, N->device));
+  GK_TRY_CUDA(cudaDeviceGetAttribute(&N->tc_reserved, cudaDevAttrReservedSharedMemoryPerBlock, N->device));
   // weight-gradient slots: the largest layer's count
   int64_t pf = 0;
   const int64_t blocks = static_cast<int64_t>((H + kWgradRows - 1) / kWgradRows) * batch_max;

@@ -802,8 +802,9 @@ def run_learned(dev, problems=8):
                            "chosen_form": "jacobi_cg_" + ("learned" if best == "warm" else "zero") + "_start",
                            "speedup_vs_plain": round(plain_ms / min(summ["ms_warm"], summ["ms_zero"]), 3),
                            "learned_vs_zero_start": round(summ["ms_zero"] / summ["ms_warm"], 4)},
-        "inference": {"kernel": "conv_tc_kernel (tcgen05.mma BF16 x BF16 -> FP32 in tensor memory) for the four "
-                                "32->32 layers (98 % of the flops); first and last layer on the CUDA cores",
+        "inference": {"kernel": "conv_first_tc_kernel and conv_tc_kernel (tcgen05.mma BF16 x BF16 -> FP32 in "
+                                "tensor memory) for the first five layers (the first with K = 18 padded to 32); "
+                                "the last (32 -> 1) on the CUDA cores",
                       "batch1": {"ms": round(inf_ms, 4), "tflops": round(tfl, 2),
                                  "frac_of_bf16_peak": round(tfl / bf16_peak, 5) if bf16_peak else None,
                                  "note": "42.7 MB of activations: L2-resident, latency-bound"},

@@ -398,8 +398,9 @@ __global__ void scale_kernel(double* __restrict__ x0, const double* __restrict__
 // start address shifted by kx d rows.  Operands are K-major without
 // swizzling: a core matrix is 8 rows x 16 bytes (8 channels); rows of a
 // matrix are 16 bytes apart and its 8-channel chunks LBO bytes apart.  The
-// first layer (2 input channels) and the last (1 output channel) have no
-// GEMM worth the name and run on the CUDA cores, reading and writing NHWC.
+// first layer (2 input channels, K = 18 padded to 32) runs on the tensor
+// cores too (conv_first_tc_kernel); the last (1 output channel) has no GEMM
+// worth the name and runs on the CUDA cores, reading NHWC.
 // ---------------------------------------------------------------------------
 
 constexpr int kTcThreads = 128;                 // 4 warps: one TMEM lane quarter each
@@ -628,6 +629,124 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
   }
 }
 
+// The first layer (2 -> 32, ReLU) on the tensor cores: an implicit GEMM
+// with K = 2 channels x 9 taps = 18, padded with zeros to 32 (two MMAs of
+// K = 16).  A tile is 128 pixels of one image row (M = 128): each thread
+// gathers its pixel's 18 input values (BF16 NCHW; zeros outside the image)
+// into the A tile, K-major without swizzle like conv_tc_kernel's operands
+// (8-value chunks 128 x 16 bytes apart); the block packs the 32 x 18
+// weights the same way once ([chunk][out][8], zero-padded); the epilogue is
+// conv_tc_kernel's (bias, ReLU, BF16 NHWC).  (A CUDA-core form, one thread
+// per pixel, was bound by its 576 FP32 fused multiply-adds per pixel.)
+constexpr int kTcFirstChunkA = kTcTile * 16;  // bytes between the A tile's 8-value chunks
+
+struct TcFirstSmem {
+  __nv_bfloat16 a[4 * kTcTile * 8];  // [chunk][pixel][8 values of k]
+  __nv_bfloat16 b[4 * 32 * 8];       // [chunk][out][8 values of k]
+  float bias[32];
+  uint64_t bar;
+  uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(kTcThreads) conv_first_tc_kernel(const __nv_bfloat16* __restrict__ x,
+                                                                   const __nv_bfloat16* __restrict__ w,
+                                                                   const __nv_bfloat16* __restrict__ bias, int B,
+                                                                   int H, int W, int dil,
+                                                                   __nv_bfloat16* __restrict__ y, int* err) {
+  __shared__ __align__(1024) TcFirstSmem S;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  // weights [chunk j][out n][e] = w[n][8 j + e] (k = channel * 9 + tap), zero past k = 17
+  for (int i = t; i < 4 * 32 * 8; i += kTcThreads) {
+    const int e = i & 7, n = (i >> 3) & 31, j = i >> 8;
+    const int k = 8 * j + e;
+    S.b[i] = k < 18 ? w[n * 18 + k] : __float2bfloat16_rn(0.0f);
+  }
+  if (t < 32) S.bias[t] = __bfloat162float(bias[t]);
+  if (t == 0) {
+    mbar_init(&S.bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&S.tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t a_base = smem_u32(S.a), b_base = smem_u32(S.b);
+  const int tiles_x = (W + kTcTile - 1) / kTcTile;
+  const int n_tiles = B * H * tiles_x;
+  const int64_t HW = static_cast<int64_t>(H) * W;
+  uint32_t phase = 0;
+  bool pending = false;  // an MMA group whose completion was not observed
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int row = tile / tiles_x;  // b * H + yy
+    const int x0 = (tile - row * tiles_x) * kTcTile;
+    const int yy = row % H;
+    const int b = row / H;
+    const int px = x0 + t;  // this thread's pixel
+    const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * 2 * HW;
+    __align__(16) __nv_bfloat16 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __float2bfloat16_rn(0.0f);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const int ii = yy + dil * (ky - 1), jj = px + dil * (kx - 1);
+          if (px < W && ii >= 0 && ii < H && jj >= 0 && jj < W)
+            v[c * 9 + ky * 3 + kx] = xb[c * HW + static_cast<int64_t>(ii) * W + jj];
+        }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      reinterpret_cast<uint4*>(S.a)[j * kTcTile + t] = *reinterpret_cast<const uint4*>(v + 8 * j);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        tc_mma(tmem, tc_desc(a_base + 2 * h * kTcFirstChunkA, kTcFirstChunkA, 128),
+               tc_desc(b_base + 2 * h * kTcChunkB, kTcChunkB, 128), h);
+      tc_commit(&S.bar);
+    }
+    pending = true;
+    const bool ok = __syncthreads_and(mbar_wait(&S.bar, phase, err));
+    if (!ok) break;
+    pending = false;
+    phase ^= 1u;
+    tc_fence_after();
+    float acc[32];
+    tc_load32(tmem + (static_cast<uint32_t>(warp * 32) << 16), acc);
+    const int po = x0 + warp * 32 + lane;  // TMEM lane = pixel
+    if (po < W) {
+      uint4* dst = reinterpret_cast<uint4*>(y + (static_cast<int64_t>(b) * HW + static_cast<int64_t>(yy) * W + po) * 32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = fmaxf(acc[c * 8 + e] + S.bias[c * 8 + e], 0.0f);
+        dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                            pack_bf16x2(o[6], o[7]));
+      }
+    }
+  }
+  // an MMA whose completion was not seen is waited for once more (bounded)
+  // before its accumulator's tensor memory is released
+  if (pending) mbar_wait(&S.bar, phase, err);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+  }
+}
+
 // Packs the 32 -> 32 layers' FP32 weights (out, in, 3, 3) into the MMA's B
 // layout [tap][chunk][out][8 channels], rounded to BF16.
 __global__ void pack_tc_kernel(const float* __restrict__ p, int64_t off0, int64_t stride,
@@ -638,60 +757,6 @@ __global__ void pack_tc_kernel(const float* __restrict__ p, int64_t off0, int64_
   const int e = r & 7, o = (r >> 3) & 31, kc = (r >> 8) & 3, tap = r >> 10;
   const int c = kc * 8 + e;
   out[i] = __float2bfloat16_rn(p[off0 + l * stride + (o * 32 + c) * 9 + tap]);
-}
-
-// The first layer (2 -> 32, ReLU): x NCHW BF16 (B, 2, H, W), y NHWC BF16.
-// Weights and bias are the BF16 parameter copy.
-__global__ void __launch_bounds__(256) conv_first_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
-                                                              const __nv_bfloat16* __restrict__ w,
-                                                              const __nv_bfloat16* __restrict__ bias, int H, int W,
-                                                              int dil, __nv_bfloat16* __restrict__ y) {
-  __shared__ __align__(16) float ws[18 * 32];
-  __shared__ float bs[32];
-  for (int idx = threadIdx.x; idx < 18 * 32; idx += blockDim.x) {
-    const int ct = idx >> 5, o = idx & 31;
-    ws[idx] = __bfloat162float(w[o * 18 + ct]);
-  }
-  if (threadIdx.x < 32) bs[threadIdx.x] = __bfloat162float(bias[threadIdx.x]);
-  __syncthreads();
-  const int HW = H * W;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= HW) return;
-  const int b = blockIdx.y;
-  const int i = p / W, j = p - i * W;
-  float acc[32];
-#pragma unroll
-  for (int o = 0; o < 32; ++o) acc[o] = 0.0f;
-  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * 2 * HW;
-#pragma unroll
-  for (int c = 0; c < 2; ++c)
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const int ii = i + dil * (ky - 1), jj = j + dil * (kx - 1);
-        const float v =
-            (ii >= 0 && ii < H && jj >= 0 && jj < W) ? __bfloat162float(xb[static_cast<int64_t>(c) * HW + ii * W + jj])
-                                                     : 0.0f;
-        const float4* wr = reinterpret_cast<const float4*>(ws + (c * 9 + ky * 3 + kx) * 32);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 wv = wr[q];
-          acc[4 * q] = fmaf(wv.x, v, acc[4 * q]);
-          acc[4 * q + 1] = fmaf(wv.y, v, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(wv.z, v, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(wv.w, v, acc[4 * q + 3]);
-        }
-      }
-  uint4* dst = reinterpret_cast<uint4*>(y + (static_cast<int64_t>(b) * HW + p) * 32);
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float o[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) o[e] = fmaxf(acc[c * 8 + e] + bs[c * 8 + e], 0.0f);
-    dst[c] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
-                        pack_bf16x2(o[6], o[7]));
-  }
 }
 
 // The last layer (32 -> 1, linear): x NHWC BF16, y FP32 (B, 1, H, W).  A
@@ -975,10 +1040,11 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
   to_bf16_kernel<<<ew_grid(nin), 256, 0, s>>>(x, N.hbf[0], nin);
   GK_TRY_CUDA(cudaGetLastError());
   const dim3 pg((N.H * N.W + 255) / 256, B);
-  conv_first_nhwc_kernel<<<pg, 256, 0, s>>>(N.hbf[0], N.pbf + N.off_w[0], N.pbf + N.off_b[0], N.H, N.W, N.dil[0],
-                                            N.hbf[1]);
-  GK_TRY_CUDA(cudaGetLastError());
   const int64_t tiles = static_cast<int64_t>(B) * N.H * ((N.W + kTcTile - 1) / kTcTile);
+  conv_first_tc_kernel<<<static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tiles, 8 * sm_count()))),
+                         kTcThreads, 0, s>>>(N.hbf[0], N.pbf + N.off_w[0], N.pbf + N.off_b[0], B, N.H, N.W,
+                                             N.dil[0], N.hbf[1], N.err);
+  GK_TRY_CUDA(cudaGetLastError());
   const __nv_bfloat16* in = N.hbf[1];
   for (int l = 1; l < kLayers - 1; ++l) {
     __nv_bfloat16* out = N.hbf[1 + (l & 1)];

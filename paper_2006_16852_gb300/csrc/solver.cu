@@ -176,12 +176,17 @@ __device__ __forceinline__ void cg_update_body(const VecArgs& a, double* scratch
         rr = fma(r0, r0, rr);
         rr = fma(r1, r1, rr);
         if (PK == PREC_SCALAR) {
+          // z = D^{-1} r is kept for the direction step, which then reads
+          // z and p instead of r, D^{-1} and p (the same bytes, one FP64
+          // multiply per row fewer)
           const double2 d = ld2(a.dinv + i);
-          rz = fma(r0, d.x * r0, rz);
-          rz = fma(r1, d.y * r1, rz);
+          const double z0 = d.x * r0, z1 = d.y * r1;
+          st2(a.z + i, z0, z1);
+          rz = fma(r0, z0, rz);
+          rz = fma(r1, z1, rz);
           if (FLEX) {
-            zq = fma(d.x * r0, qv.x, zq);
-            zq = fma(d.y * r1, qv.y, zq);
+            zq = fma(z0, qv.x, zq);
+            zq = fma(z1, qv.y, zq);
           }
         } else if (FLEX) {
           zq = fma(r0, qv.x, zq);
@@ -192,8 +197,12 @@ __device__ __forceinline__ void cg_update_body(const VecArgs& a, double* scratch
         const double rn = fma(-alpha, a.q[i], a.r[i]);
         a.r[i] = rn;
         rr = fma(rn, rn, rr);
-        if (PK == PREC_SCALAR) rz = fma(rn, a.dinv[i] * rn, rz);
-        if (FLEX) zq = fma(PK == PREC_SCALAR ? a.dinv[i] * rn : rn, a.q[i], zq);
+        const double zn = PK == PREC_SCALAR ? a.dinv[i] * rn : rn;
+        if (PK == PREC_SCALAR) {
+          a.z[i] = zn;
+          rz = fma(rn, zn, rz);
+        }
+        if (FLEX) zq = fma(zn, a.q[i], zq);
       }
     }
     if (PK == PREC_NONE) rz = rr;
@@ -257,10 +266,7 @@ __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a)
     // prologue: p and the diagonal, which the running update step does not
     // write, into L2
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (i < a.n && (threadIdx.x & 7) == 0) {
-      prefetch_l2(a.p + i);
-      if (PK == PREC_SCALAR) prefetch_l2(a.dinv + i);
-    }
+    if (i < a.n && (threadIdx.x & 7) == 0) prefetch_l2(a.p + i);
   }
   pdl_wait();
   pdl_launch_dependents();
@@ -270,22 +276,11 @@ __global__ void __launch_bounds__(kVecThreads, 8) cg_direction_kernel(VecArgs a)
   FOR_PAIRS(i2) {
     const int i = 2 * i2;
     if (i + 1 < a.n) {
-      double2 zv;
-      if (PK == PREC_BLOCK) {
-        zv = ld2(a.z + i);
-      } else if (PK == PREC_SCALAR) {
-        const double2 d = ld2(a.dinv + i), rv = ld2(a.r + i);
-        zv = make_double2(d.x * rv.x, d.y * rv.y);
-      } else {
-        zv = ld2(a.r + i);
-      }
+      const double2 zv = PK == PREC_NONE ? ld2(a.r + i) : ld2(a.z + i);
       const double2 pv = ld2(a.p + i);
       st2(a.p + i, fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
     } else {
-      double zv;
-      if (PK == PREC_BLOCK) zv = a.z[i];
-      else if (PK == PREC_SCALAR) zv = a.dinv[i] * a.r[i];
-      else zv = a.r[i];
+      const double zv = PK == PREC_NONE ? a.r[i] : a.z[i];
       a.p[i] = fma(beta, a.p[i], zv);
     }
   }
@@ -756,7 +751,7 @@ extern "C" int gk_solver_generate(gk_matrix hA, gk_precond hP, int32_t kind, con
         (rc = alloc_vec(&S->r, S->n, by)) || (rc = alloc_vec(&S->p, S->n, by)) ||
         (rc = alloc_vec(&S->q, S->n, by)))
       break;
-    if ((kind == GK_CG || kind == GK_FCG) && S->pk == PREC_BLOCK && (rc = alloc_vec(&S->z, S->n, by))) break;
+    if ((kind == GK_CG || kind == GK_FCG) && S->pk != PREC_NONE && (rc = alloc_vec(&S->z, S->n, by))) break;
     if (kind == GK_CGS) {
       if ((rc = alloc_vec(&S->rh, S->n, by)) || (rc = alloc_vec(&S->s, S->n, by)) ||
           (rc = alloc_vec(&S->t, S->n, by)) || (rc = alloc_vec(&S->sh, S->n, by)))

@@ -88,11 +88,14 @@ SPMV_REPS = 3
 # ---------------------------------------------------------------------------
 
 def infer_bytes_per_pixel(width=32, layers=6):
-    """Compulsory bytes per pixel of one warm-start inference: the two FP32
-    input features read once, each hidden BF16 activation (width channels,
-    layers - 1 of them) written once and read once, the FP32 output written
-    once (weights are a few KB and stay in cache)."""
-    return 2 * 4 + (layers - 1) * width * 2 * 2 + 4
+    """Compulsory bytes per pixel of one warm-start inference as the library
+    runs it: the two FP32 input features read once, each hidden BF16
+    activation but the last (width channels, layers - 2 of them) written
+    once and read once, the nine FP32 tap planes into which the last hidden
+    layer folds the one-channel output layer written once and read once,
+    and the FP32 output written once (weights are a few KB and stay in
+    cache)."""
+    return 2 * 4 + (layers - 2) * width * 2 * 2 + 9 * 4 * 2 + 4
 
 
 def matrix_bytes(nnz, n_rows, fmt="csr", tail_nnz=0, vt=8, it=4):

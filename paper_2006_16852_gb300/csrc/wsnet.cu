@@ -433,6 +433,8 @@ struct TcSmem {
 };
 constexpr size_t kTcAOffset = (sizeof(TcSmem) + 127) / 128 * 128;
 constexpr size_t tc_smem_bytes(int dil) { return kTcAOffset + 3 * 4 * static_cast<size_t>(kTcTile + 2 * dil) * 16; }
+// ... and the folded last layer's weights after the ring (conv_tc_kernel<true>)
+constexpr size_t kTcLastBytes = 9 * 32 * sizeof(float);
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
 // 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
@@ -489,10 +491,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // One 32 -> 32 layer with ReLU: x, y NHWC BF16 (B, H, W, 32); wp the packed
 // weights [tap][chunk][out][8]; bias BF16.  Persistent over tiles; err gets
 // kErrTimeout if an MMA completion wait gives up.
+// LAST: this is the network's last 32 -> 32 layer and the 32 -> 1 layer
+// after it is folded into its epilogue: since that layer has one output
+// channel, its output is y(p) = b + sum over taps of t_tap(p + offset_tap)
+// with t_tap(q) = sum over channels of w[tap][c] h(q)[c]; the epilogue
+// rounds h to BF16 (the value the unfused form stores) and writes the nine
+// t_tap(q) as FP32 planes T[tap][pixel] to y, and conv_last_sum_kernel adds
+// them up.  The 64-byte activation is then never written nor read back.
+template <bool LAST>
 __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16* __restrict__ x,
                                                              const __nv_bfloat16* __restrict__ wp,
                                                              const __nv_bfloat16* __restrict__ bias, int B, int H,
                                                              int W, int dil, int strip,
+                                                             const __nv_bfloat16* __restrict__ w_last,
                                                              __nv_bfloat16* __restrict__ y, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
@@ -500,6 +511,11 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
   for (int i = t; i < kTcPacked / 8; i += kTcThreads)
     reinterpret_cast<uint4*>(S.b)[i] = __ldg(reinterpret_cast<const uint4*>(wp) + i);
   if (t < 32) S.bias[t] = __bfloat162float(bias[t]);
+  // LAST: the 32 -> 1 layer's weights [tap][channel], after the ring
+  float* const w_last_s =
+      reinterpret_cast<float*>(tc_raw + kTcAOffset + 3 * 4 * static_cast<size_t>(kTcTile + 2 * dil) * 16);
+  if (LAST)
+    for (int i = t; i < 9 * 32; i += kTcThreads) w_last_s[i] = __bfloat162float(w_last[(i & 31) * 9 + (i >> 5)]);
   if (t == 0) {
     mbar_init(&S.bar, 1);
     fence_mbar_init();
@@ -513,6 +529,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem;
+  const int64_t n_pix = static_cast<int64_t>(B) * H * W;  // LAST: the T planes' stride
   const int nslot = kTcTile + 2 * dil;              // pixel slots of a staged row
   const uint32_t chunk_a = static_cast<uint32_t>(nslot) * 16;  // bytes between its 8-channel chunks
   uint4* const ring = reinterpret_cast<uint4*>(tc_raw + kTcAOffset);
@@ -601,7 +618,19 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
       float v[32];
       tc_load32(tmem + (static_cast<uint32_t>(warp * 32) << 16), v);
       const int px = x0 + warp * 32 + lane;
-      if (px < W) {
+      if (px < W && LAST) {
+        float h[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) h[c] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[c] + S.bias[c], 0.0f)));
+        float* T = reinterpret_cast<float*>(y) + img + static_cast<int64_t>(yy) * W + px;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          float tt = 0.0f;
+#pragma unroll
+          for (int c = 0; c < 32; ++c) tt = fmaf(w_last_s[tap * 32 + c], h[c], tt);
+          T[tap * n_pix] = tt;
+        }
+      } else if (px < W) {
         uint4* dst = reinterpret_cast<uint4*>(y + (img + static_cast<int64_t>(yy) * W + px) * 32);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -759,115 +788,29 @@ __global__ void pack_tc_kernel(const float* __restrict__ p, int64_t off0, int64_
   out[i] = __float2bfloat16_rn(p[off0 + l * stride + (o * 32 + c) * 9 + tap]);
 }
 
-// The last layer (32 -> 1, linear): x NHWC BF16, y FP32 (B, 1, H, W).  A
-// block computes a tile of kLastTY x kLastTX outputs.  Since the output
-// channel is one, y(p) = b + sum over taps of t_tap(p + offset_tap) with
-// t_tap(q) = sum over channels of w[tap][c] h(q)[c]: each pixel of the tile
-// and its halo is read once (64 bytes) and turned into its nine t values in
-// shared memory, and each output then adds nine of them -- instead of every
-// output reading its nine neighbours' 64 bytes.
-constexpr int kLastTX = 32, kLastTY = 8;
-constexpr int kLastTileDil = 8;  // largest dilation of the tiled form (42.6 KB of shared memory)
-
-__global__ void __launch_bounds__(kLastTX * kLastTY) conv_last_nhwc_kernel(const __nv_bfloat16* __restrict__ x,
-                                                                          const __nv_bfloat16* __restrict__ w,
-                                                                          const __nv_bfloat16* __restrict__ bias,
-                                                                          int H, int W, int dil,
-                                                                          float* __restrict__ y) {
-  extern __shared__ float last_sm[];
-  float* ws = last_sm;          // [tap][c] weights
-  float* ts = last_sm + 9 * 32;  // [tap][halo pixel] t values
-  const int hx = kLastTX + 2 * dil, hy = kLastTY + 2 * dil, nh = hx * hy;
-  const int tid = threadIdx.y * kLastTX + threadIdx.x;
-  for (int idx = tid; idx < 9 * 32; idx += kLastTX * kLastTY) {
-    const int tap = idx >> 5, c = idx & 31;
-    ws[idx] = __bfloat162float(w[c * 9 + tap]);
-  }
-  __syncthreads();
-  const int b = blockIdx.z;
-  const int x0 = blockIdx.x * kLastTX - dil, y0 = blockIdx.y * kLastTY - dil;  // halo origin
-  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * H * W * 32;
-  for (int hq = tid; hq < nh; hq += kLastTX * kLastTY) {
-    const int ii = y0 + hq / hx, jj = x0 + hq % hx;
-    float t[9];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) t[tap] = 0.0f;
-    if (ii >= 0 && ii < H && jj >= 0 && jj < W) {
-      const uint4* src = reinterpret_cast<const uint4*>(xb + (static_cast<int64_t>(ii) * W + jj) * 32);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint4 q = __ldg(src + c);
-        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float lo = __uint_as_float(u[e] << 16), hi = __uint_as_float(u[e] & 0xFFFF0000u);
-#pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            t[tap] = fmaf(ws[tap * 32 + c * 8 + 2 * e], lo, t[tap]);
-            t[tap] = fmaf(ws[tap * 32 + c * 8 + 2 * e + 1], hi, t[tap]);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) ts[tap * nh + hq] = t[tap];
-  }
-  __syncthreads();
-  const int i = blockIdx.y * kLastTY + threadIdx.y, j = blockIdx.x * kLastTX + threadIdx.x;
-  if (i >= H || j >= W) return;
-  float acc = __bfloat162float(bias[0]);
-#pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-    for (int kx = 0; kx < 3; ++kx)
-      acc += ts[(ky * 3 + kx) * nh + (threadIdx.y + ky * dil) * hx + threadIdx.x + kx * dil];
-  y[static_cast<int64_t>(b) * H * W + static_cast<int64_t>(i) * W + j] = acc;
-}
-
-// The last layer for dilations whose tile halo would not fit shared memory
-// (above kLastTileDil): one thread per output, reading its nine neighbours.
-__global__ void __launch_bounds__(256) conv_last_direct_kernel(const __nv_bfloat16* __restrict__ x,
-                                                             const __nv_bfloat16* __restrict__ w,
-                                                             const __nv_bfloat16* __restrict__ bias, int H, int W,
-                                                             int dil, float* __restrict__ y) {
-  __shared__ float ws[9 * 32];  // [tap][c]
-  for (int idx = threadIdx.x; idx < 9 * 32; idx += blockDim.x) {
-    const int tap = idx >> 5, c = idx & 31;
-    ws[idx] = __bfloat162float(w[c * 9 + tap]);
-  }
-  __syncthreads();
+// The last layer (32 -> 1, linear), second half: y(p) = b + sum over the
+// nine taps of T[tap][p + offset_tap] (zero outside the image), the planes
+// the last 32 -> 32 layer's epilogue wrote (conv_tc_kernel<true>); taps in
+// (ky, kx) order.  y FP32 (B, 1, H, W).
+__global__ void __launch_bounds__(256) conv_last_sum_kernel(const float* __restrict__ T,
+                                                            const __nv_bfloat16* __restrict__ bias, int B, int H,
+                                                            int W, int dil, float* __restrict__ y) {
   const int HW = H * W;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
   const int b = blockIdx.y;
   const int i = p / W, j = p - i * W;
-  float acc = 0.0f;
-  const __nv_bfloat16* xb = x + static_cast<int64_t>(b) * HW * 32;
+  const int64_t n_pix = static_cast<int64_t>(B) * HW;
+  const float* Tb = T + static_cast<int64_t>(b) * HW;
+  float acc = __bfloat162float(bias[0]);
 #pragma unroll
   for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
     for (int kx = 0; kx < 3; ++kx) {
       const int ii = i + dil * (ky - 1), jj = j + dil * (kx - 1);
-      if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
-      const uint4* src = reinterpret_cast<const uint4*>(xb + (static_cast<int64_t>(ii) * W + jj) * 32);
-      const float* wr = ws + (ky * 3 + kx) * 32;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint4 q = __ldg(src + c);
-        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          acc = fmaf(wr[c * 8 + 2 * e], __uint_as_float(u[e] << 16), acc);
-          acc = fmaf(wr[c * 8 + 2 * e + 1], __uint_as_float(u[e] & 0xFFFF0000u), acc);
-        }
-      }
+      if (ii >= 0 && ii < H && jj >= 0 && jj < W) acc += __ldg(Tb + (ky * 3 + kx) * n_pix + ii * W + jj);
     }
-  y[static_cast<int64_t>(b) * HW + p] = acc + __bfloat162float(bias[0]);
-}
-
-// Dynamic shared memory of conv_last_nhwc_kernel for a dilation.
-inline size_t last_smem_bytes(int dil) {
-  return sizeof(float) * (9 * 32 + 9 * static_cast<size_t>(kLastTX + 2 * dil) * (kLastTY + 2 * dil));
+  y[static_cast<int64_t>(b) * HW + p] = acc;
 }
 
 int ew_grid(int64_t n) {
@@ -1051,7 +994,7 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
     // resident blocks per SM: shared memory is the limit (registers, warps
     // and the 512 tensor-memory columns allow 16 blocks of 32 columns), and
     // it depends on the dilation through the staged rows' width
-    const size_t smem = tc_smem_bytes(N.dil[l]);
+    const size_t smem = tc_smem_bytes(N.dil[l]) + (l == kLayers - 2 ? kTcLastBytes : 0);
     int per_sm = std::max(1, std::min(16, static_cast<int>(static_cast<size_t>(N.tc_smem_sm) / (smem + N.tc_reserved))));
     // small batches keep three blocks per SM (the count the widest rows
     // allow): more blocks would shorten every block's strips, and each strip
@@ -1067,20 +1010,20 @@ int infer_bf16(WsNet& N, int B, const float* x, float* y, cudaStream_t s) {
     const int per_class = (N.H + N.dil[l] - 1) / N.dil[l];
     const int n_chunks = (per_class + target - 1) / target;
     const int strip = (per_class + n_chunks - 1) / n_chunks;
-    conv_tc_kernel<<<grid, kTcThreads, smem, s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B, N.H,
-                                                  N.W, N.dil[l], strip, out, N.err);
+    // the last 32 -> 32 layer also folds in the 32 -> 1 layer: it writes the
+    // nine tap planes (36 bytes per pixel, within the 64 of the buffer)
+    if (l == kLayers - 2)
+      conv_tc_kernel<true><<<grid, kTcThreads, smem, s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B,
+                                                          N.H, N.W, N.dil[l], strip, N.pbf + N.off_w[kLayers - 1],
+                                                          out, N.err);
+    else
+      conv_tc_kernel<false><<<grid, kTcThreads, smem, s>>>(in, N.wtc + (l - 1) * kTcPacked, N.pbf + N.off_b[l], B,
+                                                           N.H, N.W, N.dil[l], strip, nullptr, out, N.err);
     GK_TRY_CUDA(cudaGetLastError());
     in = out;
   }
-  const int dl = N.dil[kLayers - 1];
-  if (dl <= kLastTileDil) {
-    const dim3 lg((N.W + kLastTX - 1) / kLastTX, (N.H + kLastTY - 1) / kLastTY, B);
-    conv_last_nhwc_kernel<<<lg, dim3(kLastTX, kLastTY), last_smem_bytes(dl), s>>>(
-        in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H, N.W, dl, y);
-  } else {
-    conv_last_direct_kernel<<<pg, 256, 0, s>>>(in, N.pbf + N.off_w[kLayers - 1], N.pbf + N.off_b[kLayers - 1], N.H,
-                                               N.W, dl, y);
-  }
+  conv_last_sum_kernel<<<pg, 256, 0, s>>>(reinterpret_cast<const float*>(in), N.pbf + N.off_b[kLayers - 1], B, N.H,
+                                          N.W, N.dil[kLayers - 1], y);
   GK_TRY_CUDA(cudaGetLastError());
   return GK_OK;
 }
@@ -1133,8 +1076,8 @@ extern "C" int gk_wsnet_create(int32_t H, int32_t W, int32_t batch_max, const in
   GK_TRY(dalloc_n(&N->wtc, static_cast<size_t>(kTcMidLayers) * kTcPacked, by));
   GK_TRY(dalloc_n(&N->err, 1, by));
   GK_TRY_CUDA(cudaMemset(N->err, 0, sizeof(int)));
-  GK_TRY(set_smem(conv_tc_kernel, tc_smem_bytes(kTcMaxDil)));
-  GK_TRY(set_smem(conv_last_nhwc_kernel, last_smem_bytes(kLastTileDil)));
+  GK_TRY(set_smem(conv_tc_kernel<false>, tc_smem_bytes(kTcMaxDil)));
+  GK_TRY(set_smem(conv_tc_kernel<true>, tc_smem_bytes(kTcMaxDil) + kTcLastBytes));
   // the grid of each layer is sized from its shared-memory footprint (the
   // occupancy query has been seen to report 1 for this kernel where 3 fit)
   GK_TRY_CUDA(cudaDeviceGetAttribute(&N->tc_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, N->device));

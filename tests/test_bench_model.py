@@ -122,12 +122,13 @@ def test_solve_launches_counts_idle_iterations():
 
 
 def test_inference_byte_model():
-    """The warm-start inference moves 652 bytes per pixel (2 FP32 features
-    in, five 32-channel BF16 activations out and back in, one FP32 output)
-    for 2 x 37,728 flops: about 116 flops per byte, below the ridge of a
-    GPU with ~1.9 PFLOP/s BF16 and ~6.7 TB/s, so HBM bounds it."""
+    """The warm-start inference moves 596 bytes per pixel (2 FP32 features
+    in, four 32-channel BF16 activations out and back in, nine FP32 tap
+    planes of the folded last layer out and back in, one FP32 output) for
+    2 x 37,728 flops: about 127 flops per byte, below the ridge of a GPU
+    with ~1.9 PFLOP/s BF16 and ~6.7 TB/s, so HBM bounds it."""
     bpp = bench.infer_bytes_per_pixel()
-    assert bpp == 2 * 4 + 5 * 32 * 2 * 2 + 4 == 652
+    assert bpp == 2 * 4 + 4 * 32 * 2 * 2 + 9 * 4 * 2 + 4 == 596
     macs = sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
     assert macs == 37728
     assert 2 * macs / bpp < 1.9e15 / 6.7e12

@@ -785,9 +785,8 @@ def run_learned(dev, problems=8):
     bf16_peak = peaks().get("bf16_tflops")
     hbm = peaks().get("hbm_gbs")
     inf_ms, tfl = inf[1]
-    # compulsory activation bytes per pixel of one inference: the FP32
-    # features (2 channels) read once, each of the five 32-channel BF16
-    # activations written once and read once, the FP32 output written once
+    # compulsory activation bytes per pixel of one inference (the byte
+    # model of infer_bytes_per_pixel)
     bpp = infer_bytes_per_pixel()
     by64 = 64 * net.H * net.W * bpp
     ai = 2.0 * macs / (net.H * net.W * bpp)
@@ -806,8 +805,9 @@ def run_learned(dev, problems=8):
                            "speedup_vs_plain": round(plain_ms / min(summ["ms_warm"], summ["ms_zero"]), 3),
                            "learned_vs_zero_start": round(summ["ms_zero"] / summ["ms_warm"], 4)},
         "inference": {"kernel": "conv_first_tc_kernel and conv_tc_kernel (tcgen05.mma BF16 x BF16 -> FP32 in "
-                                "tensor memory) for the first five layers (the first with K = 18 padded to 32); "
-                                "the last (32 -> 1) on the CUDA cores",
+                                "tensor memory) for the first five layers (the first with K = 18 padded to 32), "
+                                "the last (32 -> 1) folded into the fifth's epilogue as nine tap planes that "
+                                "conv_last_sum_kernel adds",
                       "batch1": {"ms": round(inf_ms, 4), "tflops": round(tfl, 2),
                                  "frac_of_bf16_peak": round(tfl / bf16_peak, 5) if bf16_peak else None,
                                  "note": "42.7 MB of activations: L2-resident, latency-bound"},

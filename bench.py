@@ -1249,13 +1249,20 @@ def run_gpu(args):
                 "frac": round(achieved / (hbm if hbm else 6800.0), 4),
                 "traffic": tr, "algorithmic_bytes": dom_bytes, "avg_launch_ms": round(dom_ms, 4)}
     # the same against the nominal HBM rate, and the FP64 co-bound: one FMA
-    # per stored entry at the nominal FP64 rate of a GB300
+    # per stored entry and one per row (the fused dot), at the nominal FP64
+    # rate of a GB300 and at the rate this GPU is measured to retire FP64
+    # FMAs (gk_fp64_rate, outside the timed region)
     roofline["frac_of_nominal_hbm"] = round(achieved / NOMINAL_HBM_GBS, 4)
     hbm_floor = dom_bytes / ((hbm or 6800.0) * 1e9) * 1e3
-    fp64_floor = 2.0 * step.nnza / (NOMINAL_FP64_TFLOPS * 1e12) * 1e3
-    roofline["floors_ms"] = {"hbm": round(hbm_floor, 4), "fp64_fma": round(fp64_floor, 4),
-                             "effective": round(max(hbm_floor, fp64_floor), 4)}
-    roofline["frac_of_effective_floor"] = round(max(hbm_floor, fp64_floor) / dom_ms, 4)
+    fmas = step.nnza + step.na
+    fp64_floor = 2.0 * fmas / (NOMINAL_FP64_TFLOPS * 1e12) * 1e3
+    fp64_rate = step.gk.fp64_rate()
+    fp64_floor_meas = 2.0 * fmas / (fp64_rate * 1e12) * 1e3
+    effective = max(hbm_floor, fp64_floor_meas)
+    roofline["fp64_measured_tflops"] = round(fp64_rate, 4)
+    roofline["floors_ms"] = {"hbm": round(hbm_floor, 4), "fp64_fma_nominal": round(fp64_floor, 4),
+                             "fp64_fma_measured": round(fp64_floor_meas, 4), "effective": round(effective, 4)}
+    roofline["frac_of_effective_floor"] = round(effective / dom_ms, 4)
 
     def summary(name):
         reps = SPMV_REPS if name.startswith("spmv") else 1

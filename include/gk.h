@@ -438,6 +438,17 @@ GK_API int gk_dot(int64_t n, const double* x, const double* y, double* result, v
 GK_API int gk_gather_dot(int64_t n, const int32_t* c, const double* v, const double* x, int64_t n_x,
                          double* result, void* stream);
 
+/* *tflops = the rate, in TFLOP/s, at which the current device retires FP64
+ * fused multiply-adds (2 flops each), measured: a kernel of 8 independent
+ * FMA chains per thread, 8 blocks of 256 threads per SM, iters FMAs per
+ * chain, timed with CUDA events on stream after one warm-up launch.  Not in
+ * the paper: the SpMV and Krylov kernels issue one FP64 FMA per stored entry
+ * and several per row, and on a GPU whose FP64 rate is low next to its
+ * memory bandwidth that rate is a roofline of its own, reported beside the
+ * HBM one.  Synchronous (waits for the measurement); allocates nothing but
+ * two events.  iters >= 1 (about 20,000 gives a launch of a few ms). */
+GK_API int gk_fp64_rate(int64_t iters, double* tflops, void* stream);
+
 /* gk_dot without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- for example
  * code whose GPU memory is entirely reserved by another allocator (a

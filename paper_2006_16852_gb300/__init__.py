@@ -39,7 +39,7 @@ EXPORTS = ("gk_last_error", "gk_version", "gk_matrix_create_csr", "gk_matrix_get
            "gk_wsnet_set_loss",
            "gk_wsnet_forward", "gk_wsnet_gradients", "gk_wsnet_train_step", "gk_wsnet_infer_bf16",
            "gk_wsnet_check",
-           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc", "gk_gather_dot",
+           "gk_wsnet_features", "gk_wsnet_warm_start", "gk_wsnet_destroy", "gk_dot", "gk_dot_noalloc", "gk_gather_dot", "gk_fp64_rate",
            "gk_wait_selftest")
 BATCH_CLASSES = 8
 BATCH_BLOCK_SIZES = (32, 64, 128, 256)
@@ -147,6 +147,7 @@ def load(path: str | None = None):
         "gk_dot": [i64, vp, vp, vp, vp],
         "gk_dot_noalloc": [i64, vp, vp, vp, vp],
         "gk_gather_dot": [i64, vp, vp, vp, i64, vp, vp],
+        "gk_fp64_rate": [i64, vp, vp],
         "gk_wait_selftest": [vp, vp],
     }
     for name, args in sig.items():
@@ -376,6 +377,13 @@ def gather_dot(c, v, x, result, stream=None):
     _check(lib().gk_gather_dot(n, _ptr(c), _ptr(v), _ptr(x), x.numel(), _ptr(result),
                                _stream(stream, c, v, x, result)))
     return result
+
+
+def fp64_rate(iters: int = 20000, stream=None) -> float:
+    """The device's measured FP64 fused multiply-add rate in TFLOP/s."""
+    r = ctypes.c_double(0.0)
+    _check(lib().gk_fp64_rate(iters, ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def wait_selftest(stream=None) -> int:

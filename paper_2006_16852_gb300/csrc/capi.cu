@@ -430,3 +430,59 @@ extern "C" int gk_wait_selftest(int32_t* err_out, void* stream) {
   *err_out = h;
   return GK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gk_fp64_rate: the rate at which this GPU retires FP64 fused multiply-adds,
+// measured (the SpMV and Krylov kernels issue one per stored entry and a few
+// per row; on this GPU that rate, not HBM, is often what bounds them).
+// ---------------------------------------------------------------------------
+namespace gk {
+namespace {
+
+constexpr int kRateChains = 8;  // independent FMA chains per thread
+__device__ double g_rate_sink;  // written only if a result is impossible: keeps the chains live
+
+__global__ void __launch_bounds__(256) fp64_rate_kernel(int64_t iters, double b, double c) {
+  double a[kRateChains];
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kRateChains; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) s += a[k];
+  if (s == -1.0) g_rate_sink = s;
+}
+
+}  // namespace
+}  // namespace gk
+
+extern "C" int gk_fp64_rate(int64_t iters, double* tflops, void* stream) {
+  if (!tflops || iters < 1) return set_error(GK_ERR_ARG, "gk_fp64_rate: bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = 8 * sm_count();  // 8 blocks of 256 threads: every SM full
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    fp64_rate_kernel<<<grid, 256, 0, s>>>(1, 0.999999, 1e-6);  // warm-up
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) {
+    fp64_rate_kernel<<<grid, 256, 0, s>>>(iters, 0.999999, 1e-6);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_error(e, "gk_fp64_rate");
+  const double flops = 2.0 * static_cast<double>(iters) * kRateChains * 256.0 * grid;
+  *tflops = ms > 0.0f ? flops / (static_cast<double>(ms) * 1e-3) / 1e12 : 0.0;
+  return GK_OK;
+}

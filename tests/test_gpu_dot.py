@@ -67,3 +67,13 @@ def test_gather_dot_against_oracle(gk, orc, n):
     assert got[0] == got[1]
     ref = orc.dot(v, xg)
     assert abs(got[0] - ref) <= 1e-13 * float(np.sum(np.abs(v * xg))), (got[0], ref)
+
+
+def test_fp64_rate_is_measured(gk):
+    """gk_fp64_rate times FP64 fused multiply-adds on the device: a positive
+    rate below the nominal FP64 peak of a GB300 (1.25 TFLOP/s) with some
+    margin, and more iterations give about the same rate."""
+    r1 = gk.fp64_rate(5000)
+    r2 = gk.fp64_rate(20000)
+    assert 0.05 < r1 < 1.5 and 0.05 < r2 < 1.5, (r1, r2)
+    assert abs(r1 - r2) <= 0.25 * max(r1, r2), (r1, r2)

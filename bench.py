@@ -631,6 +631,7 @@ def run_batched(dev, reps=3, n_sys=10000, only=None, tune=True, plain=True):
                       key=lambda k: forms[k]["ms"])
     cg64 = forms["fp64_cg_jacobi"]
     ach = cg64["fp64_tflops"]
+    rate = gk.fp64_rate()
     out.update({
         "time_to_tol_ms": {"plain_fp64_cg_unbatched": round(plain_ms, 3), "plain_iters": st.iters,
                            "plain_per_system_rel_res_max": float(per_sys.max()),
@@ -639,6 +640,7 @@ def run_batched(dev, reps=3, n_sys=10000, only=None, tune=True, plain=True):
         "roofline": {"kernel": "batch_kernel<double, CG, Jacobi> (one block per system, FP64)", "bound": "alu",
                      "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "peak_source": "nominal GB300 FP64 rate", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                     "measured_fp64_tflops": round(rate, 4), "frac_of_measured": round(ach / rate, 4),
                      "traffic": None},
     })
     return out
@@ -1287,6 +1289,9 @@ def run_gpu(args):
         fl = precond_fp64_ops(step.n_of(k), bs)
         p["fp64_floor_ms"] = round(fl / (NOMINAL_FP64_TFLOPS * 0.5e12) * 1e3, 4)
         p["frac_fp64"] = round(p["fp64_floor_ms"] / p["ms"], 3)
+        # the same floor at the FP64 rate this GPU is measured to retire
+        p["fp64_floor_measured_ms"] = round(fl / (fp64_rate * 0.5e12) * 1e3, 4)
+        p["frac_fp64_measured"] = round(p["fp64_floor_measured_ms"] / p["ms"], 3)
     plain = solves["a_cg_plain_csr"]["ms"]
     chosen = min(("a_cg_jacobi_ell", "a_cg_bj8_ell", "a_ircg_jacobi_ell", "a_ircg_bj8_ell"),
                  key=lambda k: solves[k]["ms"])

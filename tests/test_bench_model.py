@@ -132,3 +132,16 @@ def test_inference_byte_model():
     macs = sum(a * b * 9 for a, b in zip((2, 32, 32, 32, 32, 32), (32, 32, 32, 32, 32, 1)))
     assert macs == 37728
     assert 2 * macs / bpp < 1.9e15 / 6.7e12
+
+
+def test_spmv_launch_counts_per_format():
+    """One kernel per GK_CSR apply, two when rows of more than 512 entries are
+    summed in pieces (their second launch adds the pieces); two for the merge
+    path (tiles and fix-up); three for HYB with an overflow (COO, its fix-up,
+    ELL), one without; one for ELL."""
+    assert bench.spmv_launches({"format_name": "csr", "split_rows": 0}) == 1
+    assert bench.spmv_launches({"format_name": "csr", "split_rows": 4165}) == 2
+    assert bench.spmv_launches({"format_name": "csr_merge"}) == 2
+    assert bench.spmv_launches({"format_name": "hyb", "tail_rows": 10}) == 3
+    assert bench.spmv_launches({"format_name": "hyb", "tail_rows": 0}) == 1
+    assert bench.spmv_launches({"format_name": "ell"}) == 1
